@@ -1,0 +1,386 @@
+"""Benchmark: max-null permutation testing (NaivePT) on one or more GB300s.
+
+One step = the whole hot path on one batch: pt_prepare (per-voxel FP64
+moments, unit-norm centring, BF16 split) + pt_maxnull_naive (labels, fused
+tensor-core contraction + max-null + exceedance counts, finalise) for the
+brain-shaped workload n=100 (50/50), 91x109x91 grid masked to 231,719 voxels,
+10,000 relabellings. Metric: T entries (relabelling x voxel t statistics) per
+second. Inputs (X 361 MB, BF16 data pieces 156 MB) are larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision bf16x3|bf16x2|fp32]
+
+With N > 1 it runs under torch.distributed.run, one rank per GPU: every rank
+takes its own 10,000 relabellings of the same study (weak scaling, no data
+collective); value = entries of all ranks / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "T entries/s (perm x voxel t) & max-null wall time, NaivePT, 1 GB300"
+WORKLOAD = "brain_n100_v232k"
+PREC = {"fp32": 0, "bf16x2": 1, "bf16x3": 2}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm = []
+        mx = None
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for f in self.rows:
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(Xm_host, n1, perms, seconds_target=15.0, start_rows=1):
+    """Time the FP64 oracle on whole relabelling rows (all voxels) of the workload,
+    growing the sample until it takes about ``seconds_target``. Returns
+    (entries/s, rows, seconds, cores)."""
+    import oracle
+    cores = cpu_cores()
+    v = Xm_host.shape[1]
+    Xt = oracle.voxel_major(Xm_host)
+    rows = max(1, start_rows)
+    while True:
+        sel = perms[:rows]
+        t0 = time.perf_counter()
+        _oracle_rows(Xt, n1, sel, cores)
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target * 0.5 or rows >= perms.shape[0]:
+            return rows * v / dt, rows, dt, cores
+        grow = max(2, int(seconds_target / max(dt, 1e-3)))
+        rows = min(perms.shape[0], rows * grow)
+
+
+def _oracle_rows(Xt, n1, perms, cores):
+    import ctypes
+    import oracle
+    lib = oracle._load()
+    v, n = Xt.shape
+    P = perms.shape[0]
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    out = [np.empty(P), np.empty(P, np.int64), np.empty(P), np.empty(v, np.uint32), np.empty(v),
+           np.empty(v, np.uint32)]
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+    rc = lib.oracle_naive(p(Xt), n, v, int(n1), p(perms), P, 0, int(cores), 2e-5,
+                          *[p(a) for a in out])
+    assert rc == 0
+    return out
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle of the same workload on the host cores."""
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    import torch
+    from paper_1703_01506_gb300 import synth
+    w = synth.workload(WORKLOAD, device="cpu")
+    X, mask = w["X"], w["mask"].bool()
+    Xm = X[:, mask].numpy()
+    v = Xm.shape[1]
+    import oracle
+    oracle.build()
+    Xt = oracle.voxel_major(Xm)
+    cores = cpu_cores()
+    # size one step to ~5 s of CPU work
+    rate, rows, dt, _ = oracle_sample(Xm, w["n1"], w["perms"], seconds_target=4.0)
+    step_rows = max(1, int(round(rows * 5.0 / max(dt, 1e-6))))
+    step_rows = min(step_rows, w["perms"].shape[0])
+    for i in range(args.warmup):
+        _oracle_rows(Xt, w["n1"], w["perms"][:step_rows], cores)
+    times = []
+    for i in range(args.steps):
+        sel = w["perms"][(i * step_rows) % w["P"]:][:step_rows]
+        t0 = time.perf_counter()
+        _oracle_rows(Xt, w["n1"], sel, cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = sel.shape[0] * v / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "T entries/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD + ": n=100 (50/50), %d voxels, P=10000" % v,
+                   "sample": "%d relabellings x all voxels per step" % step_rows},
+        "cpu_baseline": {"value": value, "unit": "T entries/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d relabelling rows x %d voxels per step" % (step_rows, v)},
+        "e2e": {"value": value, "unit": "T entries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1703_01506_gb300 import binding as B
+    from paper_1703_01506_gb300 import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.load()
+    prec = PREC[args.precision]
+
+    w = synth.workload(WORKLOAD, device=dev)
+    X, mask, n1 = w["X"], w["mask"], w["n1"]
+    n = X.shape[0]
+    perms_np = w["perms"] if rank == 0 else synth.perms_pcg32(n, w["P"], seed=1, seq=1 + rank)
+    P = perms_np.shape[0]
+    perms = torch.as_tensor(perms_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    maxnull = torch.empty(P, dtype=torch.float32, device=dev)
+    argmax = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def step(profile=False):
+        ctx = B.pt_prepare(X, n1, mask, stream=stream)
+        if profile:
+            B.pt_profile_enable(ctx, True)
+        counts = step.counts
+        if counts is None or counts.numel() != B.pt_num_voxels(ctx):
+            counts = step.counts = torch.empty(B.pt_num_voxels(ctx), dtype=torch.int32, device=dev)
+        B.pt_maxnull_naive_ex(ctx, perms, B.naive_opts(prec), maxnull, argmax, counts)
+        return ctx
+    step.counts = None
+
+    ctx = step()
+    B.pt_sync(ctx)
+    v = B.pt_num_voxels(ctx)
+    ctx.close()
+    for _ in range(args.warmup):
+        ctx = step()
+        B.pt_sync(ctx)
+        ctx.close()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = B.pt_kernel_launch_count()
+    kern_ms, kern_n = 0.0, 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx = step(profile=True)
+        B.pt_sync(ctx)
+        ms_k, n_k = B.pt_profile_read(ctx)
+        kern_ms += ms_k
+        kern_n += n_k
+        ctx.close()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    launches = B.pt_kernel_launch_count() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    entries = float(P) * v
+    value = ws * entries / (ms / 1000.0)
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region ----
+    Xh = X.cpu().pin_memory()
+    mh = mask.cpu().pin_memory()
+    ph = torch.as_tensor(perms_np).pin_memory()
+    mx_h = torch.empty(P, dtype=torch.float32).pin_memory()
+    am_h = torch.empty(P, dtype=torch.int32).pin_memory()
+    ct_h = torch.empty(v, dtype=torch.int32).pin_memory()
+    Xd = torch.empty_like(X)
+    md = torch.empty_like(mask)
+    pd = torch.empty_like(perms)
+
+    def e2e_step():
+        Xd.copy_(Xh, non_blocking=True)
+        md.copy_(mh, non_blocking=True)
+        pd.copy_(ph, non_blocking=True)
+        c = B.pt_prepare(Xd, n1, md, stream=stream)
+        B.pt_maxnull_naive_ex(c, pd, B.naive_opts(prec), maxnull, argmax, step.counts)
+        mx_h.copy_(maxnull, non_blocking=True)
+        am_h.copy_(argmax, non_blocking=True)
+        ct_h.copy_(step.counts, non_blocking=True)
+        B.pt_sync(c)
+        c.close()
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = Xh.numel() * 4 + mh.numel() + ph.numel() * 4
+    d2h = P * 4 + P * 4 + v * 4
+
+    # ---- roofline of the dominant kernel (fused contraction + reduction) ----
+    pk, src = peaks()
+    avg_kern_ms = kern_ms / max(kern_n, 1)
+    if prec == 0:
+        flops = 2.0 * n * entries  # algorithmic: 2 flops per subject per entry
+        fp32_peak = None
+        roof = {"bound": "alu", "achieved": flops / (avg_kern_ms * 1e-3) / 1e12,
+                "unit": "TFLOP/s", "note": "plain FP32 CUDA-core path"}
+    else:
+        flops = 2.0 * n * entries
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        ach = flops / (avg_kern_ms * 1e-3) / 1e12
+        pieces = 2 if prec == 1 else 3
+        n_pad = (n + 15) // 16 * 16
+        hw = 2.0 * pieces * n_pad * entries / (avg_kern_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "%s bf16 sustained (MEASURED_PEAKS.json)" % src,
+                "kernel": "tc_contract_kernel<256>", "kernel_ms": avg_kern_ms,
+                "hw_tflops": hw, "hw_frac": hw / peak,
+                "algorithmic": "2n flops per T entry (n=%d); hardware issues %d BF16 pieces x "
+                               "n_pad=%d" % (n, pieces, n_pad)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "T entries/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "bf16x2/f32acc", 2: "bf16x3/f32acc"}[prec], "data": "synthetic",
+        "config": {"workload": "%s: n=100 (50/50), 91x109x91 grid, ellipsoid mask %d voxels, "
+                               "FWHM 8 smoothing, +0.3 SD effect r=10, P=%d relabellings per "
+                               "GPU (PCG32 Fisher-Yates)" % (WORKLOAD, v, P),
+                   "precision": args.precision, "parallelism": "replicas over relabellings"
+                   if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (X %.0f MB, BF16 pieces %.0f MB)"
+                         % (X.numel() * 4 / 1e6, v * ((n + 15) // 16 * 16) * 6 / 1e6),
+                   "step": "pt_prepare + pt_maxnull_naive (labels, fused contraction, finalise)"},
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": ws * entries / (ms_e2e / 1000.0), "unit": "T entries/s",
+                "ms_per_step": ms_e2e, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "kernel_launches_per_step": launches / args.steps,
+        "maxnull_wall_ms": ms,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        Xm = X[:, mask.bool()].cpu().numpy()
+        rate, rows, dt, cores = oracle_sample(Xm, n1, perms_np, seconds_target=15.0)
+        line["cpu_baseline"] = {"value": rate, "unit": "T entries/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "%d relabelling rows x %d voxels, %.1f s" % (rows, v, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

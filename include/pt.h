@@ -1,0 +1,158 @@
+/*
+ * pt.h -- C ABI of the GB300 max-null permutation-testing library (libpt.so).
+ *
+ * What it computes (arXiv 1703.01506):
+ *   - the permutation testing matrix T (relabellings x voxels) of voxel-wise
+ *     pooled-variance two-sample t statistics (Sec. 2.1, Eq. (5)), reduced to
+ *     the max-null distribution m_i = max_j T[i][j] (Sec. 2; Alg. 1), plus the
+ *     per-voxel uncorrected exceedance counts #{i : T[i][j] >= t_obs[j]};
+ *   - the same max-null recovered by RapidPT (Alg. 2, Sec. 4): full rows for
+ *     n_train training relabellings, a tracked rank-r subspace, and for every
+ *     later relabelling only a sampled subset of voxels.
+ *
+ * Conventions shared by every entry point:
+ *   - All array arguments are caller-owned pointers to DEVICE memory of the
+ *     current CUDA device unless the comment says "host". The library never
+ *     frees them and never keeps them beyond the call (pt_prepare copies what
+ *     it needs; the caller may free X and mask after it returns).
+ *   - Work is enqueued on the stream given to pt_prepare. Compute entry points
+ *     return once their kernels are enqueued; outputs are valid after the
+ *     stream is synchronised. Errors found by the kernels themselves (an input
+ *     row that is not a permutation, a bounded wait that expired) are reported
+ *     by the next pt_sync on that context.
+ *   - Scalar arguments are validated on the host before any launch; an invalid
+ *     one returns PT_ERR_INVALID and enqueues nothing.
+ *   - Voxel order is the raster order of the mask ("masked order"); v below is
+ *     the number of mask voxels. Group 1 is the first n1 entries of each
+ *     relabelling row. The observed labelling is the identity (subjects
+ *     0..n1-1 in group 1) and is not part of `perms`.
+ *   - A voxel whose n values are all equal has no t statistic: it is left out
+ *     of every maximum and its count is 0.
+ *   - No C++ exception crosses this boundary and nothing here calls exit().
+ *     Functions are safe to call from several host threads on distinct
+ *     contexts; a single context must not be used concurrently.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_ctx pt_ctx; /* opaque; owns all device workspaces */
+
+typedef enum {
+  PT_OK = 0,
+  PT_ERR_INVALID = 1,     /* bad argument or bad input data */
+  PT_ERR_NOMEM = 2,       /* device allocation failed */
+  PT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  PT_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired */
+  PT_ERR_UNSUPPORTED = 5  /* valid request this build cannot run (e.g. no sm_103 device) */
+} pt_status;
+
+/* Arithmetic of the contraction S1 = L . Xn (labels exact in every mode). */
+typedef enum {
+  PT_PREC_FP32 = 0,    /* plain FP32 CUDA-core (SIMT) kernel */
+  PT_PREC_BF16X2 = 1,  /* tcgen05 tensor cores, data split hi+lo in BF16, FP32 accumulate */
+  PT_PREC_BF16X3 = 2   /* tcgen05 tensor cores, data split hi+mid+lo in BF16, FP32 accumulate */
+} pt_precision;
+
+typedef struct {
+  int32_t precision; /* pt_precision; default PT_PREC_BF16X3 */
+  int32_t two_sided; /* 0 (default): statistic t; 1: statistic |t| (max |t|, counts |t|>=|t_obs|) */
+} pt_naive_opts;
+
+/* Fills *o with the defaults above. */
+void pt_naive_opts_default(pt_naive_opts* o);
+
+/*
+ * pt_prepare -- per-voxel centring and moments (the one-time O(n v) step that
+ * precedes Alg. 1 / Alg. 2).
+ *   X      : device, float32, n x n_grid row-major (row s = subject s over the
+ *            whole grid; the "n rows and v columns" data matrix of Sec. 5.3.1).
+ *   n      : subjects, 3 <= n <= 1024.
+ *   n_grid : columns of X (grid voxels), 1 <= n_grid < 2^31.
+ *   mask   : device, uint8, n_grid entries, nonzero = in the brain; NULL means
+ *            every grid voxel.
+ *   n1     : size of group 1, 1 <= n1 <= n-1 (group 2 has n - n1).
+ *   stream : cudaStream_t to run on (NULL = legacy default stream).
+ *   out    : host; receives the new context (unchanged on failure).
+ * Per voxel it computes, in FP64, the mean and total sum of squares SS of the
+ * n values, and stores the centred data scaled to unit norm,
+ * Xn[j][s] = (x_s - mean_j) / sqrt(SS_j), in FP32 and as BF16 pieces; and the
+ * observed statistic t_obs (identity labelling). Synchronises the stream.
+ * Errors: PT_ERR_INVALID for bad sizes or a NaN/Inf in a mask voxel,
+ * PT_ERR_NOMEM, PT_ERR_CUDA.
+ */
+pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* mask,
+                     int32_t n1, void* stream, pt_ctx** out);
+
+/*
+ * pt_maxnull_naive -- NaivePT (Alg. 1) with default options.
+ *   perms   : device, int32, P x n row-major; each row a permutation of 0..n-1.
+ *   P       : relabellings, 1 <= P <= 2^31 - 1.
+ *   maxnull : device, float32[P]: m_i = max_j t[i][j] (Alg. 1 "Max").
+ *   argmax  : device, int32[P]: masked-order voxel of m_i, smallest index on
+ *             ties; -1 when the context has no voxel with a defined t.
+ *   counts  : device, uint32[v]: #{i : t[i][j] >= t_obs[j]}; may be NULL.
+ * T is never written to memory. A row that is not a permutation makes the
+ * next pt_sync return PT_ERR_INVALID (outputs then undefined).
+ */
+pt_status pt_maxnull_naive(pt_ctx* ctx, const int32_t* perms, int64_t P, float* maxnull,
+                           int32_t* argmax, uint32_t* counts);
+
+/* pt_maxnull_naive with explicit options (opts NULL = defaults). */
+pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
+                              const pt_naive_opts* opts, float* maxnull, int32_t* argmax,
+                              uint32_t* counts);
+
+/*
+ * pt_sync -- wait for the context's stream and report errors the kernels
+ * raised since the previous pt_sync (PT_ERR_INVALID for a bad relabelling
+ * row, PT_ERR_TIMEOUT for an expired device wait), then clear them.
+ */
+pt_status pt_sync(pt_ctx* ctx);
+
+/* t_obs: device float32[v]: observed statistic per voxel (NaN where undefined).
+ * Enqueued on the context's stream. */
+pt_status pt_t_obs(pt_ctx* ctx, float* t_obs);
+
+/* grid_index: device int64[v]: grid column of each masked-order voxel. */
+pt_status pt_voxel_grid_index(pt_ctx* ctx, int64_t* grid_index);
+
+/* v (mask voxels), number of voxels with a defined t, n, n1; -1 if ctx NULL. */
+int64_t pt_num_voxels(const pt_ctx* ctx);
+int64_t pt_num_valid_voxels(const pt_ctx* ctx);
+
+/* Text of the last failure on ctx (or, for ctx NULL, of the last failure of a
+ * call without a context on this thread, e.g. pt_prepare). Never NULL. */
+const char* pt_last_error(const pt_ctx* ctx);
+
+/*
+ * Profiling of the dominant kernel. When enabled, every compute call records a
+ * pair of CUDA events on the context's stream around the launch of its main
+ * contraction kernel. pt_profile_read synchronises the stream and returns (host
+ * outputs) the summed device time in ms and the number of timed launches since
+ * the previous read, then resets both.
+ */
+pt_status pt_profile_enable(pt_ctx* ctx, int32_t on);
+pt_status pt_profile_read(pt_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Number of kernels this library has launched in this process (all contexts). */
+int64_t pt_kernel_launch_count(void);
+
+/* Frees the context's device memory (returned to the library's cache). NULL ok. */
+void pt_destroy(pt_ctx* ctx);
+
+/* Returns every cached device block to the driver (cudaFree). Call only while no
+ * context's work is in flight. */
+void pt_release_cached_memory(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of ``libpt.so`` (declared in ``include/pt.h``).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels. Functions carry the C names; array arguments are
+CUDA torch tensors (their device pointers are passed through), and a status
+other than PT_OK raises :class:`PtError` with the library's message.
+
+The library must have been built (``__graft_entry__.build()``); importing
+this module does not build it, and :func:`load` raises if it is missing.
+"""
+import ctypes
+import os
+
+import torch
+
+from .build import LIB
+
+PT_OK, PT_ERR_INVALID, PT_ERR_NOMEM, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_UNSUPPORTED = range(6)
+PT_PREC_FP32, PT_PREC_BF16X2, PT_PREC_BF16X3 = 0, 1, 2
+_STATUS = {0: "PT_OK", 1: "PT_ERR_INVALID", 2: "PT_ERR_NOMEM", 3: "PT_ERR_CUDA",
+           4: "PT_ERR_TIMEOUT", 5: "PT_ERR_UNSUPPORTED"}
+
+
+class PtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class pt_naive_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("two_sided", ctypes.c_int32)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def load(path=None):
+    """Load the built library (raises OSError/RuntimeError when it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libpt.so not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "pt_naive_opts_default": (None, [ctypes.POINTER(pt_naive_opts)]),
+        "pt_prepare": (ctypes.c_int, [_VP, i32, i64, _VP, i32, _VP, ctypes.POINTER(_VP)]),
+        "pt_maxnull_naive": (ctypes.c_int, [_VP, _VP, i64, _VP, _VP, _VP]),
+        "pt_maxnull_naive_ex": (ctypes.c_int, [_VP, _VP, i64, ctypes.POINTER(pt_naive_opts),
+                                               _VP, _VP, _VP]),
+        "pt_sync": (ctypes.c_int, [_VP]),
+        "pt_t_obs": (ctypes.c_int, [_VP, _VP]),
+        "pt_voxel_grid_index": (ctypes.c_int, [_VP, _VP]),
+        "pt_num_voxels": (i64, [_VP]),
+        "pt_num_valid_voxels": (i64, [_VP]),
+        "pt_last_error": (ctypes.c_char_p, [_VP]),
+        "pt_destroy": (None, [_VP]),
+        "pt_release_cached_memory": (None, []),
+        "pt_profile_enable": (ctypes.c_int, [_VP, i32]),
+        "pt_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(i64)]),
+        "pt_kernel_launch_count": (i64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(status, ctx_handle=None):
+    if status != PT_OK:
+        msg = load().pt_last_error(ctx_handle)
+        raise PtError(status, msg.decode() if msg else "")
+
+
+class Ctx:
+    """Owns a ``pt_ctx*``; destroyed with :meth:`close` or on garbage collection."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            load().pt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def pt_prepare(X, n1, mask=None, stream=None):
+    """X: (n, n_grid) float32 CUDA tensor; mask: (n_grid,) uint8 CUDA tensor or None."""
+    lib = load()
+    assert X.dtype == torch.float32 and X.dim() == 2
+    if mask is not None:
+        assert mask.dtype == torch.uint8 and mask.numel() == X.shape[1]
+    out = ctypes.c_void_p()
+    st = lib.pt_prepare(_ptr(X), X.shape[0], X.shape[1], _ptr(mask), int(n1), _stream_ptr(stream),
+                        ctypes.byref(out))
+    _check(st, None)
+    return Ctx(out)
+
+
+def pt_maxnull_naive(ctx, perms, maxnull, argmax, counts=None):
+    lib = load()
+    assert perms.dtype == torch.int32
+    st = lib.pt_maxnull_naive(ctx.handle, _ptr(perms), perms.shape[0], _ptr(maxnull),
+                              _ptr(argmax), _ptr(counts))
+    _check(st, ctx.handle)
+
+
+def pt_maxnull_naive_ex(ctx, perms, opts, maxnull, argmax, counts=None):
+    lib = load()
+    assert perms.dtype == torch.int32
+    st = lib.pt_maxnull_naive_ex(ctx.handle, _ptr(perms), perms.shape[0], ctypes.byref(opts),
+                                 _ptr(maxnull), _ptr(argmax), _ptr(counts))
+    _check(st, ctx.handle)
+
+
+def pt_sync(ctx):
+    _check(load().pt_sync(ctx.handle), ctx.handle)
+
+
+def pt_t_obs(ctx, t_obs):
+    _check(load().pt_t_obs(ctx.handle, _ptr(t_obs)), ctx.handle)
+
+
+def pt_voxel_grid_index(ctx, grid_index):
+    _check(load().pt_voxel_grid_index(ctx.handle, _ptr(grid_index)), ctx.handle)
+
+
+def pt_num_voxels(ctx):
+    return int(load().pt_num_voxels(ctx.handle))
+
+
+def pt_num_valid_voxels(ctx):
+    return int(load().pt_num_valid_voxels(ctx.handle))
+
+
+def pt_last_error(ctx=None):
+    msg = load().pt_last_error(ctx.handle if ctx is not None else None)
+    return msg.decode() if msg else ""
+
+
+def pt_destroy(ctx):
+    ctx.close()
+
+
+def pt_release_cached_memory():
+    load().pt_release_cached_memory()
+
+
+def naive_opts(precision=PT_PREC_BF16X3, two_sided=False):
+    o = pt_naive_opts()
+    load().pt_naive_opts_default(ctypes.byref(o))
+    o.precision = int(precision)
+    o.two_sided = int(bool(two_sided))
+    return o
+
+
+def maxnull_naive(ctx, perms, precision=PT_PREC_BF16X3, two_sided=False, counts=True, sync=True):
+    """Allocates outputs, runs pt_maxnull_naive_ex, optionally pt_sync; returns
+    (maxnull float32[P], argmax int32[P], counts int32[v] or None) as tensors."""
+    dev = perms.device
+    P = perms.shape[0]
+    mx = torch.empty(P, dtype=torch.float32, device=dev)
+    am = torch.empty(P, dtype=torch.int32, device=dev)
+    # uint32 counts held in an int32 tensor (counts < 2^31)
+    ct = torch.empty(pt_num_voxels(ctx), dtype=torch.int32, device=dev) if counts else None
+    pt_maxnull_naive_ex(ctx, perms, naive_opts(precision, two_sided), mx, am, ct)
+    if sync:
+        pt_sync(ctx)
+    return mx, am, ct
+
+
+def pt_profile_enable(ctx, on=True):
+    _check(load().pt_profile_enable(ctx.handle, int(bool(on))), ctx.handle)
+
+
+def pt_profile_read(ctx):
+    """Returns (total_ms, launches) of the dominant kernel since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().pt_profile_read(ctx.handle, ctypes.byref(ms), ctypes.byref(n)), ctx.handle)
+    return ms.value, n.value
+
+
+def pt_kernel_launch_count():
+    return int(load().pt_kernel_launch_count())

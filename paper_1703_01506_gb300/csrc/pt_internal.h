@@ -1,0 +1,112 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pt.h"
+
+namespace pt {
+
+// Device-side error bits, OR-ed into the context's status word by kernels.
+enum : uint32_t {
+  kErrBadPerm = 1u,   // a relabelling row is not a permutation of 0..n-1
+  kErrTimeout = 2u,   // a bounded spin-wait expired
+  kErrBadData = 4u,   // NaN / Inf in the input data
+};
+
+// Caching device allocator: blocks are keyed by (device, rounded size) and
+// recycled, so steady-state calls never reach cudaMalloc.
+void* dev_alloc(size_t bytes);
+void dev_free(void* p);
+
+// A device buffer owned by a context; grows on demand, never shrinks.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  bool ensure(size_t want);  // false on allocation failure
+  void release();
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// Per-precision cache of the observed statistic computed by the same
+// contraction path as the relabellings (so an exact tie with the observed
+// group set compares equal).
+struct ObsCache {
+  bool valid = false;
+  Buf u_obs;  // float[v_valid]
+};
+
+}  // namespace pt
+
+struct pt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int32_t n = 0, n1 = 0, n2 = 0, n_pad = 0;
+  int64_t n_grid = 0;
+  int64_t v = 0;        // mask voxels
+  int64_t v_valid = 0;  // voxels with a defined t
+  int64_t v_pad = 0;    // v_valid rounded up to 256
+  double k = 0.0;       // 1/n1 + 1/n2
+  double c_t = 0.0;     // sqrt(k (n - 2)): t = c_t u / sqrt(1 - k u^2)
+  std::string last_error;
+
+  pt::Buf status;       // uint32 error bits
+  pt::Buf vox_grid;     // int64[v]: grid index of masked voxel j
+  pt::Buf valid_map;    // int32[v_valid]: masked index of compact voxel c
+  pt::Buf t_obs64;      // double[v]: observed t (NaN if degenerate)
+  pt::Buf Xn32;         // float[v_pad][n_pad]: unit-norm centred data (compact order)
+  pt::Buf Xnb;          // bf16 pieces, 3 x [v_pad/8][n_pad/8][8][8] blocked layout
+  pt::ObsCache obs[3];  // indexed by pt_precision
+
+  // Per-call workspaces (grown on demand).
+  pt::Buf labels;       // float or bf16 labels
+  pt::Buf maxkey;       // uint64[P]
+  pt::Buf cnt;          // uint32[v_valid]
+  pt::Buf scratch;      // misc
+
+  // Profiling of the dominant kernel (events on `stream`).
+  bool profile = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_pool;
+};
+
+namespace pt {
+
+void set_error(pt_ctx* ctx, const std::string& msg);
+void count_launch();
+// Event pair around the dominant kernel when profiling is on (no-ops otherwise).
+void prof_begin(pt_ctx* ctx);
+void prof_end(pt_ctx* ctx);
+void set_thread_error(const std::string& msg);
+
+// ---- prepare (pt_prepare.cu) ----
+pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask);
+
+// ---- naive path (pt_naive.cu) ----
+pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,
+                     float* maxnull, int32_t* argmax, uint32_t* counts);
+
+}  // namespace pt
+
+#define PT_CUDA_TRY(ctx, call)                                                        \
+  do {                                                                                \
+    cudaError_t _e = (call);                                                          \
+    if (_e != cudaSuccess) {                                                          \
+      pt::set_error((ctx), std::string(#call) + ": " + cudaGetErrorString(_e));       \
+      return _e == cudaErrorMemoryAllocation ? PT_ERR_NOMEM : PT_ERR_CUDA;            \
+    }                                                                                 \
+  } while (0)
+
+#define PT_LAUNCH_CHECK(ctx)                                                          \
+  do {                                                                                \
+    cudaError_t _e = cudaGetLastError();                                              \
+    if (_e != cudaSuccess) {                                                          \
+      pt::set_error((ctx), std::string("kernel launch: ") + cudaGetErrorString(_e));  \
+      return PT_ERR_CUDA;                                                             \
+    }                                                                                 \
+    pt::count_launch();                                                               \
+  } while (0)

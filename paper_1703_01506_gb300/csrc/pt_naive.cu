@@ -1,0 +1,386 @@
+// NaivePT (Alg. 1) on the GPU: relabelling rows -> 0/1 label matrix L, the
+// contraction U = L . Xn^T (u = group-1 sum of unit-norm centred data), and
+// the fused reduction to the max-null and per-voxel exceedance counts.
+//
+// Because t = sqrt(k(n-2)) u / sqrt(1 - k u^2) is the same strictly
+// increasing function of u at every voxel, max_j t_ij = f(max_j u_ij), and
+// t_ij >= t_obs_j  <=>  u_ij >= u_obs_j. The kernels therefore reduce u and
+// convert only the P row maxima to t (in FP64) at the end.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "pt_internal.h"
+#include "pt_kernels.h"
+
+namespace pt {
+
+// ---------------------------------------------------------------------------
+// Labels: one warp per relabelling row. Validates the row (entries in range
+// and distinct), then writes L[i][s] = 1 for the subjects of group 1.
+// layout 0: float [P_pad][n_pad];  layout 1: bf16 8x8 core matrices (tensor-core A).
+// ---------------------------------------------------------------------------
+__global__ void labels_kernel(const int32_t* __restrict__ perms, int64_t P, int64_t P_pad, int n,
+                              int n1, int n_pad, int layout, void* __restrict__ Lout,
+                              uint32_t* __restrict__ status) {
+  __shared__ uint32_t seen_all[8][32];
+  __shared__ uint32_t g1_all[8][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* seen = seen_all[wib];
+  uint32_t* g1 = g1_all[wib];
+  const int64_t i = int64_t(blockIdx.x) * 8 + wib;
+  if (i >= P_pad) return;
+  seen[lane] = 0u;
+  g1[lane] = 0u;
+  __syncwarp();
+  bool bad = false;
+  if (i < P) {
+    const int32_t* row = perms + i * n;
+    for (int q = lane; q < n; q += 32) {
+      const int32_t e = row[q];
+      if (e < 0 || e >= n) {
+        bad = true;
+        continue;
+      }
+      const uint32_t bit = 1u << (e & 31);
+      const uint32_t old = atomicOr(&seen[e >> 5], bit);
+      if (old & bit) bad = true;
+      if (q < n1) atomicOr(&g1[e >> 5], bit);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kErrBadPerm);
+  __syncwarp();
+  for (int s = lane; s < n_pad; s += 32) {
+    const bool in = (i < P) && s < n && ((g1[s >> 5] >> (s & 31)) & 1u);
+    if (layout == 0) {
+      static_cast<float*>(Lout)[i * n_pad + s] = in ? 1.0f : 0.0f;
+    } else {
+      // 128-row blocks, inside a block k-group major: core matrix (row group rg,
+      // k group kg) of 8x8 elements at (kg * 16 + rg) * 64 -> one k-step of 16
+      // subjects is a contiguous 4 KB slab (one TMA stage).
+      const int64_t off = (i >> 7) * int64_t(128) * n_pad +
+                          ((s >> 3) * 16 + ((i & 127) >> 3)) * 64 + (i & 7) * 8 + (s & 7);
+      static_cast<__nv_bfloat16*>(Lout)[off] = __float2bfloat16(in ? 1.0f : 0.0f);
+    }
+  }
+}
+
+__global__ void iota_rows_kernel(int32_t* __restrict__ out, int n) {
+  for (int s = threadIdx.x; s < n; s += blockDim.x) out[s] = s;
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP32 CUDA-core contraction with the fused epilogue.
+// CTA tile 128 relabellings x 128 voxels, K step 16, 256 threads, 8x8 per thread.
+// mode 0: reduce (row max -> packed key atomics, counts -> cnt)
+// mode 1: write u rows to uout[row][voxel]
+// ---------------------------------------------------------------------------
+constexpr int BM = 128, BN = 128, BK = 16;
+
+__global__ void __launch_bounds__(256, 2)
+    simt_contract_kernel(const float* __restrict__ L, const float* __restrict__ Xn, int n_pad,
+                         int64_t P, int64_t v, int tiles_per_cta, int mode, int two_sided,
+                         const float* __restrict__ u_obs, unsigned long long* __restrict__ maxkey,
+                         uint32_t* __restrict__ cnt, float* __restrict__ uout) {
+  __shared__ __align__(16) float As[2][BK][BM];
+  __shared__ __align__(16) float Bs[2][BK][BN];
+  __shared__ uint32_t scnt[BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t v0 = int64_t(blockIdx.x) * BN;
+  const int64_t ptiles = (P + BM - 1) / BM;
+  const int64_t t_begin = int64_t(blockIdx.y) * tiles_per_cta;
+  const int64_t t_end = min(ptiles, t_begin + tiles_per_cta);
+  if (tid < BN) scnt[tid] = 0u;
+
+  // loader mapping: row = tid >> 1 (0..127), k offset (tid & 1) * 8
+  const int lrow = tid >> 1, lk = (tid & 1) * 8;
+  const int ksteps = n_pad / BK;
+
+  float uo[8];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int col = (b < 4) ? (tx * 4 + b) : (64 + tx * 4 + b - 4);
+    const int64_t gc = v0 + col;
+    float x = (mode == 0 && gc < v) ? u_obs[gc] : 0.0f;
+    uo[b] = two_sided ? fabsf(x) : x;
+  }
+
+  for (int64_t pt = t_begin; pt < t_end; ++pt) {
+    const int64_t p0 = pt * BM;
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+
+    const float* Lrow = L + (p0 + lrow) * n_pad + lk;      // L is padded to whole tiles
+    const float* Xrow = Xn + (v0 + lrow) * n_pad + lk;     // Xn is padded to 256 voxels
+    float4 ra0 = *reinterpret_cast<const float4*>(Lrow);
+    float4 ra1 = *reinterpret_cast<const float4*>(Lrow + 4);
+    float4 rb0 = *reinterpret_cast<const float4*>(Xrow);
+    float4 rb1 = *reinterpret_cast<const float4*>(Xrow + 4);
+    __syncthreads();
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int buf = ks & 1;
+      As[buf][lk + 0][lrow] = ra0.x; As[buf][lk + 1][lrow] = ra0.y;
+      As[buf][lk + 2][lrow] = ra0.z; As[buf][lk + 3][lrow] = ra0.w;
+      As[buf][lk + 4][lrow] = ra1.x; As[buf][lk + 5][lrow] = ra1.y;
+      As[buf][lk + 6][lrow] = ra1.z; As[buf][lk + 7][lrow] = ra1.w;
+      Bs[buf][lk + 0][lrow] = rb0.x; Bs[buf][lk + 1][lrow] = rb0.y;
+      Bs[buf][lk + 2][lrow] = rb0.z; Bs[buf][lk + 3][lrow] = rb0.w;
+      Bs[buf][lk + 4][lrow] = rb1.x; Bs[buf][lk + 5][lrow] = rb1.y;
+      Bs[buf][lk + 6][lrow] = rb1.z; Bs[buf][lk + 7][lrow] = rb1.w;
+      __syncthreads();
+      if (ks + 1 < ksteps) {
+        const int ko = (ks + 1) * BK;
+        ra0 = *reinterpret_cast<const float4*>(Lrow + ko);
+        ra1 = *reinterpret_cast<const float4*>(Lrow + ko + 4);
+        rb0 = *reinterpret_cast<const float4*>(Xrow + ko);
+        rb1 = *reinterpret_cast<const float4*>(Xrow + ko + 4);
+      }
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + tx * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+      }
+    }
+
+    if (mode == 1) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int64_t row = p0 + ((a < 4) ? (ty * 4 + a) : (64 + ty * 4 + a - 4));
+        if (row >= P) continue;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int64_t col = v0 + ((b < 4) ? (tx * 4 + b) : (64 + tx * 4 + b - 4));
+          if (col < v) uout[row * v + col] = acc[a][b];
+        }
+      }
+      continue;
+    }
+
+    // ---- fused epilogue: row max (with smallest-index ties) and counts ----
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t row = p0 + ((a < 4) ? (ty * 4 + a) : (64 + ty * 4 + a - 4));
+      float best = -INFINITY;
+      uint32_t bj = 0xffffffffu;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int64_t col = v0 + ((b < 4) ? (tx * 4 + b) : (64 + tx * 4 + b - 4));
+        const float s = two_sided ? fabsf(acc[a][b]) : acc[a][b];
+        if (col < v && (s > best || (s == best && uint32_t(col) < bj))) {
+          best = s;
+          bj = uint32_t(col);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const uint32_t oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob > best || (ob == best && oj < bj)) {
+          best = ob;
+          bj = oj;
+        }
+      }
+      if (tx == 0 && row < P && bj != 0xffffffffu) {
+        const unsigned long long key = pack_key(best, bj);
+        if (key > maxkey[row]) atomicMax(&maxkey[row], key);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int colo = (b < 4) ? (tx * 4 + b) : (64 + tx * 4 + b - 4);
+      uint32_t c = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int64_t row = p0 + ((a < 4) ? (ty * 4 + a) : (64 + ty * 4 + a - 4));
+        const float s = two_sided ? fabsf(acc[a][b]) : acc[a][b];
+        c += (row < P && s >= uo[b]) ? 1u : 0u;
+      }
+      // reduce over the two ty rows of this warp, then shared atomics
+      c += __shfl_xor_sync(0xffffffffu, c, 16);
+      if ((tid & 16) == 0 && c) atomicAdd(&scnt[colo], c);
+    }
+  }
+  if (mode == 0) {
+    __syncthreads();
+    if (tid < BN) {
+      const int64_t col = v0 + tid;
+      if (col < v && scnt[tid]) atomicAdd(&cnt[col], scnt[tid]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Finalise: packed keys -> t (FP64 from u), masked argmax; counts -> masked order.
+// ---------------------------------------------------------------------------
+__global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxkey, int64_t P,
+                                    const int32_t* __restrict__ valid_map, double k, double c_t,
+                                    float* __restrict__ maxnull, int32_t* __restrict__ argmax) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < P;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const unsigned long long key = maxkey[i];
+    if (key == 0ull) {
+      maxnull[i] = -INFINITY;
+      argmax[i] = -1;
+      continue;
+    }
+    const double u = double(unpack_key_value(key));
+    const uint32_t c = unpack_key_index(key);
+    const double den = 1.0 - k * u * u;
+    double t;
+    if (den > 0.0) t = c_t * u / sqrt(den);
+    else t = u > 0 ? INFINITY : (u < 0 ? -INFINITY : 0.0);
+    maxnull[i] = float(t);
+    argmax[i] = valid_map[c];
+  }
+}
+
+__global__ void scatter_counts_kernel(const uint32_t* __restrict__ cnt, int64_t v_valid,
+                                      const int32_t* __restrict__ valid_map,
+                                      uint32_t* __restrict__ counts) {
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < v_valid;
+       c += int64_t(gridDim.x) * blockDim.x)
+    counts[valid_map[c]] = cnt[c];
+}
+
+static int grid_1d(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return int(b);
+}
+
+// Build labels for P rows into ctx->labels (layout per path).
+pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout, int64_t* P_pad_out) {
+  const int64_t P_pad = (P + 127) / 128 * 128;
+  const size_t elem = layout == 0 ? sizeof(float) : sizeof(__nv_bfloat16);
+  if (!ctx->labels.ensure(elem * size_t(P_pad) * ctx->n_pad)) {
+    set_error(ctx, "out of device memory (labels)");
+    return PT_ERR_NOMEM;
+  }
+  labels_kernel<<<unsigned((P_pad + 7) / 8), 256, 0, ctx->stream>>>(
+      perms, P, P_pad, ctx->n, ctx->n1, ctx->n_pad, layout, ctx->labels.p,
+      ctx->status.as<uint32_t>());
+  PT_LAUNCH_CHECK(ctx);
+  *P_pad_out = P_pad;
+  return PT_OK;
+}
+
+// SIMT launch helper: grid (voxel tiles, relabelling chunks).
+static pt_status launch_simt(pt_ctx* ctx, const float* L, int64_t P, int mode, int two_sided,
+                             const float* u_obs, unsigned long long* maxkey, uint32_t* cnt,
+                             float* uout) {
+  const int64_t vt = (ctx->v_valid + BN - 1) / BN;
+  const int64_t ptiles = (P + BM - 1) / BM;
+  int64_t chunks = (152 * 2 * 4 + vt - 1) / vt;
+  if (chunks > ptiles) chunks = ptiles;
+  if (chunks < 1) chunks = 1;
+  if (chunks > 65535) chunks = 65535;
+  const int per = int((ptiles + chunks - 1) / chunks);
+  chunks = (ptiles + per - 1) / per;
+  const dim3 grid{unsigned(vt), unsigned(chunks), 1u};
+  if (mode == 0) prof_begin(ctx);
+  simt_contract_kernel<<<grid, 256, 0, ctx->stream>>>(L, ctx->Xn32.as<float>(), ctx->n_pad, P,
+                                                      ctx->v_valid, per, mode, two_sided, u_obs,
+                                                      maxkey, cnt, uout);
+  if (mode == 0) prof_end(ctx);
+  PT_LAUNCH_CHECK(ctx);
+  return PT_OK;
+}
+
+// u at the observed (identity) labelling, by the same contraction path.
+pt_status ensure_u_obs(pt_ctx* ctx, int precision) {
+  ObsCache& oc = ctx->obs[precision];
+  if (oc.valid) return PT_OK;
+  if (!oc.u_obs.ensure(sizeof(float) * ctx->v_pad)) {
+    set_error(ctx, "out of device memory (u_obs)");
+    return PT_ERR_NOMEM;
+  }
+  Buf idp;
+  if (!idp.ensure(sizeof(int32_t) * ctx->n)) {
+    set_error(ctx, "out of device memory");
+    return PT_ERR_NOMEM;
+  }
+  iota_rows_kernel<<<1, 256, 0, ctx->stream>>>(idp.as<int32_t>(), ctx->n);
+  PT_LAUNCH_CHECK(ctx);
+  int64_t P_pad = 0;
+  pt_status s;
+  if (precision == PT_PREC_FP32) {
+    s = build_labels(ctx, idp.as<int32_t>(), 1, 0, &P_pad);
+    if (s == PT_OK)
+      s = launch_simt(ctx, ctx->labels.as<float>(), 1, 1, 0, nullptr, nullptr, nullptr,
+                      oc.u_obs.as<float>());
+  } else {
+    s = build_labels(ctx, idp.as<int32_t>(), 1, 1, &P_pad);
+    if (s == PT_OK) s = tc_write_u(ctx, ctx->labels.p, 1, precision, oc.u_obs.as<float>());
+  }
+  cudaStreamSynchronize(ctx->stream);
+  idp.release();
+  if (s != PT_OK) return s;
+  oc.valid = true;
+  return PT_OK;
+}
+
+pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,
+                     float* maxnull, int32_t* argmax, uint32_t* counts) {
+  cudaStream_t st = ctx->stream;
+  if (o.precision != PT_PREC_FP32) {
+    pt_status s = tc_supported(ctx);
+    if (s != PT_OK) return s;
+  }
+  pt_status s = ensure_u_obs(ctx, o.precision);
+  if (s != PT_OK) return s;
+  if (!ctx->maxkey.ensure(sizeof(unsigned long long) * P) ||
+      !ctx->cnt.ensure(sizeof(uint32_t) * (ctx->v_valid > 0 ? ctx->v_valid : 1))) {
+    set_error(ctx, "out of device memory (workspace)");
+    return PT_ERR_NOMEM;
+  }
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->maxkey.p, 0, sizeof(unsigned long long) * P, st));
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(uint32_t) * (ctx->v_valid > 0 ? ctx->v_valid : 1), st));
+  if (counts) PT_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ctx->v, st));
+  int64_t P_pad = 0;
+  if (ctx->v_valid > 0) {
+    if (o.precision == PT_PREC_FP32) {
+      s = build_labels(ctx, perms, P, 0, &P_pad);
+      if (s != PT_OK) return s;
+      s = launch_simt(ctx, ctx->labels.as<float>(), P, 0, o.two_sided,
+                      ctx->obs[o.precision].u_obs.as<float>(), ctx->maxkey.as<unsigned long long>(),
+                      ctx->cnt.as<uint32_t>(), nullptr);
+    } else {
+      s = build_labels(ctx, perms, P, 1, &P_pad);
+      if (s != PT_OK) return s;
+      s = tc_reduce(ctx, ctx->labels.p, P, o.precision, o.two_sided,
+                    ctx->obs[o.precision].u_obs.as<float>(), ctx->maxkey.as<unsigned long long>(),
+                    ctx->cnt.as<uint32_t>());
+    }
+    if (s != PT_OK) return s;
+  } else {
+    // still validate the relabellings
+    s = build_labels(ctx, perms, P, 0, &P_pad);
+    if (s != PT_OK) return s;
+  }
+  finalize_max_kernel<<<grid_1d(P, 256), 256, 0, st>>>(ctx->maxkey.as<unsigned long long>(), P,
+                                                        ctx->valid_map.as<int32_t>(), ctx->k,
+                                                        ctx->c_t, maxnull, argmax);
+  PT_LAUNCH_CHECK(ctx);
+  if (counts && ctx->v_valid > 0) {
+    scatter_counts_kernel<<<grid_1d(ctx->v_valid, 256), 256, 0, st>>>(
+        ctx->cnt.as<uint32_t>(), ctx->v_valid, ctx->valid_map.as<int32_t>(), counts);
+    PT_LAUNCH_CHECK(ctx);
+  }
+  return PT_OK;
+}
+
+}  // namespace pt

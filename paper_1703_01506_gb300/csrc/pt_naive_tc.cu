@@ -1,0 +1,509 @@
+// Tensor-core (tcgen05) form of the NaivePT contraction U = L . Xn^T fused
+// with the max-null / exceedance-count reduction (Alg. 1; Eq. (5) through the
+// monotone map u -> t).
+//
+// Roles (one CTA per SM, persistent over work items = (voxel tile, block range)):
+//   warp 0      TMA producer: the resident Xn tile (BF16 pieces) once per item,
+//               then the label matrix L streamed one k-step (128 x 16) per stage.
+//   warp 1      MMA issuer: per k-step, one tcgen05.mma per data piece into a
+//               128 x NT FP32 accumulator in TMEM (two accumulators, ping-pong).
+//   warps 2..9  epilogue: tcgen05.ld rows of the accumulator (lane = relabelling,
+//               column = voxel), row max -> packed (u, voxel) atomics, per-voxel
+//               exceedance counts in packed 16-bit registers, optional row writes.
+//
+// Labels are exact in BF16; the data enter as hi + mid (+ lo) BF16 pieces of
+// the FP64 unit-norm value, so the FP32 accumulator carries ~16 or ~24 bits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "pt_internal.h"
+#include "pt_kernels.h"
+
+namespace pt {
+namespace {
+
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kStageBytes = 4096;  // 128 relabellings x 16 subjects x BF16
+constexpr int kSmemLimit = 232448;
+constexpr int kMaxBlocksPerItem = 2047;  // keeps packed 16-bit lane sums below 2^16
+
+struct TcArgs {
+  int n_pad, pieces, stages, ksteps;
+  int64_t P, v, v_pad;
+  int64_t n_chunks, blocks_per_chunk, nblocks, n_items;
+  int do_reduce, write_mode, two_sided;  // write_mode: 0 none, 1 u, 2 t
+  float k_f, ct_f;
+  const float* u_obs;
+  unsigned long long* maxkey;
+  uint32_t* cnt;
+  float* uout;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+template <int R>
+__device__ __forceinline__ void flush_counts(uint32_t (&r)[R], int lane, int64_t col0, int64_t v,
+                                             uint32_t* cnt) {
+  int base = 0;
+#pragma unroll
+  for (int rnd = 0; rnd < 5; ++rnd) {
+    const int off = 16 >> rnd;
+    const int Rb = (R >> rnd) > 0 ? (R >> rnd) : 1;
+    if (Rb >= 2) {
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int q = 0; q < Rb / 2; ++q) {
+        const uint32_t send = up ? r[q] : r[q + Rb / 2];
+        const uint32_t keep = up ? r[q + Rb / 2] : r[q];
+        r[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+      if (up) base += Rb / 2;
+    } else {
+      r[0] += __shfl_xor_sync(0xffffffffu, r[0], off);
+    }
+  }
+  constexpr int Rf = (R >> 5) > 0 ? (R >> 5) : 1;
+  constexpr int dup_mask = (R >= 32) ? 0 : (32 / R - 1);
+  if ((lane & dup_mask) != 0) return;
+#pragma unroll
+  for (int f = 0; f < Rf; ++f) {
+    const int kreg = base + f;
+    const uint32_t pk = r[f];
+    const int64_t c0 = col0 + 2 * kreg;
+    const uint32_t lo = pk & 0xffffu, hi = pk >> 16;
+    if (lo && c0 < v) atomicAdd(&cnt[c0], lo);
+    if (hi && c0 + 1 < v) atomicAdd(&cnt[c0 + 1], hi);
+  }
+}
+
+// One 32-column chunk of a row: max and exceedance counts.
+template <bool RAGGED>
+__device__ __forceinline__ float chunk_reduce(const uint32_t (&r)[32], const float* su_chunk,
+                                              int two_sided, int64_t gcol0, int64_t v,
+                                              uint32_t* cntp16) {
+  float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
+  const float4* s4 = reinterpret_cast<const float4*>(su_chunk);
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    const float4 o = s4[g];
+    const float ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int jj = g * 4 + e;
+      const float u = __uint_as_float(r[jj]);
+      float s = two_sided ? fabsf(u) : u;
+      if (RAGGED && gcol0 + jj >= v) s = -INFINITY;
+      if (e == 0) m0 = fmaxf(m0, s);
+      if (e == 1) m1 = fmaxf(m1, s);
+      if (e == 2) m2 = fmaxf(m2, s);
+      if (e == 3) m3 = fmaxf(m3, s);
+      if (s >= ov[e]) cntp16[jj >> 1] += (jj & 1) ? 0x10000u : 1u;
+    }
+  }
+  return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_contract_kernel(const __grid_constant__ CUtensorMap tmL,
+                       const __grid_constant__ CUtensorMap tmX, const TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int CH = NT / 64;  // 32-column chunks per epilogue thread (NT/2 columns)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = a.stages;
+  const uint32_t xtile_bytes = uint32_t(NT) * a.n_pad * 2;
+  uint8_t* xs = smem;
+  uint8_t* ls = smem + a.pieces * xtile_bytes;
+  float* su = reinterpret_cast<float*>(ls + S * kStageBytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(su + NT);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7 + 2 * S);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t bar0 = smem_addr(bars);
+#define BAR(i) (bar0 + 8u * uint32_t(i))
+  // 0 xfull, 1 xempty, 2..3 accfull, 4..5 accempty, 6 mma_done, 7.. lfull[S], 7+S.. lempty[S]
+#define LFULL(s) BAR(7 + (s))
+#define LEMPTY(s) BAR(7 + S + (s))
+
+  if (threadIdx.x == 0) {
+    mbar_init(BAR(0), 1);
+    mbar_init(BAR(1), 1);
+    mbar_init(BAR(2), 1);
+    mbar_init(BAR(3), 1);
+    mbar_init(BAR(4), kEpiWarps);
+    mbar_init(BAR(5), kEpiWarps);
+    mbar_init(BAR(6), 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(LFULL(s), 1);
+      mbar_init(LEMPTY(s), 1);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(smem_addr(tmem_slot), 2 * NT);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      int w = 0;
+      bool ok = true;
+      int x_armed = -1;  // parity of the last armed phase of xfull (-1: none)
+      for (int64_t item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, ++w) {
+        const int64_t vt = item / a.n_chunks, pc = item % a.n_chunks;
+        const int64_t b0 = pc * a.blocks_per_chunk;
+        const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
+        if (!mbar_wait(BAR(1), (w & 1) ^ 1, a.status, abort_flag)) break;
+        mbar_arrive_expect_tx(BAR(0), uint32_t(a.pieces) * xtile_bytes);
+        x_armed = w & 1;
+        for (int q = 0; q < a.pieces; ++q) {
+          const int64_t row0 = (int64_t(q) * a.v_pad * a.n_pad + vt * NT * a.n_pad) / 256;
+          tma_load_2d(smem_addr(xs + q * xtile_bytes), &tmX, 0, int32_t(row0), BAR(0));
+        }
+        for (int64_t b = b0; b < b1 && ok; ++b) {
+          for (int ks = 0; ks < a.ksteps; ++ks, ++it) {
+            const uint32_t s = it % uint32_t(S), ph = (it / uint32_t(S)) & 1u;
+            if (!mbar_wait(LEMPTY(s), ph ^ 1u, a.status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(LFULL(s), kStageBytes);
+            const int64_t row = b * (a.n_pad / 2) + ks * 8;
+            tma_load_2d(smem_addr(ls + s * kStageBytes), &tmL, 0, int32_t(row), LFULL(s));
+          }
+        }
+      }
+      // Drain: every copy this thread started has completed before the CTA exits.
+      const uint32_t armed = it < uint32_t(S) ? it : uint32_t(S);
+      for (uint32_t k = 0; k < armed; ++k) {
+        const uint32_t last = it - 1 - k;  // the most recent use of stage last % S
+        mbar_wait(LFULL(last % uint32_t(S)), (last / uint32_t(S)) & 1u, a.status, abort_flag,
+                  kWaitLimitNs, false);
+      }
+      if (x_armed >= 0) mbar_wait(BAR(0), uint32_t(x_armed), a.status, abort_flag, kWaitLimitNs, false);
+    }
+  } else if (warp == 1) {
+    // ------------------------------ MMA issuer ------------------------------
+    if (lane == 0) {
+      uint32_t it = 0, j = 0;
+      int w = 0;
+      const uint32_t idesc = idesc_bf16_f32(128, NT);
+      const uint32_t lbo_a = 16 * 128, sbo_a = 128;                     // L stage: k-group major
+      const uint32_t lbo_b = 128, sbo_b = uint32_t(a.n_pad / 8) * 128;  // Xn tile: row-group major
+      const uint32_t xbase = smem_addr(xs), lbase = smem_addr(ls);
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, ++w) {
+        const int64_t pc = item % a.n_chunks;
+        const int64_t b0 = pc * a.blocks_per_chunk;
+        const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
+        if (!mbar_wait(BAR(0), w & 1, a.status, abort_flag)) break;
+        tc_fence_after();
+        for (int64_t b = b0; b < b1 && ok; ++b, ++j) {
+          const uint32_t abuf = j & 1u, aph = (j >> 1) & 1u;
+          if (!mbar_wait(BAR(4 + abuf), aph ^ 1u, a.status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem + abuf * NT;
+          for (int ks = 0; ks < a.ksteps; ++ks, ++it) {
+            const uint32_t s = it % uint32_t(S), ph = (it / uint32_t(S)) & 1u;
+            if (!mbar_wait(LFULL(s), ph, a.status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint64_t adesc = smem_desc(lbase + s * kStageBytes, lbo_a, sbo_a);
+            for (int q = 0; q < a.pieces; ++q) {
+              const uint64_t bdesc =
+                  smem_desc(xbase + q * xtile_bytes + uint32_t(ks) * 256u, lbo_b, sbo_b);
+              tc_mma_f16(d, adesc, bdesc, idesc, (ks | q) != 0 ? 1u : 0u);
+            }
+            tc_commit(LEMPTY(s));
+          }
+          if (!ok) break;
+          tc_commit(BAR(2 + abuf));
+        }
+        if (!ok) break;
+        tc_commit(BAR(1));
+      }
+      // Every MMA this thread issued has completed before TMEM is released.
+      tc_commit(BAR(6));
+      mbar_wait(BAR(6), 0, a.status, abort_flag, kWaitLimitNs, false);
+    }
+  } else {
+    // ------------------------------ epilogue ------------------------------
+    // The 256 epilogue threads always walk the same items and blocks (so the
+    // named barrier stays matched); after a failed wait they only skip work.
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    const int colbase = half * (NT / 2);
+    const int etid = threadIdx.x - 64;
+    uint32_t j = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+      const int64_t vt = item / a.n_chunks, pc = item % a.n_chunks;
+      const int64_t b0 = pc * a.blocks_per_chunk;
+      const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
+      const int64_t v0 = vt * NT;
+      const bool ragged = v0 + NT > a.v;
+      epi_bar();
+      for (int c = etid; c < NT; c += 256) {
+        float x = INFINITY;
+        if (a.do_reduce && v0 + c < a.v) {
+          x = a.u_obs[v0 + c];
+          if (a.two_sided) x = fabsf(x);
+        }
+        su[c] = x;
+      }
+      epi_bar();
+      uint32_t cntp[CH * 16];
+#pragma unroll
+      for (int q = 0; q < CH * 16; ++q) cntp[q] = 0u;
+      for (int64_t b = b0; b < b1; ++b, ++j) {
+        const uint32_t abuf = j & 1u, aph = (j >> 1) & 1u;
+        const int64_t row = b * 128 + quad * 32 + lane;
+        unsigned long long gkey = 0ull;
+        if (a.do_reduce && row < a.P) gkey = __ldcg(&a.maxkey[row]);
+        if (ok && !mbar_wait(BAR(2 + abuf), aph, a.status, abort_flag)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) continue;
+        tc_fence_after();
+        const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
+        float best = -INFINITY;
+        int bestc = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          uint32_t r[32];
+          tc_ld_32x32b_x32(tbase + c * 32, r);
+          tc_wait_ld();
+          const int64_t gcol0 = v0 + colbase + c * 32;
+          if (a.write_mode && row < a.P) {
+            float* dst = a.uout + row * a.v;
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              if (gcol0 + jj < a.v) {
+                const float u = __uint_as_float(r[jj]);
+                float val = u;
+                if (a.write_mode == 2) {
+                  const float den = 1.0f - a.k_f * u * u;
+                  val = den > 0.0f ? a.ct_f * u * rsqrtf(den) : (u > 0.0f ? INFINITY : -INFINITY);
+                }
+                dst[gcol0 + jj] = val;
+              }
+            }
+          }
+          if (a.do_reduce) {
+            const float cm = ragged
+                ? chunk_reduce<true>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, cntp + c * 16)
+                : chunk_reduce<false>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, cntp + c * 16);
+            if (cm > best) {
+              best = cm;
+              bestc = c;
+            }
+          }
+        }
+        if (a.do_reduce) {
+          // Candidate for the global row maximum: find its column and publish.
+          bool need = row < a.P && best > -INFINITY;
+          if (need && gkey != 0ull) need = best >= unpack_key_value(gkey);
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const bool mine = need && bestc == c;
+            if (__any_sync(0xffffffffu, mine)) {
+              uint32_t r[32];
+              tc_ld_32x32b_x32(tbase + c * 32, r);
+              tc_wait_ld();
+              if (mine) {
+                const int64_t gcol0 = v0 + colbase + c * 32;
+                int jj_best = -1;
+#pragma unroll
+                for (int jj = 31; jj >= 0; --jj) {
+                  const float u = __uint_as_float(r[jj]);
+                  const float s = a.two_sided ? fabsf(u) : u;
+                  if (s == best && gcol0 + jj < a.v) jj_best = jj;
+                }
+                if (jj_best >= 0) {
+                  const unsigned long long key = pack_key(best, uint32_t(gcol0 + jj_best));
+                  if (key > gkey) atomicMax(&a.maxkey[row], key);
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(BAR(4 + abuf));
+      }
+      if (ok && a.do_reduce) flush_counts<CH * 16>(cntp, lane, v0 + colbase, a.v, a.cnt);
+    }
+  }
+#undef LFULL
+#undef LEMPTY
+#undef BAR
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 2 * NT);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                        &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2D view [rows][256] of a BF16 buffer, box [box_rows][256], no swizzle.
+bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {256, rows};
+  cuuint64_t strides[1] = {512};
+  cuuint32_t box[2] = {256, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int smem_bytes(int NT, int n_pad, int pieces, int stages) {
+  return pieces * NT * n_pad * 2 + stages * kStageBytes + NT * 4 + (7 + 2 * stages) * 8 + 16;
+}
+
+int num_sms(int dev) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+template <int NT>
+pt_status launch_nt(pt_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmX, const TcArgs& a,
+                    int grid, int smem) {
+  auto kern = tc_contract_kernel<NT>;
+  PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (a.do_reduce) prof_begin(ctx);
+  kern<<<grid, kThreads, smem, ctx->stream>>>(tmL, tmX, a);
+  if (a.do_reduce) prof_end(ctx);
+  PT_LAUNCH_CHECK(ctx);
+  return PT_OK;
+}
+
+pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
+                    int write_mode, int two_sided, const float* u_obs,
+                    unsigned long long* maxkey, uint32_t* cnt, float* uout) {
+  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int n_pad = ctx->n_pad;
+  int NT = 0, stages = 0;
+  for (int cand : {256, 128, 64}) {
+    if (int64_t(cand) * n_pad / 256 > 256) continue;
+    int s = 12;
+    while (s >= 4 && smem_bytes(cand, n_pad, pieces, s) > kSmemLimit - 1024) --s;
+    if (s >= 4) {
+      NT = cand;
+      stages = s;
+      break;
+    }
+  }
+  if (NT == 0) {
+    set_error(ctx, "tensor-core path: n too large for the resident data tile");
+    return PT_ERR_UNSUPPORTED;
+  }
+  TcArgs a;
+  a.n_pad = n_pad;
+  a.pieces = pieces;
+  a.stages = stages;
+  a.ksteps = n_pad / 16;
+  a.P = P;
+  a.v = ctx->v_valid;
+  a.v_pad = ctx->v_pad;
+  a.nblocks = (P + 127) / 128;
+  const int64_t n_vtiles = (a.v + NT - 1) / NT;
+  const int sms = num_sms(ctx->device);
+  int64_t chunks = (a.nblocks + kMaxBlocksPerItem - 1) / kMaxBlocksPerItem;
+  if (n_vtiles * chunks < 2 * sms) {
+    int64_t want = (2 * sms + n_vtiles - 1) / n_vtiles;
+    if (want > chunks) chunks = want;
+  }
+  if (chunks > a.nblocks) chunks = a.nblocks;
+  if (chunks < 1) chunks = 1;
+  a.blocks_per_chunk = (a.nblocks + chunks - 1) / chunks;
+  a.n_chunks = (a.nblocks + a.blocks_per_chunk - 1) / a.blocks_per_chunk;
+  a.n_items = n_vtiles * a.n_chunks;
+  a.do_reduce = do_reduce;
+  a.write_mode = write_mode;
+  a.two_sided = two_sided;
+  a.k_f = float(ctx->k);
+  a.ct_f = float(ctx->c_t);
+  a.u_obs = u_obs;
+  a.maxkey = maxkey;
+  a.cnt = cnt;
+  a.uout = uout;
+  a.status = ctx->status.as<uint32_t>();
+
+  CUtensorMap tmL, tmX;
+  const int64_t P_pad = a.nblocks * 128;
+  if (!make_map(&tmL, Lb, uint64_t(P_pad) * n_pad / 256, 8) ||
+      !make_map(&tmX, ctx->Xnb.p, uint64_t(3) * ctx->v_pad * n_pad / 256,
+                uint32_t(NT * n_pad / 256))) {
+    set_error(ctx, "cuTensorMapEncodeTiled failed");
+    return PT_ERR_CUDA;
+  }
+  const int grid = int(a.n_items < sms ? a.n_items : sms);
+  const int smem = smem_bytes(NT, n_pad, pieces, stages);
+  if (NT == 256) return launch_nt<256>(ctx, tmL, tmX, a, grid, smem);
+  if (NT == 128) return launch_nt<128>(ctx, tmL, tmX, a, grid, smem);
+  return launch_nt<64>(ctx, tmL, tmX, a, grid, smem);
+}
+
+}  // namespace
+
+pt_status tc_supported(pt_ctx* ctx) {
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, ctx->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, ctx->device);
+  if (major != 10 || minor != 3) {
+    set_error(ctx, "tensor-core path needs an sm_103 (GB300) device; got sm_" +
+                       std::to_string(major) + std::to_string(minor));
+    return PT_ERR_UNSUPPORTED;
+  }
+  if (!encode_fn()) {
+    set_error(ctx, "cuTensorMapEncodeTiled entry point unavailable");
+    return PT_ERR_UNSUPPORTED;
+  }
+  return PT_OK;
+}
+
+pt_status tc_reduce(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int two_sided,
+                    const float* u_obs, unsigned long long* maxkey, uint32_t* cnt) {
+  return tc_launch(ctx, Lb, P, precision, 1, 0, two_sided, u_obs, maxkey, cnt, nullptr);
+}
+
+pt_status tc_write_u(pt_ctx* ctx, const void* Lb, int64_t P, int precision, float* uout) {
+  return tc_launch(ctx, Lb, P, precision, 0, 1, 0, nullptr, nullptr, nullptr, uout);
+}
+
+}  // namespace pt

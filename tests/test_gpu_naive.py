@@ -1,0 +1,188 @@
+"""GPU NaivePT (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (t-class paths, FP32 accumulation): max-null within 1e-5 relative
+(absolute floor 1e-5), argmax equal except at recorded near-ties, per-voxel
+counts equal except for entries the oracle records as near-ties with the
+observed statistic.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1703_01506_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [0, 1, 2]  # PT_PREC_FP32, PT_PREC_BF16X2, PT_PREC_BF16X3
+TIE = {0: 2e-5, 1: 1e-4, 2: 2e-5}
+
+
+def run_gpu(B, X, n1, perms, precision, two_sided=False, mask=None):
+    dev = torch.device("cuda:0")
+    Xd = torch.as_tensor(X).to(dev).contiguous()
+    md = None if mask is None else torch.as_tensor(mask.astype(np.uint8)).to(dev)
+    ctx = B.pt_prepare(Xd, n1, md)
+    pd = torch.as_tensor(perms).to(dev).contiguous()
+    mx, am, ct = B.maxnull_naive(ctx, pd, precision=precision, two_sided=two_sided)
+    out = (mx.cpu().numpy().astype(np.float64), am.cpu().numpy().astype(np.int64),
+           ct.cpu().numpy().astype(np.int64))
+    ctx.close()
+    return out
+
+
+def check(ref, got, precision, name=""):
+    mx, am, ct = got
+    tol = 1e-5
+    err = np.abs(mx - ref.maxnull) / np.maximum(np.abs(ref.maxnull), 1.0)
+    assert np.all(err <= tol), (name, float(err.max()), int(np.argmax(err)))
+    gap = ref.maxnull - ref.second
+    near_tie = gap <= 2e-5 * np.maximum(np.abs(ref.maxnull), 1.0)
+    bad = (am != ref.argmax) & ~near_tie
+    assert not bad.any(), (name, np.flatnonzero(bad)[:10], am[bad][:5], ref.argmax[bad][:5])
+    dc = np.abs(ct - ref.counts.astype(np.int64))
+    badc = dc > ref.near.astype(np.int64)
+    assert not badc.any(), (name, np.flatnonzero(badc)[:10], dc[badc][:10])
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("two_sided", [False, True])
+def test_parity_gauss_n20_v2000(cuda_lib, precision, two_sided):
+    n, n1, v, P = 20, 10, 2000, 1000
+    X = synth.gaussian_mean_shift(n, v, seed=1)
+    perms = synth.perms_pcg32(n, P, seed=1)
+    ref = oracle.naive(X, n1, perms, two_sided=two_sided, tie_tol=TIE[precision])
+    got = run_gpu(cuda_lib, X, n1, perms, precision, two_sided)
+    check(ref, got, precision, "cfg0")
+
+
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("n,n1,v,P", [(37, 15, 1007, 300), (100, 50, 3000, 1000),
+                                      (3, 1, 129, 5), (64, 63, 513, 129), (200, 100, 700, 260)])
+def test_parity_ragged_shapes(cuda_lib, precision, n, n1, v, P):
+    X = synth.two_group_gaussian(n1, n - n1, v, frac=0.02, effect=1.0, seed=n + v)
+    perms = synth.perms_pcg32(n, P, seed=7)
+    ref = oracle.naive(X, n1, perms, tie_tol=TIE[precision])
+    got = run_gpu(cuda_lib, X, n1, perms, precision)
+    check(ref, got, precision, (n, n1, v, P))
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_parity_large_n(cuda_lib, precision):
+    n, n1, v, P = 400, 200, 600, 200
+    X = synth.gaussian_mean_shift(n, v, seed=4)
+    perms = synth.perms_pcg32(n, P, seed=3)
+    ref = oracle.naive(X, n1, perms, tie_tol=TIE[precision])
+    got = run_gpu(cuda_lib, X, n1, perms, precision)
+    check(ref, got, precision, "n400")
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_masked_brain_with_degenerate_voxels(cuda_lib, precision):
+    n, n1, P = 24, 12, 400
+    X, mask = synth.brain_field(n, n1, grid=(20, 24, 20), center=(10, 12, 10),
+                                semi_axes=(8, 10, 8), fwhm=4.0, effect=0.5, effect_radius=3.0,
+                                seed=2, device="cpu")
+    X = X.numpy().copy()
+    mask = mask.numpy().astype(bool)
+    idx = np.flatnonzero(mask)
+    X[:, idx[5]] = 0.5   # constant inside the mask -> excluded
+    X[:, idx[77]] = 0.0
+    perms = synth.perms_pcg32(n, P, seed=5)
+    ref = oracle.naive(X[:, mask], n1, perms, tie_tol=TIE[precision])
+    mx, am, ct = run_gpu(cuda_lib, X, n1, perms, precision, mask=mask)
+    check(ref, (mx, am, ct), precision, "brain")
+    assert ct[5] == 0 and ct[77] == 0
+
+
+def test_identity_relabelling_counts_itself(cuda_lib):
+    """An exact tie with the observed statistic (same group-1 set, any order) counts."""
+    n, n1, v = 30, 15, 500
+    X = synth.gaussian_mean_shift(n, v, seed=8)
+    base = np.arange(n, dtype=np.int32)
+    rows = np.stack([base, np.concatenate([base[:n1][::-1], base[n1:][::-1]])]).astype(np.int32)
+    for prec in PRECS:
+        _, _, ct = run_gpu(cuda_lib, X, n1, rows, prec)
+        assert np.all(ct == 2), prec
+
+
+def test_t_obs_matches_oracle(cuda_lib):
+    B = cuda_lib
+    n, n1, v = 33, 11, 777
+    X = synth.gaussian_mean_shift(n, v, seed=9)
+    ref = oracle.naive(X, n1, synth.identity_perm(n))
+    ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1)
+    t = torch.empty(v, dtype=torch.float32, device="cuda")
+    B.pt_t_obs(ctx, t)
+    B.pt_sync(ctx)
+    np.testing.assert_allclose(t.cpu().numpy(), ref.t_obs, rtol=2e-7, atol=1e-7)
+    assert B.pt_num_voxels(ctx) == v and B.pt_num_valid_voxels(ctx) == v
+    ctx.close()
+
+
+def test_invalid_relabelling_reported_and_context_survives(cuda_lib):
+    B = cuda_lib
+    n, n1, v, P = 16, 8, 300, 50
+    X = synth.gaussian_mean_shift(n, v, seed=10)
+    perms = synth.perms_pcg32(n, P, seed=1)
+    bad = perms.copy()
+    bad[17, 3] = bad[17, 4]
+    ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1)
+    for prec in PRECS:
+        with pytest.raises(B.PtError) as e:
+            B.maxnull_naive(ctx, torch.as_tensor(bad).cuda(), precision=prec)
+        assert e.value.status == B.PT_ERR_INVALID
+        mx, _, _ = B.maxnull_naive(ctx, torch.as_tensor(perms).cuda(), precision=prec)
+        ref = oracle.naive(X, n1, perms)
+        assert np.allclose(mx.cpu().numpy(), ref.maxnull, rtol=1e-5)
+    ctx.close()
+
+
+def test_nan_input_rejected(cuda_lib):
+    B = cuda_lib
+    X = synth.gaussian_mean_shift(10, 50, seed=1)
+    X[3, 7] = np.nan
+    with pytest.raises(B.PtError) as e:
+        B.pt_prepare(torch.as_tensor(X).cuda(), 5)
+    assert e.value.status == B.PT_ERR_INVALID
+
+
+def test_deterministic_repeat(cuda_lib):
+    n, n1, v, P = 50, 25, 5000, 700
+    X = synth.gaussian_mean_shift(n, v, seed=12)
+    perms = synth.perms_pcg32(n, P, seed=12)
+    for prec in PRECS:
+        a = run_gpu(cuda_lib, X, n1, perms, prec)
+        b = run_gpu(cuda_lib, X, n1, perms, prec)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_full_brain_n100_sampled(cuda_lib):
+    """The benchmark workload (n=100, ~232k voxels, 10k relabellings, split-BF16x3)
+    in the launch configuration bench.py times: sampled rows against the oracle's
+    full-row maxima, sampled voxels against the oracle's counts over all rows."""
+    B = cuda_lib
+    w = synth.workload("brain_n100_v232k", device="cuda")
+    X, mask, n1, perms = w["X"], w["mask"], w["n1"], w["perms"]
+    ctx = B.pt_prepare(X, n1, mask)
+    v = B.pt_num_voxels(ctx)
+    pd = torch.as_tensor(perms).cuda()
+    mx, am, ct = B.maxnull_naive(ctx, pd, precision=B.PT_PREC_BF16X3)
+    mx = mx.cpu().numpy().astype(np.float64)
+    am = am.cpu().numpy()
+    ct = ct.cpu().numpy().astype(np.int64)
+    Xm = X[:, mask.bool()].cpu().numpy()
+    assert Xm.shape[1] == v
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(perms.shape[0], 12, replace=False))
+    ref = oracle.naive(Xm, n1, perms[rows])
+    err = np.abs(mx[rows] - ref.maxnull) / np.maximum(np.abs(ref.maxnull), 1.0)
+    assert np.all(err <= 1e-5), err.max()
+    near = (ref.maxnull - ref.second) <= 2e-5 * np.abs(ref.maxnull)
+    assert np.all((am[rows] == ref.argmax) | near)
+    vox = np.sort(rng.choice(v, 48, replace=False))
+    refc = oracle.naive(Xm[:, vox], n1, perms)
+    dc = np.abs(ct[vox] - refc.counts.astype(np.int64))
+    assert np.all(dc <= refc.near.astype(np.int64)), dc
+    ctx.close()
