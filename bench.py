@@ -143,9 +143,9 @@ def _oracle_rows(Xt, n1, perms, cores):
     P = perms.shape[0]
     perms = np.ascontiguousarray(perms, dtype=np.int32)
     out = [np.empty(P), np.empty(P, np.int64), np.empty(P), np.empty(v, np.uint32), np.empty(v),
-           np.empty(v, np.uint32)]
+           np.empty(v, np.uint32), np.empty(v)]
     p = lambda a: ctypes.c_void_p(a.ctypes.data)  # noqa: E731
-    rc = lib.oracle_naive(p(Xt), n, v, int(n1), p(perms), P, 0, int(cores), 2e-5,
+    rc = lib.oracle_naive(p(Xt), n, v, int(n1), p(perms), P, 0, int(cores), 0.0,
                           *[p(a) for a in out])
     assert rc == 0
     return out

@@ -49,7 +49,7 @@ def _load():
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             lib.oracle_naive.restype = i64
             lib.oracle_naive.argtypes = [P, i32, i64, i32, P, i64, i32, i32, f64,
-                                         P, P, P, P, P, P]
+                                         P, P, P, P, P, P, P]
             lib.oracle_t_rows.restype = i64
             lib.oracle_t_rows.argtypes = [P, i32, i64, i32, P, i64, i32, P]
             lib.oracle_t_entries.restype = i64
@@ -70,20 +70,31 @@ def voxel_major(X):
 class NaiveResult:
     """Outputs of :func:`naive` (all numpy arrays)."""
 
-    def __init__(self, maxnull, argmax, second, counts, t_obs, near):
+    def __init__(self, maxnull, argmax, second, counts, t_obs, near, tau, n, n1):
         self.maxnull, self.argmax, self.second = maxnull, argmax, second
-        self.counts, self.t_obs, self.near = counts, t_obs, near
+        self.counts, self.t_obs, self.near, self.tau = counts, t_obs, near, tau
+        self.n, self.n1 = n, n1
+
+    def u_of(self, t):
+        """Monotone rescaling u = t / sqrt(k(n-2) + k t^2) (group-1 share of the
+        unit-norm centred voxel); near-ties are judged on this scale."""
+        k = 1.0 / self.n1 + 1.0 / (self.n - self.n1)
+        t = np.asarray(t, dtype=np.float64)
+        with np.errstate(invalid="ignore"):
+            u = t / np.sqrt(k * (self.n - 2) + k * t * t)
+        return np.where(np.isinf(t), np.sign(t) / np.sqrt(k), u)
 
 
-def naive(X, n1, perms, two_sided=False, nthreads=0, tie_tol=2e-5):
+def naive(X, n1, perms, two_sided=False, nthreads=0, tie_rel=0.0):
     """NaivePT (Alg. 1) over the rows of ``perms``.
 
     X: (n, v) data, subject-major (any float dtype; promoted to FP64).
     perms: (P, n) int32; group 1 = first n1 entries of each row.
     Returns a :class:`NaiveResult` with maxnull (FP64, t or |t|), argmax
     (smallest voxel on ties), second (runner-up value for near-tie checks),
-    counts (#{i: stat_ij >= stat_obs_j}), t_obs and near (entries within
-    ``tie_tol`` relative of the observed statistic).
+    counts (#{i: stat_ij >= stat_obs_j}), t_obs, tau (per-voxel tie band
+    tie_rel * l1 norm of the unit-norm centred voxel) and near (entries whose
+    u lies within tau of the observed u).
     """
     lib = _load()
     Xt = voxel_major(X)
@@ -92,10 +103,12 @@ def naive(X, n1, perms, two_sided=False, nthreads=0, tie_tol=2e-5):
     P = perms.shape[0]
     assert perms.shape[1] == n
     out = NaiveResult(np.empty(P), np.empty(P, np.int64), np.empty(P),
-                      np.empty(v, np.uint32), np.empty(v), np.empty(v, np.uint32))
+                      np.empty(v, np.uint32), np.empty(v), np.empty(v, np.uint32), np.empty(v),
+                      n, int(n1))
     rc = lib.oracle_naive(_ptr(Xt), n, v, int(n1), _ptr(perms), P, int(bool(two_sided)),
-                          int(nthreads), float(tie_tol), _ptr(out.maxnull), _ptr(out.argmax),
-                          _ptr(out.second), _ptr(out.counts), _ptr(out.t_obs), _ptr(out.near))
+                          int(nthreads), float(tie_rel), _ptr(out.maxnull), _ptr(out.argmax),
+                          _ptr(out.second), _ptr(out.counts), _ptr(out.t_obs), _ptr(out.near),
+                          _ptr(out.tau))
     if rc != 0:
         raise ValueError("oracle_naive failed (rc=%d)" % rc)
     return out

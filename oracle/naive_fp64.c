@@ -73,6 +73,30 @@ static int voxel_degenerate(const double* x, int n) {
 
 static double stat_of(double t, int two_sided) { return two_sided ? fabs(t) : t; }
 
+/* The statistic as the group-1 share of the unit-norm centred voxel:
+ * u = t / sqrt(k (n-2) + k t^2), k = 1/n1 + 1/n2. It is the exact inverse of
+ * t = sqrt(k(n-2)) u / sqrt(1 - k u^2), strictly increasing, and well
+ * conditioned for every t; near-ties are judged on this scale. */
+static double u_of(double t, int n, int n1) {
+  const double k = 1.0 / n1 + 1.0 / (n - n1);
+  if (isinf(t)) return t > 0 ? 1.0 / sqrt(k) : -1.0 / sqrt(k);
+  return t / sqrt(k * (n - 2) + k * t * t);
+}
+
+/* sum_s |x_s - mean| / sqrt(sum_s (x_s - mean)^2): the l1 norm of the
+ * unit-norm centred voxel (scale of the rounding error of a group sum). */
+static double l1_unit(const double* x, int n) {
+  double m = 0.0;
+  for (int s = 0; s < n; ++s) m += x[s];
+  m /= n;
+  double ss = 0.0, a = 0.0;
+  for (int s = 0; s < n; ++s) {
+    ss += (x[s] - m) * (x[s] - m);
+    a += fabs(x[s] - m);
+  }
+  return ss > 0.0 ? a / sqrt(ss) : 0.0;
+}
+
 /*
  * Full NaivePT over P relabellings.
  *   Xt      : v x n, voxel-major FP64 data (row j = the n subjects of voxel j)
@@ -80,15 +104,17 @@ static double stat_of(double t, int two_sided) { return two_sided ? fabs(t) : t;
  *   outputs : maxnull[P], argmax[P] (smallest voxel index on ties; -1 if no
  *             valid voxel), second[P] (largest statistic over the other
  *             voxels, -inf if none), counts[v], t_obs[v] (NAN if degenerate),
- *             near[v] = #{i : |stat_ij - stat_obs_j| <= tie_tol*max(1,|stat_obs_j|)}
+ *             tau[v] = tie_rel * (l1 norm of the unit-norm centred voxel),
+ *             near[v] = #{i : |u(stat_ij) - u(stat_obs_j)| <= tau_j}, with u()
+ *             the monotone rescaling above (near-ties with the observed value)
  *   two_sided: 0 -> statistic t, 1 -> |t|
  * Returns 0 on success, 1 + (first invalid row) if a row is not a permutation,
  * -1 on bad sizes or allocation failure.
  */
 int64_t oracle_naive(const double* Xt, int n, int64_t v, int n1, const int32_t* perms,
-                     int64_t P, int two_sided, int nthreads, double tie_tol,
+                     int64_t P, int two_sided, int nthreads, double tie_rel,
                      double* maxnull, int64_t* argmax, double* second, uint32_t* counts,
-                     double* t_obs, uint32_t* near) {
+                     double* t_obs, uint32_t* near, double* tau) {
   if (n < 3 || n1 < 1 || n1 > n - 1 || v < 0 || P < 0) return -1;
   unsigned char* degen = (unsigned char*)malloc((size_t)(v > 0 ? v : 1));
   unsigned char* g1 = (unsigned char*)malloc((size_t)n);
@@ -101,6 +127,7 @@ int64_t oracle_naive(const double* Xt, int n, int64_t v, int n1, const int32_t* 
     const double* x = Xt + (size_t)j * n;
     degen[j] = (unsigned char)voxel_degenerate(x, n);
     t_obs[j] = degen[j] ? NAN : t_two_sample(x, g1, n, n1);
+    tau[j] = tie_rel * l1_unit(x, n);
   }
   int64_t bad_row = -1;
   for (int64_t i = 0; i < P; ++i) {
@@ -144,7 +171,7 @@ int64_t oracle_naive(const double* Xt, int n, int64_t v, int n1, const int32_t* 
           const double st = stat_of(t_two_sample(Xt + (size_t)j * n, lab, n, n1), two_sided);
           const double so = stat_of(t_obs[j], two_sided);
           if (st >= so) cnt[j] += 1;
-          if (fabs(st - so) <= tie_tol * fmax(1.0, fabs(so))) nr[j] += 1;
+          if (fabs(u_of(st, n, n1) - u_of(so, n, n1)) <= tau[j]) nr[j] += 1;
           if (best_j < 0 || st > best) {
             if (best_j >= 0) second_best = fmax(second_best, best);
             best = st;

@@ -61,6 +61,8 @@ struct pt_ctx {
   pt::Buf t_obs64;      // double[v]: observed t (NaN if degenerate)
   pt::Buf Xn32;         // float[v_pad][n_pad]: unit-norm centred data (compact order)
   pt::Buf Xnb;          // bf16 pieces, 3 x [v_pad/8][n_pad/8][8][8] blocked layout
+  pt::Buf Xraw;         // float[v_pad][n_pad]: the input values (compact order), for the
+                        // exact FP64 statistic of each row's winning voxel
   pt::ObsCache obs[3];  // indexed by pt_precision
 
   // Per-call workspaces (grown on demand).

@@ -225,25 +225,62 @@ __global__ void __launch_bounds__(256, 2)
 // ---------------------------------------------------------------------------
 // Finalise: packed keys -> t (FP64 from u), masked argmax; counts -> masked order.
 // ---------------------------------------------------------------------------
+// One warp per relabelling row. The contraction only selects the winning voxel
+// (u orders voxels exactly as t does); its statistic is then recomputed here in
+// FP64 from the input values, two-pass, as Eq. (5) defines it, so the reported
+// maximum carries no FP32/BF16 error even where t = f(u) is ill-conditioned
+// (few degrees of freedom, very unequal groups).
 __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxkey, int64_t P,
-                                    const int32_t* __restrict__ valid_map, double k, double c_t,
+                                    const int32_t* __restrict__ valid_map,
+                                    const float* __restrict__ Xraw, int n, int n1, int n_pad,
+                                    const int32_t* __restrict__ perms, int two_sided,
                                     float* __restrict__ maxnull, int32_t* __restrict__ argmax) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < P;
-       i += int64_t(gridDim.x) * blockDim.x) {
+  __shared__ uint32_t g1_all[8][32];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* g1 = g1_all[wib];
+  for (int64_t i = int64_t(blockIdx.x) * 8 + wib; i < P; i += int64_t(gridDim.x) * 8) {
     const unsigned long long key = maxkey[i];
     if (key == 0ull) {
-      maxnull[i] = -INFINITY;
-      argmax[i] = -1;
+      if (lane == 0) {
+        maxnull[i] = -INFINITY;
+        argmax[i] = -1;
+      }
       continue;
     }
-    const double u = double(unpack_key_value(key));
     const uint32_t c = unpack_key_index(key);
-    const double den = 1.0 - k * u * u;
-    double t;
-    if (den > 0.0) t = c_t * u / sqrt(den);
-    else t = u > 0 ? INFINITY : (u < 0 ? -INFINITY : 0.0);
-    maxnull[i] = float(t);
-    argmax[i] = valid_map[c];
+    g1[lane] = 0u;
+    __syncwarp();
+    const int32_t* row = perms + i * n;
+    for (int q = lane; q < n1; q += 32) {
+      const int32_t e = row[q];
+      atomicOr(&g1[e >> 5], 1u << (e & 31));
+    }
+    __syncwarp();
+    const float* x = Xraw + int64_t(c) * n_pad;
+    double s1 = 0.0, s2 = 0.0;
+    for (int s = lane; s < n; s += 32) {
+      const double xs = double(x[s]);
+      if ((g1[s >> 5] >> (s & 31)) & 1u) s1 += xs;
+      else s2 += xs;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    const int n2 = n - n1;
+    const double m1 = s1 / n1, m2 = s2 / n2;
+    double ss = 0.0;
+    for (int s = lane; s < n; s += 32) {
+      const double d = double(x[s]) - (((g1[s >> 5] >> (s & 31)) & 1u) ? m1 : m2);
+      ss += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double t = (m1 - m2) / sqrt(ss / double(n - 2) * (1.0 / n1 + 1.0 / n2));
+    if (lane == 0) {
+      maxnull[i] = float(two_sided ? fabs(t) : t);
+      argmax[i] = valid_map[c];
+    }
+    __syncwarp();
   }
 }
 
@@ -371,9 +408,9 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
     s = build_labels(ctx, perms, P, 0, &P_pad);
     if (s != PT_OK) return s;
   }
-  finalize_max_kernel<<<grid_1d(P, 256), 256, 0, st>>>(ctx->maxkey.as<unsigned long long>(), P,
-                                                        ctx->valid_map.as<int32_t>(), ctx->k,
-                                                        ctx->c_t, maxnull, argmax);
+  finalize_max_kernel<<<grid_1d((P + 7) / 8, 1), 256, 0, st>>>(
+      ctx->maxkey.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(),
+      ctx->Xraw.as<float>(), ctx->n, ctx->n1, ctx->n_pad, perms, o.two_sided, maxnull, argmax);
   PT_LAUNCH_CHECK(ctx);
   if (counts && ctx->v_valid > 0) {
     scatter_counts_kernel<<<grid_1d(ctx->v_valid, 256), 256, 0, st>>>(

@@ -85,10 +85,12 @@ __device__ __forceinline__ void flush_counts(uint32_t (&r)[R], int lane, int64_t
 }
 
 // One 32-column chunk of a row: max and exceedance counts.
+// RAGGED: the block has padded relabelling rows or padded voxel columns; such
+// entries take the value -inf (never counted, never a maximum).
 template <bool RAGGED>
 __device__ __forceinline__ float chunk_reduce(const uint32_t (&r)[32], const float* su_chunk,
                                               int two_sided, int64_t gcol0, int64_t v,
-                                              uint32_t* cntp16) {
+                                              bool row_ok, uint32_t* cntp16) {
   float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
   const float4* s4 = reinterpret_cast<const float4*>(su_chunk);
 #pragma unroll
@@ -100,7 +102,7 @@ __device__ __forceinline__ float chunk_reduce(const uint32_t (&r)[32], const flo
       const int jj = g * 4 + e;
       const float u = __uint_as_float(r[jj]);
       float s = two_sided ? fabsf(u) : u;
-      if (RAGGED && gcol0 + jj >= v) s = -INFINITY;
+      if (RAGGED && (!row_ok || gcol0 + jj >= v)) s = -INFINITY;
       if (e == 0) m0 = fmaxf(m0, s);
       if (e == 1) m1 = fmaxf(m1, s);
       if (e == 2) m2 = fmaxf(m2, s);
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t b0 = pc * a.blocks_per_chunk;
       const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
       const int64_t v0 = vt * NT;
-      const bool ragged = v0 + NT > a.v;
+      const bool ragged_cols = v0 + NT > a.v;
       epi_bar();
       for (int c = etid; c < NT; c += 256) {
         float x = INFINITY;
@@ -282,6 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) continue;
         tc_fence_after();
         const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
+        const bool ragged = ragged_cols || (b + 1) * 128 > a.P;
+        const bool row_ok = row < a.P;
         float best = -INFINITY;
         int bestc = 0;
 #pragma unroll
@@ -307,8 +311,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (a.do_reduce) {
             const float cm = ragged
-                ? chunk_reduce<true>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, cntp + c * 16)
-                : chunk_reduce<false>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, cntp + c * 16);
+                ? chunk_reduce<true>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, row_ok,
+                                     cntp + c * 16)
+                : chunk_reduce<false>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, row_ok,
+                                      cntp + c * 16);
             if (cm > best) {
               best = cm;
               bestc = c;

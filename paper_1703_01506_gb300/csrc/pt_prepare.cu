@@ -173,7 +173,7 @@ __global__ void normalize_kernel(const float* __restrict__ X, int64_t n_grid, in
                                  const int32_t* __restrict__ valid_map, int64_t v_valid,
                                  int64_t v_pad, const double* __restrict__ mean,
                                  const double* __restrict__ inv_norm, float* __restrict__ Xn32,
-                                 __nv_bfloat16* __restrict__ Xnb) {
+                                 __nv_bfloat16* __restrict__ Xnb, float* __restrict__ Xraw) {
   const int64_t total = v_pad * n_pad;
   const int64_t piece = v_pad * n_pad;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
@@ -181,11 +181,14 @@ __global__ void normalize_kernel(const float* __restrict__ X, int64_t n_grid, in
     const int64_t c = e / n_pad;
     const int s = int(e - c * n_pad);
     double xd = 0.0;
+    float xr = 0.0f;
     if (c < v_valid && s < n) {
       const int32_t j = valid_map[c];
       const int64_t g = vox_grid[j];
-      xd = (double(X[int64_t(s) * n_grid + g]) - mean[j]) * inv_norm[j];
+      xr = X[int64_t(s) * n_grid + g];
+      xd = (double(xr) - mean[j]) * inv_norm[j];
     }
+    Xraw[e] = xr;
     Xn32[e] = float(xd);
     const __nv_bfloat16 hi = __double2bfloat16(xd);
     const double r1 = xd - double(__bfloat162float(hi));
@@ -325,7 +328,7 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
 
   // 4. unit-norm centred data, FP32 and BF16 pieces
   const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
-  if (!ctx->Xn32.ensure(sizeof(float) * elems) ||
+  if (!ctx->Xn32.ensure(sizeof(float) * elems) || !ctx->Xraw.ensure(sizeof(float) * elems) ||
       !ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) {
     set_error(ctx, "pt_prepare: out of device memory");
     return PT_ERR_NOMEM;
@@ -333,7 +336,7 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
   normalize_kernel<<<grid_for(int64_t(elems), 256), 256, 0, st>>>(
       X, ctx->n_grid, ctx->n, ctx->n_pad, ctx->vox_grid.as<int64_t>(),
       ctx->valid_map.as<int32_t>(), ctx->v_valid, ctx->v_pad, mean, inv_norm,
-      ctx->Xn32.as<float>(), ctx->Xnb.as<__nv_bfloat16>());
+      ctx->Xn32.as<float>(), ctx->Xnb.as<__nv_bfloat16>(), ctx->Xraw.as<float>());
   PT_LAUNCH_CHECK(ctx);
   for (auto& o : ctx->obs) o.valid = false;
   PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
