@@ -270,6 +270,15 @@ def run_ours(args):
     entries = float(P) * v
     value = ws * entries / (ms / 1000.0)
 
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": ms, "value": value,
+                              "kernel_ms": kern_ms / max(kern_n, 1), "precision": args.precision}),
+                  flush=True)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
     # ---- end to end through host buffers (pinned), copies inside the timed region ----
     Xh = X.cpu().pin_memory()
     mh = mask.cpu().pin_memory()
@@ -375,6 +384,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="device-timed steps only (no e2e, no CPU leg): for profiler runs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

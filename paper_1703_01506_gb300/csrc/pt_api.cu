@@ -300,11 +300,11 @@ void pt_destroy(pt_ctx* ctx) {
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);
   }
-  pt::Buf* bufs[] = {&ctx->status, &ctx->vox_grid, &ctx->valid_map, &ctx->t_obs64,
-                     &ctx->Xn32,   &ctx->Xnb,      &ctx->Xraw,      &ctx->labels,    &ctx->maxkey,
-                     &ctx->cnt,    &ctx->scratch};
+  pt::Buf* bufs[] = {&ctx->status,  &ctx->vox_grid, &ctx->valid_map, &ctx->t_obs64,
+                     &ctx->Xraw,    &ctx->vstat,    &ctx->u_obs,     &ctx->Xn32,
+                     &ctx->Xnb,     &ctx->labels,   &ctx->rowflag,   &ctx->blockflag,
+                     &ctx->maxkey,  &ctx->cnt,      &ctx->scratch};
   for (pt::Buf* b : bufs) b->release();
-  for (auto& o : ctx->obs) o.u_obs.release();
   delete ctx;
 }
 

@@ -33,14 +33,6 @@ struct Buf {
   T* as() const { return static_cast<T*>(p); }
 };
 
-// Per-precision cache of the observed statistic computed by the same
-// contraction path as the relabellings (so an exact tie with the observed
-// group set compares equal).
-struct ObsCache {
-  bool valid = false;
-  Buf u_obs;  // float[v_valid]
-};
-
 }  // namespace pt
 
 struct pt_ctx {
@@ -59,16 +51,19 @@ struct pt_ctx {
   pt::Buf vox_grid;     // int64[v]: grid index of masked voxel j
   pt::Buf valid_map;    // int32[v_valid]: masked index of compact voxel c
   pt::Buf t_obs64;      // double[v]: observed t (NaN if degenerate)
-  pt::Buf Xn32;         // float[v_pad][n_pad]: unit-norm centred data (compact order)
-  pt::Buf Xnb;          // bf16 pieces, 3 x [v_pad/8][n_pad/8][8][8] blocked layout
-  pt::Buf Xraw;         // float[v_pad][n_pad]: the input values (compact order), for the
-                        // exact FP64 statistic of each row's winning voxel
-  pt::ObsCache obs[3];  // indexed by pt_precision
+  pt::Buf Xraw;         // float[v][n_pad]: input values, masked order, voxel-major
+  pt::Buf vstat;        // float4[v_pad]: (mean hi, mean lo, 1/sqrt(SS) hi, lo), compact order
+  pt::Buf u_obs;        // float[v_pad]: observed group-1 share of the unit-norm voxel, compact
+  pt::Buf Xn32;         // float[v_pad][n_pad]: unit-norm centred data (built on first FP32 use)
+  pt::Buf Xnb;          // bf16 pieces 3 x [v_pad/8][n_pad/8][8][8] (built on first tensor-core use)
+  bool have_xn32 = false, have_xnb = false;
 
   // Per-call workspaces (grown on demand).
   pt::Buf labels;       // float or bf16 labels
+  pt::Buf rowflag;      // uint8[P_pad]: relabelling has the observed group-1 set
+  pt::Buf blockflag;    // uint8[P_pad/128]: 128-row block holds such a row
   pt::Buf maxkey;       // uint64[P]
-  pt::Buf cnt;          // uint32[v_valid]
+  pt::Buf cnt;          // uint32[v_valid + 1]; the last word counts observed-set rows
   pt::Buf scratch;      // misc
 
   // Profiling of the dominant kernel (events on `stream`).
@@ -87,6 +82,9 @@ void set_thread_error(const std::string& msg);
 
 // ---- prepare (pt_prepare.cu) ----
 pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask);
+// Operand layouts built from Xraw on first use (FP32 rows / BF16 pieces).
+pt_status ensure_xn32(pt_ctx* ctx);
+pt_status ensure_xnb(pt_ctx* ctx);
 
 // ---- naive path (pt_naive.cu) ----
 pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,

@@ -170,13 +170,17 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
 
 // ---- launchers implemented in pt_naive_tc.cu ----
 pt_status tc_supported(pt_ctx* ctx);
+// Fused contraction + max / count reduction over P relabellings (labels from
+// build_labels, layout 1); rowflag/blockflag from the labels kernel.
 pt_status tc_reduce(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int two_sided,
                     const float* u_obs, unsigned long long* maxkey, uint32_t* cnt);
-pt_status tc_write_u(pt_ctx* ctx, const void* Lb, int64_t P, int precision, float* uout);
+// Same contraction writing rows: write_mode 1 -> u, 2 -> t; optionally also reducing.
+pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int write_mode,
+                  float* out, int do_reduce, int two_sided, const float* u_obs,
+                  unsigned long long* maxkey, uint32_t* cnt);
 
 // ---- shared with pt_naive.cu ----
 pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout,
                        int64_t* P_pad_out);
-pt_status ensure_u_obs(pt_ctx* ctx, int precision);
 
 }  // namespace pt

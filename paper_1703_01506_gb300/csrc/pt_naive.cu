@@ -23,7 +23,8 @@ namespace pt {
 // ---------------------------------------------------------------------------
 __global__ void labels_kernel(const int32_t* __restrict__ perms, int64_t P, int64_t P_pad, int n,
                               int n1, int n_pad, int layout, void* __restrict__ Lout,
-                              uint32_t* __restrict__ status) {
+                              uint8_t* __restrict__ rowflag, uint8_t* __restrict__ blockflag,
+                              uint32_t* __restrict__ ident_count, uint32_t* __restrict__ status) {
   __shared__ uint32_t seen_all[8][32];
   __shared__ uint32_t g1_all[8][32];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -51,6 +52,21 @@ __global__ void labels_kernel(const int32_t* __restrict__ perms, int64_t P, int6
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kErrBadPerm);
   __syncwarp();
+  // Same group-1 set as the observed labelling (subjects 0..n1-1)? Such a row
+  // ties the observed statistic exactly at every voxel; it is counted exactly
+  // (once per voxel) instead of through a rounded comparison.
+  const int lo = lane * 32;
+  uint32_t want = 0u;
+  if (n1 >= lo + 32) want = 0xffffffffu;
+  else if (n1 > lo) want = (1u << (n1 - lo)) - 1u;
+  const bool ident = (i < P) && __all_sync(0xffffffffu, g1[lane] == want);
+  if (lane == 0) {
+    rowflag[i] = ident ? 1 : 0;
+    if (ident) {
+      atomicAdd(ident_count, 1u);
+      blockflag[i >> 7] = 1;
+    }
+  }
   for (int s = lane; s < n_pad; s += 32) {
     const bool in = (i < P) && s < n && ((g1[s >> 5] >> (s & 31)) & 1u);
     if (layout == 0) {
@@ -66,10 +82,6 @@ __global__ void labels_kernel(const int32_t* __restrict__ perms, int64_t P, int6
   }
 }
 
-__global__ void iota_rows_kernel(int32_t* __restrict__ out, int n) {
-  for (int s = threadIdx.x; s < n; s += blockDim.x) out[s] = s;
-}
-
 // ---------------------------------------------------------------------------
 // Plain FP32 CUDA-core contraction with the fused epilogue.
 // CTA tile 128 relabellings x 128 voxels, K step 16, 256 threads, 8x8 per thread.
@@ -81,8 +93,9 @@ constexpr int BM = 128, BN = 128, BK = 16;
 __global__ void __launch_bounds__(256, 2)
     simt_contract_kernel(const float* __restrict__ L, const float* __restrict__ Xn, int n_pad,
                          int64_t P, int64_t v, int tiles_per_cta, int mode, int two_sided,
-                         const float* __restrict__ u_obs, unsigned long long* __restrict__ maxkey,
-                         uint32_t* __restrict__ cnt, float* __restrict__ uout) {
+                         const float* __restrict__ u_obs, const uint8_t* __restrict__ rowflag,
+                         unsigned long long* __restrict__ maxkey, uint32_t* __restrict__ cnt,
+                         float* __restrict__ uout) {
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   __shared__ uint32_t scnt[BN];
@@ -206,7 +219,7 @@ __global__ void __launch_bounds__(256, 2)
       for (int a = 0; a < 8; ++a) {
         const int64_t row = p0 + ((a < 4) ? (ty * 4 + a) : (64 + ty * 4 + a - 4));
         const float s = two_sided ? fabsf(acc[a][b]) : acc[a][b];
-        c += (row < P && s >= uo[b]) ? 1u : 0u;
+        c += (row < P && s >= uo[b] && !rowflag[row]) ? 1u : 0u;
       }
       // reduce over the two ty rows of this warp, then shared atomics
       c += __shfl_xor_sync(0xffffffffu, c, 16);
@@ -256,7 +269,7 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
       atomicOr(&g1[e >> 5], 1u << (e & 31));
     }
     __syncwarp();
-    const float* x = Xraw + int64_t(c) * n_pad;
+    const float* x = Xraw + int64_t(valid_map[c]) * n_pad;  // Xraw is in masked order
     double s1 = 0.0, s2 = 0.0;
     for (int s = lane; s < n; s += 32) {
       const double xs = double(x[s]);
@@ -284,12 +297,15 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
   }
 }
 
+// counts[masked voxel] = comparisons counted by the contraction + relabellings
+// whose group-1 set equals the observed one (cnt[v_valid]).
 __global__ void scatter_counts_kernel(const uint32_t* __restrict__ cnt, int64_t v_valid,
                                       const int32_t* __restrict__ valid_map,
                                       uint32_t* __restrict__ counts) {
+  const uint32_t ties = cnt[v_valid];
   for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < v_valid;
        c += int64_t(gridDim.x) * blockDim.x)
-    counts[valid_map[c]] = cnt[c];
+    counts[valid_map[c]] = cnt[c] + ties;
 }
 
 static int grid_1d(int64_t work, int threads) {
@@ -299,23 +315,27 @@ static int grid_1d(int64_t work, int threads) {
   return int(b);
 }
 
-// Build labels for P rows into ctx->labels (layout per path).
+// Build labels for P rows into ctx->labels (layout per path), with the
+// observed-set flags; ctx->cnt must already hold v_valid + 1 zeroed words.
 pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout, int64_t* P_pad_out) {
   const int64_t P_pad = (P + 127) / 128 * 128;
   const size_t elem = layout == 0 ? sizeof(float) : sizeof(__nv_bfloat16);
-  if (!ctx->labels.ensure(elem * size_t(P_pad) * ctx->n_pad)) {
+  if (!ctx->labels.ensure(elem * size_t(P_pad) * ctx->n_pad) || !ctx->rowflag.ensure(P_pad) ||
+      !ctx->blockflag.ensure(P_pad / 128)) {
     set_error(ctx, "out of device memory (labels)");
     return PT_ERR_NOMEM;
   }
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->blockflag.p, 0, P_pad / 128, ctx->stream));
   labels_kernel<<<unsigned((P_pad + 7) / 8), 256, 0, ctx->stream>>>(
       perms, P, P_pad, ctx->n, ctx->n1, ctx->n_pad, layout, ctx->labels.p,
-      ctx->status.as<uint32_t>());
+      ctx->rowflag.as<uint8_t>(), ctx->blockflag.as<uint8_t>(),
+      ctx->cnt.as<uint32_t>() + ctx->v_valid, ctx->status.as<uint32_t>());
   PT_LAUNCH_CHECK(ctx);
   *P_pad_out = P_pad;
   return PT_OK;
 }
 
-// SIMT launch helper: grid (voxel tiles, relabelling chunks).
+// SIMT launch: grid (voxel tiles, relabelling chunks).
 static pt_status launch_simt(pt_ctx* ctx, const float* L, int64_t P, int mode, int two_sided,
                              const float* u_obs, unsigned long long* maxkey, uint32_t* cnt,
                              float* uout) {
@@ -329,83 +349,43 @@ static pt_status launch_simt(pt_ctx* ctx, const float* L, int64_t P, int mode, i
   chunks = (ptiles + per - 1) / per;
   const dim3 grid{unsigned(vt), unsigned(chunks), 1u};
   if (mode == 0) prof_begin(ctx);
-  simt_contract_kernel<<<grid, 256, 0, ctx->stream>>>(L, ctx->Xn32.as<float>(), ctx->n_pad, P,
-                                                      ctx->v_valid, per, mode, two_sided, u_obs,
-                                                      maxkey, cnt, uout);
+  simt_contract_kernel<<<grid, 256, 0, ctx->stream>>>(
+      L, ctx->Xn32.as<float>(), ctx->n_pad, P, ctx->v_valid, per, mode, two_sided, u_obs,
+      ctx->rowflag.as<uint8_t>(), maxkey, cnt, uout);
   if (mode == 0) prof_end(ctx);
   PT_LAUNCH_CHECK(ctx);
-  return PT_OK;
-}
-
-// u at the observed (identity) labelling, by the same contraction path.
-pt_status ensure_u_obs(pt_ctx* ctx, int precision) {
-  ObsCache& oc = ctx->obs[precision];
-  if (oc.valid) return PT_OK;
-  if (!oc.u_obs.ensure(sizeof(float) * ctx->v_pad)) {
-    set_error(ctx, "out of device memory (u_obs)");
-    return PT_ERR_NOMEM;
-  }
-  Buf idp;
-  if (!idp.ensure(sizeof(int32_t) * ctx->n)) {
-    set_error(ctx, "out of device memory");
-    return PT_ERR_NOMEM;
-  }
-  iota_rows_kernel<<<1, 256, 0, ctx->stream>>>(idp.as<int32_t>(), ctx->n);
-  PT_LAUNCH_CHECK(ctx);
-  int64_t P_pad = 0;
-  pt_status s;
-  if (precision == PT_PREC_FP32) {
-    s = build_labels(ctx, idp.as<int32_t>(), 1, 0, &P_pad);
-    if (s == PT_OK)
-      s = launch_simt(ctx, ctx->labels.as<float>(), 1, 1, 0, nullptr, nullptr, nullptr,
-                      oc.u_obs.as<float>());
-  } else {
-    s = build_labels(ctx, idp.as<int32_t>(), 1, 1, &P_pad);
-    if (s == PT_OK) s = tc_write_u(ctx, ctx->labels.p, 1, precision, oc.u_obs.as<float>());
-  }
-  cudaStreamSynchronize(ctx->stream);
-  idp.release();
-  if (s != PT_OK) return s;
-  oc.valid = true;
   return PT_OK;
 }
 
 pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,
                      float* maxnull, int32_t* argmax, uint32_t* counts) {
   cudaStream_t st = ctx->stream;
-  if (o.precision != PT_PREC_FP32) {
-    pt_status s = tc_supported(ctx);
-    if (s != PT_OK) return s;
-  }
-  pt_status s = ensure_u_obs(ctx, o.precision);
+  const bool tc = o.precision != PT_PREC_FP32;
+  pt_status s = tc ? tc_supported(ctx) : PT_OK;
   if (s != PT_OK) return s;
   if (!ctx->maxkey.ensure(sizeof(unsigned long long) * P) ||
-      !ctx->cnt.ensure(sizeof(uint32_t) * (ctx->v_valid > 0 ? ctx->v_valid : 1))) {
+      !ctx->cnt.ensure(sizeof(uint32_t) * (ctx->v_valid + 1))) {
     set_error(ctx, "out of device memory (workspace)");
     return PT_ERR_NOMEM;
   }
   PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->maxkey.p, 0, sizeof(unsigned long long) * P, st));
-  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(uint32_t) * (ctx->v_valid > 0 ? ctx->v_valid : 1), st));
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(uint32_t) * (ctx->v_valid + 1), st));
   if (counts) PT_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ctx->v, st));
   int64_t P_pad = 0;
+  s = build_labels(ctx, perms, P, tc ? 1 : 0, &P_pad);
+  if (s != PT_OK) return s;
   if (ctx->v_valid > 0) {
-    if (o.precision == PT_PREC_FP32) {
-      s = build_labels(ctx, perms, P, 0, &P_pad);
-      if (s != PT_OK) return s;
-      s = launch_simt(ctx, ctx->labels.as<float>(), P, 0, o.two_sided,
-                      ctx->obs[o.precision].u_obs.as<float>(), ctx->maxkey.as<unsigned long long>(),
-                      ctx->cnt.as<uint32_t>(), nullptr);
+    if (!tc) {
+      s = ensure_xn32(ctx);
+      if (s == PT_OK)
+        s = launch_simt(ctx, ctx->labels.as<float>(), P, 0, o.two_sided, ctx->u_obs.as<float>(),
+                        ctx->maxkey.as<unsigned long long>(), ctx->cnt.as<uint32_t>(), nullptr);
     } else {
-      s = build_labels(ctx, perms, P, 1, &P_pad);
-      if (s != PT_OK) return s;
-      s = tc_reduce(ctx, ctx->labels.p, P, o.precision, o.two_sided,
-                    ctx->obs[o.precision].u_obs.as<float>(), ctx->maxkey.as<unsigned long long>(),
-                    ctx->cnt.as<uint32_t>());
+      s = ensure_xnb(ctx);
+      if (s == PT_OK)
+        s = tc_reduce(ctx, ctx->labels.p, P, o.precision, o.two_sided, ctx->u_obs.as<float>(),
+                      ctx->maxkey.as<unsigned long long>(), ctx->cnt.as<uint32_t>());
     }
-    if (s != PT_OK) return s;
-  } else {
-    // still validate the relabellings
-    s = build_labels(ctx, perms, P, 0, &P_pad);
     if (s != PT_OK) return s;
   }
   finalize_max_kernel<<<grid_1d((P + 7) / 8, 1), 256, 0, st>>>(

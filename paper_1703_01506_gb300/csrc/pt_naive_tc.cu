@@ -41,6 +41,8 @@ struct TcArgs {
   int do_reduce, write_mode, two_sided;  // write_mode: 0 none, 1 u, 2 t
   float k_f, ct_f;
   const float* u_obs;
+  const uint8_t* rowflag;    // per relabelling: 1 = observed group-1 set (not compared)
+  const uint8_t* blockflag;  // per 128-row block: holds such a row
   unsigned long long* maxkey;
   uint32_t* cnt;
   float* uout;
@@ -85,12 +87,14 @@ __device__ __forceinline__ void flush_counts(uint32_t (&r)[R], int lane, int64_t
 }
 
 // One 32-column chunk of a row: max and exceedance counts.
-// RAGGED: the block has padded relabelling rows or padded voxel columns; such
-// entries take the value -inf (never counted, never a maximum).
+// RAGGED: the block has padded relabelling rows, padded voxel columns or a row
+// with the observed group-1 set. Padded entries take the value -inf (never
+// counted, never a maximum); an observed-set row still competes for the
+// maximum but is not compared (its count is added exactly elsewhere).
 template <bool RAGGED>
 __device__ __forceinline__ float chunk_reduce(const uint32_t (&r)[32], const float* su_chunk,
                                               int two_sided, int64_t gcol0, int64_t v,
-                                              bool row_ok, uint32_t* cntp16) {
+                                              bool row_ok, bool cnt_ok, uint32_t* cntp16) {
   float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
   const float4* s4 = reinterpret_cast<const float4*>(su_chunk);
 #pragma unroll
@@ -107,7 +111,7 @@ __device__ __forceinline__ float chunk_reduce(const uint32_t (&r)[32], const flo
       if (e == 1) m1 = fmaxf(m1, s);
       if (e == 2) m2 = fmaxf(m2, s);
       if (e == 3) m3 = fmaxf(m3, s);
-      if (s >= ov[e]) cntp16[jj >> 1] += (jj & 1) ? 0x10000u : 1u;
+      if (s >= ov[e] && (!RAGGED || cnt_ok)) cntp16[jj >> 1] += (jj & 1) ? 0x10000u : 1u;
     }
   }
   return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
@@ -284,8 +288,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) continue;
         tc_fence_after();
         const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
-        const bool ragged = ragged_cols || (b + 1) * 128 > a.P;
+        const bool ragged = ragged_cols || (b + 1) * 128 > a.P || (a.do_reduce && a.blockflag[b]);
         const bool row_ok = row < a.P;
+        const bool cnt_ok = row_ok && !(ragged && a.do_reduce && a.rowflag[row]);
         float best = -INFINITY;
         int bestc = 0;
 #pragma unroll
@@ -312,9 +317,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (a.do_reduce) {
             const float cm = ragged
                 ? chunk_reduce<true>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, row_ok,
-                                     cntp + c * 16)
+                                     cnt_ok, cntp + c * 16)
                 : chunk_reduce<false>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, row_ok,
-                                      cntp + c * 16);
+                                      cnt_ok, cntp + c * 16);
             if (cm > best) {
               best = cm;
               bestc = c;
@@ -465,6 +470,8 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
   a.k_f = float(ctx->k);
   a.ct_f = float(ctx->c_t);
   a.u_obs = u_obs;
+  a.rowflag = ctx->rowflag.as<uint8_t>();
+  a.blockflag = ctx->blockflag.as<uint8_t>();
   a.maxkey = maxkey;
   a.cnt = cnt;
   a.uout = uout;
@@ -508,8 +515,11 @@ pt_status tc_reduce(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int t
   return tc_launch(ctx, Lb, P, precision, 1, 0, two_sided, u_obs, maxkey, cnt, nullptr);
 }
 
-pt_status tc_write_u(pt_ctx* ctx, const void* Lb, int64_t P, int precision, float* uout) {
-  return tc_launch(ctx, Lb, P, precision, 0, 1, 0, nullptr, nullptr, nullptr, uout);
+pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int write_mode,
+                  float* out, int do_reduce, int two_sided, const float* u_obs,
+                  unsigned long long* maxkey, uint32_t* cnt) {
+  return tc_launch(ctx, Lb, P, precision, do_reduce, write_mode, two_sided, u_obs, maxkey, cnt,
+                   out);
 }
 
 }  // namespace pt

@@ -1,6 +1,7 @@
-// pt_prepare: mask compaction, FP64 per-voxel moments, observed t, and the
-// unit-norm centred data Xn in FP32 and as BF16 pieces (blocked 8x8 layout
-// consumed directly by the tensor-core kernel).
+// pt_prepare: mask compaction, FP64 per-voxel moments, observed t, a raw
+// voxel-major copy of the data; and, on first use, the unit-norm centred data
+// Xn in FP32 rows or as BF16 pieces (8x8 core-matrix layout read by the
+// tensor-core kernel).
 //
 // With x the n values of a voxel, mean and SS = sum (x - mean)^2 in FP64:
 //   Xn_s = (x_s - mean) / sqrt(SS),      so sum_s Xn_s = 0 and sum_s Xn_s^2 = 1.
@@ -112,89 +113,173 @@ __global__ void iota64_kernel(int64_t* __restrict__ out, int64_t N) {
     out[i] = i;
 }
 
-// One thread per masked voxel: FP64 two-pass moments, observed t, validity.
-__global__ void moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1,
-                               const int64_t* __restrict__ vox_grid, int64_t v,
-                               double* __restrict__ mean_out, double* __restrict__ inv_norm_out,
-                               double* __restrict__ t_obs, uint8_t* __restrict__ valid,
-                               uint32_t* __restrict__ status) {
-  const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (j >= v) return;
-  const int64_t g = vox_grid[j];
-  const float* x = X + g;
-  double sum = 0.0, sum1 = 0.0;
-  bool finite = true;
-  for (int s = 0; s < n; ++s) {
-    const float xs = x[int64_t(s) * n_grid];
-    finite = finite && isfinite(xs);
-    sum += double(xs);
-    if (s < n1) sum1 += double(xs);
+// ---------------------------------------------------------------------------
+// Moments. A CTA takes 32 consecutive mask voxels: the 32 x n values are staged
+// in shared memory (reads of X along a grid row are coalesced), written out as
+// voxel-major rows of Xraw, and reduced per voxel in FP64 in one pass of
+// shifted sums d = x - x_0 (exact in FP64 for FP32 inputs):
+//   S_g = sum_{s in G_g} d_s,  Q_g = sum_{s in G_g} d_s^2   (g = 1, 2 observed groups)
+//   mean = x_0 + (S_1 + S_2)/n,  SS = Q - S^2/n,  SS_w = sum_g (Q_g - S_g^2/n_g),
+//   t_obs = (S_1/n_1 - S_2/n_2) / sqrt(SS_w/(n-2) (1/n_1 + 1/n_2))      (Eq. (5)),
+//   u_obs = (S_1 - n_1 (S/n)) / sqrt(SS).
+// A voxel is degenerate (no t) exactly when all its values are equal.
+// ---------------------------------------------------------------------------
+constexpr int kMV = 32;  // voxels per CTA
+
+__global__ void __launch_bounds__(256)
+    moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1, int n_pad,
+                   const int64_t* __restrict__ vox_grid, int64_t v, double* __restrict__ mean_out,
+                   double* __restrict__ inv_norm_out, double* __restrict__ t_obs,
+                   float* __restrict__ u_obs_m, uint8_t* __restrict__ valid,
+                   float* __restrict__ Xraw, uint32_t* __restrict__ status) {
+  extern __shared__ float tile[];  // [n][kMV + 1]
+  __shared__ int64_t gidx[kMV];
+  constexpr int LD = kMV + 1;
+  const int64_t j0 = int64_t(blockIdx.x) * kMV;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kMV) gidx[tid] = (j0 + tid < v) ? vox_grid[j0 + tid] : -1;
+  __syncthreads();
+  for (int idx = tid; idx < n * kMV; idx += blockDim.x) {
+    const int s = idx / kMV, l = idx - s * kMV;
+    const int64_t g = gidx[l];
+    tile[s * LD + l] = g >= 0 ? X[int64_t(s) * n_grid + g] : 0.0f;
   }
-  if (!finite) {
-    atomicOr(status, kErrBadData);
-    valid[j] = 0;
-    t_obs[j] = nan("");
-    return;
+  __syncthreads();
+  for (int idx = tid; idx < kMV * n_pad; idx += blockDim.x) {
+    const int l = idx / n_pad, s = idx - l * n_pad;
+    if (j0 + l < v) Xraw[(j0 + l) * n_pad + s] = s < n ? tile[s * LD + l] : 0.0f;
   }
-  const double mean = sum / n;
-  const double sum2 = sum - sum1;  // not used for t (two-pass below keeps subject order)
-  (void)sum2;
-  double ss = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int s = 0; s < n; ++s) {
-    const double xs = double(x[int64_t(s) * n_grid]);
-    const double d = xs - mean;
-    ss += d * d;
-    if (s < n1) s1 += xs;
-    else s2 += xs;
-  }
-  const bool ok = ss > 0.0;
-  valid[j] = ok ? 1 : 0;
-  mean_out[j] = mean;
-  inv_norm_out[j] = ok ? 1.0 / sqrt(ss) : 0.0;
-  if (!ok) {
-    t_obs[j] = nan("");
-    return;
-  }
-  // Observed statistic, Eq. (5) with pooled variances, identity labelling.
   const int n2 = n - n1;
-  const double m1 = s1 / n1, m2 = s2 / n2;
-  double ssw = 0.0;
-  for (int s = 0; s < n; ++s) {
-    const double d = double(x[int64_t(s) * n_grid]) - (s < n1 ? m1 : m2);
-    ssw += d * d;
+  for (int l = warp * 4; l < warp * 4 + 4; ++l) {
+    const int64_t j = j0 + l;
+    if (j >= v) break;
+    const float x0f = tile[l];
+    const double x0 = double(x0f);
+    double S1 = 0.0, S2 = 0.0, Q1 = 0.0, Q2 = 0.0;
+    bool finite = true, differs = false;
+    for (int s = lane; s < n; s += 32) {
+      const float xf = tile[s * LD + l];
+      finite = finite && isfinite(xf);
+      differs = differs || (xf != x0f);
+      const double d = double(xf) - x0;
+      if (s < n1) {
+        S1 += d;
+        Q1 = fma(d, d, Q1);
+      } else {
+        S2 += d;
+        Q2 = fma(d, d, Q2);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+      Q1 += __shfl_xor_sync(0xffffffffu, Q1, o);
+      Q2 += __shfl_xor_sync(0xffffffffu, Q2, o);
+    }
+    finite = __all_sync(0xffffffffu, finite);
+    differs = __any_sync(0xffffffffu, differs);
+    if (lane != 0) continue;
+    if (!finite) {
+      atomicOr(status, kErrBadData);
+      valid[j] = 0;
+      t_obs[j] = nan("");
+      continue;
+    }
+    const double S = S1 + S2, Q = Q1 + Q2;
+    const double md = S / n;
+    double SS = Q - S * md;
+    double SSw = (Q1 - S1 * (S1 / n1)) + (Q2 - S2 * (S2 / n2));
+    if (differs && !(SS > 0.0)) SS = 0.0;  // cannot happen for FP32 inputs; kept explicit
+    const bool ok = differs && SS > 0.0;
+    valid[j] = ok ? 1 : 0;
+    mean_out[j] = x0 + md;
+    if (!ok) {
+      inv_norm_out[j] = 0.0;
+      t_obs[j] = nan("");
+      u_obs_m[j] = 0.0f;
+      continue;
+    }
+    if (SSw < 0.0) SSw = 0.0;
+    const double inv = 1.0 / sqrt(SS);
+    inv_norm_out[j] = inv;
+    const double k = 1.0 / n1 + 1.0 / n2;
+    t_obs[j] = (S1 / n1 - S2 / n2) / sqrt(SSw / double(n - 2) * k);
+    u_obs_m[j] = float((S1 - n1 * md) * inv);
   }
-  const double sp2 = ssw / double(n - 2);
-  t_obs[j] = (m1 - m2) / sqrt(sp2 * (1.0 / n1 + 1.0 / n2));
 }
 
-// Element (c, s) of the compact unit-norm data: FP32 copy and BF16 pieces.
-__global__ void normalize_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n_pad,
-                                 const int64_t* __restrict__ vox_grid,
+// Per compact voxel: the FP64 mean and 1/sqrt(SS) as float pairs (hi + lo),
+// and the observed u in compact order.
+__global__ void compact_stats_kernel(const int32_t* __restrict__ valid_map, int64_t v_valid,
+                                     int64_t v_pad, const double* __restrict__ mean,
+                                     const double* __restrict__ inv_norm,
+                                     const float* __restrict__ u_obs_m, float4* __restrict__ vstat,
+                                     float* __restrict__ u_obs) {
+  for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < v_pad;
+       c += int64_t(gridDim.x) * blockDim.x) {
+    float4 st = make_float4(0.f, 0.f, 0.f, 0.f);
+    float uo = INFINITY;
+    if (c < v_valid) {
+      const int32_t j = valid_map[c];
+      const double m = mean[j], iv = inv_norm[j];
+      st.x = float(m);
+      st.y = float(m - double(st.x));
+      st.z = float(iv);
+      st.w = float(iv - double(st.z));
+      uo = u_obs_m[j];
+    }
+    vstat[c] = st;
+    u_obs[c] = uo;
+  }
+}
+
+// (x - mean) / sqrt(SS) from an FP32 input and float-pair constants, with the
+// subtraction exact (two-sum) and the product carried to ~2^-40 before the
+// final rounding to FP32.
+__device__ __forceinline__ float unit_centre(float x, float4 st) {
+  const float s = x - st.x;
+  const float bb = s - x;
+  const float e = (x - (s - bb)) + (-st.x - bb);  // s + e == x - mean_hi exactly
+  const float dl = e - st.y;                      // + low part of -mean
+  const float p = s * st.z;
+  const float pe = fmaf(s, st.z, -p);             // exact product error
+  return p + (pe + fmaf(s, st.w, dl * st.z));
+}
+
+__global__ void build_xn32_kernel(const float* __restrict__ Xraw, int n, int n_pad,
+                                  const int32_t* __restrict__ valid_map, int64_t v_valid,
+                                  int64_t v_pad, const float4* __restrict__ vstat,
+                                  float* __restrict__ Xn32) {
+  const int64_t total = v_pad * n_pad;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t c = e / n_pad;
+    const int s = int(e - c * n_pad);
+    float y = 0.0f;
+    if (c < v_valid && s < n) y = unit_centre(Xraw[int64_t(valid_map[c]) * n_pad + s], vstat[c]);
+    Xn32[e] = y;
+  }
+}
+
+// BF16 pieces: hi = bf16(y), mid = bf16(y - hi), lo = bf16(y - hi - mid)
+// (each residual exact in FP32), stored as 8x8 core matrices, row-group major.
+__global__ void build_xnb_kernel(const float* __restrict__ Xraw, int n, int n_pad,
                                  const int32_t* __restrict__ valid_map, int64_t v_valid,
-                                 int64_t v_pad, const double* __restrict__ mean,
-                                 const double* __restrict__ inv_norm, float* __restrict__ Xn32,
-                                 __nv_bfloat16* __restrict__ Xnb, float* __restrict__ Xraw) {
+                                 int64_t v_pad, const float4* __restrict__ vstat,
+                                 __nv_bfloat16* __restrict__ Xnb) {
   const int64_t total = v_pad * n_pad;
   const int64_t piece = v_pad * n_pad;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
     const int64_t c = e / n_pad;
     const int s = int(e - c * n_pad);
-    double xd = 0.0;
-    float xr = 0.0f;
-    if (c < v_valid && s < n) {
-      const int32_t j = valid_map[c];
-      const int64_t g = vox_grid[j];
-      xr = X[int64_t(s) * n_grid + g];
-      xd = (double(xr) - mean[j]) * inv_norm[j];
-    }
-    Xraw[e] = xr;
-    Xn32[e] = float(xd);
-    const __nv_bfloat16 hi = __double2bfloat16(xd);
-    const double r1 = xd - double(__bfloat162float(hi));
-    const __nv_bfloat16 mid = __double2bfloat16(r1);
-    const double r2 = r1 - double(__bfloat162float(mid));
-    const __nv_bfloat16 lo = __double2bfloat16(r2);
+    float y = 0.0f;
+    if (c < v_valid && s < n) y = unit_centre(Xraw[int64_t(valid_map[c]) * n_pad + s], vstat[c]);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(y);
+    const float r1 = y - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(mid);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
     const int64_t off = ((c >> 3) * (n_pad >> 3) + (s >> 3)) * 64 + (c & 7) * 8 + (s & 7);
     Xnb[off] = hi;
     Xnb[piece + off] = mid;
@@ -212,19 +297,21 @@ __global__ void t_obs_to_float_kernel(const double* __restrict__ t64, float* __r
 int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
-  if (b > 148 * 64) b = 148 * 64;
+  if (b > 152 * 64) b = 152 * 64;
   return int(b);
 }
 
-// Positions of nonzero flags, in index order. Synchronises to read the total.
+pt_status nomem(pt_ctx* ctx, const char* what) {
+  set_error(ctx, std::string("out of device memory (") + what + ")");
+  return PT_ERR_NOMEM;
+}
+
+// Positions of nonzero flags, in index order, and (optionally, device) their count.
 template <class IdxT>
-pt_status compact(pt_ctx* ctx, const uint8_t* flags, int64_t N, IdxT* out, int64_t* total,
+pt_status compact(pt_ctx* ctx, const uint8_t* flags, int64_t N, IdxT* out, uint32_t** total_dev,
                   Buf& tmp) {
   const int64_t nb = (N + kScanChunk - 1) / kScanChunk;
-  if (!tmp.ensure(sizeof(uint32_t) * (nb + 1))) {
-    set_error(ctx, "pt_prepare: out of device memory");
-    return PT_ERR_NOMEM;
-  }
+  if (!tmp.ensure(sizeof(uint32_t) * (nb + 1))) return nomem(ctx, "scan");
   uint32_t* bc = tmp.as<uint32_t>();
   scan_count_kernel<<<unsigned(nb), kScanThreads, 0, ctx->stream>>>(flags, N, bc);
   PT_LAUNCH_CHECK(ctx);
@@ -234,11 +321,7 @@ pt_status compact(pt_ctx* ctx, const uint8_t* flags, int64_t N, IdxT* out, int64
     scan_write_kernel<IdxT><<<unsigned(nb), kScanThreads, 0, ctx->stream>>>(flags, N, bc, out);
     PT_LAUNCH_CHECK(ctx);
   }
-  uint32_t tot = 0;
-  PT_CUDA_TRY(ctx, cudaMemcpyAsync(&tot, bc + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                                   ctx->stream));
-  PT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  *total = tot;
+  *total_dev = bc + nb;
   return PT_OK;
 }
 
@@ -246,100 +329,116 @@ pt_status compact(pt_ctx* ctx, const uint8_t* flags, int64_t N, IdxT* out, int64
 
 pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
   cudaStream_t st = ctx->stream;
-  Buf tmp;
+  Buf tmp, tmp2, mom;
   struct Guard {
+    Buf* a;
     Buf* b;
-    ~Guard() { b->release(); }
-  } guard{&tmp};
-  if (!ctx->status.ensure(sizeof(uint32_t))) {
-    set_error(ctx, "pt_prepare: out of device memory");
-    return PT_ERR_NOMEM;
-  }
-  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.p, 0, sizeof(uint32_t), st));
-
-  // 1. masked voxel list (raster order)
-  if (mask) {
-    int64_t v = 0;
-    pt_status s = compact<int64_t>(ctx, mask, ctx->n_grid, nullptr, &v, tmp);
-    if (s != PT_OK) return s;
-    ctx->v = v;
-    if (!ctx->vox_grid.ensure(sizeof(int64_t) * (v > 0 ? v : 1))) {
-      set_error(ctx, "pt_prepare: out of device memory");
-      return PT_ERR_NOMEM;
+    Buf* c;
+    ~Guard() {
+      a->release();
+      b->release();
+      c->release();
     }
-    s = compact<int64_t>(ctx, mask, ctx->n_grid, ctx->vox_grid.as<int64_t>(), &v, tmp);
+  } guard{&tmp, &tmp2, &mom};
+  if (!ctx->status.ensure(2 * sizeof(uint32_t))) return nomem(ctx, "status");
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(uint32_t), st));
+
+  // 1. masked voxel list (raster order); one host sync to size the buffers
+  if (mask) {
+    uint32_t* tot = nullptr;
+    if (!ctx->vox_grid.ensure(sizeof(int64_t) * ctx->n_grid)) return nomem(ctx, "mask");
+    pt_status s = compact<int64_t>(ctx, mask, ctx->n_grid, ctx->vox_grid.as<int64_t>(), &tot, tmp);
     if (s != PT_OK) return s;
+    uint32_t v = 0;
+    PT_CUDA_TRY(ctx, cudaMemcpyAsync(&v, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    ctx->v = v;
   } else {
     ctx->v = ctx->n_grid;
-    if (!ctx->vox_grid.ensure(sizeof(int64_t) * ctx->v)) {
-      set_error(ctx, "pt_prepare: out of device memory");
-      return PT_ERR_NOMEM;
-    }
+    if (!ctx->vox_grid.ensure(sizeof(int64_t) * ctx->v)) return nomem(ctx, "mask");
     iota64_kernel<<<grid_for(ctx->v, 256), 256, 0, st>>>(ctx->vox_grid.as<int64_t>(), ctx->v);
     PT_LAUNCH_CHECK(ctx);
   }
   const int64_t v = ctx->v;
   const int64_t vv = v > 0 ? v : 1;
+  const int n_pad = ctx->n_pad;
 
-  // 2. FP64 moments, observed t, validity
-  Buf mom;
-  struct Guard2 {
-    Buf* b;
-    ~Guard2() { b->release(); }
-  } guard2{&mom};
-  if (!mom.ensure(vv * (2 * sizeof(double) + 1) + 64) || !ctx->t_obs64.ensure(sizeof(double) * vv)) {
-    set_error(ctx, "pt_prepare: out of device memory");
-    return PT_ERR_NOMEM;
-  }
+  // 2. FP64 moments, observed t and u, validity, raw voxel-major copy
+  if (!mom.ensure(vv * (2 * sizeof(double) + sizeof(float) + 1) + 64) ||
+      !ctx->t_obs64.ensure(sizeof(double) * vv) || !ctx->Xraw.ensure(sizeof(float) * vv * n_pad))
+    return nomem(ctx, "moments");
   double* mean = mom.as<double>();
   double* inv_norm = mean + vv;
-  uint8_t* valid = reinterpret_cast<uint8_t*>(inv_norm + vv);
+  float* u_obs_m = reinterpret_cast<float*>(inv_norm + vv);
+  uint8_t* valid = reinterpret_cast<uint8_t*>(u_obs_m + vv);
   if (v > 0) {
-    moments_kernel<<<unsigned((v + 127) / 128), 128, 0, st>>>(
-        X, ctx->n_grid, ctx->n, ctx->n1, ctx->vox_grid.as<int64_t>(), v, mean, inv_norm,
-        ctx->t_obs64.as<double>(), valid, ctx->status.as<uint32_t>());
+    const int smem = ctx->n * (kMV + 1) * int(sizeof(float));
+    if (smem > 48 * 1024)
+      PT_CUDA_TRY(ctx, cudaFuncSetAttribute(moments_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    moments_kernel<<<unsigned((v + kMV - 1) / kMV), 256, smem, st>>>(
+        X, ctx->n_grid, ctx->n, ctx->n1, n_pad, ctx->vox_grid.as<int64_t>(), v, mean, inv_norm,
+        ctx->t_obs64.as<double>(), u_obs_m, valid, ctx->Xraw.as<float>(),
+        ctx->status.as<uint32_t>());
     PT_LAUNCH_CHECK(ctx);
   }
-  uint32_t bits = 0;
-  PT_CUDA_TRY(ctx, cudaMemcpyAsync(&bits, ctx->status.p, sizeof(bits), cudaMemcpyDeviceToHost, st));
+
+  // 3. compact list of voxels with a defined t (sized by v; the count is read
+  //    together with the error bits at the single sync below)
+  if (!ctx->valid_map.ensure(sizeof(int32_t) * vv)) return nomem(ctx, "valid map");
+  uint32_t* vtot = nullptr;
+  if (v > 0) {
+    pt_status s = compact<int32_t>(ctx, valid, v, ctx->valid_map.as<int32_t>(), &vtot, tmp2);
+    if (s != PT_OK) return s;
+    PT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->status.as<uint32_t>() + 1, vtot, sizeof(uint32_t),
+                                     cudaMemcpyDeviceToDevice, st));
+  }
+  uint32_t hb[2] = {0, 0};
+  PT_CUDA_TRY(ctx, cudaMemcpyAsync(hb, ctx->status.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
   PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  if (bits & kErrBadData) {
+  if (hb[0] & kErrBadData) {
     set_error(ctx, "pt_prepare: X holds NaN or Inf in a mask voxel");
     return PT_ERR_INVALID;
   }
-
-  // 3. compact list of voxels with a defined t
-  int64_t vval = 0;
-  if (v > 0) {
-    pt_status s = compact<int32_t>(ctx, valid, v, nullptr, &vval, tmp);
-    if (s != PT_OK) return s;
-  }
-  ctx->v_valid = vval;
-  ctx->v_pad = (vval + 255) / 256 * 256;
+  ctx->v_valid = hb[1];
+  ctx->v_pad = (ctx->v_valid + 255) / 256 * 256;
   if (ctx->v_pad == 0) ctx->v_pad = 256;
-  if (!ctx->valid_map.ensure(sizeof(int32_t) * (vval > 0 ? vval : 1))) {
-    set_error(ctx, "pt_prepare: out of device memory");
-    return PT_ERR_NOMEM;
-  }
-  if (vval > 0) {
-    pt_status s = compact<int32_t>(ctx, valid, v, ctx->valid_map.as<int32_t>(), &vval, tmp);
-    if (s != PT_OK) return s;
-  }
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.as<uint32_t>() + 1, 0, sizeof(uint32_t), st));
 
-  // 4. unit-norm centred data, FP32 and BF16 pieces
-  const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
-  if (!ctx->Xn32.ensure(sizeof(float) * elems) || !ctx->Xraw.ensure(sizeof(float) * elems) ||
-      !ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) {
-    set_error(ctx, "pt_prepare: out of device memory");
-    return PT_ERR_NOMEM;
-  }
-  normalize_kernel<<<grid_for(int64_t(elems), 256), 256, 0, st>>>(
-      X, ctx->n_grid, ctx->n, ctx->n_pad, ctx->vox_grid.as<int64_t>(),
-      ctx->valid_map.as<int32_t>(), ctx->v_valid, ctx->v_pad, mean, inv_norm,
-      ctx->Xn32.as<float>(), ctx->Xnb.as<__nv_bfloat16>(), ctx->Xraw.as<float>());
+  // 4. per compact voxel constants for the operand builders
+  if (!ctx->vstat.ensure(sizeof(float4) * ctx->v_pad) ||
+      !ctx->u_obs.ensure(sizeof(float) * ctx->v_pad))
+    return nomem(ctx, "voxel constants");
+  compact_stats_kernel<<<grid_for(ctx->v_pad, 256), 256, 0, st>>>(
+      ctx->valid_map.as<int32_t>(), ctx->v_valid, ctx->v_pad, mean, inv_norm, u_obs_m,
+      ctx->vstat.as<float4>(), ctx->u_obs.as<float>());
   PT_LAUNCH_CHECK(ctx);
-  for (auto& o : ctx->obs) o.valid = false;
-  PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  ctx->have_xn32 = ctx->have_xnb = false;
+  PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // mom is released on return
+  return PT_OK;
+}
+
+pt_status ensure_xn32(pt_ctx* ctx) {
+  if (ctx->have_xn32) return PT_OK;
+  const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
+  if (!ctx->Xn32.ensure(sizeof(float) * elems)) return nomem(ctx, "Xn32");
+  build_xn32_kernel<<<grid_for(int64_t(elems), 256), 256, 0, ctx->stream>>>(
+      ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,
+      ctx->v_pad, ctx->vstat.as<float4>(), ctx->Xn32.as<float>());
+  PT_LAUNCH_CHECK(ctx);
+  ctx->have_xn32 = true;
+  return PT_OK;
+}
+
+pt_status ensure_xnb(pt_ctx* ctx) {
+  if (ctx->have_xnb) return PT_OK;
+  const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
+  if (!ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) return nomem(ctx, "Xnb");
+  build_xnb_kernel<<<grid_for(int64_t(elems), 256), 256, 0, ctx->stream>>>(
+      ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,
+      ctx->v_pad, ctx->vstat.as<float4>(), ctx->Xnb.as<__nv_bfloat16>());
+  PT_LAUNCH_CHECK(ctx);
+  ctx->have_xnb = true;
   return PT_OK;
 }
 
