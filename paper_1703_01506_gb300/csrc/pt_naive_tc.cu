@@ -7,9 +7,10 @@
 //               then the label matrix L streamed one k-step (128 x 16) per stage.
 //   warp 1      MMA issuer: per k-step, one tcgen05.mma per data piece into a
 //               128 x NT FP32 accumulator in TMEM (two accumulators, ping-pong).
-//   warps 2..9  epilogue: tcgen05.ld rows of the accumulator (lane = relabelling,
+//   warps 2..17 epilogue (16 warps, 4 per TMEM lane quadrant, each owning NT/4
+//               columns): tcgen05.ld rows of the accumulator (lane = relabelling,
 //               column = voxel), row max -> packed (u, voxel) atomics, per-voxel
-//               exceedance counts in packed 16-bit registers, optional row writes.
+//               exceedance counts in packed 8-bit registers, optional row writes.
 //
 // Labels are exact in BF16; the data enter as hi + mid (+ lo) BF16 pieces of
 // the FP64 unit-norm value, so the FP32 accumulator carries ~16 or ~24 bits.
@@ -28,17 +29,17 @@
 namespace pt {
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 64 + 32 * kEpiWarps;  // 576
 constexpr int kStageBytes = 4096;  // 128 relabellings x 16 subjects x BF16
 constexpr int kSmemLimit = 232448;
-constexpr int kMaxBlocksPerItem = 2047;  // keeps packed 16-bit lane sums below 2^16
+constexpr int kMaxBlocksPerItem = 255;  // per-thread 8-bit exceedance counters
 
 struct TcArgs {
   int n_pad, pieces, stages, ksteps;
   int64_t P, v, v_pad;
   int64_t n_chunks, blocks_per_chunk, nblocks, n_items;
-  int do_reduce, write_mode, two_sided;  // write_mode: 0 none, 1 u, 2 t
+  int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
   float k_f, ct_f;
   const float* u_obs;
   const uint8_t* rowflag;    // per relabelling: 1 = observed group-1 set (not compared)
@@ -49,11 +50,16 @@ struct TcArgs {
   uint32_t* status;
 };
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
+}
 
+// Sum packed 16-bit column counters over the 32 lanes (each lane holds R
+// registers = 2R columns of its relabelling row) and add them to cnt.
+// Register k of a lane covers local columns 2k and 2k+1.
 template <int R>
-__device__ __forceinline__ void flush_counts(uint32_t (&r)[R], int lane, int64_t col0, int64_t v,
-                                             uint32_t* cnt) {
+__device__ __forceinline__ void flush_counts16(uint32_t (&r)[R], int lane, int64_t col0, int64_t v,
+                                               uint32_t* cnt) {
   int base = 0;
 #pragma unroll
   for (int rnd = 0; rnd < 5; ++rnd) {
@@ -86,50 +92,77 @@ __device__ __forceinline__ void flush_counts(uint32_t (&r)[R], int lane, int64_t
   }
 }
 
-// One 32-column chunk of a row: max and exceedance counts.
+// 8-bit counters (register g = local columns 4g..4g+3) -> 16-bit pairs -> flush.
+template <int CW>
+__device__ __forceinline__ void flush_counts8(const uint32_t (&c8)[CW / 4], int lane, int64_t col0,
+                                              int64_t v, uint32_t* cnt) {
+  uint32_t c16[CW / 2];
+#pragma unroll
+  for (int g = 0; g < CW / 4; ++g) {
+    c16[2 * g] = (c8[g] & 0xffu) | ((c8[g] & 0xff00u) << 8);
+    c16[2 * g + 1] = ((c8[g] >> 16) & 0xffu) | ((c8[g] >> 8) & 0xff0000u);
+  }
+  flush_counts16<CW / 2>(c16, lane, col0, v, cnt);
+}
+
+template <int CW>
+__device__ __forceinline__ void tc_ld_cols(uint32_t taddr, uint32_t (&r)[CW]) {
+  if constexpr (CW == 16) {
+    tc_ld_32x32b_x16(taddr, r);
+  } else {
+#pragma unroll
+    for (int h = 0; h < CW / 32; ++h)
+      tc_ld_32x32b_x32(taddr + 32 * h, *reinterpret_cast<uint32_t(*)[32]>(&r[32 * h]));
+  }
+}
+
+// Max and exceedance counts over the CW columns of one relabelling row.
 // RAGGED: the block has padded relabelling rows, padded voxel columns or a row
 // with the observed group-1 set. Padded entries take the value -inf (never
 // counted, never a maximum); an observed-set row still competes for the
 // maximum but is not compared (its count is added exactly elsewhere).
-template <bool RAGGED>
-__device__ __forceinline__ float chunk_reduce(const uint32_t (&r)[32], const float* su_chunk,
-                                              int two_sided, int64_t gcol0, int64_t v,
-                                              bool row_ok, bool cnt_ok, uint32_t* cntp16) {
+template <int CW, bool TWO, bool RAGGED>
+__device__ __forceinline__ float cols_reduce(const uint32_t (&r)[CW], const float* su_cols,
+                                             int64_t gcol0, int64_t v, bool row_ok, bool cnt_ok,
+                                             uint32_t (&c8)[CW / 4]) {
   float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
-  const float4* s4 = reinterpret_cast<const float4*>(su_chunk);
+  const float4* s4 = reinterpret_cast<const float4*>(su_cols);
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
+  for (int g = 0; g < CW / 4; ++g) {
     const float4 o = s4[g];
     const float ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int jj = g * 4 + e;
-      const float u = __uint_as_float(r[jj]);
-      float s = two_sided ? fabsf(u) : u;
+      float s = __uint_as_float(r[jj]);
+      if (TWO) s = fabsf(s);
       if (RAGGED && (!row_ok || gcol0 + jj >= v)) s = -INFINITY;
       if (e == 0) m0 = fmaxf(m0, s);
       if (e == 1) m1 = fmaxf(m1, s);
       if (e == 2) m2 = fmaxf(m2, s);
       if (e == 3) m3 = fmaxf(m3, s);
-      if (s >= ov[e] && (!RAGGED || cnt_ok)) cntp16[jj >> 1] += (jj & 1) ? 0x10000u : 1u;
+      if (s >= ov[e] && (!RAGGED || cnt_ok)) c8[g] += 1u << (8 * e);
     }
   }
   return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
 }
 
-template <int NT>
+template <int NT, bool TWO, int PIECES>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_contract_kernel(const __grid_constant__ CUtensorMap tmL,
                        const __grid_constant__ CUtensorMap tmX, const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int CH = NT / 64;  // 32-column chunks per epilogue thread (NT/2 columns)
+  constexpr int CW = NT / 4;                 // accumulator columns per epilogue thread
+  constexpr int CHK = CW < 32 ? CW : 32;     // columns per TMEM load
+  constexpr int NCH = CW / CHK;              // loads per block
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = a.stages;
   const uint32_t xtile_bytes = uint32_t(NT) * a.n_pad * 2;
   uint8_t* xs = smem;
-  uint8_t* ls = smem + a.pieces * xtile_bytes;
+  uint8_t* ls = smem + PIECES * xtile_bytes;
   float* su = reinterpret_cast<float*>(ls + S * kStageBytes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(su + NT);
+  uint8_t* sbf = reinterpret_cast<uint8_t*>(su + NT);  // block flags of the current item
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sbf + kMaxBlocksPerItem + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7 + 2 * S);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const uint32_t bar0 = smem_addr(bars);
@@ -166,27 +199,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       int w = 0;
       bool ok = true;
       int x_armed = -1;  // parity of the last armed phase of xfull (-1: none)
+      uint32_t ps = 0, pph = 0;  // ring stage and its phase parity
       for (int64_t item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, ++w) {
         const int64_t vt = item / a.n_chunks, pc = item % a.n_chunks;
         const int64_t b0 = pc * a.blocks_per_chunk;
         const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
         if (!mbar_wait(BAR(1), (w & 1) ^ 1, a.status, abort_flag)) break;
-        mbar_arrive_expect_tx(BAR(0), uint32_t(a.pieces) * xtile_bytes);
+        mbar_arrive_expect_tx(BAR(0), uint32_t(PIECES) * xtile_bytes);
         x_armed = w & 1;
-        for (int q = 0; q < a.pieces; ++q) {
+        for (int q = 0; q < PIECES; ++q) {
           const int64_t row0 = (int64_t(q) * a.v_pad * a.n_pad + vt * NT * a.n_pad) / 256;
           tma_load_2d(smem_addr(xs + q * xtile_bytes), &tmX, 0, int32_t(row0), BAR(0));
         }
-        for (int64_t b = b0; b < b1 && ok; ++b) {
+        const int64_t nb = b1 - b0, rot = (int64_t(blockIdx.x) * 17) % nb;
+        for (int64_t kb = 0; kb < nb && ok; ++kb) {
+          const int64_t b = b0 + (kb + rot) % nb;
           for (int ks = 0; ks < a.ksteps; ++ks, ++it) {
-            const uint32_t s = it % uint32_t(S), ph = (it / uint32_t(S)) & 1u;
-            if (!mbar_wait(LEMPTY(s), ph ^ 1u, a.status, abort_flag)) {
+            if (!mbar_wait(LEMPTY(ps), pph ^ 1u, a.status, abort_flag)) {
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(LFULL(s), kStageBytes);
+            mbar_arrive_expect_tx(LFULL(ps), kStageBytes);
             const int64_t row = b * (a.n_pad / 2) + ks * 8;
-            tma_load_2d(smem_addr(ls + s * kStageBytes), &tmL, 0, int32_t(row), LFULL(s));
+            tma_load_2d(smem_addr(ls + ps * kStageBytes), &tmL, 0, int32_t(row), LFULL(ps));
+            if (++ps == uint32_t(S)) {
+              ps = 0;
+              pph ^= 1u;
+            }
           }
         }
       }
@@ -197,17 +236,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_wait(LFULL(last % uint32_t(S)), (last / uint32_t(S)) & 1u, a.status, abort_flag,
                   kWaitLimitNs, false);
       }
-      if (x_armed >= 0) mbar_wait(BAR(0), uint32_t(x_armed), a.status, abort_flag, kWaitLimitNs, false);
+      if (x_armed >= 0)
+        mbar_wait(BAR(0), uint32_t(x_armed), a.status, abort_flag, kWaitLimitNs, false);
     }
   } else if (warp == 1) {
     // ------------------------------ MMA issuer ------------------------------
     if (lane == 0) {
-      uint32_t it = 0, j = 0;
+      uint32_t j = 0, ms = 0, mph = 0;  // block counter; ring stage and phase
       int w = 0;
       const uint32_t idesc = idesc_bf16_f32(128, NT);
-      const uint32_t lbo_a = 16 * 128, sbo_a = 128;                     // L stage: k-group major
-      const uint32_t lbo_b = 128, sbo_b = uint32_t(a.n_pad / 8) * 128;  // Xn tile: row-group major
-      const uint32_t xbase = smem_addr(xs), lbase = smem_addr(ls);
+      // L stage: k-group major (k-groups 2 KB apart, 8-row groups adjacent);
+      // Xn tile: row-group major (k-groups adjacent, 8-row groups n_pad/8 x 128 B apart).
+      const uint64_t adesc0 = smem_desc(smem_addr(ls), 16 * 128, 128);
+      uint64_t bdesc0[PIECES];
+#pragma unroll
+      for (int q = 0; q < PIECES; ++q)
+        bdesc0[q] = smem_desc(smem_addr(xs) + q * xtile_bytes, 128, uint32_t(a.n_pad / 8) * 128);
       bool ok = true;
       for (int64_t item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, ++w) {
         const int64_t pc = item % a.n_chunks;
@@ -223,20 +267,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + abuf * NT;
-          for (int ks = 0; ks < a.ksteps; ++ks, ++it) {
-            const uint32_t s = it % uint32_t(S), ph = (it / uint32_t(S)) & 1u;
-            if (!mbar_wait(LFULL(s), ph, a.status, abort_flag)) {
+          for (int ks = 0; ks < a.ksteps; ++ks) {
+            if (!mbar_wait(LFULL(ms), mph, a.status, abort_flag)) {
               ok = false;
               break;
             }
-            tc_fence_after();
-            const uint64_t adesc = smem_desc(lbase + s * kStageBytes, lbo_a, sbo_a);
-            for (int q = 0; q < a.pieces; ++q) {
-              const uint64_t bdesc =
-                  smem_desc(xbase + q * xtile_bytes + uint32_t(ks) * 256u, lbo_b, sbo_b);
-              tc_mma_f16(d, adesc, bdesc, idesc, (ks | q) != 0 ? 1u : 0u);
+            // descriptor start addresses advance in 16-byte units
+            const uint64_t adesc = adesc0 + uint64_t(ms * (kStageBytes >> 4));
+#pragma unroll
+            for (int q = 0; q < PIECES; ++q)
+              tc_mma_f16(d, adesc, bdesc0[q] + uint64_t(ks * 16), idesc, (ks | q) != 0 ? 1u : 0u);
+            tc_commit(LEMPTY(ms));
+            if (++ms == uint32_t(S)) {
+              ms = 0;
+              mph ^= 1u;
             }
-            tc_commit(LEMPTY(s));
           }
           if (!ok) break;
           tc_commit(BAR(2 + abuf));
@@ -250,12 +295,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------ epilogue ------------------------------
-    // The 256 epilogue threads always walk the same items and blocks (so the
+    // The epilogue threads always walk the same items and blocks (so the
     // named barrier stays matched); after a failed wait they only skip work.
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int half = ew >> 2;
-    const int colbase = half * (NT / 2);
+    const int colbase = (ew >> 2) * CW;
     const int etid = threadIdx.x - 64;
     uint32_t j = 0;
     bool ok = true;
@@ -264,62 +308,83 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t b0 = pc * a.blocks_per_chunk;
       const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
       const int64_t v0 = vt * NT;
+      const int64_t gcol0 = v0 + colbase;
       const bool ragged_cols = v0 + NT > a.v;
       epi_bar();
-      for (int c = etid; c < NT; c += 256) {
+      for (int c = etid; c < NT; c += 32 * kEpiWarps) {
         float x = INFINITY;
         if (a.do_reduce && v0 + c < a.v) {
           x = a.u_obs[v0 + c];
-          if (a.two_sided) x = fabsf(x);
+          if (TWO) x = fabsf(x);
         }
         su[c] = x;
       }
+      for (int64_t c = etid; c < b1 - b0; c += 32 * kEpiWarps)
+        sbf[c] = (a.do_reduce && a.blockflag[b0 + c]) || (b0 + c + 1) * 128 > a.P ? 1 : 0;
       epi_bar();
-      uint32_t cntp[CH * 16];
+      uint32_t c8[CW / 4];
 #pragma unroll
-      for (int q = 0; q < CH * 16; ++q) cntp[q] = 0u;
-      for (int64_t b = b0; b < b1; ++b, ++j) {
+      for (int q = 0; q < CW / 4; ++q) c8[q] = 0u;
+      const int64_t nb = b1 - b0, rot = (int64_t(blockIdx.x) * 17) % nb;
+      // current row maximum (possibly stale), fetched one block ahead
+      unsigned long long gkey_next = 0ull;
+      {
+        const int64_t rowf = (b0 + rot % nb) * 128 + quad * 32 + lane;
+        if (a.do_reduce && rowf < a.P) gkey_next = __ldcg(&a.maxkey[rowf]);
+      }
+      for (int64_t kb = 0; kb < nb; ++kb, ++j) {
+        // Blocks run in a per-CTA rotated order so that the CTAs do not all
+        // stream the same label slab from the same L2 lines at once.
+        int64_t bi = kb + rot;
+        if (bi >= nb) bi -= nb;
+        const int64_t b = b0 + bi;
         const uint32_t abuf = j & 1u, aph = (j >> 1) & 1u;
         const int64_t row = b * 128 + quad * 32 + lane;
-        unsigned long long gkey = 0ull;
-        if (a.do_reduce && row < a.P) gkey = __ldcg(&a.maxkey[row]);
+        const unsigned long long gkey = gkey_next;
+        if (kb + 1 < nb) {
+          int64_t bn = bi + 1;
+          if (bn >= nb) bn -= nb;
+          const int64_t rown = (b0 + bn) * 128 + quad * 32 + lane;
+          if (a.do_reduce && rown < a.P) gkey_next = __ldcg(&a.maxkey[rown]);
+        }
+        const bool ragged = ragged_cols || sbf[bi];
         if (ok && !mbar_wait(BAR(2 + abuf), aph, a.status, abort_flag)) ok = false;
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) continue;
         tc_fence_after();
-        const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
-        const bool ragged = ragged_cols || (b + 1) * 128 > a.P || (a.do_reduce && a.blockflag[b]);
+        const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
         const bool row_ok = row < a.P;
         const bool cnt_ok = row_ok && !(ragged && a.do_reduce && a.rowflag[row]);
         float best = -INFINITY;
         int bestc = 0;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          uint32_t r[32];
-          tc_ld_32x32b_x32(tbase + c * 32, r);
+        for (int c = 0; c < NCH; ++c) {
+          uint32_t r[CHK];
+          tc_ld_cols<CHK>(taddr + c * CHK, r);
           tc_wait_ld();
-          const int64_t gcol0 = v0 + colbase + c * 32;
-          if (a.write_mode && row < a.P) {
+          const int64_t g0 = gcol0 + c * CHK;
+          if (a.write_mode && row_ok) {
             float* dst = a.uout + row * a.v;
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              if (gcol0 + jj < a.v) {
+            for (int jj = 0; jj < CHK; ++jj) {
+              if (g0 + jj < a.v) {
                 const float u = __uint_as_float(r[jj]);
                 float val = u;
                 if (a.write_mode == 2) {
                   const float den = 1.0f - a.k_f * u * u;
                   val = den > 0.0f ? a.ct_f * u * rsqrtf(den) : (u > 0.0f ? INFINITY : -INFINITY);
                 }
-                dst[gcol0 + jj] = val;
+                dst[g0 + jj] = val;
               }
             }
           }
           if (a.do_reduce) {
-            const float cm = ragged
-                ? chunk_reduce<true>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, row_ok,
-                                     cnt_ok, cntp + c * 16)
-                : chunk_reduce<false>(r, su + colbase + c * 32, a.two_sided, gcol0, a.v, row_ok,
-                                      cnt_ok, cntp + c * 16);
+            uint32_t(&cc)[CHK / 4] = *reinterpret_cast<uint32_t(*)[CHK / 4]>(&c8[c * (CHK / 4)]);
+            const float cm =
+                ragged ? cols_reduce<CHK, TWO, true>(r, su + colbase + c * CHK, g0, a.v, row_ok,
+                                                     cnt_ok, cc)
+                       : cols_reduce<CHK, TWO, false>(r, su + colbase + c * CHK, g0, a.v, true,
+                                                      true, cc);
             if (cm > best) {
               best = cm;
               bestc = c;
@@ -328,26 +393,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (a.do_reduce) {
           // Candidate for the global row maximum: find its column and publish.
-          bool need = row < a.P && best > -INFINITY;
+          bool need = row_ok && best > -INFINITY;
           if (need && gkey != 0ull) need = best >= unpack_key_value(gkey);
 #pragma unroll
-          for (int c = 0; c < CH; ++c) {
+          for (int c = 0; c < NCH; ++c) {
             const bool mine = need && bestc == c;
             if (__any_sync(0xffffffffu, mine)) {
-              uint32_t r[32];
-              tc_ld_32x32b_x32(tbase + c * 32, r);
+              uint32_t r[CHK];
+              tc_ld_cols<CHK>(taddr + c * CHK, r);
               tc_wait_ld();
               if (mine) {
-                const int64_t gcol0 = v0 + colbase + c * 32;
+                const int64_t g0 = gcol0 + c * CHK;
                 int jj_best = -1;
 #pragma unroll
-                for (int jj = 31; jj >= 0; --jj) {
-                  const float u = __uint_as_float(r[jj]);
-                  const float s = a.two_sided ? fabsf(u) : u;
-                  if (s == best && gcol0 + jj < a.v) jj_best = jj;
+                for (int jj = CHK - 1; jj >= 0; --jj) {
+                  float sv = __uint_as_float(r[jj]);
+                  if (TWO) sv = fabsf(sv);
+                  if (sv == best && g0 + jj < a.v) jj_best = jj;
                 }
                 if (jj_best >= 0) {
-                  const unsigned long long key = pack_key(best, uint32_t(gcol0 + jj_best));
+                  const unsigned long long key = pack_key(best, uint32_t(g0 + jj_best));
                   if (key > gkey) atomicMax(&a.maxkey[row], key);
                 }
               }
@@ -358,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(BAR(4 + abuf));
       }
-      if (ok && a.do_reduce) flush_counts<CH * 16>(cntp, lane, v0 + colbase, a.v, a.cnt);
+      if (ok && a.do_reduce) flush_counts8<CW>(c8, lane, gcol0, a.v, a.cnt);
     }
   }
 #undef LFULL
@@ -402,7 +467,8 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows
 }
 
 int smem_bytes(int NT, int n_pad, int pieces, int stages) {
-  return pieces * NT * n_pad * 2 + stages * kStageBytes + NT * 4 + (7 + 2 * stages) * 8 + 16;
+  return pieces * NT * n_pad * 2 + stages * kStageBytes + NT * 4 + (kMaxBlocksPerItem + 1) +
+         (7 + 2 * stages) * 8 + 16;
 }
 
 int num_sms(int dev) {
@@ -411,10 +477,10 @@ int num_sms(int dev) {
   return n > 0 ? n : 1;
 }
 
-template <int NT>
+template <int NT, bool TWO>
 pt_status launch_nt(pt_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmX, const TcArgs& a,
                     int grid, int smem) {
-  auto kern = tc_contract_kernel<NT>;
+  auto kern = a.pieces == 2 ? tc_contract_kernel<NT, TWO, 2> : tc_contract_kernel<NT, TWO, 3>;
   PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   if (a.do_reduce) prof_begin(ctx);
   kern<<<grid, kThreads, smem, ctx->stream>>>(tmL, tmX, a);
@@ -466,7 +532,6 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
   a.n_items = n_vtiles * a.n_chunks;
   a.do_reduce = do_reduce;
   a.write_mode = write_mode;
-  a.two_sided = two_sided;
   a.k_f = float(ctx->k);
   a.ct_f = float(ctx->c_t);
   a.u_obs = u_obs;
@@ -487,9 +552,14 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
   }
   const int grid = int(a.n_items < sms ? a.n_items : sms);
   const int smem = smem_bytes(NT, n_pad, pieces, stages);
-  if (NT == 256) return launch_nt<256>(ctx, tmL, tmX, a, grid, smem);
-  if (NT == 128) return launch_nt<128>(ctx, tmL, tmX, a, grid, smem);
-  return launch_nt<64>(ctx, tmL, tmX, a, grid, smem);
+  if (two_sided) {
+    if (NT == 256) return launch_nt<256, true>(ctx, tmL, tmX, a, grid, smem);
+    if (NT == 128) return launch_nt<128, true>(ctx, tmL, tmX, a, grid, smem);
+    return launch_nt<64, true>(ctx, tmL, tmX, a, grid, smem);
+  }
+  if (NT == 256) return launch_nt<256, false>(ctx, tmL, tmX, a, grid, smem);
+  if (NT == 128) return launch_nt<128, false>(ctx, tmL, tmX, a, grid, smem);
+  return launch_nt<64, false>(ctx, tmL, tmX, a, grid, smem);
 }
 
 }  // namespace

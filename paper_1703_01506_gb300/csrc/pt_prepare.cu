@@ -124,9 +124,10 @@ __global__ void iota64_kernel(int64_t* __restrict__ out, int64_t N) {
 //   u_obs = (S_1 - n_1 (S/n)) / sqrt(SS).
 // A voxel is degenerate (no t) exactly when all its values are equal.
 // ---------------------------------------------------------------------------
-constexpr int kMV = 32;  // voxels per CTA
+constexpr int kMV = 32;  // voxels per CTA (one per lane)
+constexpr int kMW = 8;   // warps per CTA; warp w sums subjects s = w, w + 8, ...
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * kMW)
     moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1, int n_pad,
                    const int64_t* __restrict__ vox_grid, int64_t v, double* __restrict__ mean_out,
                    double* __restrict__ inv_norm_out, double* __restrict__ t_obs,
@@ -134,6 +135,8 @@ __global__ void __launch_bounds__(256)
                    float* __restrict__ Xraw, uint32_t* __restrict__ status) {
   extern __shared__ float tile[];  // [n][kMV + 1]
   __shared__ int64_t gidx[kMV];
+  __shared__ double part[kMW][4][kMV];
+  __shared__ uint32_t flags[kMW][kMV];
   constexpr int LD = kMV + 1;
   const int64_t j0 = int64_t(blockIdx.x) * kMV;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -149,18 +152,16 @@ __global__ void __launch_bounds__(256)
     const int l = idx / n_pad, s = idx - l * n_pad;
     if (j0 + l < v) Xraw[(j0 + l) * n_pad + s] = s < n ? tile[s * LD + l] : 0.0f;
   }
-  const int n2 = n - n1;
-  for (int l = warp * 4; l < warp * 4 + 4; ++l) {
-    const int64_t j = j0 + l;
-    if (j >= v) break;
-    const float x0f = tile[l];
+  // Partial shifted sums: lane = voxel, this warp's subjects. All lanes active.
+  {
+    const float x0f = tile[lane];
     const double x0 = double(x0f);
     double S1 = 0.0, S2 = 0.0, Q1 = 0.0, Q2 = 0.0;
-    bool finite = true, differs = false;
-    for (int s = lane; s < n; s += 32) {
-      const float xf = tile[s * LD + l];
-      finite = finite && isfinite(xf);
-      differs = differs || (xf != x0f);
+    uint32_t fl = 0u;  // bit 0: non-finite seen, bit 1: a value differs from x_0
+    for (int s = warp; s < n; s += kMW) {
+      const float xf = tile[s * LD + lane];
+      if (!isfinite(xf)) fl |= 1u;
+      if (xf != x0f) fl |= 2u;
       const double d = double(xf) - x0;
       if (s < n1) {
         S1 += d;
@@ -170,42 +171,52 @@ __global__ void __launch_bounds__(256)
         Q2 = fma(d, d, Q2);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      S1 += __shfl_xor_sync(0xffffffffu, S1, o);
-      S2 += __shfl_xor_sync(0xffffffffu, S2, o);
-      Q1 += __shfl_xor_sync(0xffffffffu, Q1, o);
-      Q2 += __shfl_xor_sync(0xffffffffu, Q2, o);
-    }
-    finite = __all_sync(0xffffffffu, finite);
-    differs = __any_sync(0xffffffffu, differs);
-    if (lane != 0) continue;
-    if (!finite) {
-      atomicOr(status, kErrBadData);
-      valid[j] = 0;
-      t_obs[j] = nan("");
-      continue;
-    }
-    const double S = S1 + S2, Q = Q1 + Q2;
-    const double md = S / n;
-    double SS = Q - S * md;
-    double SSw = (Q1 - S1 * (S1 / n1)) + (Q2 - S2 * (S2 / n2));
-    if (differs && !(SS > 0.0)) SS = 0.0;  // cannot happen for FP32 inputs; kept explicit
-    const bool ok = differs && SS > 0.0;
-    valid[j] = ok ? 1 : 0;
-    mean_out[j] = x0 + md;
-    if (!ok) {
-      inv_norm_out[j] = 0.0;
-      t_obs[j] = nan("");
-      u_obs_m[j] = 0.0f;
-      continue;
-    }
-    if (SSw < 0.0) SSw = 0.0;
-    const double inv = 1.0 / sqrt(SS);
-    inv_norm_out[j] = inv;
-    const double k = 1.0 / n1 + 1.0 / n2;
-    t_obs[j] = (S1 / n1 - S2 / n2) / sqrt(SSw / double(n - 2) * k);
-    u_obs_m[j] = float((S1 - n1 * md) * inv);
+    part[warp][0][lane] = S1;
+    part[warp][1][lane] = S2;
+    part[warp][2][lane] = Q1;
+    part[warp][3][lane] = Q2;
+    flags[warp][lane] = fl;
   }
+  __syncthreads();
+  if (warp != 0) return;
+  const int64_t j = j0 + lane;
+  double S1 = 0.0, S2 = 0.0, Q1 = 0.0, Q2 = 0.0;
+  uint32_t fl = 0u;
+  for (int w = 0; w < kMW; ++w) {
+    S1 += part[w][0][lane];
+    S2 += part[w][1][lane];
+    Q1 += part[w][2][lane];
+    Q2 += part[w][3][lane];
+    fl |= flags[w][lane];
+  }
+  if (j >= v) return;
+  if (fl & 1u) {
+    atomicOr(status, kErrBadData);
+    valid[j] = 0;
+    t_obs[j] = nan("");
+    return;
+  }
+  const int n2 = n - n1;
+  const double x0 = double(tile[lane]);
+  const double S = S1 + S2, Q = Q1 + Q2;
+  const double md = S / n;
+  const double SS = Q - S * md;
+  double SSw = (Q1 - S1 * (S1 / n1)) + (Q2 - S2 * (S2 / n2));
+  const bool ok = (fl & 2u) && SS > 0.0;
+  valid[j] = ok ? 1 : 0;
+  mean_out[j] = x0 + md;
+  if (!ok) {
+    inv_norm_out[j] = 0.0;
+    t_obs[j] = nan("");
+    u_obs_m[j] = 0.0f;
+    return;
+  }
+  if (SSw < 0.0) SSw = 0.0;
+  const double inv = 1.0 / sqrt(SS);
+  inv_norm_out[j] = inv;
+  const double k = 1.0 / n1 + 1.0 / n2;
+  t_obs[j] = (S1 / n1 - S2 / n2) / sqrt(SSw / double(n - 2) * k);
+  u_obs_m[j] = float((S1 - n1 * md) * inv);
 }
 
 // Per compact voxel: the FP64 mean and 1/sqrt(SS) as float pairs (hi + lo),
@@ -263,27 +274,43 @@ __global__ void build_xn32_kernel(const float* __restrict__ Xraw, int n, int n_p
 
 // BF16 pieces: hi = bf16(y), mid = bf16(y - hi), lo = bf16(y - hi - mid)
 // (each residual exact in FP32), stored as 8x8 core matrices, row-group major.
+// One thread per core-matrix row (8 consecutive subjects): 16-byte stores.
 __global__ void build_xnb_kernel(const float* __restrict__ Xraw, int n, int n_pad,
                                  const int32_t* __restrict__ valid_map, int64_t v_valid,
                                  int64_t v_pad, const float4* __restrict__ vstat,
                                  __nv_bfloat16* __restrict__ Xnb) {
-  const int64_t total = v_pad * n_pad;
+  const int kg_n = n_pad >> 3;
+  const int64_t total = v_pad * kg_n;
   const int64_t piece = v_pad * n_pad;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
        e += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t c = e / n_pad;
-    const int s = int(e - c * n_pad);
-    float y = 0.0f;
-    if (c < v_valid && s < n) y = unit_centre(Xraw[int64_t(valid_map[c]) * n_pad + s], vstat[c]);
-    const __nv_bfloat16 hi = __float2bfloat16_rn(y);
-    const float r1 = y - __bfloat162float(hi);
-    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(mid);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
-    const int64_t off = ((c >> 3) * (n_pad >> 3) + (s >> 3)) * 64 + (c & 7) * 8 + (s & 7);
-    Xnb[off] = hi;
-    Xnb[piece + off] = mid;
-    Xnb[2 * piece + off] = lo;
+    const int64_t c = e / kg_n;
+    const int kg = int(e - c * kg_n);
+    float y[8];
+    if (c < v_valid) {
+      const float4 st = vstat[c];
+      const float4* src =
+          reinterpret_cast<const float4*>(Xraw + int64_t(valid_map[c]) * n_pad + kg * 8);
+      const float4 a = src[0], b = src[1];
+      const float xv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) y[q] = (kg * 8 + q < n) ? unit_centre(xv[q], st) : 0.0f;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) y[q] = 0.0f;
+    }
+    __align__(16) __nv_bfloat16 hi[8], mid[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      hi[q] = __float2bfloat16_rn(y[q]);
+      const float r1 = y[q] - __bfloat162float(hi[q]);
+      mid[q] = __float2bfloat16_rn(r1);
+      lo[q] = __float2bfloat16_rn(r1 - __bfloat162float(mid[q]));
+    }
+    const int64_t off = ((c >> 3) * kg_n + kg) * 64 + (c & 7) * 8;
+    *reinterpret_cast<uint4*>(Xnb + off) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(Xnb + piece + off) = *reinterpret_cast<const uint4*>(mid);
+    *reinterpret_cast<uint4*>(Xnb + 2 * piece + off) = *reinterpret_cast<const uint4*>(lo);
   }
 }
 
@@ -376,7 +403,7 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
     if (smem > 48 * 1024)
       PT_CUDA_TRY(ctx, cudaFuncSetAttribute(moments_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    moments_kernel<<<unsigned((v + kMV - 1) / kMV), 256, smem, st>>>(
+    moments_kernel<<<unsigned((v + kMV - 1) / kMV), 32 * kMW, smem, st>>>(
         X, ctx->n_grid, ctx->n, ctx->n1, n_pad, ctx->vox_grid.as<int64_t>(), v, mean, inv_norm,
         ctx->t_obs64.as<double>(), u_obs_m, valid, ctx->Xraw.as<float>(),
         ctx->status.as<uint32_t>());
@@ -434,7 +461,7 @@ pt_status ensure_xnb(pt_ctx* ctx) {
   if (ctx->have_xnb) return PT_OK;
   const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
   if (!ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) return nomem(ctx, "Xnb");
-  build_xnb_kernel<<<grid_for(int64_t(elems), 256), 256, 0, ctx->stream>>>(
+  build_xnb_kernel<<<grid_for(int64_t(elems / 8), 256), 256, 0, ctx->stream>>>(
       ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,
       ctx->v_pad, ctx->vstat.as<float4>(), ctx->Xnb.as<__nv_bfloat16>());
   PT_LAUNCH_CHECK(ctx);
