@@ -144,6 +144,33 @@ pt_status pt_profile_read(pt_ctx* ctx, double* total_ms, int64_t* launches);
 /* Number of kernels this library has launched in this process (all contexts). */
 int64_t pt_kernel_launch_count(void);
 
+/*
+ * pt_maxnull_naive_noalloc -- NaivePT (FP32 CUDA-core contraction) for callers
+ * that cannot allocate device memory. The paper has no counterpart: this entry
+ * point exists for callers that must not call cudaMalloc (code running inside
+ * another runtime's memory pool or a host callback, or under a fixed memory
+ * budget after start-up). It allocates nothing: all intermediate buffers live
+ * in one static device array of 64 MiB that every GPU loading this library
+ * holds until the process exits.
+ *   X       : device, float32, n x v row-major (every column is a voxel; no mask).
+ *   n, n1   : as pt_prepare (3 <= n <= 1024, 1 <= n1 <= n-1); v >= 1.
+ *   perms, P, maxnull, argmax, counts : as pt_maxnull_naive (argmax is the
+ *             column of X; counts may be NULL).
+ *   two_sided: 0 statistic t, 1 statistic |t|.
+ *   stream  : cudaStream_t to run on (NULL = legacy default stream).
+ * Synchronous: returns after the stream has finished the work, with
+ * PT_ERR_INVALID for a bad argument, NaN/Inf in X, a row that is not a
+ * permutation, or a problem whose buffers exceed the 64 MiB array (the message
+ * gives the bytes needed). The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make it
+ * before any stream capture. Calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller.
+ */
+pt_status pt_maxnull_naive_noalloc(const float* X, int32_t n, int64_t v, int32_t n1,
+                                   const int32_t* perms, int64_t P, int32_t two_sided,
+                                   float* maxnull, int32_t* argmax, uint32_t* counts,
+                                   void* stream);
+
 /* Frees the context's device memory (returned to the library's cache). NULL ok. */
 void pt_destroy(pt_ctx* ctx);
 

@@ -63,6 +63,8 @@ def load(path=None):
         "pt_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(i64)]),
         "pt_kernel_launch_count": (i64, []),
+        "pt_maxnull_naive_noalloc": (ctypes.c_int, [_VP, i32, i64, i32, _VP, i64, i32, _VP, _VP,
+                                                    _VP, _VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -211,3 +213,15 @@ def pt_profile_read(ctx):
 
 def pt_kernel_launch_count():
     return int(load().pt_kernel_launch_count())
+
+
+def pt_maxnull_naive_noalloc(X, n1, perms, maxnull, argmax, counts=None, two_sided=False,
+                             stream=None):
+    """NaivePT without any device allocation (see include/pt.h). X: (n, v)
+    float32 CUDA tensor, every column a voxel. Synchronous."""
+    lib = load()
+    assert X.dtype == torch.float32 and X.dim() == 2 and perms.dtype == torch.int32
+    st = lib.pt_maxnull_naive_noalloc(_ptr(X), X.shape[0], X.shape[1], int(n1), _ptr(perms),
+                                      perms.shape[0], int(bool(two_sided)), _ptr(maxnull),
+                                      _ptr(argmax), _ptr(counts), _stream_ptr(stream))
+    _check(st, None)
