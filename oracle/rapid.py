@@ -1,0 +1,277 @@
+"""RapidPT oracle (test infrastructure only): plain numpy FP64 statement of
+Alg. 2 (Sec. 4.1 training, Sec. 4.2 recovery).
+
+The paper cites GROUSE/GRASTA for its subspace tracking and gives no formulas
+(its supplement is not available), so the tracking step below is one explicit
+reading, written out the same way on both sides:
+
+* weights (``Complete``): the l1 fit min_w ||U_O w - b||_1 solved by ADMM on
+  min ||s||_1 s.t. U_O w + s = b (scaled dual y, penalty rho, fixed iterations):
+      w <- (U_O^T U_O)^{-1} U_O^T (b - s - y/rho)
+      s <- soft(b - U_O w - y/rho, 1/rho)
+      y <- y + rho (U_O w + s - b)
+* update of U (training only): a rank-one geodesic step on the Grassmannian
+  towards the residual of that fit, r = b - U_O w, lifted to all voxels
+  (entries summed where a voxel was drawn twice) and projected off span(U):
+      Gamma = lift(r) - U (U_O^T r),  theta = step * arctan(||r|| / ||w||),
+      U <- U + [(cos theta - 1) U w / ||w|| + sin theta Gamma / ||Gamma||] w^T / ||w||
+  (||w|| = ||U w||, the full prediction, as in GROUSE; with every voxel
+  sampled and step 1 the new span contains the fitted column exactly), a QR
+  re-orthonormalisation (positive diagonal of R) every qr_every steps and
+  after the last one, and several passes over the training columns (Sec. 4.1:
+  "multiple passes over the training set ... until convergence"; Alg. 2
+  lists one).
+* sampling: the ceil(eta v) voxels of a column are drawn i.i.d. UNIF over the
+  voxels (Alg. 2 writes k ~ UNIF[1, v]); random numbers come from the
+  counter-based generator Philox4x32-10 (Salmon et al., SC 2011), keyed by the
+  seed, with a per-use counter, as documented in ``draws``.
+* after training: W_ex = U^T T_ex (least squares, U orthonormal), residual
+  R = T_ex - U W_ex, sigma = std of R at the entries sampled in the last pass
+  (Alg. 2, "{T_ex - U W_ex}_Omega"), and the shift mu either literally as in
+  Alg. 2 (shift_mode 0: the largest residual over all training entries) or as
+  the amount the maximum moves (shift_mode 1, Sec. 4.1 "Bias-variance
+  trade-off": the mean over training columns of max_j T_ex minus the maximum
+  of the model U W_ex + sigma z).
+* recovery (Sec. 4.2, Alg. 2): per later relabelling, exact t at its sampled
+  voxels, w = Complete(U, t, Omega) with U frozen, T_hat = U w + s with s
+  i.i.d. N(0, sigma^2), m_i = max_j T_hat + mu; training columns enter the
+  max-null exactly (m_i = max_j T_ex[i, j], no mu).
+
+Voxels are the ones with a defined t (not all values equal), in mask order.
+"""
+import math
+
+import numpy as np
+
+from . import t_rows, t_entries, voxel_major
+
+MASK32 = np.uint64(0xFFFFFFFF)
+PHILOX_M0, PHILOX_M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
+PHILOX_W0, PHILOX_W1 = np.uint64(0x9E3779B9), np.uint64(0xBB67AE85)
+
+TAG_U0, TAG_TRAIN, TAG_REC, TAG_NOISE, TAG_SHIFT = 1, 2, 3, 4, 5
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32 with 10 rounds (Random123). All arguments are arrays (or
+    scalars) of uint32 values held in uint64; returns the four output words."""
+    c0, c1, c2, c3 = (np.asarray(x, dtype=np.uint64) & MASK32 for x in (c0, c1, c2, c3))
+    k0 = np.asarray(k0, dtype=np.uint64) & MASK32
+    k1 = np.asarray(k1, dtype=np.uint64) & MASK32
+    for rnd in range(10):
+        if rnd > 0:
+            k0 = (k0 + PHILOX_W0) & MASK32
+            k1 = (k1 + PHILOX_W1) & MASK32
+        p0 = PHILOX_M0 * c0
+        p1 = PHILOX_M1 * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & MASK32
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+    return c0, c1, c2, c3
+
+
+def _key(seed):
+    seed = int(seed)
+    return np.uint64(seed & 0xFFFFFFFF), np.uint64((seed >> 32) & 0xFFFFFFFF)
+
+
+class draws:
+    """The random numbers of the method, by counter (a, b, c, tag):
+
+    normal(tag, a, b)      z = sqrt(-2 ln u1) cos(2 pi u2) from words (x0, x1),
+                           u1 = (x0 + 1) 2^-32, u2 = x1 2^-32   (counter (a, b, 0, tag))
+    index(tag, q, i, p, v) floor((x1 2^32 + x0) v / 2^64)         (counter (q, i, p, tag))
+
+    U0[j, c]            = normal(TAG_U0, j, c)
+    training sample q   = index(TAG_TRAIN, q, i, pass, v)   of column i in a pass
+    recovery sample q   = index(TAG_REC, q, i, 0, v)        of relabelling i
+    recovery noise      = normal(TAG_NOISE, j, i)           at voxel j, relabelling i
+    shift-estimate noise= normal(TAG_SHIFT, j, i)           at voxel j, training column i
+    """
+
+    def __init__(self, seed):
+        self.k0, self.k1 = _key(seed)
+
+    def words(self, a, b, c, tag):
+        return philox4x32_10(a, b, c, np.uint64(tag), self.k0, self.k1)
+
+    def normal(self, tag, a, b):
+        x0, x1, _, _ = self.words(a, b, 0, tag)
+        u1 = (x0.astype(np.float64) + 1.0) * 2.0 ** -32
+        u2 = x1.astype(np.float64) * 2.0 ** -32
+        return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+    def index(self, tag, q, i, p, v):
+        x0, x1, _, _ = self.words(q, i, p, tag)
+        v = np.uint64(v)
+        # floor((x1 * 2^32 + x0) * v / 2^64) with exact 64-bit pieces
+        return ((x1 * v + ((x0 * v) >> np.uint64(32))) >> np.uint64(32)).astype(np.int64)
+
+
+def qr_posdiag(A):
+    """Orthonormal factor of A with the diagonal of R made positive (unique)."""
+    Q, R = np.linalg.qr(A)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d[None, :]
+
+
+def soft(x, tau):
+    return np.sign(x) * np.maximum(np.abs(x) - tau, 0.0)
+
+
+def admm_l1(A, b, rho, iters):
+    """GRASTA-style ADMM for min ||s||_1 s.t. A w + s = b (scaled dual y)."""
+    G = A.T @ A
+    C = np.linalg.cholesky(G)
+    s = np.zeros_like(b)
+    y = np.zeros_like(b)
+    w = np.zeros(A.shape[1])
+    for _ in range(iters):
+        rhs = A.T @ (b - s - y / rho)
+        w = np.linalg.solve(C.T, np.linalg.solve(C, rhs))
+        Aw = A @ w
+        s = soft(b - Aw - y / rho, 1.0 / rho)
+        y = y + rho * (Aw + s - b)
+    return w, s, y
+
+
+def geodesic_step(U, idx, b, w, step):
+    """Rank-one Grassmannian update of U towards the residual of the fit."""
+    UO = U[idx]
+    Uw_O = UO @ w
+    r = b - Uw_O
+    lift = np.zeros(U.shape[0])
+    np.add.at(lift, idx, r)
+    Gam = lift - U @ (UO.T @ r)
+    nG, nw, nr = (np.linalg.norm(x) for x in (Gam, w, r))
+    if nG == 0.0 or nw == 0.0:
+        return U
+    theta = step * math.atan(nr / nw)
+    p = U @ w
+    dirv = (math.cos(theta) - 1.0) * p / nw + math.sin(theta) * Gam / nG
+    return U + np.outer(dirv, w / nw)
+
+
+class RapidOpts:
+    def __init__(self, train_passes=10, qr_every=100, admm_iters=30, admm_rho=2.0, step=1.0,
+                 shift_mode=1, seed=1, stat="t"):
+        self.train_passes, self.qr_every = train_passes, qr_every
+        self.admm_iters, self.admm_rho, self.step = admm_iters, admm_rho, step
+        self.shift_mode, self.seed, self.stat = shift_mode, seed, stat
+
+
+class RapidResult:
+    pass
+
+
+def valid_voxels(X):
+    Xd = np.asarray(X, dtype=np.float64)
+    return ~np.all(Xd == Xd[:1], axis=0)
+
+
+def rapid(X, n1, perms, rank, sample_rate, n_train, opts=None, keep=False):
+    """RapidPT (Alg. 2) over relabellings ``perms`` (P x n); first n_train rows train.
+
+    Returns a RapidResult with maxnull (P), counts (exceedances over the n_train
+    exactly computed rows, per mask voxel), sigma, mu, m (samples per column),
+    and, with keep=True, U, W_ex, T_ex and the per-step weights.
+    """
+    o = opts or RapidOpts()
+    X = np.asarray(X)
+    n = X.shape[0]
+    P = perms.shape[0]
+    assert 1 <= n_train < P and rank >= 1
+    valid = valid_voxels(X)
+    vox = np.flatnonzero(valid)
+    Xt = voxel_major(X[:, valid])
+    V = Xt.shape[0]
+    m = int(math.ceil(sample_rate * V))
+    dr = draws(o.seed)
+    ell = n_train
+    if o.stat == "t":
+        def rows(sel):
+            return t_rows(None, n1, sel, Xt=Xt)
+
+        def entries(i, idx):
+            return t_entries(Xt, n1, perms, np.full(idx.size, i), idx)
+    else:  # "meandiff": mean(group 1) - mean(group 2), a linear statistic (T has rank <= n-1)
+        def rows(sel):
+            Lm = np.full(sel.shape, -1.0 / (n - n1))
+            Lm[:, :n1] = 1.0 / n1
+            Lw = np.zeros((sel.shape[0], n))
+            np.put_along_axis(Lw, sel, Lm, axis=1)
+            return Lw @ Xt.T
+
+        def entries(i, idx):
+            return rows(perms[i:i + 1])[0, idx]
+    # Training set: ell columns of T computed in full (Sec. 4.1)
+    T_ex = rows(perms[:ell])
+    jj, cc = np.meshgrid(np.arange(V), np.arange(rank), indexing="ij")
+    U = qr_posdiag(dr.normal(TAG_U0, jj, cc))
+    steps = 0
+    w_hist = []
+    last_idx = [None] * ell
+    for p in range(o.train_passes):
+        for i in range(ell):
+            idx = dr.index(TAG_TRAIN, np.arange(m), i, p, V)
+            b = T_ex[i, idx]
+            w, _, _ = admm_l1(U[idx], b, o.admm_rho, o.admm_iters)
+            if keep:
+                w_hist.append(w.copy())
+            U = geodesic_step(U, idx, b, w, o.step)
+            steps += 1
+            if steps % o.qr_every == 0:
+                U = qr_posdiag(U)
+            last_idx[i] = idx
+    U = qr_posdiag(U)
+    W_ex = U.T @ T_ex.T                       # r x ell
+    model = (U @ W_ex).T                      # ell x V
+    R = T_ex - model
+    sampled = np.concatenate([R[i, last_idx[i]] for i in range(ell)])
+    sigma = float(np.std(sampled))
+    if o.shift_mode == 0:
+        mu = float(np.max(R))
+    else:
+        gaps = np.empty(ell)
+        for i in range(ell):
+            z = dr.normal(TAG_SHIFT, np.arange(V), i)
+            gaps[i] = np.max(T_ex[i]) - np.max(model[i] + sigma * z)
+        mu = float(np.mean(gaps))
+    maxnull = np.empty(P)
+    maxnull[:ell] = T_ex.max(axis=1)
+    for i in range(ell, P):
+        idx = dr.index(TAG_REC, np.arange(m), i, 0, V)
+        tt = entries(i, idx)
+        w, _, _ = admm_l1(U[idx], tt, o.admm_rho, o.admm_iters)
+        z = dr.normal(TAG_NOISE, np.arange(V), i)
+        maxnull[i] = np.max(U @ w + sigma * z) + mu
+    # exceedance counts over the exactly computed training rows
+    T_obs = rows(np.arange(n, dtype=np.int32)[None, :])[0]
+    counts = np.zeros(X.shape[1], dtype=np.int64)
+    counts[vox] = (T_ex >= T_obs[None, :]).sum(axis=0)
+    res = RapidResult()
+    res.maxnull, res.counts, res.sigma, res.mu, res.m = maxnull, counts, sigma, mu, m
+    res.steps = steps
+    if keep:
+        res.U, res.W_ex, res.T_ex, res.w_hist = U, W_ex, T_ex, w_hist
+    return res
+
+
+def kl_divergence(p_samples, q_samples, bins=100, eps=1e-10):
+    """KL(P || Q) between two samples' histograms on a common equal-width grid
+    over [min, max] of the union; eps added to every bin before normalising."""
+    lo = min(np.min(p_samples), np.min(q_samples))
+    hi = max(np.max(p_samples), np.max(q_samples))
+    hp, _ = np.histogram(p_samples, bins=bins, range=(lo, hi))
+    hq, _ = np.histogram(q_samples, bins=bins, range=(lo, hi))
+    pp = (hp + eps) / (hp + eps).sum()
+    qq = (hq + eps) / (hq + eps).sum()
+    return float(np.sum(pp * np.log(pp / qq)))
+
+
+def fwer_threshold(maxnull, alpha):
+    """The c-th largest max-null value, c = floor(alpha P) + 1."""
+    s = np.sort(np.asarray(maxnull))[::-1]
+    c = int(math.floor(alpha * s.size)) + 1
+    return float(s[min(c, s.size) - 1])

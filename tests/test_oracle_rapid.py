@@ -1,0 +1,149 @@
+"""Pins for the RapidPT oracle (Alg. 2, Sec. 4.1-4.2).
+
+* Philox4x32-10 against its published known-answer vectors.
+* Normal and index draws against N(0,1) / uniformity and the Box-Muller bound.
+* The l1 weight solve (ADMM) against scipy's LP solution of the same
+  least-absolute-deviations problem.
+* QR with positive diagonal; the geodesic update keeps U orthonormal and, with
+  every voxel sampled and step 1, puts the fitted column exactly in span(U)
+  (GROUSE's greedy step).
+* Exact low-rank special case: with the linear statistic mean1 - mean2, T has
+  rank <= n-1; with r = n-1 the recovered max-null equals the exhaustive one.
+Beyond these, RapidPT's t-statistic result is an approximation with no exact
+value ("parity unpinned"); it is compared statistically with NaivePT.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.stats as st
+
+import oracle
+from oracle import rapid as R
+from paper_1703_01506_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = [int(x, 16) for x in line.split()]
+        out = R.philox4x32_10(*f[:6])
+        assert [int(x) for x in out] == f[6:]
+
+
+def test_normal_draws():
+    d = R.draws(12345)
+    j, c = np.meshgrid(np.arange(2000), np.arange(100), indexing="ij")
+    z = d.normal(R.TAG_NOISE, j, c).ravel()
+    assert abs(z.mean()) < 0.01 and abs(z.var() - 1.0) < 0.01
+    assert st.kstest(z, "norm").pvalue > 1e-3
+    assert np.max(np.abs(z)) <= math.sqrt(-2.0 * math.log(2.0 ** -32))
+    z2 = R.draws(12346).normal(R.TAG_NOISE, j, c).ravel()
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 0.01  # another key, another stream
+
+
+def test_index_draws_uniform_in_range():
+    d = R.draws(7)
+    v = 37
+    k = d.index(R.TAG_REC, np.arange(200000), 5, 0, v)
+    assert k.min() >= 0 and k.max() < v
+    assert st.chisquare(np.bincount(k, minlength=v)).pvalue > 1e-3
+    big = d.index(R.TAG_TRAIN, np.arange(1000), 1, 2, 600000)
+    assert big.max() < 600000 and big.min() >= 0
+
+
+def test_admm_l1_matches_linear_program():
+    rng = np.random.default_rng(3)
+    m, r = 60, 5
+    A = rng.standard_normal((m, r))
+    b = A @ rng.standard_normal(r) + rng.laplace(size=m) * 0.3
+    b[:4] += 8.0  # outliers
+    w, s, y = R.admm_l1(A, b, rho=1.0, iters=4000)
+    # LP: min sum(t) s.t. -t <= A w - b <= t
+    c = np.concatenate([np.zeros(r), np.ones(m)])
+    A_ub = np.block([[A, -np.eye(m)], [-A, -np.eye(m)]])
+    b_ub = np.concatenate([b, -b])
+    lp = so.linprog(c, A_ub=A_ub, b_ub=b_ub, bounds=[(None, None)] * r + [(0, None)] * m)
+    obj = np.abs(A @ w - b).sum()
+    assert abs(obj - lp.fun) <= 1e-6 * lp.fun
+    assert np.max(np.abs(y)) <= 1.0 + 1e-6  # dual of an l1 fit lies in the unit box
+
+
+def test_qr_posdiag():
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((300, 12))
+    Q = R.qr_posdiag(A)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(12), atol=1e-12)
+    Rm = Q.T @ A
+    assert np.all(np.diag(Rm) > 0) and np.allclose(np.tril(Rm, -1), 0, atol=1e-12)
+
+
+def test_geodesic_step_greedy_and_orthonormal():
+    rng = np.random.default_rng(5)
+    v, r = 200, 6
+    U = R.qr_posdiag(rng.standard_normal((v, r)))
+    b = rng.standard_normal(v)
+    idx = np.arange(v)
+    w = U.T @ b  # least-squares weights with every voxel sampled
+    U1 = R.geodesic_step(U, idx, b, w, 1.0)
+    np.testing.assert_allclose(U1.T @ U1, np.eye(r), atol=1e-12)
+    resid = b - U1 @ (U1.T @ b)
+    assert np.linalg.norm(resid) <= 1e-10 * np.linalg.norm(b)
+    # half a step: still orthonormal, but b is not yet in the span
+    U2 = R.geodesic_step(U, idx, b, w, 0.5)
+    np.testing.assert_allclose(U2.T @ U2, np.eye(r), atol=1e-12)
+    assert np.linalg.norm(b - U2 @ (U2.T @ b)) > 1e-3 * np.linalg.norm(b)
+    # sampled step: orthonormal too (the direction is projected off span(U))
+    idx_s = np.random.default_rng(6).integers(0, v, 40)
+    ws, _, _ = R.admm_l1(U[idx_s], b[idx_s], 2.0, 30)
+    U3 = R.geodesic_step(U, idx_s, b[idx_s], ws, 1.0)
+    np.testing.assert_allclose(U3.T @ U3, np.eye(r), atol=1e-10)
+
+
+def test_exact_low_rank_recovery():
+    n, n1, v, P = 8, 4, 300, 120
+    X = synth.gaussian_mean_shift(n, v, seed=4)
+    perms = synth.perms_pcg32(n, P, seed=2)
+    o = R.RapidOpts(train_passes=60, stat="meandiff", admm_iters=300, qr_every=50)
+    res = R.rapid(X, n1, perms, n - 1, 0.3, 40, o)
+    Lm = np.full(perms.shape, -1.0 / (n - n1))
+    Lm[:, :n1] = 1.0 / n1
+    Lw = np.zeros((P, n))
+    np.put_along_axis(Lw, perms, Lm, axis=1)
+    exact = (Lw @ X.astype(np.float64)).max(axis=1)
+    assert res.sigma < 1e-9 and abs(res.mu) < 1e-9
+    np.testing.assert_allclose(res.maxnull, exact, atol=1e-9)
+
+
+def test_training_rows_exact_and_counts():
+    n, n1, P = 24, 12, 300
+    X, mask = synth.brain_field(n, n1, grid=(16, 18, 16), center=(8, 9, 8), semi_axes=(6, 7, 6),
+                                fwhm=4.0, seed=2)
+    X = X.numpy()[:, mask.numpy().astype(bool)]
+    perms = synth.perms_pcg32(n, P, seed=3)
+    res = R.rapid(X, n1, perms, 6, 0.05, 40, R.RapidOpts(train_passes=2))
+    ref = oracle.naive(X, n1, perms[:40])
+    np.testing.assert_allclose(res.maxnull[:40], ref.maxnull, rtol=1e-12)
+    np.testing.assert_array_equal(res.counts, ref.counts)
+
+
+def test_rapid_tracks_naive_max_null_on_smooth_field():
+    """Statistical check on a smoothed field (no exact value exists): the
+    recovered max-null is close to the exhaustive one in KL and thresholds."""
+    n, n1, P = 40, 20, 1500
+    X, mask = synth.brain_field(n, n1, grid=(30, 36, 30), center=(15, 18, 15),
+                                semi_axes=(12, 15, 12), fwhm=6.0, seed=3)
+    X = X.numpy()[:, mask.numpy().astype(bool)]
+    perms = synth.perms_pcg32(n, P, seed=1)
+    ref = oracle.naive(X, n1, perms)
+    res = R.rapid(X, n1, perms, 20, 0.02, 80, R.RapidOpts(train_passes=20))
+    kl = R.kl_divergence(ref.maxnull, res.maxnull)
+    assert kl < 0.6, kl
+    for a in (0.05, 0.01):
+        t_ref, t_rap = R.fwer_threshold(ref.maxnull, a), R.fwer_threshold(res.maxnull, a)
+        assert abs(t_rap - t_ref) / t_ref < 0.15, (a, t_ref, t_rap)
