@@ -109,6 +109,78 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
                               const pt_naive_opts* opts, float* maxnull, int32_t* argmax,
                               uint32_t* counts);
 
+/* ------------------------------------------------------------------------- */
+/* RapidPT (Alg. 2; Sec. 4.1 training, Sec. 4.2 recovery)                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t precision;    /* contraction of the training rows (pt_precision); default BF16X3 */
+  int32_t train_passes; /* passes over the training columns (Sec. 4.1 "multiple passes");
+                           default 10 */
+  int32_t qr_every;     /* re-orthonormalise U (FP64-factorised QR) every this many steps;
+                           default 100 */
+  int32_t admm_iters;   /* iterations of each l1 weight solve; default 30 */
+  float admm_rho;       /* ADMM penalty rho; default 2 */
+  float step;           /* geodesic step: theta = step * atan(||r|| / ||w||); default 1 */
+  int32_t shift_mode;   /* 0: mu = largest training residual (Alg. 2 as printed);
+                           1 (default): mu = mean shift of the maximum (Sec. 4.1) */
+  uint64_t seed;        /* key of the Philox4x32-10 draws; default 1 */
+} pt_rapid_opts;
+
+typedef struct {
+  double sigma;         /* std of the sampled training residuals */
+  double mu;            /* shift added to every recovered maximum */
+  int64_t m_per_perm;   /* sampled voxels per relabelling, ceil(sample_rate * v_valid) */
+  int64_t train_steps;  /* subspace-tracking steps taken (train_passes * n_train) */
+} pt_rapid_info;
+
+void pt_rapid_opts_default(pt_rapid_opts* o);
+
+/*
+ * pt_maxnull_rapid -- RapidPT max-null (Alg. 2).
+ *   perms, P   : device int32 P x n relabellings; rows 0..n_train-1 train.
+ *   rank       : r, 1 <= r <= min(n, 128).
+ *   sample_rate: eta in (0, 1]; m = ceil(eta * v_valid) >= r voxels are drawn
+ *                (i.i.d. uniform, Alg. 2 "UNIF[1, v]") per relabelling.
+ *   n_train    : l, 1 <= l < P.
+ *   maxnull    : device float32[P]; rows < l: exact maxima of the training rows
+ *                (statistic recomputed in FP64); rows >= l: max_j (U w + s)_j + mu.
+ *   counts     : device uint32[v] or NULL: exceedances t >= t_obs over the l
+ *                training rows (the only rows computed in full).
+ *   info       : host, or NULL: sigma, mu, m, steps.
+ * One-sided statistic only. Synchronises the stream; a bad relabelling row makes
+ * the next pt_sync return PT_ERR_INVALID.
+ */
+pt_status pt_maxnull_rapid(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t rank,
+                           double sample_rate, int32_t n_train, const pt_rapid_opts* opts,
+                           float* maxnull, uint32_t* counts, pt_rapid_info* info);
+
+/*
+ * pt_rapid_train -- the training phase alone (Sec. 4.1) on relabellings 0..n_train-1.
+ *   U_out    : device float32 v_valid x rank (row j = voxel j in the compact order of
+ *              voxels with a defined t), or NULL.
+ *   train_max: device float32[n_train] or NULL (exact training maxima).
+ *   counts   : device uint32[v] or NULL (as pt_maxnull_rapid).
+ *   w_hist   : device float32[train_steps][rank] or NULL: weights of every step.
+ *   info     : host or NULL.
+ * Synchronises the stream.
+ */
+pt_status pt_rapid_train(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int32_t rank,
+                         double sample_rate, const pt_rapid_opts* opts, float* U_out,
+                         float* train_max, uint32_t* counts, float* w_hist,
+                         pt_rapid_info* info);
+
+/*
+ * pt_rapid_recover -- the recovery phase alone (Sec. 4.2) for rows
+ * first_row..P-1 of perms with a given basis U (v_valid x rank, device), sigma and
+ * mu. Draws are keyed by the row index, so ranges can be split across calls or
+ * devices with identical results.
+ *   maxnull: device float32[P - first_row].  W_out: device float32[P - first_row][rank]
+ *   or NULL (weights). Synchronises the stream.
+ */
+pt_status pt_rapid_recover(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t first_row,
+                           const float* U, int32_t rank, double sample_rate, double sigma,
+                           double mu, const pt_rapid_opts* opts, float* maxnull, float* W_out);
+
 /*
  * pt_sync -- wait for the context's stream and report errors the kernels
  * raised since the previous pt_sync (PT_ERR_INVALID for a bad relabelling

@@ -170,25 +170,10 @@ def valid_voxels(X):
     return ~np.all(Xd == Xd[:1], axis=0)
 
 
-def rapid(X, n1, perms, rank, sample_rate, n_train, opts=None, keep=False):
-    """RapidPT (Alg. 2) over relabellings ``perms`` (P x n); first n_train rows train.
-
-    Returns a RapidResult with maxnull (P), counts (exceedances over the n_train
-    exactly computed rows, per mask voxel), sigma, mu, m (samples per column),
-    and, with keep=True, U, W_ex, T_ex and the per-step weights.
-    """
-    o = opts or RapidOpts()
-    X = np.asarray(X)
+def _stat_fns(X, n1, perms, o):
     n = X.shape[0]
-    P = perms.shape[0]
-    assert 1 <= n_train < P and rank >= 1
     valid = valid_voxels(X)
-    vox = np.flatnonzero(valid)
     Xt = voxel_major(X[:, valid])
-    V = Xt.shape[0]
-    m = int(math.ceil(sample_rate * V))
-    dr = draws(o.seed)
-    ell = n_train
     if o.stat == "t":
         def rows(sel):
             return t_rows(None, n1, sel, Xt=Xt)
@@ -205,6 +190,21 @@ def rapid(X, n1, perms, rank, sample_rate, n_train, opts=None, keep=False):
 
         def entries(i, idx):
             return rows(perms[i:i + 1])[0, idx]
+    return valid, Xt, rows, entries
+
+
+def rapid_train(X, n1, perms, rank, sample_rate, n_train, opts=None):
+    """Training phase (Sec. 4.1, Alg. 2 TRAINING): U, W_ex, sigma, mu from the
+    first n_train relabellings. Returns a RapidResult (U, W_ex, T_ex, sigma, mu,
+    m, steps, w_hist = per-step weights, counts over the training rows)."""
+    o = opts or RapidOpts()
+    X = np.asarray(X)
+    n = X.shape[0]
+    valid, Xt, rows, _ = _stat_fns(X, n1, perms, o)
+    V = Xt.shape[0]
+    m = int(math.ceil(sample_rate * V))
+    dr = draws(o.seed)
+    ell = n_train
     # Training set: ell columns of T computed in full (Sec. 4.1)
     T_ex = rows(perms[:ell])
     jj, cc = np.meshgrid(np.arange(V), np.arange(rank), indexing="ij")
@@ -217,8 +217,7 @@ def rapid(X, n1, perms, rank, sample_rate, n_train, opts=None, keep=False):
             idx = dr.index(TAG_TRAIN, np.arange(m), i, p, V)
             b = T_ex[i, idx]
             w, _, _ = admm_l1(U[idx], b, o.admm_rho, o.admm_iters)
-            if keep:
-                w_hist.append(w.copy())
+            w_hist.append(w.copy())
             U = geodesic_step(U, idx, b, w, o.step)
             steps += 1
             if steps % o.qr_every == 0:
@@ -238,23 +237,58 @@ def rapid(X, n1, perms, rank, sample_rate, n_train, opts=None, keep=False):
             z = dr.normal(TAG_SHIFT, np.arange(V), i)
             gaps[i] = np.max(T_ex[i]) - np.max(model[i] + sigma * z)
         mu = float(np.mean(gaps))
-    maxnull = np.empty(P)
-    maxnull[:ell] = T_ex.max(axis=1)
-    for i in range(ell, P):
-        idx = dr.index(TAG_REC, np.arange(m), i, 0, V)
-        tt = entries(i, idx)
-        w, _, _ = admm_l1(U[idx], tt, o.admm_rho, o.admm_iters)
-        z = dr.normal(TAG_NOISE, np.arange(V), i)
-        maxnull[i] = np.max(U @ w + sigma * z) + mu
-    # exceedance counts over the exactly computed training rows
     T_obs = rows(np.arange(n, dtype=np.int32)[None, :])[0]
     counts = np.zeros(X.shape[1], dtype=np.int64)
-    counts[vox] = (T_ex >= T_obs[None, :]).sum(axis=0)
+    counts[np.flatnonzero(valid)] = (T_ex >= T_obs[None, :]).sum(axis=0)
     res = RapidResult()
-    res.maxnull, res.counts, res.sigma, res.mu, res.m = maxnull, counts, sigma, mu, m
-    res.steps = steps
+    res.U, res.W_ex, res.T_ex, res.sigma, res.mu, res.m = U, W_ex, T_ex, sigma, mu, m
+    res.steps, res.w_hist, res.counts = steps, w_hist, counts
+    res.train_max = T_ex.max(axis=1)
+    return res
+
+
+def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=False):
+    """Recovery phase (Sec. 4.2, Alg. 2 RECOVERY) for relabellings rows_sel with
+    U frozen: exact statistic at the m sampled voxels, w = Complete(U, t, Omega),
+    m_i = max_j (U w + sigma z)_j + mu."""
+    o = opts or RapidOpts()
+    X = np.asarray(X)
+    _, Xt, _, entries = _stat_fns(X, n1, perms, o)
+    V = Xt.shape[0]
+    dr = draws(o.seed)
+    out = np.empty(len(rows_sel))
+    ws = []
+    for k, i in enumerate(rows_sel):
+        idx = dr.index(TAG_REC, np.arange(m), int(i), 0, V)
+        tt = entries(int(i), idx)
+        w, _, _ = admm_l1(U[idx], tt, o.admm_rho, o.admm_iters)
+        ws.append(w)
+        z = dr.normal(TAG_NOISE, np.arange(V), int(i))
+        out[k] = np.max(U @ w + sigma * z) + mu
+    return (out, np.array(ws)) if return_w else out
+
+
+def rapid(X, n1, perms, rank, sample_rate, n_train, opts=None, keep=False):
+    """RapidPT (Alg. 2) over relabellings ``perms`` (P x n); first n_train rows train.
+
+    Returns a RapidResult with maxnull (P; training rows exact, no shift),
+    counts (exceedances over the n_train exactly computed rows, per mask
+    voxel), sigma, mu, m (samples per column), and with keep=True the
+    training state (U, W_ex, T_ex, w_hist).
+    """
+    o = opts or RapidOpts()
+    P = perms.shape[0]
+    assert 1 <= n_train < P and rank >= 1
+    tr = rapid_train(X, n1, perms, rank, sample_rate, n_train, o)
+    maxnull = np.empty(P)
+    maxnull[:n_train] = tr.train_max
+    maxnull[n_train:] = rapid_recover(X, n1, perms, range(n_train, P), tr.U, tr.sigma, tr.mu,
+                                      tr.m, o)
+    res = RapidResult()
+    res.maxnull, res.counts, res.sigma, res.mu, res.m = maxnull, tr.counts, tr.sigma, tr.mu, tr.m
+    res.steps = tr.steps
     if keep:
-        res.U, res.W_ex, res.T_ex, res.w_hist = U, W_ex, T_ex, w_hist
+        res.U, res.W_ex, res.T_ex, res.w_hist = tr.U, tr.W_ex, tr.T_ex, tr.w_hist
     return res
 
 

@@ -31,6 +31,18 @@ class pt_naive_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("two_sided", ctypes.c_int32)]
 
 
+class pt_rapid_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("train_passes", ctypes.c_int32),
+                ("qr_every", ctypes.c_int32), ("admm_iters", ctypes.c_int32),
+                ("admm_rho", ctypes.c_float), ("step", ctypes.c_float),
+                ("shift_mode", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class pt_rapid_info(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("mu", ctypes.c_double),
+                ("m_per_perm", ctypes.c_int64), ("train_steps", ctypes.c_int64)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -65,6 +77,16 @@ def load(path=None):
         "pt_kernel_launch_count": (i64, []),
         "pt_maxnull_naive_noalloc": (ctypes.c_int, [_VP, i32, i64, i32, _VP, i64, i32, _VP, _VP,
                                                     _VP, _VP]),
+        "pt_rapid_opts_default": (None, [ctypes.POINTER(pt_rapid_opts)]),
+        "pt_maxnull_rapid": (ctypes.c_int, [_VP, _VP, i64, i32, ctypes.c_double, i32,
+                                            ctypes.POINTER(pt_rapid_opts), _VP, _VP,
+                                            ctypes.POINTER(pt_rapid_info)]),
+        "pt_rapid_train": (ctypes.c_int, [_VP, _VP, i32, i32, ctypes.c_double,
+                                          ctypes.POINTER(pt_rapid_opts), _VP, _VP, _VP, _VP,
+                                          ctypes.POINTER(pt_rapid_info)]),
+        "pt_rapid_recover": (ctypes.c_int, [_VP, _VP, i64, i64, _VP, i32, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(pt_rapid_opts), _VP, _VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -225,3 +247,40 @@ def pt_maxnull_naive_noalloc(X, n1, perms, maxnull, argmax, counts=None, two_sid
                                       perms.shape[0], int(bool(two_sided)), _ptr(maxnull),
                                       _ptr(argmax), _ptr(counts), _stream_ptr(stream))
     _check(st, None)
+
+
+def rapid_opts(**kw):
+    """pt_rapid_opts with the library defaults, overridden by keyword."""
+    o = pt_rapid_opts()
+    load().pt_rapid_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def pt_maxnull_rapid(ctx, perms, rank, sample_rate, n_train, opts, maxnull, counts=None):
+    """Returns a pt_rapid_info (sigma, mu, m_per_perm, train_steps)."""
+    info = pt_rapid_info()
+    st = load().pt_maxnull_rapid(ctx.handle, _ptr(perms), perms.shape[0], int(rank),
+                                 float(sample_rate), int(n_train), ctypes.byref(opts),
+                                 _ptr(maxnull), _ptr(counts), ctypes.byref(info))
+    _check(st, ctx.handle)
+    return info
+
+
+def pt_rapid_train(ctx, perms, n_train, rank, sample_rate, opts, U_out=None, train_max=None,
+                   counts=None, w_hist=None):
+    info = pt_rapid_info()
+    st = load().pt_rapid_train(ctx.handle, _ptr(perms), int(n_train), int(rank),
+                               float(sample_rate), ctypes.byref(opts), _ptr(U_out),
+                               _ptr(train_max), _ptr(counts), _ptr(w_hist), ctypes.byref(info))
+    _check(st, ctx.handle)
+    return info
+
+
+def pt_rapid_recover(ctx, perms, first_row, U, rank, sample_rate, sigma, mu, opts, maxnull,
+                     W_out=None):
+    st = load().pt_rapid_recover(ctx.handle, _ptr(perms), perms.shape[0], int(first_row), _ptr(U),
+                                 int(rank), float(sample_rate), float(sigma), float(mu),
+                                 ctypes.byref(opts), _ptr(maxnull), _ptr(W_out))
+    _check(st, ctx.handle)

@@ -86,6 +86,15 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask);
 pt_status ensure_xn32(pt_ctx* ctx);
 pt_status ensure_xnb(pt_ctx* ctx);
 
+// ---- RapidPT (pt_rapid.cu) ----
+pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int32_t rank,
+                           double sample_rate, const pt_rapid_opts& o, float* U_out,
+                           float* train_max, uint32_t* counts, float* w_hist,
+                           pt_rapid_info* info);
+pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t first_row,
+                             const float* U_in, int32_t rank, double sample_rate, double sigma,
+                             double mu, const pt_rapid_opts& o, float* maxnull, float* W_out);
+
 // ---- naive path (pt_naive.cu) ----
 pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,
                      float* maxnull, int32_t* argmax, uint32_t* counts);
