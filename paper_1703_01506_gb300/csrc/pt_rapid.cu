@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -94,6 +95,9 @@ __device__ __forceinline__ uint32_t draw_index(uint32_t k0, uint32_t k1, uint32_
 // columns zero), b: m. s, y: m scratch. Shared: G, Gi (RP x RP), red (32 x RP),
 // stage (32 x RP), wv, rhs (RP). Leaves w in wv.
 // ---------------------------------------------------------------------------
+// Rows of A staged per Gram step: kStageFloats / RP.
+constexpr int kStageFloats = 8192;
+
 struct FitSmem {
   float* G;
   float* Gi;
@@ -109,30 +113,53 @@ __device__ void carve_fit_smem(float* base, int RP, FitSmem& f) {
   f.Gi = f.G + RP * RP;
   f.red = f.Gi + RP * RP;
   f.stage = f.red + 32 * RP;
-  f.wv = f.stage + 32 * RP;
+  f.wv = f.stage + kStageFloats;
   f.rhs = f.wv + RP;
   f.scal = f.rhs + RP;
 }
 
-// out[c] = sum_q A[q][c] * x(q) for c < R (warps split q, lanes split c).
-template <class XF>
-__device__ void block_AtX(const float* __restrict__ A, int m, int R, int RP, XF xf, float* red,
-                          float* out) {
+// The fit's m-length vectors (b, s, y, x) live in shared memory up to this m.
+constexpr int kSmemVecM = 4096;
+
+// out[c] = sum_q A[q][c] * x[q] for c < R (warps split q, lanes split c; four
+// rows in flight per warp so the loads from L2 overlap).
+template <int RP>
+__device__ void block_AtX(const float* __restrict__ A, int m, int R, const float* __restrict__ x,
+                          float* red, float* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float acc[kMaxRank / 32];
+  constexpr int KC = kMaxRank / 32;
+  float acc[KC];
 #pragma unroll
-  for (int k = 0; k < kMaxRank / 32; ++k) acc[k] = 0.0f;
-  for (int q = w; q < m; q += 32) {
-    const float xq = xf(q);
+  for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
+  int q = w;
+  for (; q + 96 < m; q += 128) {
+    float xv[4], av[4][KC];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xv[u] = x[q + 32 * u];
+      const float* row = A + int64_t(q + 32 * u) * RP;
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        av[u][k] = c < RP ? row[c] : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < KC; ++k) acc[k] = fmaf(av[u][k], xv[u], acc[k]);
+  }
+  for (; q < m; q += 32) {
+    const float xq = x[q];
     const float* row = A + int64_t(q) * RP;
 #pragma unroll
-    for (int k = 0; k < kMaxRank / 32; ++k) {
+    for (int k = 0; k < KC; ++k) {
       const int c = lane + 32 * k;
       if (c < RP) acc[k] = fmaf(row[c], xq, acc[k]);
     }
   }
 #pragma unroll
-  for (int k = 0; k < kMaxRank / 32; ++k) {
+  for (int k = 0; k < KC; ++k) {
     const int c = lane + 32 * k;
     if (c < RP) red[w * RP + c] = acc[k];
   }
@@ -145,23 +172,36 @@ __device__ void block_AtX(const float* __restrict__ A, int m, int R, int RP, XF 
   __syncthreads();
 }
 
-__device__ __forceinline__ float row_dot(const float* __restrict__ row, const float* __restrict__ v,
-                                         int RP) {
-  float t = 0.0f;
+template <int RP>
+__device__ __forceinline__ float row_dot(const float* __restrict__ row,
+                                         const float* __restrict__ v) {
+  float4 a[RP / 4];
   const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int c4 = 0; c4 < RP / 4; ++c4) a[c4] = r4[c4];  // all loads in flight together
+  float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
   for (int c4 = 0; c4 < RP / 4; ++c4) {
-    const float4 a = r4[c4];
-    t = fmaf(a.x, v[4 * c4], t);
-    t = fmaf(a.y, v[4 * c4 + 1], t);
-    t = fmaf(a.z, v[4 * c4 + 2], t);
-    t = fmaf(a.w, v[4 * c4 + 3], t);
+    t0 = fmaf(a[c4].x, v[4 * c4], t0);
+    t1 = fmaf(a[c4].y, v[4 * c4 + 1], t1);
+    t0 = fmaf(a[c4].z, v[4 * c4 + 2], t0);
+    t1 = fmaf(a[c4].w, v[4 * c4 + 3], t1);
   }
+  return t0 + t1;
+}
+
+__device__ __forceinline__ float row_dot_rt(const float* __restrict__ row,
+                                            const float* __restrict__ v, int RP) {
+  float t = 0.0f;
+  for (int c = 0; c < RP; ++c) t = fmaf(row[c], v[c], t);
   return t;
 }
 
-__device__ void block_l1_fit(const float* __restrict__ A, const float* __restrict__ b,
-                             float* __restrict__ s, float* __restrict__ y, int m, int R, int RP,
-                             float rho, int iters, FitSmem& f) {
+// b, s, y, x: m floats each (shared memory when they fit, else global scratch).
+template <int RP>
+__device__ void block_l1_fit(const float* __restrict__ A, const float* b, float* s, float* y,
+                             float* x, int m, int R, float rho, int iters, FitSmem& f) {
+  constexpr int CH = kStageFloats / RP;  // rows staged per Gram step
   const int tid = threadIdx.x;
   const int npairs = R * (R + 1) / 2;
   // --- Gram G = A^T A (upper triangle by pairs, then mirrored) ---
@@ -179,25 +219,32 @@ __device__ void block_l1_fit(const float* __restrict__ A, const float* __restric
     pc[k] = c;
     pd[k] = c + rem;
   }
-  for (int q0 = 0; q0 < m; q0 += 32) {
-    const int rows = min(32, m - q0);
-    for (int e = tid; e < 32 * RP; e += blockDim.x) {
-      const int rr = e / RP;
-      f.stage[e] = rr < rows ? A[int64_t(q0 + rr) * RP + (e - rr * RP)] : 0.0f;
-    }
+  for (int q0 = 0; q0 < m; q0 += CH) {
+    const int rows = min(CH, m - q0);
+    const float4* src = reinterpret_cast<const float4*>(A + int64_t(q0) * RP);
+    float4* dst = reinterpret_cast<float4*>(f.stage);
+    for (int e = tid; e < CH * RP / 4; e += blockDim.x)
+      dst[e] = (e < rows * RP / 4) ? src[e] : make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       if (tid + k * blockDim.x < npairs) {
         const int c = pc[k], d = pd[k];
-        float t = acc[k];
-        for (int rr = 0; rr < 32; ++rr) t = fmaf(f.stage[rr * RP + c], f.stage[rr * RP + d], t);
-        acc[k] = t;
+        float t0 = acc[k], t1 = 0.0f;
+#pragma unroll 8
+        for (int rr = 0; rr < CH; rr += 2) {
+          t0 = fmaf(f.stage[rr * RP + c], f.stage[rr * RP + d], t0);
+          t1 = fmaf(f.stage[(rr + 1) * RP + c], f.stage[(rr + 1) * RP + d], t1);
+        }
+        acc[k] = t0 + t1;
       }
     }
     __syncthreads();
   }
-  for (int e = tid; e < RP * RP; e += blockDim.x) f.G[e] = 0.0f;
+  for (int e = tid; e < RP * RP; e += blockDim.x) {
+    f.G[e] = 0.0f;
+    f.Gi[e] = (e / RP == e % RP) ? 1.0f : 0.0f;
+  }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -207,37 +254,27 @@ __device__ void block_l1_fit(const float* __restrict__ A, const float* __restric
     }
   }
   __syncthreads();
-  // --- Cholesky G = L L^T in place (lower) ---
+  // --- G^-1 by Gauss-Jordan on [G | I] (G symmetric positive definite: no pivoting) ---
+  float* fac = f.red;  // R factors of the current column
   for (int k = 0; k < R; ++k) {
-    if (tid == 0) f.G[k * RP + k] = sqrtf(fmaxf(f.G[k * RP + k], 1e-30f));
+    const float inv = 1.0f / f.G[k * RP + k];
     __syncthreads();
-    const float dk = f.G[k * RP + k];
-    for (int i = k + 1 + tid; i < R; i += blockDim.x) f.G[i * RP + k] /= dk;
+    for (int j = tid; j < 2 * R; j += blockDim.x) {
+      if (j < R) f.G[k * RP + j] *= inv;
+      else f.Gi[k * RP + (j - R)] *= inv;
+    }
+    for (int i = tid; i < R; i += blockDim.x) fac[i] = (i == k) ? 0.0f : f.G[i * RP + k];
     __syncthreads();
-    const int nt = R - k - 1;
-    for (int e = tid; e < nt * nt; e += blockDim.x) {
-      const int i = k + 1 + e / nt, j = k + 1 + e % nt;
-      if (j <= i) f.G[i * RP + j] -= f.G[i * RP + k] * f.G[j * RP + k];
+    for (int e = tid; e < R * 2 * R; e += blockDim.x) {
+      const int i = e / (2 * R), j = e - i * 2 * R;
+      const float fi = fac[i];
+      if (fi != 0.0f) {
+        if (j < R) f.G[i * RP + j] -= fi * f.G[k * RP + j];
+        else f.Gi[i * RP + (j - R)] -= fi * f.Gi[k * RP + (j - R)];
+      }
     }
     __syncthreads();
   }
-  // --- L^-1 by columns (forward substitution), stored in stage-free Gi (upper part unused) ---
-  for (int c = tid; c < R; c += blockDim.x) {
-    for (int i = 0; i < R; ++i) {
-      float t = (i == c) ? 1.0f : 0.0f;
-      for (int k = c; k < i; ++k) t -= f.G[i * RP + k] * f.Gi[k * RP + c];
-      f.Gi[i * RP + c] = (i < c) ? 0.0f : t / f.G[i * RP + i];
-    }
-  }
-  __syncthreads();
-  // --- G^-1 = L^-T L^-1, written into G (L no longer needed) ---
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    const int i = e / R, j = e % R;
-    float t = 0.0f;
-    for (int k = max(i, j); k < R; ++k) t = fmaf(f.Gi[k * RP + i], f.Gi[k * RP + j], t);
-    f.G[i * RP + j] = t;
-  }
-  __syncthreads();
   // --- ADMM ---
   for (int q = tid; q < m; q += blockDim.x) {
     s[q] = 0.0f;
@@ -247,15 +284,17 @@ __device__ void block_l1_fit(const float* __restrict__ A, const float* __restric
   __syncthreads();
   const float irho = 1.0f / rho;
   for (int it = 0; it < iters; ++it) {
-    block_AtX(A, m, R, RP, [&](int q) { return b[q] - s[q] - y[q] * irho; }, f.red, f.rhs);
+    for (int q = tid; q < m; q += blockDim.x) x[q] = b[q] - s[q] - y[q] * irho;
+    __syncthreads();
+    block_AtX<RP>(A, m, R, x, f.red, f.rhs);
     for (int c = tid; c < R; c += blockDim.x) {
       float t = 0.0f;
-      for (int d = 0; d < R; ++d) t = fmaf(f.G[c * RP + d], f.rhs[d], t);
+      for (int d = 0; d < R; ++d) t = fmaf(f.Gi[c * RP + d], f.rhs[d], t);
       f.wv[c] = t;
     }
     __syncthreads();
     for (int q = tid; q < m; q += blockDim.x) {
-      const float aw = row_dot(A + int64_t(q) * RP, f.wv, RP);
+      const float aw = row_dot<RP>(A + int64_t(q) * RP, f.wv);
       const float e = b[q] - aw - y[q] * irho;
       const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
       s[q] = sq;
@@ -438,42 +477,51 @@ struct StepArgs {
   float* A;
   float* s;
   float* y;
+  float* x;         // b, s, y, x: global fallback when m > kSmemVecM
   float* lift;      // v, zero on entry
   float* upd;       // [3 * RP + 4]: w, w/||w||, g2, alpha, beta
   float* w_hist;    // nullable: this step's weights (RP)
 };
 
+template <int RP>
 __global__ void __launch_bounds__(kFitThreads) train_step_kernel(StepArgs a) {
   extern __shared__ float sm[];
   FitSmem f;
-  carve_fit_smem(sm, a.RP, f);
+  carve_fit_smem(sm, RP, f);
   const int tid = threadIdx.x;
+  float *b = a.b, *sv = a.s, *yv = a.y, *xv = a.x;
+  if (a.m <= kSmemVecM) {
+    b = f.scal + 8;
+    sv = b + a.m;
+    yv = sv + a.m;
+    xv = yv + a.m;
+  }
   for (int q = tid; q < a.m; q += blockDim.x) {
     const uint32_t j = draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q), uint32_t(a.col),
                                   uint32_t(a.pass), a.V);
     a.idx[q] = int32_t(j);
-    a.b[q] = a.Trow[j];
-    const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * a.RP);
-    float4* dst = reinterpret_cast<float4*>(a.A + int64_t(q) * a.RP);
-    for (int c4 = 0; c4 < a.RP / 4; ++c4) dst[c4] = src[c4];
+    b[q] = a.Trow[j];
+    const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
+    float4* dst = reinterpret_cast<float4*>(a.A + int64_t(q) * RP);
+    for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
   }
   __syncthreads();
-  block_l1_fit(a.A, a.b, a.s, a.y, a.m, a.R, a.RP, a.rho, a.iters, f);
-  // residual r (into s), lift, ||r||^2
+  block_l1_fit<RP>(a.A, b, sv, yv, xv, a.m, a.R, a.rho, a.iters, f);
+  // residual r (into x), lift, ||r||^2
   float rr = 0.0f;
   for (int q = tid; q < a.m; q += blockDim.x) {
-    const float r = a.b[q] - row_dot(a.A + int64_t(q) * a.RP, f.wv, a.RP);
-    a.s[q] = r;
+    const float r = b[q] - row_dot<RP>(a.A + int64_t(q) * RP, f.wv);
+    xv[q] = r;
     atomicAdd(&a.lift[a.idx[q]], r);
     rr = fmaf(r, r, rr);
   }
   __syncthreads();
   const float nr2 = block_sum(rr, f.red);
   float* g2 = f.rhs;
-  block_AtX(a.A, a.m, a.R, a.RP, [&](int q) { return a.s[q]; }, f.red, g2);
+  block_AtX<RP>(a.A, a.m, a.R, xv, f.red, g2);
   // ||lift||^2 = sum_q lift[idx_q] r_q (duplicates counted once per voxel)
   float ll = 0.0f;
-  for (int q = tid; q < a.m; q += blockDim.x) ll = fmaf(a.lift[a.idx[q]], a.s[q], ll);
+  for (int q = tid; q < a.m; q += blockDim.x) ll = fmaf(a.lift[a.idx[q]], xv[q], ll);
   __syncthreads();
   const float nl2 = block_sum(ll, f.red);
   if (tid == 0) {
@@ -496,21 +544,22 @@ __global__ void __launch_bounds__(kFitThreads) train_step_kernel(StepArgs a) {
   }
   __syncthreads();
   const float nw = f.scal[2];
-  for (int c = tid; c < a.RP; c += blockDim.x) {
+  for (int c = tid; c < RP; c += blockDim.x) {
     const float wc = c < a.R ? f.wv[c] : 0.0f;
     a.upd[c] = wc;
-    a.upd[a.RP + c] = nw > 0.0f ? wc / nw : 0.0f;
-    a.upd[2 * a.RP + c] = c < a.R ? g2[c] : 0.0f;
+    a.upd[RP + c] = nw > 0.0f ? wc / nw : 0.0f;
+    a.upd[2 * RP + c] = c < a.R ? g2[c] : 0.0f;
     if (a.w_hist && c < a.R) a.w_hist[c] = wc;
   }
   if (tid == 0) {
-    a.upd[3 * a.RP] = f.scal[0];
-    a.upd[3 * a.RP + 1] = f.scal[1];
+    a.upd[3 * RP] = f.scal[0];
+    a.upd[3 * RP + 1] = f.scal[1];
   }
 }
 
 // U_j += (alpha (U_j . w) + beta (lift_j - U_j . g2)) w^T/||w||; lift_j <- 0.
-__global__ void geodesic_update_kernel(float* __restrict__ U, int64_t V, int RP,
+template <int RP>
+__global__ void geodesic_update_kernel(float* __restrict__ U, int64_t V,
                                        float* __restrict__ lift, const float* __restrict__ upd) {
   extern __shared__ float su[];
   for (int e = threadIdx.x; e < 3 * RP + 2; e += blockDim.x) su[e] = upd[e];
@@ -522,23 +571,26 @@ __global__ void geodesic_update_kernel(float* __restrict__ U, int64_t V, int RP,
   for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < V;
        j += int64_t(gridDim.x) * blockDim.x) {
     float4* u4 = reinterpret_cast<float4*>(U + j * RP);
-    float p = 0.0f, g = 0.0f;
-    for (int c4 = 0; c4 < RP / 4; ++c4) {
-      const float4 x = u4[c4];
-      p = fmaf(x.x, w[4 * c4], fmaf(x.y, w[4 * c4 + 1], fmaf(x.z, w[4 * c4 + 2], fmaf(x.w, w[4 * c4 + 3], p))));
-      g = fmaf(x.x, g2[4 * c4], fmaf(x.y, g2[4 * c4 + 1], fmaf(x.z, g2[4 * c4 + 2], fmaf(x.w, g2[4 * c4 + 3], g))));
-    }
+    float4 x[RP / 4];
+#pragma unroll
+    for (int c4 = 0; c4 < RP / 4; ++c4) x[c4] = u4[c4];
     const float lj = lift[j];
+    float p = 0.0f, g = 0.0f;
+#pragma unroll
+    for (int c4 = 0; c4 < RP / 4; ++c4) {
+      p = fmaf(x[c4].x, w[4 * c4], fmaf(x[c4].y, w[4 * c4 + 1], fmaf(x[c4].z, w[4 * c4 + 2], fmaf(x[c4].w, w[4 * c4 + 3], p))));
+      g = fmaf(x[c4].x, g2[4 * c4], fmaf(x[c4].y, g2[4 * c4 + 1], fmaf(x[c4].z, g2[4 * c4 + 2], fmaf(x[c4].w, g2[4 * c4 + 3], g))));
+    }
     const float coef = alpha * p + beta * (lj - g);
     if (lj != 0.0f) lift[j] = 0.0f;
     if (coef != 0.0f) {
+#pragma unroll
       for (int c4 = 0; c4 < RP / 4; ++c4) {
-        float4 x = u4[c4];
-        x.x = fmaf(coef, wh[4 * c4], x.x);
-        x.y = fmaf(coef, wh[4 * c4 + 1], x.y);
-        x.z = fmaf(coef, wh[4 * c4 + 2], x.z);
-        x.w = fmaf(coef, wh[4 * c4 + 3], x.w);
-        u4[c4] = x;
+        x[c4].x = fmaf(coef, wh[4 * c4], x[c4].x);
+        x[c4].y = fmaf(coef, wh[4 * c4 + 1], x[c4].y);
+        x[c4].z = fmaf(coef, wh[4 * c4 + 2], x[c4].z);
+        x[c4].w = fmaf(coef, wh[4 * c4 + 3], x[c4].w);
+        u4[c4] = x[c4];
       }
     }
   }
@@ -615,7 +667,7 @@ __global__ void __launch_bounds__(256) sigma_partial_kernel(
        e += int64_t(gridDim.x) * blockDim.x) {
     const int i = int(e / m), q = int(e - int64_t(i) * m);
     const uint32_t j = draw_index(k0, k1, TAG_TRAIN, uint32_t(q), uint32_t(i), uint32_t(pass), V);
-    const float r = Tex[int64_t(i) * V + j] - row_dot(U + int64_t(j) * RP, W + int64_t(i) * RP, RP);
+    const float r = Tex[int64_t(i) * V + j] - row_dot_rt(U + int64_t(j) * RP, W + int64_t(i) * RP, RP);
     s1 += r;
     s2 += double(r) * r;
   }
@@ -659,15 +711,23 @@ struct RecArgs {
   float* W;        // (row - row_first) x RP
 };
 
+template <int RP>
 __global__ void __launch_bounds__(kFitThreads) recover_fit_kernel(RecArgs a) {
   extern __shared__ float sm[];
   FitSmem f;
-  carve_fit_smem(sm, a.RP, f);
+  carve_fit_smem(sm, RP, f);
   float* Lrow = f.scal + 8;  // n_pad
   float* A = a.scratch + int64_t(blockIdx.x) * a.block_stride;
-  float* b = A + int64_t(a.m) * a.RP;
+  float* b = A + int64_t(a.m) * RP;
   float* s = b + a.m;
   float* y = s + a.m;
+  float* x = y + a.m;
+  if (a.m <= kSmemVecM) {
+    b = Lrow + a.n_pad;
+    s = b + a.m;
+    y = s + a.m;
+    x = y + a.m;
+  }
   for (int64_t i = a.row_first + blockIdx.x; i < a.row_end; i += gridDim.x) {
     for (int sidx = threadIdx.x; sidx < a.n_pad; sidx += blockDim.x) Lrow[sidx] = 0.0f;
     __syncthreads();
@@ -687,14 +747,14 @@ __global__ void __launch_bounds__(kFitThreads) recover_fit_kernel(RecArgs a) {
       }
       const float den = 1.0f - a.kf * u * u;
       b[q] = den > 0.0f ? a.ctf * u * rsqrtf(den) : (u > 0.0f ? 3.0e38f : -3.0e38f);
-      const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * a.RP);
-      float4* dst = reinterpret_cast<float4*>(A + int64_t(q) * a.RP);
-      for (int c4 = 0; c4 < a.RP / 4; ++c4) dst[c4] = src[c4];
+      const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
+      float4* dst = reinterpret_cast<float4*>(A + int64_t(q) * RP);
+      for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
     }
     __syncthreads();
-    block_l1_fit(A, b, s, y, a.m, a.R, a.RP, a.rho, a.iters, f);
-    for (int c = threadIdx.x; c < a.RP; c += blockDim.x)
-      a.W[(i - a.row_first) * a.RP + c] = c < a.R ? f.wv[c] : 0.0f;
+    block_l1_fit<RP>(A, b, s, y, x, a.m, a.R, a.rho, a.iters, f);
+    for (int c = threadIdx.x; c < RP; c += blockDim.x)
+      a.W[(i - a.row_first) * RP + c] = c < a.R ? f.wv[c] : 0.0f;
     __syncthreads();
   }
 }
@@ -878,6 +938,22 @@ __global__ void pack_u_kernel(const float* __restrict__ Uin, int64_t V, int R, i
   }
 }
 
+// Calls f(std::integral_constant<int, RP>) for the padded rank RP (16..128).
+template <class F>
+bool with_rp(int rp, F&& f) {
+  switch (rp) {
+    case 16: f(std::integral_constant<int, 16>{}); return true;
+    case 32: f(std::integral_constant<int, 32>{}); return true;
+    case 48: f(std::integral_constant<int, 48>{}); return true;
+    case 64: f(std::integral_constant<int, 64>{}); return true;
+    case 80: f(std::integral_constant<int, 80>{}); return true;
+    case 96: f(std::integral_constant<int, 96>{}); return true;
+    case 112: f(std::integral_constant<int, 112>{}); return true;
+    case 128: f(std::integral_constant<int, 128>{}); return true;
+    default: return false;
+  }
+}
+
 int grid_n(int64_t work, int threads, int cap = 152 * 16) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -885,8 +961,9 @@ int grid_n(int64_t work, int threads, int cap = 152 * 16) {
   return int(b);
 }
 
-size_t fit_smem_bytes(int RP, int n_pad) {
-  return sizeof(float) * (2 * RP * RP + 64 * RP + 2 * RP + 8 + n_pad);
+size_t fit_smem_bytes(int RP, int n_pad, int m) {
+  const size_t vec = m <= kSmemVecM ? 4 * size_t(m) : 0;
+  return sizeof(float) * (2 * RP * RP + 32 * RP + kStageFloats + 2 * RP + 8 + n_pad + vec);
 }
 
 pt_status nomem_r(pt_ctx* ctx, const char* what) {
@@ -1023,7 +1100,7 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   } guard{{&Ub, &Tex, &lift, &sc, &upd, &part, &rinv, &Wex, &keys, &sig, &tmax}};
   if (!Ub.ensure(sizeof(float) * size_t(V) * pl.RP) || !Tex.ensure(sizeof(float) * size_t(ell) * V) ||
       !lift.ensure(sizeof(float) * V) ||
-      !sc.ensure(sizeof(float) * (size_t(pl.m) * pl.RP + 4 * size_t(pl.m)) + 256) ||
+      !sc.ensure(sizeof(float) * (size_t(pl.m) * pl.RP + 5 * size_t(pl.m)) + 256) ||
       !upd.ensure(sizeof(float) * (3 * pl.RP + 4)) || !Wex.ensure(sizeof(float) * size_t(ell) * pl.RP) ||
       !keys.ensure(sizeof(unsigned long long) * ell) || !tmax.ensure(sizeof(float) * ell))
     return nomem_r(ctx, "RapidPT training");
@@ -1110,33 +1187,44 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   sa.b = scb + size_t(pl.m) * pl.RP;
   sa.s = sa.b + pl.m;
   sa.y = sa.s + pl.m;
-  sa.idx = reinterpret_cast<int32_t*>(sa.y + pl.m);
+  sa.x = sa.y + pl.m;
+  sa.idx = reinterpret_cast<int32_t*>(sa.x + pl.m);
   sa.lift = lift.as<float>();
   sa.upd = upd.as<float>();
-  const int fsm = int(fit_smem_bytes(pl.RP, 0));
-  PT_CUDA_TRY(ctx, cudaFuncSetAttribute(train_step_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, fsm));
+  const int fsm = int(fit_smem_bytes(pl.RP, 0, pl.m));
   const int usm = (3 * pl.RP + 2) * int(sizeof(float));
   int64_t steps = 0;
-  for (int p = 0; p < o.train_passes; ++p) {
-    for (int i = 0; i < ell; ++i) {
-      sa.pass = p;
-      sa.col = i;
-      sa.Trow = Tex.as<float>() + int64_t(i) * V;
-      sa.w_hist = w_hist ? w_hist + steps * pl.R : nullptr;
-      train_step_kernel<<<1, kFitThreads, fsm, st>>>(sa);
-      PT_LAUNCH_CHECK(ctx);
-      geodesic_update_kernel<<<grid_n(V, 256, 152 * 8), 256, usm, st>>>(U, V, pl.RP,
-                                                                         lift.as<float>(),
-                                                                         upd.as<float>());
-      PT_LAUNCH_CHECK(ctx);
-      ++steps;
-      if (steps % o.qr_every == 0) {
-        s = qr_inplace(ctx, U, pl, part, rinv);
-        if (s != PT_OK) return s;
+  cudaError_t lerr = cudaSuccess;
+  with_rp(pl.RP, [&](auto rpc) {
+    constexpr int RPc = decltype(rpc)::value;
+    lerr = cudaFuncSetAttribute(train_step_kernel<RPc>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    for (int p = 0; p < o.train_passes && lerr == cudaSuccess && s == PT_OK; ++p) {
+      for (int i = 0; i < ell; ++i) {
+        sa.pass = p;
+        sa.col = i;
+        sa.Trow = Tex.as<float>() + int64_t(i) * V;
+        sa.w_hist = w_hist ? w_hist + steps * pl.R : nullptr;
+        train_step_kernel<RPc><<<1, kFitThreads, fsm, st>>>(sa);
+        geodesic_update_kernel<RPc><<<grid_n(V, 256, 152 * 8), 256, usm, st>>>(
+            U, V, lift.as<float>(), upd.as<float>());
+        lerr = cudaGetLastError();
+        if (lerr != cudaSuccess) break;
+        count_launch();
+        count_launch();
+        ++steps;
+        if (steps % o.qr_every == 0) {
+          s = qr_inplace(ctx, U, pl, part, rinv);
+          if (s != PT_OK) break;
+        }
       }
     }
+  });
+  if (lerr != cudaSuccess) {
+    set_error(ctx, std::string("RapidPT training launch: ") + cudaGetErrorString(lerr));
+    return PT_ERR_CUDA;
   }
+  if (s != PT_OK) return s;
   s = qr_inplace(ctx, U, pl, part, rinv);
   if (s != PT_OK) return s;
 
@@ -1243,7 +1331,7 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
     }
   } guard{{&Ub, &scr, &Wb, &keys}};
   const int nblk = int(std::min<int64_t>(rows, 152));
-  const int64_t block_stride = (int64_t(pl.m) * pl.RP + 3 * int64_t(pl.m) + 63) / 64 * 64;
+  const int64_t block_stride = (int64_t(pl.m) * pl.RP + 4 * int64_t(pl.m) + 63) / 64 * 64;
   if (!Ub.ensure(sizeof(float) * size_t(pl.V) * pl.RP) ||
       !scr.ensure(sizeof(float) * size_t(nblk) * size_t(block_stride)) ||
       !Wb.ensure(sizeof(float) * size_t(rows) * pl.RP) ||
@@ -1277,11 +1365,22 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
   a.scratch = scr.as<float>();
   a.block_stride = block_stride;
   a.W = Wb.as<float>();
-  const int fsm = int(fit_smem_bytes(pl.RP, ctx->n_pad));
-  PT_CUDA_TRY(ctx, cudaFuncSetAttribute(recover_fit_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, fsm));
-  recover_fit_kernel<<<nblk, kFitThreads, fsm, st>>>(a);
-  PT_LAUNCH_CHECK(ctx);
+  const int fsm = int(fit_smem_bytes(pl.RP, ctx->n_pad, pl.m));
+  cudaError_t lerr = cudaSuccess;
+  with_rp(pl.RP, [&](auto rpc) {
+    constexpr int RPc = decltype(rpc)::value;
+    lerr = cudaFuncSetAttribute(recover_fit_kernel<RPc>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
+    if (lerr == cudaSuccess) {
+      recover_fit_kernel<RPc><<<nblk, kFitThreads, fsm, st>>>(a);
+      lerr = cudaGetLastError();
+    }
+  });
+  if (lerr != cudaSuccess) {
+    set_error(ctx, std::string("RapidPT recovery launch: ") + cudaGetErrorString(lerr));
+    return PT_ERR_CUDA;
+  }
+  count_launch();
   s = reconstruct(ctx, Wb.as<float>(), rows, first_row, Ub.as<float>(), pl, float(sigma),
                   TAG_NOISE, 0, nullptr, keys.as<unsigned long long>());
   if (s != PT_OK) return s;
