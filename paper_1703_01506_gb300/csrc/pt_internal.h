@@ -65,6 +65,7 @@ struct pt_ctx {
   pt::Buf maxkey;       // uint64[P]
   pt::Buf cnt;          // uint32[v_valid + 1]; the last word counts observed-set rows
   pt::Buf scratch;      // misc
+  pt::Buf tcdesc;       // device copy of the tensor-core launch descriptor
 
   // Profiling of the dominant kernel (events on `stream`).
   bool profile = false;

@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -35,18 +36,30 @@ constexpr int kStageBytes = 4096;  // 128 relabellings x 16 subjects x BF16
 constexpr int kSmemLimit = 232448;
 constexpr int kMaxBlocksPerItem = 255;  // per-thread 8-bit exceedance counters
 
-struct TcArgs {
-  int n_pad, pieces, stages, ksteps;
+// One study (one prepared context and its relabellings) of a launch. Launches
+// with several studies (pt_maxnull_naive_batched) walk the concatenation of
+// their work items; tensor maps live in global memory with the descriptor.
+struct alignas(64) TcStudy {
+  CUtensorMap tmL;  // labels, [P_pad * n_pad / 256][256] BF16 view
+  CUtensorMap tmX;  // data pieces, [3 * v_pad * n_pad / 256][256] BF16 view
+  int n_pad, ksteps;
   int64_t P, v, v_pad;
-  int64_t n_chunks, blocks_per_chunk, nblocks, n_items;
-  int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
-  float k_f, ct_f;
+  int64_t n_chunks, blocks_per_chunk, nblocks, item_begin;
   const float* u_obs;
   const uint8_t* rowflag;    // per relabelling: 1 = observed group-1 set (not compared)
   const uint8_t* blockflag;  // per 128-row block: holds such a row
   unsigned long long* maxkey;
   uint32_t* cnt;
-  float* uout;
+  float* uout;  // row writes (single-study launches only)
+};
+
+struct TcArgs {
+  const TcStudy* studies;
+  int n_studies, stages;
+  int n_pad_max;
+  int64_t n_items;
+  int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
+  float k_f, ct_f;
   uint32_t* status;
 };
 
@@ -149,17 +162,15 @@ __device__ __forceinline__ float cols_reduce(const uint32_t (&r)[CW], const floa
 
 template <int NT, bool TWO, int PIECES>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_contract_kernel(const __grid_constant__ CUtensorMap tmL,
-                       const __grid_constant__ CUtensorMap tmX, const TcArgs a) {
+    tc_contract_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int CW = NT / 4;                 // accumulator columns per epilogue thread
   constexpr int CHK = CW < 32 ? CW : 32;     // columns per TMEM load
   constexpr int NCH = CW / CHK;              // loads per block
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = a.stages;
-  const uint32_t xtile_bytes = uint32_t(NT) * a.n_pad * 2;
   uint8_t* xs = smem;
-  uint8_t* ls = smem + PIECES * xtile_bytes;
+  uint8_t* ls = smem + PIECES * uint32_t(NT) * a.n_pad_max * 2;
   float* su = reinterpret_cast<float*>(ls + S * kStageBytes);
   uint8_t* sbf = reinterpret_cast<uint8_t*>(su + NT);  // block flags of the current item
   uint64_t* bars = reinterpret_cast<uint64_t*>(sbf + kMaxBlocksPerItem + 1);
@@ -200,28 +211,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       int x_armed = -1;  // parity of the last armed phase of xfull (-1: none)
       uint32_t ps = 0, pph = 0;  // ring stage and its phase parity
+      int sid = 0;
       for (int64_t item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, ++w) {
-        const int64_t vt = item / a.n_chunks, pc = item % a.n_chunks;
-        const int64_t b0 = pc * a.blocks_per_chunk;
-        const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
+        while (sid + 1 < a.n_studies && item >= a.studies[sid + 1].item_begin) ++sid;
+        const TcStudy& st = a.studies[sid];
+        const int64_t local = item - st.item_begin;
+        const int64_t vt = local / st.n_chunks, pc = local % st.n_chunks;
+        const int64_t b0 = pc * st.blocks_per_chunk;
+        const int64_t b1 = min(st.nblocks, b0 + st.blocks_per_chunk);
+        const int n_pad = st.n_pad;
+        const uint32_t xtile_bytes = uint32_t(NT) * n_pad * 2;
         if (!mbar_wait(BAR(1), (w & 1) ^ 1, a.status, abort_flag)) break;
         mbar_arrive_expect_tx(BAR(0), uint32_t(PIECES) * xtile_bytes);
         x_armed = w & 1;
         for (int q = 0; q < PIECES; ++q) {
-          const int64_t row0 = (int64_t(q) * a.v_pad * a.n_pad + vt * NT * a.n_pad) / 256;
-          tma_load_2d(smem_addr(xs + q * xtile_bytes), &tmX, 0, int32_t(row0), BAR(0));
+          const int64_t row0 = (int64_t(q) * st.v_pad * n_pad + vt * NT * n_pad) / 256;
+          tma_load_2d(smem_addr(xs + q * xtile_bytes), &st.tmX, 0, int32_t(row0), BAR(0));
         }
         const int64_t nb = b1 - b0, rot = (int64_t(blockIdx.x) * 17) % nb;
         for (int64_t kb = 0; kb < nb && ok; ++kb) {
           const int64_t b = b0 + (kb + rot) % nb;
-          for (int ks = 0; ks < a.ksteps; ++ks, ++it) {
+          for (int ks = 0; ks < st.ksteps; ++ks, ++it) {
             if (!mbar_wait(LEMPTY(ps), pph ^ 1u, a.status, abort_flag)) {
               ok = false;
               break;
             }
             mbar_arrive_expect_tx(LFULL(ps), kStageBytes);
-            const int64_t row = b * (a.n_pad / 2) + ks * 8;
-            tma_load_2d(smem_addr(ls + ps * kStageBytes), &tmL, 0, int32_t(row), LFULL(ps));
+            const int64_t row = b * (n_pad / 2) + ks * 8;
+            tma_load_2d(smem_addr(ls + ps * kStageBytes), &st.tmL, 0, int32_t(row), LFULL(ps));
             if (++ps == uint32_t(S)) {
               ps = 0;
               pph ^= 1u;
@@ -248,15 +265,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       // L stage: k-group major (k-groups 2 KB apart, 8-row groups adjacent);
       // Xn tile: row-group major (k-groups adjacent, 8-row groups n_pad/8 x 128 B apart).
       const uint64_t adesc0 = smem_desc(smem_addr(ls), 16 * 128, 128);
-      uint64_t bdesc0[PIECES];
-#pragma unroll
-      for (int q = 0; q < PIECES; ++q)
-        bdesc0[q] = smem_desc(smem_addr(xs) + q * xtile_bytes, 128, uint32_t(a.n_pad / 8) * 128);
       bool ok = true;
+      int sid = 0;
       for (int64_t item = blockIdx.x; item < a.n_items && ok; item += gridDim.x, ++w) {
-        const int64_t pc = item % a.n_chunks;
-        const int64_t b0 = pc * a.blocks_per_chunk;
-        const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
+        while (sid + 1 < a.n_studies && item >= a.studies[sid + 1].item_begin) ++sid;
+        const TcStudy& st = a.studies[sid];
+        const int64_t local = item - st.item_begin;
+        const int64_t pc = local % st.n_chunks;
+        const int64_t b0 = pc * st.blocks_per_chunk;
+        const int64_t b1 = min(st.nblocks, b0 + st.blocks_per_chunk);
+        const int ksteps = st.ksteps;
+        const uint32_t xtile_bytes = uint32_t(NT) * st.n_pad * 2;
+        uint64_t bdesc0[PIECES];
+#pragma unroll
+        for (int q = 0; q < PIECES; ++q)
+          bdesc0[q] = smem_desc(smem_addr(xs) + q * xtile_bytes, 128, uint32_t(st.n_pad / 8) * 128);
         if (!mbar_wait(BAR(0), w & 1, a.status, abort_flag)) break;
         tc_fence_after();
         for (int64_t b = b0; b < b1 && ok; ++b, ++j) {
@@ -267,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + abuf * NT;
-          for (int ks = 0; ks < a.ksteps; ++ks) {
+          for (int ks = 0; ks < ksteps; ++ks) {
             if (!mbar_wait(LFULL(ms), mph, a.status, abort_flag)) {
               ok = false;
               break;
@@ -303,24 +326,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int etid = threadIdx.x - 64;
     uint32_t j = 0;
     bool ok = true;
+    int sid = 0;
     for (int64_t item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-      const int64_t vt = item / a.n_chunks, pc = item % a.n_chunks;
-      const int64_t b0 = pc * a.blocks_per_chunk;
-      const int64_t b1 = min(a.nblocks, b0 + a.blocks_per_chunk);
+      while (sid + 1 < a.n_studies && item >= a.studies[sid + 1].item_begin) ++sid;
+      const TcStudy& st = a.studies[sid];
+      const int64_t local = item - st.item_begin;
+      const int64_t vt = local / st.n_chunks, pc = local % st.n_chunks;
+      const int64_t b0 = pc * st.blocks_per_chunk;
+      const int64_t b1 = min(st.nblocks, b0 + st.blocks_per_chunk);
+      const int64_t V = st.v, Pn = st.P;
+      const float* u_obs = st.u_obs;
+      const uint8_t* rowflag = st.rowflag;
+      unsigned long long* maxkey = st.maxkey;
       const int64_t v0 = vt * NT;
       const int64_t gcol0 = v0 + colbase;
-      const bool ragged_cols = v0 + NT > a.v;
+      const bool ragged_cols = v0 + NT > V;
       epi_bar();
       for (int c = etid; c < NT; c += 32 * kEpiWarps) {
         float x = INFINITY;
-        if (a.do_reduce && v0 + c < a.v) {
-          x = a.u_obs[v0 + c];
+        if (a.do_reduce && v0 + c < V) {
+          x = u_obs[v0 + c];
           if (TWO) x = fabsf(x);
         }
         su[c] = x;
       }
       for (int64_t c = etid; c < b1 - b0; c += 32 * kEpiWarps)
-        sbf[c] = (a.do_reduce && a.blockflag[b0 + c]) || (b0 + c + 1) * 128 > a.P ? 1 : 0;
+        sbf[c] = (a.do_reduce && st.blockflag[b0 + c]) || (b0 + c + 1) * 128 > Pn ? 1 : 0;
       epi_bar();
       uint32_t c8[CW / 4];
 #pragma unroll
@@ -330,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       unsigned long long gkey_next = 0ull;
       {
         const int64_t rowf = (b0 + rot % nb) * 128 + quad * 32 + lane;
-        if (a.do_reduce && rowf < a.P) gkey_next = __ldcg(&a.maxkey[rowf]);
+        if (a.do_reduce && rowf < Pn) gkey_next = __ldcg(&maxkey[rowf]);
       }
       for (int64_t kb = 0; kb < nb; ++kb, ++j) {
         // Blocks run in a per-CTA rotated order so that the CTAs do not all
@@ -345,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           int64_t bn = bi + 1;
           if (bn >= nb) bn -= nb;
           const int64_t rown = (b0 + bn) * 128 + quad * 32 + lane;
-          if (a.do_reduce && rown < a.P) gkey_next = __ldcg(&a.maxkey[rown]);
+          if (a.do_reduce && rown < Pn) gkey_next = __ldcg(&maxkey[rown]);
         }
         const bool ragged = ragged_cols || sbf[bi];
         if (ok && !mbar_wait(BAR(2 + abuf), aph, a.status, abort_flag)) ok = false;
@@ -353,8 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) continue;
         tc_fence_after();
         const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
-        const bool row_ok = row < a.P;
-        const bool cnt_ok = row_ok && !(ragged && a.do_reduce && a.rowflag[row]);
+        const bool row_ok = row < Pn;
+        const bool cnt_ok = row_ok && !(ragged && a.do_reduce && rowflag[row]);
         float best = -INFINITY;
         int bestc = 0;
 #pragma unroll
@@ -364,10 +395,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_wait_ld();
           const int64_t g0 = gcol0 + c * CHK;
           if (a.write_mode && row_ok) {
-            float* dst = a.uout + row * a.v;
+            float* dst = st.uout + row * V;
 #pragma unroll
             for (int jj = 0; jj < CHK; ++jj) {
-              if (g0 + jj < a.v) {
+              if (g0 + jj < V) {
                 const float u = __uint_as_float(r[jj]);
                 float val = u;
                 if (a.write_mode == 2) {
@@ -381,9 +412,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (a.do_reduce) {
             uint32_t(&cc)[CHK / 4] = *reinterpret_cast<uint32_t(*)[CHK / 4]>(&c8[c * (CHK / 4)]);
             const float cm =
-                ragged ? cols_reduce<CHK, TWO, true>(r, su + colbase + c * CHK, g0, a.v, row_ok,
+                ragged ? cols_reduce<CHK, TWO, true>(r, su + colbase + c * CHK, g0, V, row_ok,
                                                      cnt_ok, cc)
-                       : cols_reduce<CHK, TWO, false>(r, su + colbase + c * CHK, g0, a.v, true,
+                       : cols_reduce<CHK, TWO, false>(r, su + colbase + c * CHK, g0, V, true,
                                                       true, cc);
             if (cm > best) {
               best = cm;
@@ -409,11 +440,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int jj = CHK - 1; jj >= 0; --jj) {
                   float sv = __uint_as_float(r[jj]);
                   if (TWO) sv = fabsf(sv);
-                  if (sv == best && g0 + jj < a.v) jj_best = jj;
+                  if (sv == best && g0 + jj < V) jj_best = jj;
                 }
                 if (jj_best >= 0) {
                   const unsigned long long key = pack_key(best, uint32_t(g0 + jj_best));
-                  if (key > gkey) atomicMax(&a.maxkey[row], key);
+                  if (key > gkey) atomicMax(&maxkey[row], key);
                 }
               }
             }
@@ -423,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(BAR(4 + abuf));
       }
-      if (ok && a.do_reduce) flush_counts8<CW>(c8, lane, gcol0, a.v, a.cnt);
+      if (ok && a.do_reduce) flush_counts8<CW>(c8, lane, gcol0, V, st.cnt);
     }
   }
 #undef LFULL
@@ -478,88 +509,123 @@ int num_sms(int dev) {
 }
 
 template <int NT, bool TWO>
-pt_status launch_nt(pt_ctx* ctx, const CUtensorMap& tmL, const CUtensorMap& tmX, const TcArgs& a,
-                    int grid, int smem) {
-  auto kern = a.pieces == 2 ? tc_contract_kernel<NT, TWO, 2> : tc_contract_kernel<NT, TWO, 3>;
+pt_status launch_nt(pt_ctx* ctx, const TcArgs& a, int pieces, int grid, int smem) {
+  auto kern = pieces == 2 ? tc_contract_kernel<NT, TWO, 2> : tc_contract_kernel<NT, TWO, 3>;
   PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   if (a.do_reduce) prof_begin(ctx);
-  kern<<<grid, kThreads, smem, ctx->stream>>>(tmL, tmX, a);
+  kern<<<grid, kThreads, smem, ctx->stream>>>(a);
   if (a.do_reduce) prof_end(ctx);
   PT_LAUNCH_CHECK(ctx);
   return PT_OK;
+}
+
+// Largest voxel tile NT (and its stage count) whose resident data tile fits.
+bool choose_tile(int n_pad, int pieces, int* NT, int* stages) {
+  for (int cand : {256, 128, 64}) {
+    if (int64_t(cand) * n_pad / 256 > 256) continue;
+    int s = 12;
+    while (s >= 4 && smem_bytes(cand, n_pad, pieces, s) > kSmemLimit - 1024) --s;
+    if (s >= 4) {
+      *NT = cand;
+      *stages = s;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Work split of one study into items (voxel tile x block range) and its
+// descriptor; target_items spreads small studies over more block ranges.
+bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int64_t target_items,
+                int64_t item_begin, const float* u_obs, unsigned long long* maxkey, uint32_t* cnt,
+                float* uout, TcStudy* st) {
+  memset(st, 0, sizeof(*st));
+  st->n_pad = c->n_pad;
+  st->ksteps = c->n_pad / 16;
+  st->P = P;
+  st->v = c->v_valid;
+  st->v_pad = c->v_pad;
+  st->nblocks = (P + 127) / 128;
+  const int64_t n_vtiles = (st->v + NT - 1) / NT;
+  int64_t chunks = (st->nblocks + kMaxBlocksPerItem - 1) / kMaxBlocksPerItem;
+  if (n_vtiles * chunks < target_items) {
+    const int64_t want = (target_items + n_vtiles - 1) / n_vtiles;
+    if (want > chunks) chunks = want;
+  }
+  if (chunks > st->nblocks) chunks = st->nblocks;
+  if (chunks < 1) chunks = 1;
+  st->blocks_per_chunk = (st->nblocks + chunks - 1) / chunks;
+  st->n_chunks = (st->nblocks + st->blocks_per_chunk - 1) / st->blocks_per_chunk;
+  st->item_begin = item_begin;
+  st->u_obs = u_obs;
+  st->rowflag = c->rowflag.as<uint8_t>();
+  st->blockflag = c->blockflag.as<uint8_t>();
+  st->maxkey = maxkey;
+  st->cnt = cnt;
+  st->uout = uout;
+  const int64_t P_pad = st->nblocks * 128;
+  return make_map(&st->tmL, Lb, uint64_t(P_pad) * c->n_pad / 256, 8) &&
+         make_map(&st->tmX, c->Xnb.p, uint64_t(3) * c->v_pad * c->n_pad / 256,
+                  uint32_t(NT * c->n_pad / 256));
+}
+
+// Launch the fused kernel over n studies sharing tile NT and piece count.
+// descs: device copy of the descriptors (filled by the caller).
+pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_items, int NT,
+                         int pieces, int n_pad_max, int do_reduce, int write_mode, int two_sided,
+                         float kf, float ctf) {
+  int NTc = 0, stages = 0;
+  if (!choose_tile(n_pad_max, pieces, &NTc, &stages) || NTc < NT) {
+    set_error(ctx, "tensor-core path: n too large for the resident data tile");
+    return PT_ERR_UNSUPPORTED;
+  }
+  TcArgs a;
+  a.studies = descs;
+  a.n_studies = n;
+  a.stages = stages;
+  a.n_pad_max = n_pad_max;
+  a.n_items = n_items;
+  a.do_reduce = do_reduce;
+  a.write_mode = write_mode;
+  a.k_f = kf;
+  a.ct_f = ctf;
+  a.status = ctx->status.as<uint32_t>();
+  const int sms = num_sms(ctx->device);
+  const int grid = int(n_items < sms ? n_items : sms);
+  const int smem = smem_bytes(NT, n_pad_max, pieces, stages);
+  if (two_sided) {
+    if (NT == 256) return launch_nt<256, true>(ctx, a, pieces, grid, smem);
+    if (NT == 128) return launch_nt<128, true>(ctx, a, pieces, grid, smem);
+    return launch_nt<64, true>(ctx, a, pieces, grid, smem);
+  }
+  if (NT == 256) return launch_nt<256, false>(ctx, a, pieces, grid, smem);
+  if (NT == 128) return launch_nt<128, false>(ctx, a, pieces, grid, smem);
+  return launch_nt<64, false>(ctx, a, pieces, grid, smem);
 }
 
 pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
                     int write_mode, int two_sided, const float* u_obs,
                     unsigned long long* maxkey, uint32_t* cnt, float* uout) {
   const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
-  const int n_pad = ctx->n_pad;
   int NT = 0, stages = 0;
-  for (int cand : {256, 128, 64}) {
-    if (int64_t(cand) * n_pad / 256 > 256) continue;
-    int s = 12;
-    while (s >= 4 && smem_bytes(cand, n_pad, pieces, s) > kSmemLimit - 1024) --s;
-    if (s >= 4) {
-      NT = cand;
-      stages = s;
-      break;
-    }
-  }
-  if (NT == 0) {
+  if (!choose_tile(ctx->n_pad, pieces, &NT, &stages)) {
     set_error(ctx, "tensor-core path: n too large for the resident data tile");
     return PT_ERR_UNSUPPORTED;
   }
-  TcArgs a;
-  a.n_pad = n_pad;
-  a.pieces = pieces;
-  a.stages = stages;
-  a.ksteps = n_pad / 16;
-  a.P = P;
-  a.v = ctx->v_valid;
-  a.v_pad = ctx->v_pad;
-  a.nblocks = (P + 127) / 128;
-  const int64_t n_vtiles = (a.v + NT - 1) / NT;
-  const int sms = num_sms(ctx->device);
-  int64_t chunks = (a.nblocks + kMaxBlocksPerItem - 1) / kMaxBlocksPerItem;
-  if (n_vtiles * chunks < 2 * sms) {
-    int64_t want = (2 * sms + n_vtiles - 1) / n_vtiles;
-    if (want > chunks) chunks = want;
-  }
-  if (chunks > a.nblocks) chunks = a.nblocks;
-  if (chunks < 1) chunks = 1;
-  a.blocks_per_chunk = (a.nblocks + chunks - 1) / chunks;
-  a.n_chunks = (a.nblocks + a.blocks_per_chunk - 1) / a.blocks_per_chunk;
-  a.n_items = n_vtiles * a.n_chunks;
-  a.do_reduce = do_reduce;
-  a.write_mode = write_mode;
-  a.k_f = float(ctx->k);
-  a.ct_f = float(ctx->c_t);
-  a.u_obs = u_obs;
-  a.rowflag = ctx->rowflag.as<uint8_t>();
-  a.blockflag = ctx->blockflag.as<uint8_t>();
-  a.maxkey = maxkey;
-  a.cnt = cnt;
-  a.uout = uout;
-  a.status = ctx->status.as<uint32_t>();
-
-  CUtensorMap tmL, tmX;
-  const int64_t P_pad = a.nblocks * 128;
-  if (!make_map(&tmL, Lb, uint64_t(P_pad) * n_pad / 256, 8) ||
-      !make_map(&tmX, ctx->Xnb.p, uint64_t(3) * ctx->v_pad * n_pad / 256,
-                uint32_t(NT * n_pad / 256))) {
+  TcStudy st;
+  if (!fill_study(ctx, Lb, P, NT, 2 * num_sms(ctx->device), 0, u_obs, maxkey, cnt, uout, &st)) {
     set_error(ctx, "cuTensorMapEncodeTiled failed");
     return PT_ERR_CUDA;
   }
-  const int grid = int(a.n_items < sms ? a.n_items : sms);
-  const int smem = smem_bytes(NT, n_pad, pieces, stages);
-  if (two_sided) {
-    if (NT == 256) return launch_nt<256, true>(ctx, tmL, tmX, a, grid, smem);
-    if (NT == 128) return launch_nt<128, true>(ctx, tmL, tmX, a, grid, smem);
-    return launch_nt<64, true>(ctx, tmL, tmX, a, grid, smem);
+  if (!ctx->tcdesc.ensure(sizeof(TcStudy))) {
+    set_error(ctx, "out of device memory (descriptor)");
+    return PT_ERR_NOMEM;
   }
-  if (NT == 256) return launch_nt<256, false>(ctx, tmL, tmX, a, grid, smem);
-  if (NT == 128) return launch_nt<128, false>(ctx, tmL, tmX, a, grid, smem);
-  return launch_nt<64, false>(ctx, tmL, tmX, a, grid, smem);
+  PT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->tcdesc.p, &st, sizeof(TcStudy), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  const int64_t items = ((st.v + NT - 1) / NT) * st.n_chunks;
+  return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, pieces, ctx->n_pad,
+                        do_reduce, write_mode, two_sided, float(ctx->k), float(ctx->c_t));
 }
 
 }  // namespace
