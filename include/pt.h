@@ -109,6 +109,37 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
                               const pt_naive_opts* opts, float* maxnull, int32_t* argmax,
                               uint32_t* counts);
 
+/*
+ * pt_maxnull_naive_batched -- NaivePT (Alg. 1) for several independent
+ * studies in one call: per study i, exactly what pt_maxnull_naive_ex computes
+ * for (ctxs[i], perms[i], P[i]) into maxnull[i], argmax[i], counts[i]. The
+ * paper runs one study at a time (Sec. 5); batching only packs the studies'
+ * (relabelling block x voxel tile) work into one persistent tensor-core launch
+ * per tile class, so small studies share the GPU instead of each leaving SMs idle.
+ *   ctxs      : host array of n_studies distinct contexts, all on one device.
+ *               Work runs on ctxs[0]'s stream; every context's own stream is
+ *               synchronised once when the batch is (re)planned.
+ *   n_studies : 1 <= n_studies <= 4096.
+ *   perms, P, maxnull, argmax, counts : host arrays of n_studies entries with
+ *               the meaning of pt_maxnull_naive's arguments (device buffers);
+ *               counts may be NULL, as may any counts[i].
+ *   opts      : precision must be PT_PREC_BF16X2 or PT_PREC_BF16X3
+ *               (PT_ERR_UNSUPPORTED for FP32); two_sided applies to all.
+ * The first call with a given set of arguments plans the launch (host work and
+ * one synchronisation), captures it in a CUDA graph and runs the graph; a
+ * later call with the same contexts, buffers and sizes replays that graph
+ * without host work. One graph is cached per process; pt_destroy of a member
+ * context drops it. Errors: PT_ERR_INVALID (NULL entries, P out of range, a
+ * context listed twice, contexts on different devices), PT_ERR_UNSUPPORTED,
+ * PT_ERR_NOMEM, PT_ERR_CUDA. A row of perms[i] that is not a permutation
+ * sets the error flag of ctxs[i]: after pt_sync(ctxs[0]), pt_sync(ctxs[i])
+ * returns PT_ERR_INVALID.
+ */
+pt_status pt_maxnull_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
+                                   const int32_t* const* perms, const int64_t* P,
+                                   const pt_naive_opts* opts, float* const* maxnull,
+                                   int32_t* const* argmax, uint32_t* const* counts);
+
 /* ------------------------------------------------------------------------- */
 /* RapidPT (Alg. 2; Sec. 4.1 training, Sec. 4.2 recovery)                     */
 /* ------------------------------------------------------------------------- */

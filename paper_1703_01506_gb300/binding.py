@@ -63,6 +63,9 @@ def load(path=None):
         "pt_maxnull_naive": (ctypes.c_int, [_VP, _VP, i64, _VP, _VP, _VP]),
         "pt_maxnull_naive_ex": (ctypes.c_int, [_VP, _VP, i64, ctypes.POINTER(pt_naive_opts),
                                                _VP, _VP, _VP]),
+        "pt_maxnull_naive_batched": (ctypes.c_int, [_VP, i32, _VP, _VP,
+                                                    ctypes.POINTER(pt_naive_opts), _VP, _VP,
+                                                    _VP]),
         "pt_sync": (ctypes.c_int, [_VP]),
         "pt_t_obs": (ctypes.c_int, [_VP, _VP]),
         "pt_voxel_grid_index": (ctypes.c_int, [_VP, _VP]),
@@ -163,6 +166,26 @@ def pt_maxnull_naive_ex(ctx, perms, opts, maxnull, argmax, counts=None):
     st = lib.pt_maxnull_naive_ex(ctx.handle, _ptr(perms), perms.shape[0], ctypes.byref(opts),
                                  _ptr(maxnull), _ptr(argmax), _ptr(counts))
     _check(st, ctx.handle)
+
+
+def pt_maxnull_naive_batched(ctxs, perms, opts, maxnull, argmax, counts=None):
+    """Lists of equal length: contexts, int32 perms (P_i x n_i), float32[P_i]
+    maxnull, int32[P_i] argmax and uint32[v_i] counts (or None)."""
+    lib = load()
+    m = len(ctxs)
+    if not (len(perms) == len(maxnull) == len(argmax) == m) or (counts is not None and
+                                                                 len(counts) != m):
+        raise ValueError("per-study lists must have one entry per context")
+    for p in perms:
+        assert p.dtype == torch.int32
+    h = (_VP * m)(*[c.handle for c in ctxs])
+    pp = (_VP * m)(*[_ptr(p) for p in perms])
+    P = (ctypes.c_int64 * m)(*[p.shape[0] for p in perms])
+    mx = (_VP * m)(*[_ptr(t) for t in maxnull])
+    am = (_VP * m)(*[_ptr(t) for t in argmax])
+    cn = None if counts is None else (_VP * m)(*[_ptr(t) for t in counts])
+    st = lib.pt_maxnull_naive_batched(h, m, pp, P, ctypes.byref(opts), mx, am, cn)
+    _check(st, None)
 
 
 def pt_sync(ctx):

@@ -108,6 +108,8 @@ namespace {
 std::atomic<int64_t> g_launches{0};
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launch_count(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_counter() { return g_launches.load(std::memory_order_relaxed); }
 
 void prof_begin(pt_ctx* ctx) {
   if (!ctx->profile) return;
@@ -210,6 +212,51 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
   }
 }
 
+pt_status pt_maxnull_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
+                                   const int32_t* const* perms, const int64_t* P,
+                                   const pt_naive_opts* opts, float* const* maxnull,
+                                   int32_t* const* argmax, uint32_t* const* counts) {
+  if (!ctxs || n_studies < 1 || n_studies > 4096 || !perms || !P || !maxnull || !argmax) {
+    pt::set_thread_error(
+        "pt_maxnull_naive_batched: need 1 <= n_studies <= 4096 and non-NULL arrays");
+    return PT_ERR_INVALID;
+  }
+  pt_ctx* lead = ctxs[0];
+  try {
+    pt_naive_opts o;
+    pt_naive_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_BF16X3 || o.two_sided < 0 ||
+        o.two_sided > 1) {
+      pt::set_thread_error("pt_maxnull_naive_batched: bad options");
+      return PT_ERR_INVALID;
+    }
+    for (int32_t i = 0; i < n_studies; ++i) {
+      if (!ctxs[i] || !perms[i] || !maxnull[i] || !argmax[i] || P[i] < 1 || P[i] > INT32_MAX) {
+        pt::set_thread_error("pt_maxnull_naive_batched: study " + std::to_string(i) +
+                             ": need ctx, perms, maxnull, argmax non-NULL and 1 <= P < 2^31");
+        return PT_ERR_INVALID;
+      }
+      for (int32_t j = 0; j < i; ++j)
+        if (ctxs[j] == ctxs[i]) {
+          pt::set_thread_error("pt_maxnull_naive_batched: a context appears twice");
+          return PT_ERR_INVALID;
+        }
+    }
+    if (cudaSetDevice(lead->device) != cudaSuccess) {
+      set_error(lead, "pt_maxnull_naive_batched: cudaSetDevice failed");
+      return PT_ERR_CUDA;
+    }
+    const pt_status s =
+        pt::naive_batched_impl(ctxs, n_studies, perms, P, o, maxnull, argmax, counts);
+    if (s != PT_OK) pt::set_thread_error(lead->last_error);
+    return s;
+  } catch (...) {
+    set_error(lead, "pt_maxnull_naive_batched: internal error");
+    return PT_ERR_CUDA;
+  }
+}
+
 pt_status pt_maxnull_naive(pt_ctx* ctx, const int32_t* perms, int64_t P, float* maxnull,
                            int32_t* argmax, uint32_t* counts) {
   return pt_maxnull_naive_ex(ctx, perms, P, nullptr, maxnull, argmax, counts);
@@ -295,6 +342,7 @@ void pt_destroy(pt_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  pt::batch_forget(ctx);
   for (auto& ev : ctx->ev_pending) ctx->ev_pool.push_back(ev);
   for (auto& ev : ctx->ev_pool) {
     cudaEventDestroy(ev.first);

@@ -76,6 +76,8 @@ namespace pt {
 
 void set_error(pt_ctx* ctx, const std::string& msg);
 void count_launch();
+void add_launch_count(int64_t k);
+int64_t launch_counter();
 // Event pair around the dominant kernel when profiling is on (no-ops otherwise).
 void prof_begin(pt_ctx* ctx);
 void prof_end(pt_ctx* ctx);
@@ -99,6 +101,11 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
 // ---- naive path (pt_naive.cu) ----
 pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,
                      float* maxnull, int32_t* argmax, uint32_t* counts);
+pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
+                             const int64_t* P, const pt_naive_opts& o, float* const* maxnull,
+                             int32_t* const* argmax, uint32_t* const* counts);
+// Drops a cached batched graph that names this context (from pt_destroy).
+void batch_forget(const pt_ctx* ctx);
 
 }  // namespace pt
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "pt_internal.h"
 
 namespace pt {
@@ -189,6 +191,20 @@ pt_status tc_reduce(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int t
 pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int write_mode,
                   float* out, int do_reduce, int two_sided, const float* u_obs,
                   unsigned long long* maxkey, uint32_t* cnt);
+
+// Several studies in one persistent launch per tile class. tc_batch_plan
+// encodes every study's tensor maps and work split (labels and workspaces of
+// every context already allocated) and uploads them; tc_batch_launch enqueues
+// one fused launch per tile class on lead->stream and can be graph-captured.
+struct TcGroup {
+  int NT, first, count, n_pad_max;
+  int64_t items;
+};
+pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int n,
+                        int precision, Buf& descbuf, std::vector<char>& host_desc,
+                        std::vector<TcGroup>& groups);
+pt_status tc_batch_launch(pt_ctx* lead, const Buf& descbuf, const std::vector<TcGroup>& groups,
+                          int precision, int two_sided);
 
 // ---- shared with pt_naive.cu ----
 pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout,

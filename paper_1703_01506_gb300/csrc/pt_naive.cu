@@ -10,6 +10,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "pt_internal.h"
 #include "pt_kernels.h"
@@ -397,6 +400,203 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
         ctx->cnt.as<uint32_t>(), ctx->v_valid, ctx->valid_map.as<int32_t>(), counts);
     PT_LAUNCH_CHECK(ctx);
   }
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pt_maxnull_naive_batched: every study's labels, one persistent fused launch
+// per tile class over all studies of that class, then every study's
+// finalisation. The sequence is captured once into a CUDA graph on a private
+// stream and replayed on the caller's stream while the arguments repeat.
+// ---------------------------------------------------------------------------
+namespace {
+struct BatchGraph {
+  std::vector<const void*> key;
+  cudaGraphExec_t exec = nullptr;
+  int device = -1;
+  cudaStream_t capture = nullptr;
+  int64_t launches = 0;  // kernels in the graph
+  Buf desc;
+  std::vector<char> host_desc;
+  std::vector<TcGroup> groups;
+  std::vector<const pt_ctx*> members;
+};
+std::mutex g_batch_mu;
+BatchGraph g_batch;
+
+void drop_graph_locked() {
+  if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+  g_batch.exec = nullptr;
+  g_batch.key.clear();
+  g_batch.members.clear();
+}
+}  // namespace
+
+// Called by pt_destroy: a cached graph must not outlive the buffers it names.
+void batch_forget(const pt_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (const pt_ctx* m : g_batch.members)
+    if (m == ctx) {
+      drop_graph_locked();
+      return;
+    }
+}
+
+static pt_status batched_enqueue(pt_ctx* lead, pt_ctx* const* ctxs, int n,
+                                 const int32_t* const* perms, const int64_t* P,
+                                 const pt_naive_opts& o, float* const* maxnull,
+                                 int32_t* const* argmax, uint32_t* const* counts) {
+  cudaStream_t st = lead->stream;
+  for (int i = 0; i < n; ++i) {
+    pt_ctx* c = ctxs[i];
+    PT_CUDA_TRY(lead, cudaMemsetAsync(c->maxkey.p, 0, sizeof(unsigned long long) * P[i], st));
+    PT_CUDA_TRY(lead, cudaMemsetAsync(c->cnt.p, 0, sizeof(uint32_t) * (c->v_valid + 1), st));
+    if (counts && counts[i])
+      PT_CUDA_TRY(lead, cudaMemsetAsync(counts[i], 0, sizeof(uint32_t) * c->v, st));
+    int64_t P_pad = 0;
+    pt_status s = build_labels(c, perms[i], P[i], 1, &P_pad);
+    if (s != PT_OK) return s;
+  }
+  pt_status s = tc_batch_launch(lead, g_batch.desc, g_batch.groups, o.precision, o.two_sided);
+  if (s != PT_OK) return s;
+  for (int i = 0; i < n; ++i) {
+    pt_ctx* c = ctxs[i];
+    finalize_max_kernel<<<grid_1d((P[i] + 7) / 8, 1), 256, 0, st>>>(
+        c->maxkey.as<unsigned long long>(), P[i], c->valid_map.as<int32_t>(), c->Xraw.as<float>(),
+        c->n, c->n1, c->n_pad, perms[i], o.two_sided, maxnull[i], argmax[i]);
+    PT_LAUNCH_CHECK(lead);
+    if (counts && counts[i] && c->v_valid > 0) {
+      scatter_counts_kernel<<<grid_1d(c->v_valid, 256), 256, 0, st>>>(
+          c->cnt.as<uint32_t>(), c->v_valid, c->valid_map.as<int32_t>(), counts[i]);
+      PT_LAUNCH_CHECK(lead);
+    }
+  }
+  return PT_OK;
+}
+
+// Everything a captured batch names: replay only while all of it is unchanged.
+static std::vector<const void*> batch_key(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
+                                          const int64_t* P, const pt_naive_opts& o,
+                                          float* const* maxnull, int32_t* const* argmax,
+                                          uint32_t* const* counts) {
+  std::vector<const void*> key;
+  key.push_back(reinterpret_cast<const void*>(intptr_t(n)));
+  key.push_back(reinterpret_cast<const void*>(intptr_t(o.precision * 2 + o.two_sided)));
+  key.push_back(reinterpret_cast<const void*>(intptr_t(ctxs[0]->device)));
+  for (int i = 0; i < n; ++i) {
+    key.push_back(ctxs[i]);
+    key.push_back(perms[i]);
+    key.push_back(reinterpret_cast<const void*>(intptr_t(P[i])));
+    key.push_back(maxnull[i]);
+    key.push_back(argmax[i]);
+    key.push_back(counts ? counts[i] : nullptr);
+    // workspaces named by the graph (a single-study call may have regrown them)
+    for (const Buf* b : {&ctxs[i]->labels, &ctxs[i]->maxkey, &ctxs[i]->cnt, &ctxs[i]->rowflag,
+                         &ctxs[i]->blockflag, &ctxs[i]->Xnb}) {
+      key.push_back(b->p);
+      key.push_back(reinterpret_cast<const void*>(b->bytes));
+    }
+  }
+  return key;
+}
+
+pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
+                             const int64_t* P, const pt_naive_opts& o, float* const* maxnull,
+                             int32_t* const* argmax, uint32_t* const* counts) {
+  pt_ctx* lead = ctxs[0];
+  if (o.precision == PT_PREC_FP32) {
+    set_error(lead, "pt_maxnull_naive_batched runs the tensor-core path (BF16x2 or BF16x3)");
+    return PT_ERR_UNSUPPORTED;
+  }
+  pt_status s = tc_supported(lead);
+  if (s != PT_OK) return s;
+
+  const std::vector<const void*> key = batch_key(ctxs, n, perms, P, o, maxnull, argmax, counts);
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (g_batch.exec && g_batch.key == key) {
+    PT_CUDA_TRY(lead, cudaGraphLaunch(g_batch.exec, lead->stream));
+    for (int64_t k = 0; k < g_batch.launches; ++k) count_launch();
+    return PT_OK;
+  }
+  drop_graph_locked();
+
+  // Everything that allocates or copies from the host happens before capture.
+  for (int i = 0; i < n; ++i) {
+    pt_ctx* c = ctxs[i];
+    if (c->device != lead->device) {
+      set_error(lead, "pt_maxnull_naive_batched: all contexts must be on one device");
+      return PT_ERR_INVALID;
+    }
+    if (c->v_valid > 0) {
+      s = ensure_xnb(c);
+      if (s != PT_OK) return s;
+    }
+    const int64_t P_pad = (P[i] + 127) / 128 * 128;
+    if (!c->maxkey.ensure(sizeof(unsigned long long) * P[i]) ||
+        !c->cnt.ensure(sizeof(uint32_t) * (c->v_valid + 1)) ||
+        !c->labels.ensure(sizeof(__nv_bfloat16) * size_t(P_pad) * c->n_pad) ||
+        !c->rowflag.ensure(P_pad) || !c->blockflag.ensure(P_pad / 128)) {
+      set_error(lead, "out of device memory (batched workspaces)");
+      return PT_ERR_NOMEM;
+    }
+    PT_CUDA_TRY(lead, cudaStreamSynchronize(c->stream));
+  }
+  s = tc_batch_plan(lead, ctxs, P, n, o.precision, g_batch.desc, g_batch.host_desc,
+                    g_batch.groups);
+  if (s != PT_OK) return s;
+  if (g_batch.device != lead->device) {
+    if (g_batch.capture) cudaStreamDestroy(g_batch.capture);
+    g_batch.capture = nullptr;
+    g_batch.device = lead->device;
+  }
+  if (!g_batch.capture)
+    PT_CUDA_TRY(lead, cudaStreamCreateWithFlags(&g_batch.capture, cudaStreamNonBlocking));
+
+  // Capture on the private stream (the caller's may be the legacy default stream).
+  std::vector<cudaStream_t> saved(n);
+  std::vector<bool> saved_prof(n);
+  for (int i = 0; i < n; ++i) {
+    saved[i] = ctxs[i]->stream;
+    saved_prof[i] = ctxs[i]->profile;
+    ctxs[i]->stream = g_batch.capture;
+    ctxs[i]->profile = false;
+  }
+  const cudaStream_t user = saved[0];
+  const int64_t before = launch_counter();
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamBeginCapture(g_batch.capture, cudaStreamCaptureModeThreadLocal);
+  if (ce == cudaSuccess) {
+    s = batched_enqueue(lead, ctxs, n, perms, P, o, maxnull, argmax, counts);
+    ce = cudaStreamEndCapture(g_batch.capture, &graph);
+  }
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->stream = saved[i];
+    ctxs[i]->profile = saved_prof[i];
+  }
+  const int64_t captured = launch_counter() - before;
+  add_launch_count(-captured);  // counted when the graph runs
+  if (s != PT_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (s == PT_OK) {
+      set_error(lead, std::string("graph capture: ") + cudaGetErrorString(ce));
+      s = PT_ERR_CUDA;
+    }
+    return s;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    set_error(lead, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    return PT_ERR_CUDA;
+  }
+  g_batch.exec = exec;
+  g_batch.key = batch_key(ctxs, n, perms, P, o, maxnull, argmax, counts);
+  g_batch.launches = captured;
+  g_batch.members.assign(ctxs, ctxs + n);
+  PT_CUDA_TRY(lead, cudaGraphLaunch(exec, user));
+  add_launch_count(captured);
   return PT_OK;
 }
 

@@ -23,6 +23,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
+#include <algorithm>
 
 #include "pt_internal.h"
 #include "pt_kernels.h"
@@ -656,6 +658,65 @@ pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int wri
                   unsigned long long* maxkey, uint32_t* cnt) {
   return tc_launch(ctx, Lb, P, precision, do_reduce, write_mode, two_sided, u_obs, maxkey, cnt,
                    out);
+}
+
+// ---------------------------------------------------------------------------
+// Several prepared studies in one persistent launch per tile class
+// ---------------------------------------------------------------------------
+pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int n,
+                        int precision, Buf& descbuf, std::vector<char>& host_desc,
+                        std::vector<TcGroup>& groups) {
+  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  std::vector<int> nt(n);
+  for (int i = 0; i < n; ++i) {
+    int stages = 0;
+    if (!choose_tile(ctxs[i]->n_pad, pieces, &nt[i], &stages)) {
+      set_error(lead, "tensor-core path: a study's n is too large for the resident data tile");
+      return PT_ERR_UNSUPPORTED;
+    }
+  }
+  host_desc.assign(sizeof(TcStudy) * size_t(n), 0);
+  TcStudy* hd = reinterpret_cast<TcStudy*>(host_desc.data());
+  groups.clear();
+  int filled = 0;
+  for (int NT : {256, 128, 64}) {
+    TcGroup g{NT, filled, 0, 16, 0};
+    for (int i = 0; i < n; ++i) {
+      pt_ctx* c = ctxs[i];
+      if (nt[i] != NT || c->v_valid < 1) continue;  // nothing to contract
+      if (!fill_study(c, c->labels.p, P[i], NT, 0, g.items, c->u_obs.as<float>(),
+                      c->maxkey.as<unsigned long long>(), c->cnt.as<uint32_t>(), nullptr,
+                      &hd[filled])) {
+        set_error(lead, "cuTensorMapEncodeTiled failed");
+        return PT_ERR_CUDA;
+      }
+      g.items += ((hd[filled].v + NT - 1) / NT) * hd[filled].n_chunks;
+      g.n_pad_max = std::max(g.n_pad_max, c->n_pad);
+      ++filled;
+      ++g.count;
+    }
+    if (g.count) groups.push_back(g);
+  }
+  if (!filled) return PT_OK;
+  if (!descbuf.ensure(sizeof(TcStudy) * size_t(filled))) {
+    set_error(lead, "out of device memory (descriptors)");
+    return PT_ERR_NOMEM;
+  }
+  PT_CUDA_TRY(lead, cudaMemcpyAsync(descbuf.p, hd, sizeof(TcStudy) * size_t(filled),
+                                    cudaMemcpyHostToDevice, lead->stream));
+  PT_CUDA_TRY(lead, cudaStreamSynchronize(lead->stream));
+  return PT_OK;
+}
+
+pt_status tc_batch_launch(pt_ctx* lead, const Buf& descbuf, const std::vector<TcGroup>& groups,
+                          int precision, int two_sided) {
+  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  for (const TcGroup& g : groups) {
+    pt_status s = launch_studies(lead, static_cast<const TcStudy*>(descbuf.p) + g.first, g.count,
+                                 g.items, g.NT, pieces, g.n_pad_max, 1, 0, two_sided, 0.0f, 0.0f);
+    if (s != PT_OK) return s;
+  }
+  return PT_OK;
 }
 
 }  // namespace pt
