@@ -1,9 +1,9 @@
-// pt_prepare: mask compaction, FP64 per-voxel moments, observed t, a raw
+// pt_prepare: mask compaction, per-voxel moments, observed t, a raw
 // voxel-major copy of the data; and, on first use, the unit-norm centred data
 // Xn in FP32 rows or as BF16 pieces (8x8 core-matrix layout read by the
 // tensor-core kernel).
 //
-// With x the n values of a voxel, mean and SS = sum (x - mean)^2 in FP64:
+// With x the n values of a voxel, mean and SS = sum (x - mean)^2 (see Moments):
 //   Xn_s = (x_s - mean) / sqrt(SS),      so sum_s Xn_s = 0 and sum_s Xn_s^2 = 1.
 // For a relabelling with group-1 sum u = sum_{s in G1} Xn_s the pooled t of
 // Eq. (5) is t = sqrt(k (n-2)) u / sqrt(1 - k u^2), k = 1/n1 + 1/n2, because
@@ -114,18 +114,43 @@ __global__ void iota64_kernel(int64_t* __restrict__ out, int64_t N) {
 }
 
 // ---------------------------------------------------------------------------
-// Moments. A CTA takes 32 consecutive mask voxels: the 32 x n values are staged
-// in shared memory (reads of X along a grid row are coalesced), written out as
-// voxel-major rows of Xraw, and reduced per voxel in FP64 in one pass of
-// shifted sums d = x - x_0 (exact in FP64 for FP32 inputs):
-//   S_g = sum_{s in G_g} d_s,  Q_g = sum_{s in G_g} d_s^2   (g = 1, 2 observed groups)
-//   mean = x_0 + (S_1 + S_2)/n,  SS = Q - S^2/n,  SS_w = sum_g (Q_g - S_g^2/n_g),
-//   t_obs = (S_1/n_1 - S_2/n_2) / sqrt(SS_w/(n-2) (1/n_1 + 1/n_2))      (Eq. (5)),
-//   u_obs = (S_1 - n_1 (S/n)) / sqrt(SS).
+// Moments. A CTA takes 32 consecutive mask voxels (lane = voxel); warp w loads
+// subjects w, w + 8, ... of them into shared memory (reads of X along a grid
+// row are coalesced) and the tile is written out as voxel-major rows of Xraw.
+// Per voxel the values are scaled by the power of two that brings max |x| into
+// [1, 2) (exact; no overflow of squares for any finite input), then reduced in
+// float-float arithmetic (an unevaluated pair h + l, about 44 significant
+// bits; FP64 throughput on this part is a small fraction of FP32):
+//   pass 1: S = sum_s y_s, mean = S / n                 (y = scaled x)
+//   pass 2: d = y - mean, D_g = sum_{G_g} d, Q_g = sum_{G_g} d^2  (g = 1, 2)
+// and finished in FP64 per voxel (the textbook corrected two-pass formulas):
+//   delta = (D_1 + D_2)/n,  SS = Q_1 + Q_2 - (D_1 + D_2) delta,
+//   A_g = D_g - n_g delta = sum_{G_g} (y - mean(y)),
+//   SS_w = sum_g (Q_g - D_g^2 / n_g),
+//   t_obs = (A_1/n_1 - A_2/n_2) / sqrt(SS_w/(n-2) (1/n_1 + 1/n_2))   (Eq. (5)),
+//   u_obs = A_1 / sqrt(SS).
+// t and u do not depend on the scale; mean and 1/sqrt(SS) are unscaled.
 // A voxel is degenerate (no t) exactly when all its values are equal.
-// ---------------------------------------------------------------------------
 constexpr int kMV = 32;  // voxels per CTA (one per lane)
 constexpr int kMW = 8;   // warps per CTA; warp w sums subjects s = w, w + 8, ...
+
+// s + e = a + b exactly (Knuth's branch-free two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (h, l) += (bh, bl), renormalised so that |l| <= ulp(h)/2.
+__device__ __forceinline__ void ff_acc(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+__device__ __forceinline__ double ff_d(float h, float l) { return double(h) + double(l); }
 
 __global__ void __launch_bounds__(32 * kMW)
     moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1, int n_pad,
@@ -134,61 +159,107 @@ __global__ void __launch_bounds__(32 * kMW)
                    float* __restrict__ u_obs_m, uint8_t* __restrict__ valid,
                    float* __restrict__ Xraw, uint32_t* __restrict__ status) {
   extern __shared__ float tile[];  // [n][kMV + 1]
-  __shared__ int64_t gidx[kMV];
-  __shared__ double part[kMW][4][kMV];
+  __shared__ float part[kMW][6][kMV];
   __shared__ uint32_t flags[kMW][kMV];
   constexpr int LD = kMV + 1;
   const int64_t j0 = int64_t(blockIdx.x) * kMV;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid < kMV) gidx[tid] = (j0 + tid < v) ? vox_grid[j0 + tid] : -1;
-  __syncthreads();
-  for (int idx = tid; idx < n * kMV; idx += blockDim.x) {
-    const int s = idx / kMV, l = idx - s * kMV;
-    const int64_t g = gidx[l];
-    tile[s * LD + l] = g >= 0 ? X[int64_t(s) * n_grid + g] : 0.0f;
+  const int64_t j = j0 + lane;
+  const int64_t g = j < v ? vox_grid[j] : -1;
+
+  // Load: lane = voxel; max |x| and the flags on the way.
+  const float x0f = g >= 0 ? X[g] : 0.0f;
+  float amax = 0.0f;
+  uint32_t fl = 0u;  // bit 0: non-finite seen, bit 1: a value differs from x_0
+  for (int s = warp; s < n; s += kMW) {
+    const float xf = g >= 0 ? X[int64_t(s) * n_grid + g] : 0.0f;
+    tile[s * LD + lane] = xf;
+    if (!isfinite(xf)) fl |= 1u;
+    if (xf != x0f) fl |= 2u;
+    amax = fmaxf(amax, fabsf(xf));
   }
+  part[warp][0][lane] = amax;
+  flags[warp][lane] = fl;
   __syncthreads();
   for (int idx = tid; idx < kMV * n_pad; idx += blockDim.x) {
     const int l = idx / n_pad, s = idx - l * n_pad;
     if (j0 + l < v) Xraw[(j0 + l) * n_pad + s] = s < n ? tile[s * LD + l] : 0.0f;
   }
-  // Partial shifted sums: lane = voxel, this warp's subjects. All lanes active.
-  {
-    const float x0f = tile[lane];
-    const double x0 = double(x0f);
-    double S1 = 0.0, S2 = 0.0, Q1 = 0.0, Q2 = 0.0;
-    uint32_t fl = 0u;  // bit 0: non-finite seen, bit 1: a value differs from x_0
-    for (int s = warp; s < n; s += kMW) {
-      const float xf = tile[s * LD + lane];
-      if (!isfinite(xf)) fl |= 1u;
-      if (xf != x0f) fl |= 2u;
-      const double d = double(xf) - x0;
-      if (s < n1) {
-        S1 += d;
-        Q1 = fma(d, d, Q1);
-      } else {
-        S2 += d;
-        Q2 = fma(d, d, Q2);
-      }
-    }
-    part[warp][0][lane] = S1;
-    part[warp][1][lane] = S2;
-    part[warp][2][lane] = Q1;
-    part[warp][3][lane] = Q2;
-    flags[warp][lane] = fl;
-  }
-  __syncthreads();
-  if (warp != 0) return;
-  const int64_t j = j0 + lane;
-  double S1 = 0.0, S2 = 0.0, Q1 = 0.0, Q2 = 0.0;
-  uint32_t fl = 0u;
+  fl = 0u;
+  amax = 0.0f;
+#pragma unroll
   for (int w = 0; w < kMW; ++w) {
-    S1 += part[w][0][lane];
-    S2 += part[w][1][lane];
-    Q1 += part[w][2][lane];
-    Q2 += part[w][3][lane];
+    amax = fmaxf(amax, part[w][0][lane]);
     fl |= flags[w][lane];
   }
+  if (fl & 1u) amax = 1.0f;  // reported below; keep the arithmetic finite
+  int ex = int((__float_as_uint(amax) >> 23) & 0xffu) - 127;
+  ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
+  const float scale = __uint_as_float(uint32_t(127 - ex) << 23);  // 2^-ex, exact
+
+  // Pass 1: sum of the scaled values, then the float-float mean.
+  float Sh = 0.0f, Sl = 0.0f;
+  for (int s = warp; s < n; s += kMW) ff_acc(Sh, Sl, tile[s * LD + lane] * scale, 0.0f);
+  __syncthreads();  // everyone has read part[.][0]
+  part[warp][0][lane] = Sh;
+  part[warp][1][lane] = Sl;
+  __syncthreads();
+  Sh = 0.0f;
+  Sl = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kMW; ++w) ff_acc(Sh, Sl, part[w][0][lane], part[w][1][lane]);
+  const float nf = float(n);
+  const float q1 = Sh / nf;
+  const float q2 = (fmaf(-q1, nf, Sh) + Sl) / nf;  // the residual Sh - q1 n is exact
+  float mh, ml;
+  two_sum(q1, q2, mh, ml);
+
+  // Pass 2: centred sums per observed group.
+  float D1h = 0.f, D1l = 0.f, D2h = 0.f, D2l = 0.f, Q1h = 0.f, Q1l = 0.f, Q2h = 0.f, Q2l = 0.f;
+  for (int s = warp; s < n; s += kMW) {
+    float dh, dl;
+    two_sum(tile[s * LD + lane] * scale, -mh, dh, dl);
+    dl -= ml;
+    const float t = dh + dl;  // renormalise d
+    dl = dl - (t - dh);
+    dh = t;
+    const float p = dh * dh;
+    const float pe = fmaf(2.0f * dh, dl, fmaf(dh, dh, -p));
+    if (s < n1) {
+      ff_acc(D1h, D1l, dh, dl);
+      ff_acc(Q1h, Q1l, p, pe);
+    } else {
+      ff_acc(D2h, D2l, dh, dl);
+      ff_acc(Q2h, Q2l, p, pe);
+    }
+  }
+  __syncthreads();  // everyone has read the pass-1 partials
+  float* pp = &part[warp][0][0];
+  pp[0 * kMV + lane] = D1h;
+  pp[1 * kMV + lane] = D1l;
+  pp[2 * kMV + lane] = D2h;
+  pp[3 * kMV + lane] = D2l;
+  pp[4 * kMV + lane] = Q1h;
+  pp[5 * kMV + lane] = Q1l;
+  __syncthreads();
+  // Q2 stays in registers: a second round of partials after the first is read.
+  if (warp == 0) {
+    D1h = D1l = D2h = D2l = Q1h = Q1l = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kMW; ++w) {
+      ff_acc(D1h, D1l, part[w][0][lane], part[w][1][lane]);
+      ff_acc(D2h, D2l, part[w][2][lane], part[w][3][lane]);
+      ff_acc(Q1h, Q1l, part[w][4][lane], part[w][5][lane]);
+    }
+  }
+  __syncthreads();
+  part[warp][0][lane] = Q2h;
+  part[warp][1][lane] = Q2l;
+  __syncthreads();
+  if (warp != 0) return;
+  Q2h = Q2l = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kMW; ++w) ff_acc(Q2h, Q2l, part[w][0][lane], part[w][1][lane]);
   if (j >= v) return;
   if (fl & 1u) {
     atomicOr(status, kErrBadData);
@@ -197,14 +268,16 @@ __global__ void __launch_bounds__(32 * kMW)
     return;
   }
   const int n2 = n - n1;
-  const double x0 = double(tile[lane]);
-  const double S = S1 + S2, Q = Q1 + Q2;
-  const double md = S / n;
-  const double SS = Q - S * md;
-  double SSw = (Q1 - S1 * (S1 / n1)) + (Q2 - S2 * (S2 / n2));
+  const double D1 = ff_d(D1h, D1l), D2 = ff_d(D2h, D2l);
+  const double Q1 = ff_d(Q1h, Q1l), Q2 = ff_d(Q2h, Q2l);
+  const double delta = (D1 + D2) / n;
+  const double SS = (Q1 + Q2) - (D1 + D2) * delta;
+  const double A1 = D1 - n1 * delta, A2 = D2 - n2 * delta;
+  double SSw = (Q1 - D1 * D1 / n1) + (Q2 - D2 * D2 / n2);
+  const double inv_scale = 1.0 / double(scale);  // exact power of two
   const bool ok = (fl & 2u) && SS > 0.0;
   valid[j] = ok ? 1 : 0;
-  mean_out[j] = x0 + md;
+  mean_out[j] = (ff_d(mh, ml) + delta) * inv_scale;
   if (!ok) {
     inv_norm_out[j] = 0.0;
     t_obs[j] = nan("");
@@ -212,11 +285,11 @@ __global__ void __launch_bounds__(32 * kMW)
     return;
   }
   if (SSw < 0.0) SSw = 0.0;
-  const double inv = 1.0 / sqrt(SS);
-  inv_norm_out[j] = inv;
+  const double rs = 1.0 / sqrt(SS);
+  inv_norm_out[j] = rs * double(scale);
   const double k = 1.0 / n1 + 1.0 / n2;
-  t_obs[j] = (S1 / n1 - S2 / n2) / sqrt(SSw / double(n - 2) * k);
-  u_obs_m[j] = float((S1 - n1 * md) * inv);
+  t_obs[j] = (A1 / n1 - A2 / n2) / sqrt(SSw / double(n - 2) * k);
+  u_obs_m[j] = float(A1 * rs);
 }
 
 // Per compact voxel: the FP64 mean and 1/sqrt(SS) as float pairs (hi + lo),
