@@ -162,13 +162,16 @@ __device__ __forceinline__ float cols_reduce(const uint32_t (&r)[CW], const floa
   return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
 }
 
-template <int NT, bool TWO, int PIECES>
+// WRITE = false: reduce only (the NaivePT path); true: rows of u or t are
+// written (training rows of Alg. 2), optionally also reduced.
+template <int NT, bool TWO, int PIECES, bool WRITE>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_contract_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int CW = NT / 4;                 // accumulator columns per epilogue thread
   constexpr int CHK = CW < 32 ? CW : 32;     // columns per TMEM load
   constexpr int NCH = CW / CHK;              // loads per block
+  const bool do_reduce = !WRITE || a.do_reduce;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = a.stages;
   uint8_t* xs = smem;
@@ -346,14 +349,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       epi_bar();
       for (int c = etid; c < NT; c += 32 * kEpiWarps) {
         float x = INFINITY;
-        if (a.do_reduce && v0 + c < V) {
+        if (do_reduce && v0 + c < V) {
           x = u_obs[v0 + c];
           if (TWO) x = fabsf(x);
         }
         su[c] = x;
       }
       for (int64_t c = etid; c < b1 - b0; c += 32 * kEpiWarps)
-        sbf[c] = (a.do_reduce && st.blockflag[b0 + c]) || (b0 + c + 1) * 128 > Pn ? 1 : 0;
+        sbf[c] = (do_reduce && st.blockflag[b0 + c]) || (b0 + c + 1) * 128 > Pn ? 1 : 0;
       epi_bar();
       uint32_t c8[CW / 4];
 #pragma unroll
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       unsigned long long gkey_next = 0ull;
       {
         const int64_t rowf = (b0 + rot % nb) * 128 + quad * 32 + lane;
-        if (a.do_reduce && rowf < Pn) gkey_next = __ldcg(&maxkey[rowf]);
+        if (do_reduce && rowf < Pn) gkey_next = __ldcg(&maxkey[rowf]);
       }
       for (int64_t kb = 0; kb < nb; ++kb, ++j) {
         // Blocks run in a per-CTA rotated order so that the CTAs do not all
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           int64_t bn = bi + 1;
           if (bn >= nb) bn -= nb;
           const int64_t rown = (b0 + bn) * 128 + quad * 32 + lane;
-          if (a.do_reduce && rown < Pn) gkey_next = __ldcg(&maxkey[rown]);
+          if (do_reduce && rown < Pn) gkey_next = __ldcg(&maxkey[rown]);
         }
         const bool ragged = ragged_cols || sbf[bi];
         if (ok && !mbar_wait(BAR(2 + abuf), aph, a.status, abort_flag)) ok = false;
@@ -387,16 +390,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
         const bool row_ok = row < Pn;
-        const bool cnt_ok = row_ok && !(ragged && a.do_reduce && rowflag[row]);
+        const bool cnt_ok = row_ok && !(ragged && do_reduce && rowflag[row]);
+        // Running row maximum over the chunks and, for a maximum that can beat
+        // the row's current global key, its first column (found while the
+        // chunk is still in registers).
+        const float gval = gkey != 0ull ? unpack_key_value(gkey) : -INFINITY;
         float best = -INFINITY;
-        int bestc = 0;
+        int64_t bestcol = -1;
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
           uint32_t r[CHK];
           tc_ld_cols<CHK>(taddr + c * CHK, r);
           tc_wait_ld();
           const int64_t g0 = gcol0 + c * CHK;
-          if (a.write_mode && row_ok) {
+          if (WRITE && a.write_mode && row_ok) {
             float* dst = st.uout + row * V;
 #pragma unroll
             for (int jj = 0; jj < CHK; ++jj) {
@@ -411,52 +418,39 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
-          if (a.do_reduce) {
+          if (do_reduce) {
             uint32_t(&cc)[CHK / 4] = *reinterpret_cast<uint32_t(*)[CHK / 4]>(&c8[c * (CHK / 4)]);
             const float cm =
                 ragged ? cols_reduce<CHK, TWO, true>(r, su + colbase + c * CHK, g0, V, row_ok,
                                                      cnt_ok, cc)
                        : cols_reduce<CHK, TWO, false>(r, su + colbase + c * CHK, g0, V, true,
                                                       true, cc);
+            const bool cand = row_ok && cm > best && cm >= gval && cm > -INFINITY;
             if (cm > best) {
               best = cm;
-              bestc = c;
+              bestcol = -1;
+            }
+            if (__any_sync(0xffffffffu, cand) && cand) {
+              int jj_best = -1;
+#pragma unroll
+              for (int jj = CHK - 1; jj >= 0; --jj) {
+                float sv = __uint_as_float(r[jj]);
+                if (TWO) sv = fabsf(sv);
+                if (sv == cm && g0 + jj < V) jj_best = jj;
+              }
+              bestcol = jj_best >= 0 ? g0 + jj_best : -1;
             }
           }
         }
-        if (a.do_reduce) {
-          // Candidate for the global row maximum: find its column and publish.
-          bool need = row_ok && best > -INFINITY;
-          if (need && gkey != 0ull) need = best >= unpack_key_value(gkey);
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) {
-            const bool mine = need && bestc == c;
-            if (__any_sync(0xffffffffu, mine)) {
-              uint32_t r[CHK];
-              tc_ld_cols<CHK>(taddr + c * CHK, r);
-              tc_wait_ld();
-              if (mine) {
-                const int64_t g0 = gcol0 + c * CHK;
-                int jj_best = -1;
-#pragma unroll
-                for (int jj = CHK - 1; jj >= 0; --jj) {
-                  float sv = __uint_as_float(r[jj]);
-                  if (TWO) sv = fabsf(sv);
-                  if (sv == best && g0 + jj < V) jj_best = jj;
-                }
-                if (jj_best >= 0) {
-                  const unsigned long long key = pack_key(best, uint32_t(g0 + jj_best));
-                  if (key > gkey) atomicMax(&maxkey[row], key);
-                }
-              }
-            }
-          }
+        if (do_reduce && bestcol >= 0) {
+          const unsigned long long key = pack_key(best, uint32_t(bestcol));
+          if (key > gkey) atomicMax(&maxkey[row], key);
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(BAR(4 + abuf));
       }
-      if (ok && a.do_reduce) flush_counts8<CW>(c8, lane, gcol0, V, st.cnt);
+      if (ok && do_reduce) flush_counts8<CW>(c8, lane, gcol0, V, st.cnt);
     }
   }
 #undef LFULL
@@ -512,7 +506,10 @@ int num_sms(int dev) {
 
 template <int NT, bool TWO>
 pt_status launch_nt(pt_ctx* ctx, const TcArgs& a, int pieces, int grid, int smem) {
-  auto kern = pieces == 2 ? tc_contract_kernel<NT, TWO, 2> : tc_contract_kernel<NT, TWO, 3>;
+  auto kern = a.write_mode ? (pieces == 2 ? tc_contract_kernel<NT, TWO, 2, true>
+                                          : tc_contract_kernel<NT, TWO, 3, true>)
+                           : (pieces == 2 ? tc_contract_kernel<NT, TWO, 2, false>
+                                          : tc_contract_kernel<NT, TWO, 3, false>);
   PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   if (a.do_reduce) prof_begin(ctx);
   kern<<<grid, kThreads, smem, ctx->stream>>>(a);
