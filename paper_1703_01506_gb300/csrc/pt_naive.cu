@@ -283,16 +283,24 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
+    // FP64 divisions and the square root on one lane only (FP64 throughput
+    // is shared by every active lane).
     const int n2 = n - n1;
-    const double m1 = s1 / n1, m2 = s2 / n2;
+    double m1 = 0.0, m2 = 0.0;
+    if (lane == 0) {
+      m1 = s1 / n1;
+      m2 = s2 / n2;
+    }
+    m1 = __shfl_sync(0xffffffffu, m1, 0);
+    m2 = __shfl_sync(0xffffffffu, m2, 0);
     double ss = 0.0;
     for (int s = lane; s < n; s += 32) {
       const double d = double(x[s]) - (((g1[s >> 5] >> (s & 31)) & 1u) ? m1 : m2);
       ss += d * d;
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const double t = (m1 - m2) / sqrt(ss / double(n - 2) * (1.0 / n1 + 1.0 / n2));
     if (lane == 0) {
+      const double t = (m1 - m2) / sqrt(ss / double(n - 2) * (1.0 / n1 + 1.0 / n2));
       maxnull[i] = float(two_sided ? fabs(t) : t);
       argmax[i] = valid_map[c];
     }

@@ -152,8 +152,14 @@ __device__ __forceinline__ void ff_acc(float& h, float& l, float bh, float bl) {
 
 __device__ __forceinline__ double ff_d(float h, float l) { return double(h) + double(l); }
 
+// 1/n, 1/n_1, 1/n_2 and (1/n_1 + 1/n_2)/(n - 2), rounded once on the host.
+struct MomentRecips {
+  double rn, rn1, rn2, kw;
+};
+
 __global__ void __launch_bounds__(32 * kMW)
     moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1, int n_pad,
+                   const MomentRecips rc,
                    const int64_t* __restrict__ vox_grid, int64_t v, double* __restrict__ mean_out,
                    double* __restrict__ inv_norm_out, double* __restrict__ t_obs,
                    float* __restrict__ u_obs_m, uint8_t* __restrict__ valid,
@@ -267,13 +273,15 @@ __global__ void __launch_bounds__(32 * kMW)
     t_obs[j] = nan("");
     return;
   }
+  // FP64 from here on, with the reciprocals of n, n_1, n_2 and k/(n-2) passed
+  // in and reciprocal square roots (FP64 divides are many FP64 operations).
   const int n2 = n - n1;
   const double D1 = ff_d(D1h, D1l), D2 = ff_d(D2h, D2l);
   const double Q1 = ff_d(Q1h, Q1l), Q2 = ff_d(Q2h, Q2l);
-  const double delta = (D1 + D2) / n;
+  const double delta = (D1 + D2) * rc.rn;
   const double SS = (Q1 + Q2) - (D1 + D2) * delta;
   const double A1 = D1 - n1 * delta, A2 = D2 - n2 * delta;
-  double SSw = (Q1 - D1 * D1 / n1) + (Q2 - D2 * D2 / n2);
+  double SSw = (Q1 - D1 * D1 * rc.rn1) + (Q2 - D2 * D2 * rc.rn2);
   const double inv_scale = 1.0 / double(scale);  // exact power of two
   const bool ok = (fl & 2u) && SS > 0.0;
   valid[j] = ok ? 1 : 0;
@@ -285,10 +293,9 @@ __global__ void __launch_bounds__(32 * kMW)
     return;
   }
   if (SSw < 0.0) SSw = 0.0;
-  const double rs = 1.0 / sqrt(SS);
+  const double rs = rsqrt(SS);
   inv_norm_out[j] = rs * double(scale);
-  const double k = 1.0 / n1 + 1.0 / n2;
-  t_obs[j] = (A1 / n1 - A2 / n2) / sqrt(SSw / double(n - 2) * k);
+  t_obs[j] = (A1 * rc.rn1 - A2 * rc.rn2) * rsqrt(SSw * rc.kw);
   u_obs_m[j] = float(A1 * rs);
 }
 
@@ -477,7 +484,9 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
       PT_CUDA_TRY(ctx, cudaFuncSetAttribute(moments_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     moments_kernel<<<unsigned((v + kMV - 1) / kMV), 32 * kMW, smem, st>>>(
-        X, ctx->n_grid, ctx->n, ctx->n1, n_pad, ctx->vox_grid.as<int64_t>(), v, mean, inv_norm,
+        X, ctx->n_grid, ctx->n, ctx->n1, n_pad,
+        MomentRecips{1.0 / ctx->n, 1.0 / ctx->n1, 1.0 / ctx->n2, ctx->k / (ctx->n - 2)},
+        ctx->vox_grid.as<int64_t>(), v, mean, inv_norm,
         ctx->t_obs64.as<double>(), u_obs_m, valid, ctx->Xraw.as<float>(),
         ctx->status.as<uint32_t>());
     PT_LAUNCH_CHECK(ctx);
