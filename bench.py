@@ -1,14 +1,20 @@
-"""Benchmark: max-null permutation testing (NaivePT) on one or more GB300s.
+"""Benchmark: max-null permutation testing, NaivePT and RapidPT, on GB300s.
 
-One step = the whole hot path on one batch: pt_prepare (per-voxel FP64
+One step = the whole NaivePT hot path on one batch: pt_prepare (per-voxel
 moments, unit-norm centring, BF16 split) + pt_maxnull_naive (labels, fused
 tensor-core contraction + max-null + exceedance counts, finalise) for the
 brain-shaped workload n=100 (50/50), 91x109x91 grid masked to 231,719 voxels,
 10,000 relabellings. Metric: T entries (relabelling x voxel t statistics) per
 second. Inputs (X 361 MB, BF16 data pieces 156 MB) are larger than L2.
 
+At one GPU the line also carries "rapidpt": RapidPT (Alg. 2: training rows,
+subspace tracking, sampled recovery) against NaivePT on the RapidPT workload
+(n=200, 500,000 voxels, 100,000 relabellings, r=50, 400 training rows, 0.35%
+sampling): each method's max-null wall time, and RapidPT's accuracy against
+the exhaustive max-null (KL divergence, FWER 0.05/0.01 thresholds).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision bf16x3|bf16x2|fp32]
+                  [--precision bf16x3|bf16x2|fp32] [--no-rapid] [--no-cpu-baseline]
 
 With N > 1 it runs under torch.distributed.run, one rank per GPU: every rank
 takes its own 10,000 relabellings of the same study (weak scaling, no data
@@ -29,7 +35,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "T entries/s (perm x voxel t) & max-null wall time, NaivePT, 1 GB300"
+METRIC = "T entries/s (perm x voxel t) & max-null wall time, RapidPT vs NaivePT, 1 GB300"
 WORKLOAD = "brain_n100_v232k"
 PREC = {"fp32": 0, "bf16x2": 1, "bf16x3": 2}
 
@@ -193,6 +199,101 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def hist_kl(p_samples, q_samples, bins=100):
+    """KL(P || Q) of two max-null samples over a common histogram (empty
+    bins of Q smoothed by one count): the accuracy summary of the paper's
+    Sec. 5.5, computed on the host."""
+    lo = float(min(p_samples.min(), q_samples.min()))
+    hi = float(max(p_samples.max(), q_samples.max()))
+    hp, edges = np.histogram(p_samples, bins=bins, range=(lo, hi))
+    hq, _ = np.histogram(q_samples, bins=edges)
+    pp = (hp + 1e-12) / hp.sum()
+    qq = (hq + 1.0) / (hq + 1.0).sum()
+    m = hp > 0
+    return float(np.sum(pp[m] * np.log(pp[m] / qq[m])))
+
+
+def rapid_leg(dev, B, synth, torch):
+    """RapidPT vs NaivePT max-null wall time on the RapidPT workload (n=200,
+    500,000 voxels, 100,000 relabellings, r=50, 400 training rows, 0.35%
+    sampling): each method's time from pt_prepare to the max-null vector, with
+    the exhaustive NaivePT result as the accuracy reference."""
+    name = "brain_n200_v500k"
+    w = synth.workload(name, device=dev)
+    X, mask, n1 = w["X"], w["mask"], w["n1"]
+    perms = torch.as_tensor(w["perms"]).to(dev)
+    P, r, ell, eta = perms.shape[0], w["rank"], w["n_train"], w["sample_rate"]
+    stream = torch.cuda.current_stream(dev)
+    mx_naive = torch.empty(P, dtype=torch.float32, device=dev)
+    am = torch.empty(P, dtype=torch.int32, device=dev)
+
+    def naive_run():
+        c = B.pt_prepare(X, n1, mask, stream=stream)
+        B.pt_maxnull_naive_ex(c, perms, B.naive_opts(2), mx_naive, am, None)
+        B.pt_sync(c)
+        v = B.pt_num_valid_voxels(c)
+        c.close()
+        return v
+
+    opts = B.rapid_opts()
+    mx_rapid = torch.empty(P, dtype=torch.float32, device=dev)
+    phase = {}
+
+    def rapid_run():
+        t0 = time.perf_counter()
+        c = B.pt_prepare(X, n1, mask, stream=stream)
+        V = B.pt_num_valid_voxels(c)
+        U = torch.empty((V, r), dtype=torch.float32, device=dev)
+        t1 = time.perf_counter()
+        info = B.pt_rapid_train(c, perms, ell, r, eta, opts, U, mx_rapid[:ell])
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        B.pt_rapid_recover(c, perms, ell, U, r, eta, info.sigma, info.mu, opts, mx_rapid[ell:])
+        torch.cuda.synchronize(dev)
+        t3 = time.perf_counter()
+        c.close()
+        phase.update(prepare_ms=(t1 - t0) * 1e3, train_ms=(t2 - t1) * 1e3,
+                     recover_ms=(t3 - t2) * 1e3, sigma=info.sigma, mu=info.mu,
+                     train_steps=int(info.train_steps), m_per_perm=int(info.m_per_perm))
+
+    def timed(fn, reps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1) / reps
+
+    v = naive_run()
+    naive_ms = timed(naive_run, 3)
+    rapid_run()
+    rapid_ms = timed(rapid_run, 1)
+    a = mx_naive.cpu().numpy().astype(np.float64)
+    b = mx_rapid.cpu().numpy().astype(np.float64)
+    thr = {}
+    for alpha in (0.05, 0.01):
+        ta, tb = np.quantile(a, 1 - alpha), np.quantile(b, 1 - alpha)
+        thr["fwer%g" % alpha] = {"naive": float(ta), "rapid": float(tb),
+                                 "rel_diff": float((tb - ta) / ta)}
+    return {
+        "workload": "%s: n=200 (100/100), %d voxels, no signal, P=%d, r=%d, n_train=%d, "
+                    "sample_rate=%g" % (name, v, P, r, ell, eta),
+        "naive_ms": naive_ms, "rapid_ms": rapid_ms, "rapid_over_naive": rapid_ms / naive_ms,
+        "naive_entries_per_s": P * v / (naive_ms * 1e-3),
+        "rapid_entries_per_s": P * v / (rapid_ms * 1e-3),
+        "rapid_phases_ms": {k: phase[k] for k in ("prepare_ms", "train_ms", "recover_ms")},
+        "rapid_info": {k: phase[k] for k in ("sigma", "mu", "train_steps", "m_per_perm")},
+        "opts": {"train_passes": opts.train_passes, "qr_every": opts.qr_every,
+                 "admm_iters": opts.admm_iters, "admm_rho": opts.admm_rho,
+                 "shift_mode": opts.shift_mode, "precision": "bf16x3"},
+        "accuracy_vs_naive": {"kl": hist_kl(a, b), **thr},
+        "timing": "device events; NaivePT 3 runs, RapidPT 1 run after 1 warm-up each",
+    }
 
 
 def run_ours(args):
@@ -364,6 +465,8 @@ def run_ours(args):
         "kernel_launches_per_step": launches / args.steps,
         "maxnull_wall_ms": ms,
     }
+    if ws == 1 and not args.no_rapid:
+        line["rapidpt"] = rapid_leg(dev, B, synth, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         Xm = X[:, mask.bool()].cpu().numpy()
         rate, rows, dt, cores = oracle_sample(Xm, n1, perms_np, seconds_target=15.0)
@@ -384,6 +487,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rapid", action="store_true",
+                    help="skip the RapidPT vs NaivePT leg (n=200, 500k voxels, 1e5 relabellings)")
     ap.add_argument("--quick", action="store_true",
                     help="device-timed steps only (no e2e, no CPU leg): for profiler runs")
     args = ap.parse_args()

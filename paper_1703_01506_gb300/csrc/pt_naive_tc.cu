@@ -41,7 +41,7 @@ constexpr int kMaxBlocksPerItem = 255;  // per-thread 8-bit exceedance counters
 // One study (one prepared context and its relabellings) of a launch. Launches
 // with several studies (pt_maxnull_naive_batched) walk the concatenation of
 // their work items; tensor maps live in global memory with the descriptor.
-struct alignas(64) TcStudy {
+struct TcStudy {  // CUtensorMap members carry their own alignment
   CUtensorMap tmL;  // labels, [P_pad * n_pad / 256][256] BF16 view
   CUtensorMap tmX;  // data pieces, [3 * v_pad * n_pad / 256][256] BF16 view
   int n_pad, ksteps;

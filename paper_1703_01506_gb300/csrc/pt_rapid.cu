@@ -24,6 +24,7 @@
 // Random numbers: Philox4x32-10 (Salmon et al., SC 2011) keyed by the seed,
 // counters (a, b, c, tag): normals by Box-Muller from the first two words,
 // voxel indices as floor((x1 2^32 + x0) v / 2^64).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,10 +51,11 @@ __global__ void simt_contract_kernel(const float* L, const float* Xn, int n_pad,
                                      const float* u_obs, const uint8_t* rowflag,
                                      unsigned long long* maxkey, uint32_t* cnt, float* uout);
 
+namespace cg = cooperative_groups;
+
 namespace {
 
 constexpr uint32_t TAG_U0 = 1, TAG_TRAIN = 2, TAG_REC = 3, TAG_NOISE = 4, TAG_SHIFT = 5;
-constexpr int kFitThreads = 1024;
 constexpr int kMaxRank = 128;
 constexpr float kNoiseBound = 6.6604f;  // sqrt(-2 ln 2^-32) rounded up: |z| of every draw
 
@@ -91,67 +93,105 @@ __device__ __forceinline__ uint32_t draw_index(uint32_t k0, uint32_t k1, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Block-level l1 weight solve (1024 threads). A: m x RP (row-major, padded
-// columns zero), b: m. s, y: m scratch. Shared: G, Gi (RP x RP), red (32 x RP),
-// stage (32 x RP), wv, rhs (RP). Leaves w in wv.
+// Cluster l1 weight solve (Sec. 4.1 / 4.2, the Complete step). The m sampled
+// rows are split over the CL CTAs of a thread-block cluster: each CTA keeps
+// its rows of A = U_Omega and of b, s, y, x in shared memory, and the R-length
+// reductions (Gram matrix, A^T x, A^T r) are summed across the cluster
+// through distributed shared memory, in rank order, so every CTA holds
+// bit-identical sums and hence the same weights w.
 // ---------------------------------------------------------------------------
-// Rows of A staged per Gram step: kStageFloats / RP.
-constexpr int kStageFloats = 8192;
+constexpr int kCluThreads = 512;  // 16 warps per CTA
+constexpr int kCluWarps = kCluThreads / 32;
 
-struct FitSmem {
-  float* G;
-  float* Gi;
-  float* red;
-  float* stage;
-  float* wv;
-  float* rhs;
-  float* scal;  // 8 scalars
+struct CluSmem {
+  float* A;      // mloc x RS, RS = RP + 4 (16-byte rows; row-wise float4 reads conflict-free)
+  float* b;      // mloc each: b, s, y, x
+  float* s;
+  float* y;
+  float* x;
+  int32_t* idx;  // mloc sampled voxel of each local row
+  float* G;      // R x R
+  float* Gi;     // R x R
+  float* Gp;     // R x RG (RG = R rounded up to 4), upper triangle: this CTA's Gram
+                 // partial, read by the whole cluster in float4 steps
+  float* slot;   // 2 x kSlot: this CTA's partial vectors (parity-alternated)
+  float* red;    // kCluWarps x RP cross-warp partials
+  float* vec;    // kSlot: a cluster sum
+  float* wv;     // RP: weights
+  float* misc;   // 8 scalars, then one partial per warp
+  float* Lrow;   // n_pad labels of the relabelling (recovery)
 };
+constexpr int kSlot = kMaxRank + 8;
 
-__device__ void carve_fit_smem(float* base, int RP, FitSmem& f) {
-  f.G = base;
-  f.Gi = f.G + RP * RP;
-  f.red = f.Gi + RP * RP;
-  f.stage = f.red + 32 * RP;
-  f.wv = f.stage + kStageFloats;
-  f.rhs = f.wv + RP;
-  f.scal = f.rhs + RP;
+__host__ __device__ inline size_t clu_carve(float* base, int mloc, int R, int RP, int n_pad,
+                                            CluSmem* f) {
+  const int RS = RP + 4;
+  size_t o = 0;
+  auto take = [&](size_t nfl) {
+    float* p = base ? base + o : nullptr;
+    o += (nfl + 3) / 4 * 4;  // keep 16-byte alignment
+    return p;
+  };
+  CluSmem t;
+  t.A = take(size_t(mloc) * RS);
+  t.b = take(mloc);
+  t.s = take(mloc);
+  t.y = take(mloc);
+  t.x = take(mloc);
+  t.idx = reinterpret_cast<int32_t*>(take(mloc));
+  t.G = take(size_t(R) * R);
+  t.Gi = take(size_t(R) * R);
+  t.Gp = take(size_t(R) * ((R + 3) / 4 * 4));
+  t.slot = take(2 * kSlot);
+  t.red = take(size_t(kCluWarps) * RP);
+  t.vec = take(kSlot);
+  t.wv = take(RP);
+  t.misc = take(8 + kCluWarps);
+  t.Lrow = take(n_pad);
+  if (f) *f = t;
+  return o * sizeof(float);
 }
 
-// The fit's m-length vectors (b, s, y, x) live in shared memory up to this m.
-constexpr int kSmemVecM = 4096;
+// sum over the cluster's CTAs, in rank order, of p[e] (p in this CTA's shared
+// memory, mapped to each rank's copy); the loads are all issued before the
+// adds so their distributed-shared-memory latencies overlap.
+constexpr int kMaxCluster = 16;
+__device__ __forceinline__ float clu_gather_sum(cg::cluster_group& cl, const float* p, int e,
+                                                int CL) {
+  float t[kMaxCluster];
+#pragma unroll
+  for (int r = 0; r < kMaxCluster; ++r)
+    t[r] = r < CL ? cl.map_shared_rank(const_cast<float*>(p), r)[e] : 0.0f;
+  float sum = 0.0f;
+#pragma unroll
+  for (int r = 0; r < kMaxCluster; ++r)
+    if (r < CL) sum += t[r];
+  return sum;
+}
 
-// out[c] = sum_q A[q][c] * x[q] for c < R (warps split q, lanes split c; four
-// rows in flight per warp so the loads from L2 overlap).
+// Sum over the cluster's CTAs (rank order) of slot[par][0..len) into vec.
+__device__ __forceinline__ void clu_sum(cg::cluster_group& cl, const CluSmem& f, int& par,
+                                        int len, int CL) {
+  __syncthreads();
+  cl.sync();
+  float* mine = f.slot + par * kSlot;
+  for (int c = threadIdx.x; c < len; c += blockDim.x) f.vec[c] = clu_gather_sum(cl, mine, c, CL);
+  par ^= 1;
+  __syncthreads();
+}
+
+// slot[par][c] = sum over local rows q of A[q][c] x[q], c < R.
 template <int RP>
-__device__ void block_AtX(const float* __restrict__ A, int m, int R, const float* __restrict__ x,
-                          float* red, float* out) {
+__device__ __forceinline__ void clu_AtX(const CluSmem& f, int mloc, int R, const float* x,
+                                        float* out) {
+  constexpr int RS = RP + 4, KC = (RP + 31) / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  constexpr int KC = kMaxRank / 32;
   float acc[KC];
 #pragma unroll
   for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
-  int q = w;
-  for (; q + 96 < m; q += 128) {
-    float xv[4], av[4][KC];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      xv[u] = x[q + 32 * u];
-      const float* row = A + int64_t(q + 32 * u) * RP;
-#pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        const int c = lane + 32 * k;
-        av[u][k] = c < RP ? row[c] : 0.0f;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int k = 0; k < KC; ++k) acc[k] = fmaf(av[u][k], xv[u], acc[k]);
-  }
-  for (; q < m; q += 32) {
+  for (int q = w; q < mloc; q += kCluWarps) {
     const float xq = x[q];
-    const float* row = A + int64_t(q) * RP;
+    const float* row = f.A + q * RS;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       const int c = lane + 32 * k;
@@ -161,24 +201,35 @@ __device__ void block_AtX(const float* __restrict__ A, int m, int R, const float
 #pragma unroll
   for (int k = 0; k < KC; ++k) {
     const int c = lane + 32 * k;
-    if (c < RP) red[w * RP + c] = acc[k];
+    if (c < RP) f.red[w * RP + c] = acc[k];
   }
   __syncthreads();
   for (int c = threadIdx.x; c < R; c += blockDim.x) {
     float t = 0.0f;
-    for (int ww = 0; ww < 32; ++ww) t += red[ww * RP + c];
+#pragma unroll
+    for (int ww = 0; ww < kCluWarps; ++ww) t += f.red[ww * RP + c];
     out[c] = t;
   }
+}
+
+// Block sum of one value per thread into slot position `pos` (thread 0 writes).
+__device__ __forceinline__ void clu_block_sum_to(float v, const CluSmem& f, float* dst) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) f.misc[8 + (threadIdx.x >> 5)] = v;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < kCluWarps; ++w) t += f.misc[8 + w];
+    *dst = t;
+  }
 }
 
 template <int RP>
-__device__ __forceinline__ float row_dot(const float* __restrict__ row,
-                                         const float* __restrict__ v) {
-  float4 a[RP / 4];
+__device__ __forceinline__ float clu_row_dot(const float* row, const float* v) {
   const float4* r4 = reinterpret_cast<const float4*>(row);
+  float4 a[RP / 4];
 #pragma unroll
-  for (int c4 = 0; c4 < RP / 4; ++c4) a[c4] = r4[c4];  // all loads in flight together
+  for (int c4 = 0; c4 < RP / 4; ++c4) a[c4] = r4[c4];
   float t0 = 0.0f, t1 = 0.0f;
 #pragma unroll
   for (int c4 = 0; c4 < RP / 4; ++c4) {
@@ -190,133 +241,444 @@ __device__ __forceinline__ float row_dot(const float* __restrict__ row,
   return t0 + t1;
 }
 
+// Gram G = A^T A over the cluster, then G^-1 (Gauss-Jordan, no pivoting: G is
+// symmetric positive definite), then ADMM; leaves w in f.wv (zero-padded to RP).
+// In the ADMM loop warp w owns the local rows q = w, w + 8, ... and lane l the
+// columns l + 32k: one pass over a warp's rows applies the s, y update of the
+// current iteration and accumulates A^T x of the next one, so an iteration
+// costs one block barrier and one cluster barrier.
+template <int RP>
+__device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, int R, float rho,
+                           int iters, int CL, int& par) {
+  constexpr int RS = RP + 4, KC = (RP + 31) / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int RG = (R + 3) / 4 * 4;
+  // --- local Gram partial by 4x4 register tiles of the upper triangle ---
+  constexpr int RT = RP / 4;
+  const int ntile = RT * (RT + 1) / 2;
+  for (int t = tid; t < ntile; t += blockDim.x) {
+    int ti = 0, rem = t;
+    while (rem >= RT - ti) {
+      rem -= RT - ti;
+      ++ti;
+    }
+    const int tj = ti + rem;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.0f;
+    for (int q = 0; q < mloc; ++q) {
+      const float4 u = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * ti);
+      const float4 v = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * tj);
+      const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(uu[a], vv[b2], acc[a][b2]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) {
+        const int c = 4 * ti + a, d = 4 * tj + b2;
+        if (c < R && d < RG) f.Gp[c * RG + d] = (c <= d && d < R) ? acc[a][b2] : 0.0f;
+      }
+  }
+  __syncthreads();
+  cl.sync();
+  // cluster sum of the upper triangle in float4 steps (rank order), mirrored
+  const int rg4 = RG / 4;
+  for (int e = tid; e < R * rg4; e += blockDim.x) {
+    const int c = e / rg4, d4 = e - c * rg4;
+    if (4 * d4 + 3 < c) continue;  // wholly below the diagonal
+    float4 t[kMaxCluster];
+#pragma unroll
+    for (int r = 0; r < kMaxCluster; ++r)
+      t[r] = r < CL ? *reinterpret_cast<const float4*>(cl.map_shared_rank(f.Gp, r) + c * RG + 4 * d4)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kMaxCluster; ++r)
+      if (r < CL) {
+        sum.x += t[r].x;
+        sum.y += t[r].y;
+        sum.z += t[r].z;
+        sum.w += t[r].w;
+      }
+    const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int d = 4 * d4 + u;
+      if (d >= c && d < R) {
+        f.G[c * R + d] = sv[u];
+        f.G[d * R + c] = sv[u];
+      }
+    }
+  }
+  for (int e = tid; e < R * R; e += blockDim.x) f.Gi[e] = 0.0f;
+  __syncthreads();
+  for (int c = tid; c < R; c += blockDim.x) f.Gi[c * R + c] = 1.0f;
+  // --- G^-1 by Gauss-Jordan (no pivoting: G is symmetric positive definite).
+  // Pivot k: the scaled pivot row goes to rowk and the column to fac (phase
+  // 1), then every row is updated from them (phase 2): two barriers a pivot.
+  float* fac = f.red;       // R
+  float* rowk = f.red + R;  // 2R: scaled pivot row of [G | G^-1]
+  constexpr int kRowsPerWarp = (RP + kCluWarps - 1) / kCluWarps;
+  for (int k = 0; k < R; ++k) {
+    __syncthreads();
+    const float inv = 1.0f / f.G[k * R + k];
+    for (int j = tid; j < 2 * R; j += blockDim.x)
+      rowk[j] = (j < R ? f.G[k * R + j] : f.Gi[k * R + (j - R)]) * inv;
+    for (int i = tid; i < R; i += blockDim.x) fac[i] = (i == k) ? 0.0f : f.G[i * R + k];
+    __syncthreads();
+    // all loads of a thread's entries before its stores (the compiler cannot
+    // reorder loads past stores through these aliasing shared pointers)
+    for (int j = lane; j < R; j += 32) {
+      const float rg = rowk[j], ri = rowk[R + j];
+      float gv[kRowsPerWarp], hv[kRowsPerWarp], fv[kRowsPerWarp];
+#pragma unroll
+      for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int i = warp + kCluWarps * t;
+        gv[t] = i < R ? f.G[i * R + j] : 0.0f;
+        hv[t] = i < R ? f.Gi[i * R + j] : 0.0f;
+        fv[t] = i < R ? fac[i] : 0.0f;
+      }
+#pragma unroll
+      for (int t = 0; t < kRowsPerWarp; ++t) {
+        const int i = warp + kCluWarps * t;
+        if (i < R) {
+          f.G[i * R + j] = i == k ? rg : fmaf(-fv[t], rg, gv[t]);
+          f.Gi[i * R + j] = i == k ? ri : fmaf(-fv[t], ri, hv[t]);
+        }
+      }
+    }
+  }
+  __syncthreads();  // fac and rowk (in red) are read until here
+  // --- ADMM on min ||s||_1 s.t. A w + s = b (s = y = 0 at the start, so x = b).
+  // Warp w owns the local rows q = w, w + 8, ... and lane l the columns
+  // l + 32k; one pass over a warp's rows (four at a time) applies the s, y
+  // update of the current iteration and accumulates A^T x of the next one.
+  const float irho = 1.0f / rho;
+  float acc[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
+  for (int q = warp; q < mloc; q += kCluWarps) {
+    const float xq = f.b[q];
+    if (lane == 0) {
+      f.s[q] = 0.0f;
+      f.y[q] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const int c = lane + 32 * k;
+      if (c < RP) acc[k] = fmaf(f.A[q * RS + c], xq, acc[k]);
+    }
+  }
+  for (int it = 0; it < iters; ++it) {
+    // A^T x: warps -> this CTA's slot -> cluster sum (threads c < R)
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const int c = lane + 32 * k;
+      if (c < RP) f.red[warp * RP + c] = acc[k];
+    }
+    __syncthreads();
+    float* mine = f.slot + par * kSlot;
+    for (int c = tid; c < R; c += blockDim.x) {
+      float t = 0.0f;
+#pragma unroll
+      for (int ww = 0; ww < kCluWarps; ++ww) t += f.red[ww * RP + c];
+      mine[c] = t;
+    }
+    cl.sync();
+    for (int c = tid; c < R; c += blockDim.x) f.vec[c] = clu_gather_sum(cl, mine, c, CL);
+    par ^= 1;
+    __syncthreads();
+    // w = G^-1 v (G^-1 symmetric: column c read along d, conflict-free); the
+    // d range is split over kCluWarps / KC groups, partials summed in order
+    {
+      constexpr int NG = kCluWarps / KC;  // groups of KC warps: one column each per lane
+      const int g = warp / KC, c = lane + 32 * (warp % KC);
+      const int per = (R + NG - 1) / NG, d0 = g * per, d1 = min(R, d0 + per);
+      float t = 0.0f;
+      if (c < R)
+        for (int d = d0; d < d1; ++d) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
+      if (c < RP) f.red[g * RP + c] = t;
+      __syncthreads();
+      for (int c2 = tid; c2 < R; c2 += blockDim.x) {
+        float w = 0.0f;
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) w += f.red[gg * RP + c2];
+        f.wv[c2] = w;
+      }
+      __syncthreads();
+    }
+    float wc[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const int c = lane + 32 * k;
+      wc[k] = c < R ? f.wv[c] : 0.0f;
+      acc[k] = 0.0f;
+    }
+    // rows: s, y update of this iteration, then A^T x of the next
+    for (int q0 = warp; q0 < mloc; q0 += 4 * kCluWarps) {
+      float a[4][KC], p[4], bv[4], yv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * kCluWarps;
+        bv[u] = q < mloc ? f.b[q] : 0.0f;
+        yv[u] = q < mloc ? f.y[q] : 0.0f;
+        p[u] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+          const int c = lane + 32 * k;
+          a[u][k] = (q < mloc && c < RP) ? f.A[q * RS + c] : 0.0f;
+          p[u] = fmaf(a[u][k], wc[k], p[u]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u] += __shfl_xor_sync(0xffffffffu, p[u], o);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * kCluWarps;
+        if (q >= mloc) break;
+        const float bq = bv[u], yq = yv[u];
+        const float e = bq - p[u] - yq * irho;
+        const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
+        const float yn = yq + rho * (p[u] + sq - bq);
+        const float xn = bq - sq - yn * irho;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) acc[k] = fmaf(a[u][k], xn, acc[k]);
+        __syncwarp();
+        if (lane == 0) {
+          f.s[q] = sq;
+          f.y[q] = yn;
+        }
+      }
+    }
+  }
+  // f.wv holds the last iteration's w (entries c >= R are zero)
+  for (int c = R + tid; c < RP; c += blockDim.x) f.wv[c] = 0.0f;
+  __syncthreads();
+}
+
+// Rows [q0, q0 + mloc) of the m sampled rows belong to cluster rank `rank`.
+__device__ __forceinline__ void clu_rows(int m, int CL, int rank, int& q0, int& mloc) {
+  const int per = (m + CL - 1) / CL;
+  q0 = rank * per;
+  mloc = m - q0 < per ? m - q0 : per;
+  if (mloc < 0) mloc = 0;
+}
+
+// One training step (Sec. 4.1): sampled rows of the training column, l1
+// weights, residual lifted onto the sampled voxels, and the geodesic step's
+// coefficients (written to upd for geodesic_update_kernel).
+struct CluStepArgs {
+  const float* U;     // V x RP
+  const float* Trow;  // t of this training column (V values)
+  uint32_t V;
+  int R, m, CL;
+  uint32_t k0, k1;
+  int pass, col;
+  float rho, step;
+  int iters;
+  float* lift;    // V, zero on entry
+  float* upd;     // 3 RP + 4: w, w/||w||, g2, alpha, beta
+  float* w_hist;  // nullable
+};
+
+template <int RP>
+__global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluStepArgs a) {
+  extern __shared__ __align__(16) float smc[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = int(cl.block_rank());
+  constexpr int RS = RP + 4;
+  int q0, mloc;
+  clu_rows(a.m, a.CL, rank, q0, mloc);
+  CluSmem f;
+  clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, &f);
+  const int tid = threadIdx.x;
+  for (int q = tid; q < mloc; q += blockDim.x) {
+    const uint32_t j = draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q0 + q), uint32_t(a.col),
+                                  uint32_t(a.pass), a.V);
+    f.idx[q] = int32_t(j);
+    f.b[q] = a.Trow[j];
+    const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
+    float4* dst = reinterpret_cast<float4*>(f.A + q * RS);
+#pragma unroll
+    for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
+  }
+  __syncthreads();
+  int par = 0;
+  clu_l1_fit<RP>(cl, f, mloc, a.R, a.rho, a.iters, a.CL, par);
+  // residual r (into x), lifted onto the sampled voxels; A^T r and ||r||^2
+  float rr = 0.0f;
+  for (int q = tid; q < mloc; q += blockDim.x) {
+    const float r = f.b[q] - clu_row_dot<RP>(f.A + q * RS, f.wv);
+    f.x[q] = r;
+    atomicAdd(&a.lift[f.idx[q]], r);
+    rr = fmaf(r, r, rr);
+  }
+  __syncthreads();
+  float* sl = f.slot + par * kSlot;
+  clu_AtX<RP>(f, mloc, a.R, f.x, sl);
+  clu_block_sum_to(rr, f, sl + a.R);
+  clu_sum(cl, f, par, a.R + 1, a.CL);  // the barrier also publishes the lift atomics
+  float* g2 = f.misc;                   // keep g2 and ||r||^2 before vec is reused
+  if (tid == 0) f.misc[0] = f.vec[a.R];
+  float* g2v = f.red;  // R values (red is free now)
+  for (int c = tid; c < a.R; c += blockDim.x) g2v[c] = f.vec[c];
+  // ||lift||^2 = sum_q lift[idx_q] r_q (a voxel sampled twice holds both r)
+  float ll = 0.0f;
+  for (int q = tid; q < mloc; q += blockDim.x) ll = fmaf(__ldcg(&a.lift[f.idx[q]]), f.x[q], ll);
+  __syncthreads();
+  clu_block_sum_to(ll, f, f.slot + par * kSlot);
+  clu_sum(cl, f, par, 1, a.CL);
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+  if (rank != 0) return;
+  if (tid == 0) {
+    const float nr2 = g2[0], nl2 = f.vec[0];
+    float nw2 = 0.0f, ng2 = 0.0f;
+    for (int c = 0; c < a.R; ++c) {
+      nw2 = fmaf(f.wv[c], f.wv[c], nw2);
+      ng2 = fmaf(g2v[c], g2v[c], ng2);
+    }
+    const float nw = sqrtf(nw2);
+    const float nG = sqrtf(fmaxf(nl2 - ng2, 0.0f));
+    float alpha = 0.0f, beta = 0.0f;
+    if (nw > 0.0f && nG > 0.0f) {
+      const float theta = a.step * atanf(sqrtf(nr2) / nw);
+      alpha = (cosf(theta) - 1.0f) / nw;
+      beta = sinf(theta) / nG;
+    }
+    f.misc[1] = alpha;
+    f.misc[2] = beta;
+    f.misc[3] = nw;
+  }
+  __syncthreads();
+  const float nw = f.misc[3];
+  for (int c = tid; c < RP; c += blockDim.x) {
+    const float wc = c < a.R ? f.wv[c] : 0.0f;
+    a.upd[c] = wc;
+    a.upd[RP + c] = nw > 0.0f ? wc / nw : 0.0f;
+    a.upd[2 * RP + c] = c < a.R ? g2v[c] : 0.0f;
+    if (a.w_hist && c < a.R) a.w_hist[c] = wc;
+  }
+  if (tid == 0) {
+    a.upd[3 * RP] = f.misc[1];
+    a.upd[3 * RP + 1] = f.misc[2];
+  }
+}
+
+// Sampled t (Alg. 2 recovery): Tt[i - row0][q] = t of relabelling i at its
+// q-th drawn voxel. A CTA takes one relabelling (labels in shared memory) and
+// 64 draws; a warp computes S dot products at once, lanes over the n_pad
+// subjects in float4 steps (T per lane), so many row loads are in flight.
+template <int T>
+__global__ void __launch_bounds__(256) sampled_t_kernel(const int32_t* __restrict__ perms, int n,
+                                                        int n1, int n_pad,
+                                                        const float* __restrict__ Xn32,
+                                                        uint32_t V, int m, uint32_t k0,
+                                                        uint32_t k1, float kf, float ctf,
+                                                        int64_t row0, float* __restrict__ Tt) {
+  constexpr int S = T <= 2 ? 4 : (T == 4 ? 2 : 1);
+  __shared__ __align__(16) float L[32 * 4 * T];
+  const int64_t i = row0 + blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int s = threadIdx.x; s < 32 * 4 * T; s += blockDim.x) L[s] = 0.0f;
+  __syncthreads();
+  for (int q = threadIdx.x; q < n1; q += blockDim.x) {
+    const int32_t e = perms[i * n + q];
+    if (e >= 0 && e < n) L[e] = 1.0f;  // bad rows are reported by validate_perms_kernel
+  }
+  __syncthreads();
+  const int nf4 = n_pad / 4;
+  const float4* L4 = reinterpret_cast<const float4*>(L);
+  const int qb = blockIdx.y * 64 + warp * 8;
+  for (int g = 0; g < 8; g += S) {
+    float4 x[S][T];
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      const int q = qb + g + u;
+      const uint32_t j = q < m ? draw_index(k0, k1, TAG_REC, uint32_t(q), uint32_t(i), 0u, V) : 0u;
+      const float4* xr = reinterpret_cast<const float4*>(Xn32 + int64_t(j) * n_pad);
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int f4 = lane + 32 * t;
+        x[u][t] = (q < m && f4 < nf4) ? xr[f4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      float p = 0.0f;
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const float4 l = L4[lane + 32 * t];
+        p = fmaf(x[u][t].x, l.x, fmaf(x[u][t].y, l.y, fmaf(x[u][t].z, l.z, fmaf(x[u][t].w, l.w, p))));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      const int q = qb + g + u;
+      if (lane == 0 && q < m) {
+        const float den = 1.0f - kf * p * p;
+        Tt[(i - row0) * m + q] = den > 0.0f ? ctf * p * rsqrtf(den) : (p > 0.0f ? 3.0e38f : -3.0e38f);
+      }
+    }
+  }
+}
+
+// Recovery fits (Sec. 4.2), one cluster per relabelling at a time.
+struct CluRecArgs {
+  const float* Tt;    // (row - row_first) x m: t at the sampled voxels
+  uint32_t V;
+  int R, m, CL;
+  const float* U;     // V x RP
+  uint32_t k0, k1;
+  float rho;
+  int iters;
+  int64_t row_first, row_end;
+  float* W;           // (row - row_first) x RP
+};
+
+template <int RP>
+__global__ void __launch_bounds__(kCluThreads, 1) recover_fit_cluster_kernel(CluRecArgs a) {
+  extern __shared__ __align__(16) float smc[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = int(cl.block_rank());
+  const int64_t cid = blockIdx.x / a.CL, ncl = gridDim.x / a.CL;
+  constexpr int RS = RP + 4;
+  int q0, mloc;
+  clu_rows(a.m, a.CL, rank, q0, mloc);
+  CluSmem f;
+  clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, &f);
+  const int tid = threadIdx.x;
+  int par = 0;
+  for (int64_t i = a.row_first + cid; i < a.row_end; i += ncl) {
+    const float* trow = a.Tt + (i - a.row_first) * a.m + q0;
+    for (int q = tid; q < mloc; q += blockDim.x) {
+      const uint32_t j = draw_index(a.k0, a.k1, TAG_REC, uint32_t(q0 + q), uint32_t(i), 0u, a.V);
+      f.b[q] = trow[q];
+      const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
+      float4* dst = reinterpret_cast<float4*>(f.A + q * RS);
+#pragma unroll
+      for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
+    }
+    __syncthreads();
+    clu_l1_fit<RP>(cl, f, mloc, a.R, a.rho, a.iters, a.CL, par);
+    if (rank == 0)
+      for (int c = tid; c < RP; c += blockDim.x)
+        a.W[(i - a.row_first) * RP + c] = c < a.R ? f.wv[c] : 0.0f;
+    __syncthreads();
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 __device__ __forceinline__ float row_dot_rt(const float* __restrict__ row,
                                             const float* __restrict__ v, int RP) {
   float t = 0.0f;
   for (int c = 0; c < RP; ++c) t = fmaf(row[c], v[c], t);
-  return t;
-}
-
-// b, s, y, x: m floats each (shared memory when they fit, else global scratch).
-template <int RP>
-__device__ void block_l1_fit(const float* __restrict__ A, const float* b, float* s, float* y,
-                             float* x, int m, int R, float rho, int iters, FitSmem& f) {
-  constexpr int CH = kStageFloats / RP;  // rows staged per Gram step
-  const int tid = threadIdx.x;
-  const int npairs = R * (R + 1) / 2;
-  // --- Gram G = A^T A (upper triangle by pairs, then mirrored) ---
-  float acc[9];
-  int pc[9], pd[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    acc[k] = 0.0f;
-    const int pi = tid + k * blockDim.x;
-    int c = 0, rem = pi < npairs ? pi : 0;
-    while (rem >= R - c) {
-      rem -= R - c;
-      ++c;
-    }
-    pc[k] = c;
-    pd[k] = c + rem;
-  }
-  for (int q0 = 0; q0 < m; q0 += CH) {
-    const int rows = min(CH, m - q0);
-    const float4* src = reinterpret_cast<const float4*>(A + int64_t(q0) * RP);
-    float4* dst = reinterpret_cast<float4*>(f.stage);
-    for (int e = tid; e < CH * RP / 4; e += blockDim.x)
-      dst[e] = (e < rows * RP / 4) ? src[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      if (tid + k * blockDim.x < npairs) {
-        const int c = pc[k], d = pd[k];
-        float t0 = acc[k], t1 = 0.0f;
-#pragma unroll 8
-        for (int rr = 0; rr < CH; rr += 2) {
-          t0 = fmaf(f.stage[rr * RP + c], f.stage[rr * RP + d], t0);
-          t1 = fmaf(f.stage[(rr + 1) * RP + c], f.stage[(rr + 1) * RP + d], t1);
-        }
-        acc[k] = t0 + t1;
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < RP * RP; e += blockDim.x) {
-    f.G[e] = 0.0f;
-    f.Gi[e] = (e / RP == e % RP) ? 1.0f : 0.0f;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    if (tid + k * blockDim.x < npairs) {
-      f.G[pc[k] * RP + pd[k]] = acc[k];
-      f.G[pd[k] * RP + pc[k]] = acc[k];
-    }
-  }
-  __syncthreads();
-  // --- G^-1 by Gauss-Jordan on [G | I] (G symmetric positive definite: no pivoting) ---
-  float* fac = f.red;  // R factors of the current column
-  for (int k = 0; k < R; ++k) {
-    const float inv = 1.0f / f.G[k * RP + k];
-    __syncthreads();
-    for (int j = tid; j < 2 * R; j += blockDim.x) {
-      if (j < R) f.G[k * RP + j] *= inv;
-      else f.Gi[k * RP + (j - R)] *= inv;
-    }
-    for (int i = tid; i < R; i += blockDim.x) fac[i] = (i == k) ? 0.0f : f.G[i * RP + k];
-    __syncthreads();
-    for (int e = tid; e < R * 2 * R; e += blockDim.x) {
-      const int i = e / (2 * R), j = e - i * 2 * R;
-      const float fi = fac[i];
-      if (fi != 0.0f) {
-        if (j < R) f.G[i * RP + j] -= fi * f.G[k * RP + j];
-        else f.Gi[i * RP + (j - R)] -= fi * f.Gi[k * RP + (j - R)];
-      }
-    }
-    __syncthreads();
-  }
-  // --- ADMM ---
-  for (int q = tid; q < m; q += blockDim.x) {
-    s[q] = 0.0f;
-    y[q] = 0.0f;
-  }
-  for (int c = tid; c < RP; c += blockDim.x) f.wv[c] = 0.0f;
-  __syncthreads();
-  const float irho = 1.0f / rho;
-  for (int it = 0; it < iters; ++it) {
-    for (int q = tid; q < m; q += blockDim.x) x[q] = b[q] - s[q] - y[q] * irho;
-    __syncthreads();
-    block_AtX<RP>(A, m, R, x, f.red, f.rhs);
-    for (int c = tid; c < R; c += blockDim.x) {
-      float t = 0.0f;
-      for (int d = 0; d < R; ++d) t = fmaf(f.Gi[c * RP + d], f.rhs[d], t);
-      f.wv[c] = t;
-    }
-    __syncthreads();
-    for (int q = tid; q < m; q += blockDim.x) {
-      const float aw = row_dot<RP>(A + int64_t(q) * RP, f.wv);
-      const float e = b[q] - aw - y[q] * irho;
-      const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
-      s[q] = sq;
-      y[q] = y[q] + rho * (aw + sq - b[q]);
-    }
-    __syncthreads();
-  }
-}
-
-__device__ float block_sum(float v, float* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float t = 0.0f;
-  if (threadIdx.x < 32) {
-    t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[0] = t;
-  }
-  __syncthreads();
-  t = red[0];
-  __syncthreads();
   return t;
 }
 
@@ -462,101 +824,6 @@ __global__ void qr_apply_kernel(float* __restrict__ U, int64_t V, int R, int RP,
 // ---------------------------------------------------------------------------
 // Training step (one block) and geodesic update (whole grid)
 // ---------------------------------------------------------------------------
-struct StepArgs {
-  const float* U;
-  const float* Trow;  // T_ex row of this column (v values)
-  uint32_t V;
-  int R, RP, m;
-  uint32_t k0, k1;
-  int pass, col;
-  float rho;
-  int iters;
-  float step;
-  int32_t* idx;
-  float* b;
-  float* A;
-  float* s;
-  float* y;
-  float* x;         // b, s, y, x: global fallback when m > kSmemVecM
-  float* lift;      // v, zero on entry
-  float* upd;       // [3 * RP + 4]: w, w/||w||, g2, alpha, beta
-  float* w_hist;    // nullable: this step's weights (RP)
-};
-
-template <int RP>
-__global__ void __launch_bounds__(kFitThreads) train_step_kernel(StepArgs a) {
-  extern __shared__ float sm[];
-  FitSmem f;
-  carve_fit_smem(sm, RP, f);
-  const int tid = threadIdx.x;
-  float *b = a.b, *sv = a.s, *yv = a.y, *xv = a.x;
-  if (a.m <= kSmemVecM) {
-    b = f.scal + 8;
-    sv = b + a.m;
-    yv = sv + a.m;
-    xv = yv + a.m;
-  }
-  for (int q = tid; q < a.m; q += blockDim.x) {
-    const uint32_t j = draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q), uint32_t(a.col),
-                                  uint32_t(a.pass), a.V);
-    a.idx[q] = int32_t(j);
-    b[q] = a.Trow[j];
-    const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
-    float4* dst = reinterpret_cast<float4*>(a.A + int64_t(q) * RP);
-    for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
-  }
-  __syncthreads();
-  block_l1_fit<RP>(a.A, b, sv, yv, xv, a.m, a.R, a.rho, a.iters, f);
-  // residual r (into x), lift, ||r||^2
-  float rr = 0.0f;
-  for (int q = tid; q < a.m; q += blockDim.x) {
-    const float r = b[q] - row_dot<RP>(a.A + int64_t(q) * RP, f.wv);
-    xv[q] = r;
-    atomicAdd(&a.lift[a.idx[q]], r);
-    rr = fmaf(r, r, rr);
-  }
-  __syncthreads();
-  const float nr2 = block_sum(rr, f.red);
-  float* g2 = f.rhs;
-  block_AtX<RP>(a.A, a.m, a.R, xv, f.red, g2);
-  // ||lift||^2 = sum_q lift[idx_q] r_q (duplicates counted once per voxel)
-  float ll = 0.0f;
-  for (int q = tid; q < a.m; q += blockDim.x) ll = fmaf(a.lift[a.idx[q]], xv[q], ll);
-  __syncthreads();
-  const float nl2 = block_sum(ll, f.red);
-  if (tid == 0) {
-    float nw2 = 0.0f, ng2 = 0.0f;
-    for (int c = 0; c < a.R; ++c) {
-      nw2 = fmaf(f.wv[c], f.wv[c], nw2);
-      ng2 = fmaf(g2[c], g2[c], ng2);
-    }
-    const float nw = sqrtf(nw2);
-    const float nG = sqrtf(fmaxf(nl2 - ng2, 0.0f));
-    float alpha = 0.0f, beta = 0.0f;
-    if (nw > 0.0f && nG > 0.0f) {
-      const float theta = a.step * atanf(sqrtf(nr2) / nw);
-      alpha = (cosf(theta) - 1.0f) / nw;
-      beta = sinf(theta) / nG;
-    }
-    f.scal[0] = alpha;
-    f.scal[1] = beta;
-    f.scal[2] = nw;
-  }
-  __syncthreads();
-  const float nw = f.scal[2];
-  for (int c = tid; c < RP; c += blockDim.x) {
-    const float wc = c < a.R ? f.wv[c] : 0.0f;
-    a.upd[c] = wc;
-    a.upd[RP + c] = nw > 0.0f ? wc / nw : 0.0f;
-    a.upd[2 * RP + c] = c < a.R ? g2[c] : 0.0f;
-    if (a.w_hist && c < a.R) a.w_hist[c] = wc;
-  }
-  if (tid == 0) {
-    a.upd[3 * RP] = f.scal[0];
-    a.upd[3 * RP + 1] = f.scal[1];
-  }
-}
-
 // U_j += (alpha (U_j . w) + beta (lift_j - U_j . g2)) w^T/||w||; lift_j <- 0.
 template <int RP>
 __global__ void geodesic_update_kernel(float* __restrict__ U, int64_t V,
@@ -688,74 +955,6 @@ __global__ void __launch_bounds__(256) sigma_partial_kernel(
     }
     part[2 * blockIdx.x] = a;
     part[2 * blockIdx.x + 1] = c;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Recovery: sampled t, l1 weights (one block per relabelling, persistent)
-// ---------------------------------------------------------------------------
-struct RecArgs {
-  const int32_t* perms;
-  int n, n1, n_pad;
-  const float* Xn32;  // v_pad x n_pad, unit-norm centred data
-  uint32_t V;
-  int R, RP, m;
-  const float* U;
-  uint32_t k0, k1;
-  float rho;
-  int iters;
-  float kf, ctf;
-  int64_t row_first, row_end;
-  float* scratch;  // per block: A (m x RP), b, s, y (m each), blocks block_stride floats apart
-  int64_t block_stride;  // multiple of 64 floats, so every A row stays 16-byte aligned
-  float* W;        // (row - row_first) x RP
-};
-
-template <int RP>
-__global__ void __launch_bounds__(kFitThreads) recover_fit_kernel(RecArgs a) {
-  extern __shared__ float sm[];
-  FitSmem f;
-  carve_fit_smem(sm, RP, f);
-  float* Lrow = f.scal + 8;  // n_pad
-  float* A = a.scratch + int64_t(blockIdx.x) * a.block_stride;
-  float* b = A + int64_t(a.m) * RP;
-  float* s = b + a.m;
-  float* y = s + a.m;
-  float* x = y + a.m;
-  if (a.m <= kSmemVecM) {
-    b = Lrow + a.n_pad;
-    s = b + a.m;
-    y = s + a.m;
-    x = y + a.m;
-  }
-  for (int64_t i = a.row_first + blockIdx.x; i < a.row_end; i += gridDim.x) {
-    for (int sidx = threadIdx.x; sidx < a.n_pad; sidx += blockDim.x) Lrow[sidx] = 0.0f;
-    __syncthreads();
-    for (int q = threadIdx.x; q < a.n1; q += blockDim.x) {
-      const int32_t e = a.perms[i * a.n + q];
-      if (e >= 0 && e < a.n) Lrow[e] = 1.0f;  // bad rows are reported by validate_perms_kernel
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < a.m; q += blockDim.x) {
-      const uint32_t j = draw_index(a.k0, a.k1, TAG_REC, uint32_t(q), uint32_t(i), 0u, a.V);
-      const float4* xr = reinterpret_cast<const float4*>(a.Xn32 + int64_t(j) * a.n_pad);
-      float u = 0.0f;
-      for (int s4 = 0; s4 < a.n_pad / 4; ++s4) {
-        const float4 x = xr[s4];
-        u = fmaf(x.x, Lrow[4 * s4], fmaf(x.y, Lrow[4 * s4 + 1],
-                 fmaf(x.z, Lrow[4 * s4 + 2], fmaf(x.w, Lrow[4 * s4 + 3], u))));
-      }
-      const float den = 1.0f - a.kf * u * u;
-      b[q] = den > 0.0f ? a.ctf * u * rsqrtf(den) : (u > 0.0f ? 3.0e38f : -3.0e38f);
-      const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
-      float4* dst = reinterpret_cast<float4*>(A + int64_t(q) * RP);
-      for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
-    }
-    __syncthreads();
-    block_l1_fit<RP>(A, b, s, y, x, a.m, a.R, a.rho, a.iters, f);
-    for (int c = threadIdx.x; c < RP; c += blockDim.x)
-      a.W[(i - a.row_first) * RP + c] = c < a.R ? f.wv[c] : 0.0f;
-    __syncthreads();
   }
 }
 
@@ -961,9 +1160,53 @@ int grid_n(int64_t work, int threads, int cap = 152 * 16) {
   return int(b);
 }
 
-size_t fit_smem_bytes(int RP, int n_pad, int m) {
-  const size_t vec = m <= kSmemVecM ? 4 * size_t(m) : 0;
-  return sizeof(float) * (2 * RP * RP + 32 * RP + kStageFloats + 2 * RP + 8 + n_pad + vec);
+constexpr size_t kCluSmemLimit = 227 * 1024;
+
+// Smallest cluster size (from `first`, doubling up to 16) whose per-CTA share
+// of the sampled rows fits in shared memory; 0 if none does.
+int choose_cluster(int m, int R, int RP, int n_pad, int first, size_t* smem) {
+  for (int CL = first; CL <= 16; CL *= 2) {
+    const size_t b = clu_carve(nullptr, (m + CL - 1) / CL, R, RP, n_pad, nullptr);
+    if (b <= kCluSmemLimit) {
+      *smem = b;
+      return CL;
+    }
+  }
+  return 0;
+}
+
+// Launches `kernel` as nclusters clusters of CL CTAs of kCluThreads threads;
+// nclusters <= 0 asks for as many clusters as can be resident at once.
+template <class Arg>
+cudaError_t launch_cluster(void (*kernel)(Arg), int nclusters, int CL, size_t smem,
+                           cudaStream_t st, const Arg& arg, int* used = nullptr) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem));
+  if (e == cudaSuccess && CL > 8)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = unsigned(CL);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kCluThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (nclusters <= 0) {
+    cfg.gridDim = dim3(unsigned(CL) * 152u, 1, 1);
+    int maxc = 0;
+    e = cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (maxc < 1) return cudaErrorInvalidConfiguration;
+    nclusters = -nclusters > 0 && -nclusters < maxc ? -nclusters : maxc;
+  }
+  cfg.gridDim = dim3(unsigned(CL) * unsigned(nclusters), 1, 1);
+  if (used) *used = nclusters;
+  return cudaLaunchKernelEx(&cfg, kernel, arg);
 }
 
 pt_status nomem_r(pt_ctx* ctx, const char* what) {
@@ -1091,16 +1334,15 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   cudaStream_t st = ctx->stream;
   const int64_t V = pl.V;
   const int ell = n_train;
-  Buf Ub, Tex, lift, sc, upd, part, rinv, Wex, keys, sig, tmax;
+  Buf Ub, Tex, lift, upd, part, rinv, Wex, keys, sig, tmax;
   struct G {
     std::vector<Buf*> v;
     ~G() {
       for (Buf* b : v) b->release();
     }
-  } guard{{&Ub, &Tex, &lift, &sc, &upd, &part, &rinv, &Wex, &keys, &sig, &tmax}};
+  } guard{{&Ub, &Tex, &lift, &upd, &part, &rinv, &Wex, &keys, &sig, &tmax}};
   if (!Ub.ensure(sizeof(float) * size_t(V) * pl.RP) || !Tex.ensure(sizeof(float) * size_t(ell) * V) ||
       !lift.ensure(sizeof(float) * V) ||
-      !sc.ensure(sizeof(float) * (size_t(pl.m) * pl.RP + 5 * size_t(pl.m)) + 256) ||
       !upd.ensure(sizeof(float) * (3 * pl.RP + 4)) || !Wex.ensure(sizeof(float) * size_t(ell) * pl.RP) ||
       !keys.ensure(sizeof(unsigned long long) * ell) || !tmax.ensure(sizeof(float) * ell))
     return nomem_r(ctx, "RapidPT training");
@@ -1170,42 +1412,40 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   if (s != PT_OK) return s;
   PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * V, st));
 
-  // 3. sequential subspace tracking over passes x columns
-  float* scb = sc.as<float>();
-  StepArgs sa;
+  // 3. sequential subspace tracking over passes x columns: each step's l1
+  //    fit on one thread-block cluster, then the geodesic update over all of U
+  size_t csm = 0;
+  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 16, &csm);
+  if (CL == 0) {
+    set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
+    return PT_ERR_UNSUPPORTED;
+  }
+  CluStepArgs sa;
   sa.U = U;
   sa.V = uint32_t(V);
   sa.R = pl.R;
-  sa.RP = pl.RP;
   sa.m = pl.m;
+  sa.CL = CL;
   sa.k0 = pl.k0;
   sa.k1 = pl.k1;
   sa.rho = o.admm_rho;
   sa.iters = o.admm_iters;
   sa.step = o.step;
-  sa.A = scb;
-  sa.b = scb + size_t(pl.m) * pl.RP;
-  sa.s = sa.b + pl.m;
-  sa.y = sa.s + pl.m;
-  sa.x = sa.y + pl.m;
-  sa.idx = reinterpret_cast<int32_t*>(sa.x + pl.m);
   sa.lift = lift.as<float>();
   sa.upd = upd.as<float>();
-  const int fsm = int(fit_smem_bytes(pl.RP, 0, pl.m));
   const int usm = (3 * pl.RP + 2) * int(sizeof(float));
   int64_t steps = 0;
   cudaError_t lerr = cudaSuccess;
   with_rp(pl.RP, [&](auto rpc) {
     constexpr int RPc = decltype(rpc)::value;
-    lerr = cudaFuncSetAttribute(train_step_kernel<RPc>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
     for (int p = 0; p < o.train_passes && lerr == cudaSuccess && s == PT_OK; ++p) {
       for (int i = 0; i < ell; ++i) {
         sa.pass = p;
         sa.col = i;
         sa.Trow = Tex.as<float>() + int64_t(i) * V;
         sa.w_hist = w_hist ? w_hist + steps * pl.R : nullptr;
-        train_step_kernel<RPc><<<1, kFitThreads, fsm, st>>>(sa);
+        lerr = launch_cluster(train_step_cluster_kernel<RPc>, 1, CL, csm, st, sa);
+        if (lerr != cudaSuccess) break;
         geodesic_update_kernel<RPc><<<grid_n(V, 256, 152 * 8), 256, usm, st>>>(
             U, V, lift.as<float>(), upd.as<float>());
         lerr = cudaGetLastError();
@@ -1323,19 +1563,23 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
   const int64_t rows = P - first_row;
   s = ensure_xn32(ctx);
   if (s != PT_OK) return s;
-  Buf Ub, scr, Wb, keys;
+  Buf Ub, Wb, keys, Tt;
   struct G {
     std::vector<Buf*> v;
     ~G() {
       for (Buf* b : v) b->release();
     }
-  } guard{{&Ub, &scr, &Wb, &keys}};
-  const int nblk = int(std::min<int64_t>(rows, 152));
-  const int64_t block_stride = (int64_t(pl.m) * pl.RP + 4 * int64_t(pl.m) + 63) / 64 * 64;
+  } guard{{&Ub, &Wb, &keys, &Tt}};
+  size_t csm = 0;
+  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 4, &csm);
+  if (CL == 0) {
+    set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
+    return PT_ERR_UNSUPPORTED;
+  }
   if (!Ub.ensure(sizeof(float) * size_t(pl.V) * pl.RP) ||
-      !scr.ensure(sizeof(float) * size_t(nblk) * size_t(block_stride)) ||
       !Wb.ensure(sizeof(float) * size_t(rows) * pl.RP) ||
-      !keys.ensure(sizeof(unsigned long long) * rows))
+      !keys.ensure(sizeof(unsigned long long) * rows) ||
+      !Tt.ensure(sizeof(float) * size_t(rows) * size_t(pl.m)))
     return nomem_r(ctx, "RapidPT recovery");
   validate_perms_kernel<<<grid_n((rows + 7) / 8, 1), 256, 0, st>>>(perms, first_row, P, ctx->n,
                                                                    ctx->status.as<uint32_t>());
@@ -1343,38 +1587,41 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
   pack_u_kernel<<<grid_n(pl.V * pl.RP, 256), 256, 0, st>>>(U_in, pl.V, pl.R, pl.RP,
                                                           Ub.as<float>(), 1);
   PT_LAUNCH_CHECK(ctx);
-  RecArgs a;
-  a.perms = perms;
-  a.n = ctx->n;
-  a.n1 = ctx->n1;
-  a.n_pad = ctx->n_pad;
-  a.Xn32 = ctx->Xn32.as<float>();
+  // t at every recovery relabelling's sampled voxels, all at once
+  {
+    const int T = ctx->n_pad <= 128 ? 1 : ctx->n_pad <= 256 ? 2 : ctx->n_pad <= 512 ? 4 : 8;
+    const dim3 grid{unsigned(rows), unsigned((pl.m + 63) / 64), 1u};
+    const float kf = float(ctx->k), ctf = float(ctx->c_t);
+#define PT_SAMPLED_T(TT)                                                                    \
+  sampled_t_kernel<TT><<<grid, 256, 0, st>>>(perms, ctx->n, ctx->n1, ctx->n_pad,            \
+                                             ctx->Xn32.as<float>(), uint32_t(pl.V), pl.m,   \
+                                             pl.k0, pl.k1, kf, ctf, first_row, Tt.as<float>())
+    if (T == 1) PT_SAMPLED_T(1);
+    else if (T == 2) PT_SAMPLED_T(2);
+    else if (T == 4) PT_SAMPLED_T(4);
+    else PT_SAMPLED_T(8);
+#undef PT_SAMPLED_T
+    PT_LAUNCH_CHECK(ctx);
+  }
+  CluRecArgs a;
+  a.Tt = Tt.as<float>();
   a.V = uint32_t(pl.V);
   a.R = pl.R;
-  a.RP = pl.RP;
   a.m = pl.m;
+  a.CL = CL;
   a.U = Ub.as<float>();
   a.k0 = pl.k0;
   a.k1 = pl.k1;
   a.rho = o.admm_rho;
   a.iters = o.admm_iters;
-  a.kf = float(ctx->k);
-  a.ctf = float(ctx->c_t);
   a.row_first = first_row;
   a.row_end = P;
-  a.scratch = scr.as<float>();
-  a.block_stride = block_stride;
   a.W = Wb.as<float>();
-  const int fsm = int(fit_smem_bytes(pl.RP, ctx->n_pad, pl.m));
   cudaError_t lerr = cudaSuccess;
   with_rp(pl.RP, [&](auto rpc) {
     constexpr int RPc = decltype(rpc)::value;
-    lerr = cudaFuncSetAttribute(recover_fit_kernel<RPc>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, fsm);
-    if (lerr == cudaSuccess) {
-      recover_fit_kernel<RPc><<<nblk, kFitThreads, fsm, st>>>(a);
-      lerr = cudaGetLastError();
-    }
+    const int want = int(std::min<int64_t>(rows, 152));
+    lerr = launch_cluster(recover_fit_cluster_kernel<RPc>, -want, CL, csm, st, a);
   });
   if (lerr != cudaSuccess) {
     set_error(ctx, std::string("RapidPT recovery launch: ") + cudaGetErrorString(lerr));
