@@ -358,7 +358,7 @@ def run_ours(args):
         ms_k, n_k = B.pt_profile_read(ctx)
         kern_ms += ms_k
         kern_n += n_k
-        ctx.close()
+        ctx.close()  # workspaces go back to the library's cache for the next step
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     launches = B.pt_kernel_launch_count() - launches0
@@ -436,8 +436,13 @@ def run_ours(args):
         pieces = 2 if prec == 1 else 3
         n_pad = (n + 15) // 16 * 16
         hw = 2.0 * pieces * n_pad * entries / (avg_kern_ms * 1e-3) / 1e12
+        # DRAM bytes per launch of this kernel from the ncu capture summarised in
+        # profiles/tc_contract_kernel_brain_n100_v232k.md (BF16x3 only).
+        traffic = 164.57e6 if prec == 2 and WORKLOAD == "brain_n100_v232k" else None
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+                if traffic else None,
                 "peak_source": "%s bf16 sustained (MEASURED_PEAKS.json)" % src,
                 "kernel": "tc_contract_kernel<256>", "kernel_ms": avg_kern_ms,
                 "hw_tflops": hw, "hw_frac": hw / peak,

@@ -252,8 +252,15 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
                                     const int32_t* __restrict__ perms, int two_sided,
                                     float* __restrict__ maxnull, int32_t* __restrict__ argmax) {
   __shared__ uint32_t g1_all[8][32];
+  __shared__ double rc[3];  // 1/n1, 1/n2, (1/n1 + 1/n2)/(n - 2)
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* g1 = g1_all[wib];
+  if (threadIdx.x == 0) {
+    rc[0] = __drcp_rn(double(n1));
+    rc[1] = __drcp_rn(double(n - n1));
+    rc[2] = (rc[0] + rc[1]) * __drcp_rn(double(n - 2));
+  }
+  __syncthreads();
   for (int64_t i = int64_t(blockIdx.x) * 8 + wib; i < P; i += int64_t(gridDim.x) * 8) {
     const unsigned long long key = maxkey[i];
     if (key == 0ull) {
@@ -283,16 +290,10 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     }
-    // FP64 divisions and the square root on one lane only (FP64 throughput
-    // is shared by every active lane).
-    const int n2 = n - n1;
-    double m1 = 0.0, m2 = 0.0;
-    if (lane == 0) {
-      m1 = s1 / n1;
-      m2 = s2 / n2;
-    }
-    m1 = __shfl_sync(0xffffffffu, m1, 0);
-    m2 = __shfl_sync(0xffffffffu, m2, 0);
+    // Reciprocals per block and a reciprocal square root: FP64 divides and
+    // square roots are long FP64 sequences, and every warp instruction
+    // occupies the (narrow) FP64 pipe whatever its active lanes.
+    const double m1 = s1 * rc[0], m2 = s2 * rc[1];
     double ss = 0.0;
     for (int s = lane; s < n; s += 32) {
       const double d = double(x[s]) - (((g1[s >> 5] >> (s & 31)) & 1u) ? m1 : m2);
@@ -300,7 +301,7 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (lane == 0) {
-      const double t = (m1 - m2) / sqrt(ss / double(n - 2) * (1.0 / n1 + 1.0 / n2));
+      const double t = (m1 - m2) * rsqrt(ss * rc[2]);
       maxnull[i] = float(two_sided ? fabs(t) : t);
       argmax[i] = valid_map[c];
     }
