@@ -380,22 +380,20 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # ---- end to end through host buffers (pinned), copies inside the timed region ----
+    # ---- end to end through host buffers (pinned), transfers inside the timed region:
+    # the library reads X and the mask straight from page-locked host memory (only the
+    # mask voxels' values cross the link); relabellings are copied; results copied back.
     Xh = X.cpu().pin_memory()
     mh = mask.cpu().pin_memory()
     ph = torch.as_tensor(perms_np).pin_memory()
     mx_h = torch.empty(P, dtype=torch.float32).pin_memory()
     am_h = torch.empty(P, dtype=torch.int32).pin_memory()
     ct_h = torch.empty(v, dtype=torch.int32).pin_memory()
-    Xd = torch.empty_like(X)
-    md = torch.empty_like(mask)
     pd = torch.empty_like(perms)
 
     def e2e_step():
-        Xd.copy_(Xh, non_blocking=True)
-        md.copy_(mh, non_blocking=True)
         pd.copy_(ph, non_blocking=True)
-        c = B.pt_prepare(Xd, n1, md, stream=stream)
+        c = B.pt_prepare(Xh, n1, mh, stream=stream)
         B.pt_maxnull_naive_ex(c, pd, B.naive_opts(prec), maxnull, argmax, step.counts)
         mx_h.copy_(maxnull, non_blocking=True)
         am_h.copy_(argmax, non_blocking=True)
@@ -418,7 +416,7 @@ def run_ours(args):
         t = torch.tensor([ms_e2e], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_e2e = float(t.item())
-    h2d = Xh.numel() * 4 + mh.numel() + ph.numel() * 4
+    h2d = n * v * 4 + mh.numel() + ph.numel() * 4  # mask voxels' values, mask, relabellings
     d2h = P * 4 + P * 4 + v * 4
 
     # ---- roofline of the dominant kernel (fused contraction + reduction) ----

@@ -73,10 +73,13 @@ void pt_naive_opts_default(pt_naive_opts* o);
  * precedes Alg. 1 / Alg. 2).
  *   X      : device, float32, n x n_grid row-major (row s = subject s over the
  *            whole grid; the "n rows and v columns" data matrix of Sec. 5.3.1).
+ *            May also be page-locked host memory that the device can address
+ *            (cudaHostAlloc / cudaHostRegister): the kernels then read it over
+ *            the host link directly, and only the values of mask voxels.
  *   n      : subjects, 3 <= n <= 1024.
  *   n_grid : columns of X (grid voxels), 1 <= n_grid < 2^31.
- *   mask   : device, uint8, n_grid entries, nonzero = in the brain; NULL means
- *            every grid voxel.
+ *   mask   : device (or device-addressable page-locked host) memory, uint8,
+ *            n_grid entries, nonzero = in the brain; NULL means every grid voxel.
  *   n1     : size of group 1, 1 <= n1 <= n-1 (group 2 has n - n1).
  *   stream : cudaStream_t to run on (NULL = legacy default stream).
  *   out    : host; receives the new context (unchanged on failure).

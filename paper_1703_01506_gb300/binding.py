@@ -99,11 +99,15 @@ def load(path=None):
     return lib
 
 
-def _ptr(t):
+def _ptr(t, host_ok=False):
+    """Device pointer of a CUDA tensor; with host_ok, also of a page-locked
+    (pinned) CPU tensor, which the device addresses directly."""
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("expected a CUDA tensor")
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a tensor")
+    if not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise TypeError("expected a CUDA tensor" + (" or a pinned CPU tensor" if host_ok else ""))
     if not t.is_contiguous():
         raise ValueError("expected a contiguous tensor")
     return ctypes.c_void_p(t.data_ptr())
@@ -140,14 +144,15 @@ def _stream_ptr(stream):
 
 
 def pt_prepare(X, n1, mask=None, stream=None):
-    """X: (n, n_grid) float32 CUDA tensor; mask: (n_grid,) uint8 CUDA tensor or None."""
+    """X: (n, n_grid) float32 CUDA tensor, or pinned CPU tensor read by the
+    kernels over the host link; mask: (n_grid,) uint8 (same choice) or None."""
     lib = load()
     assert X.dtype == torch.float32 and X.dim() == 2
     if mask is not None:
         assert mask.dtype == torch.uint8 and mask.numel() == X.shape[1]
     out = ctypes.c_void_p()
-    st = lib.pt_prepare(_ptr(X), X.shape[0], X.shape[1], _ptr(mask), int(n1), _stream_ptr(stream),
-                        ctypes.byref(out))
+    st = lib.pt_prepare(_ptr(X, True), X.shape[0], X.shape[1], _ptr(mask, True), int(n1),
+                        _stream_ptr(stream), ctypes.byref(out))
     _check(st, None)
     return Ctx(out)
 

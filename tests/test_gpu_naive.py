@@ -201,3 +201,24 @@ def test_full_brain_n100_sampled(cuda_lib):
     dc = np.abs(ct[vox] - refc.counts.astype(np.int64))
     assert np.all(dc <= refc.near.astype(np.int64)), dc
     ctx.close()
+
+
+def test_prepare_from_pinned_host_memory(cuda_lib):
+    """X and mask in page-locked host memory (read by the kernels over the
+    host link) give results identical to device copies."""
+    B = cuda_lib
+    n, n1, P = 24, 12, 300
+    X, mask = synth.brain_field(n, n1, grid=(20, 24, 20), center=(10, 12, 10),
+                                semi_axes=(8, 10, 8), fwhm=4.0, effect=0.5, effect_radius=3.0,
+                                seed=6, device="cpu")
+    perms = torch.as_tensor(synth.perms_pcg32(n, P, seed=9)).cuda()
+    outs = []
+    for host in (False, True):
+        Xa = X.contiguous().pin_memory() if host else X.cuda()
+        ma = mask.to(torch.uint8).contiguous()
+        ma = ma.pin_memory() if host else ma.cuda()
+        ctx = B.pt_prepare(Xa, n1, ma)
+        outs.append([t.cpu() for t in B.maxnull_naive(ctx, perms, precision=2)])
+        ctx.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
