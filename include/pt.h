@@ -86,7 +86,10 @@ void pt_naive_opts_default(pt_naive_opts* o);
  * Per voxel it computes, in FP64, the mean and total sum of squares SS of the
  * n values, and stores the centred data scaled to unit norm,
  * Xn[j][s] = (x_s - mean_j) / sqrt(SS_j), in FP32 and as BF16 pieces; and the
- * observed statistic t_obs (identity labelling). Synchronises the stream.
+ * observed statistic t_obs (identity labelling). It waits on the stream
+ * while it runs (to size its buffers from the mask and valid-voxel counts and
+ * to report bad input); X and mask are no longer read once it returns, and
+ * its last kernel may still be running (stream order covers every later call).
  * Errors: PT_ERR_INVALID for bad sizes or a NaN/Inf in a mask voxel,
  * PT_ERR_NOMEM, PT_ERR_CUDA.
  */

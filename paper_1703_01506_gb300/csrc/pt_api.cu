@@ -351,7 +351,8 @@ void pt_destroy(pt_ctx* ctx) {
   pt::Buf* bufs[] = {&ctx->status,  &ctx->vox_grid, &ctx->valid_map, &ctx->t_obs64,
                      &ctx->Xraw,    &ctx->vstat,    &ctx->u_obs,     &ctx->Xn32,
                      &ctx->Xnb,     &ctx->labels,   &ctx->rowflag,   &ctx->blockflag,
-                     &ctx->maxkey,  &ctx->cnt,      &ctx->scratch,   &ctx->tcdesc};
+                     &ctx->maxkey,  &ctx->cnt,      &ctx->scratch,   &ctx->tcdesc,
+                     &ctx->moments};
   for (pt::Buf* b : bufs) b->release();
   delete ctx;
 }

@@ -65,6 +65,7 @@ struct pt_ctx {
   pt::Buf maxkey;       // uint64[P]
   pt::Buf cnt;          // uint32[v_valid + 1]; the last word counts observed-set rows
   pt::Buf scratch;      // misc
+  pt::Buf moments;      // pt_prepare's per-voxel FP64 moments (read by kernels it enqueues)
   pt::Buf tcdesc;       // device copy of the tensor-core launch descriptor
 
   // Profiling of the dominant kernel (events on `stream`).

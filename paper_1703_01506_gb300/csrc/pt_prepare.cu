@@ -436,17 +436,13 @@ pt_status compact(pt_ctx* ctx, const uint8_t* flags, int64_t N, IdxT* out, uint3
 
 pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
   cudaStream_t st = ctx->stream;
-  Buf tmp, tmp2, mom;
+  Buf& tmp = ctx->scratch;  // scan scratch, kept by the context (kernels may still read it)
+  Buf tmp2;
   struct Guard {
-    Buf* a;
     Buf* b;
-    Buf* c;
-    ~Guard() {
-      a->release();
-      b->release();
-      c->release();
-    }
-  } guard{&tmp, &tmp2, &mom};
+    ~Guard() { b->release(); }
+  } guard{&tmp2};
+  Buf& mom = ctx->moments;
   if (!ctx->status.ensure(2 * sizeof(uint32_t))) return nomem(ctx, "status");
   PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(uint32_t), st));
 
@@ -523,7 +519,6 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
       ctx->vstat.as<float4>(), ctx->u_obs.as<float>());
   PT_LAUNCH_CHECK(ctx);
   ctx->have_xn32 = ctx->have_xnb = false;
-  PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));  // mom is released on return
   return PT_OK;
 }
 
