@@ -31,6 +31,25 @@ __device__ __forceinline__ uint32_t unpack_key_index(unsigned long long key) {
   return ~static_cast<uint32_t>(key & 0xffffffffull);
 }
 
+// ---- float-float arithmetic (an unevaluated pair h + l, ~44 significant bits) ----
+// s + e = a + b exactly (Knuth's branch-free two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (h, l) += (bh, bl), renormalised so that |l| <= ulp(h)/2.
+__device__ __forceinline__ void ff_acc(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+__device__ __forceinline__ double ff_d(float h, float l) { return double(h) + double(l); }
+
 // ---- bounded waits ----
 // Every spin-wait in this library gives up after kWaitLimitNs of wall time,
 // records kErrTimeout in the context's status word and returns false.

@@ -280,26 +280,48 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
     }
     __syncwarp();
     const float* x = Xraw + int64_t(valid_map[c]) * n_pad;  // Xraw is in masked order
-    double s1 = 0.0, s2 = 0.0;
+    // Two-pass group sums in float-float (FP32 pipes; ~44 significant bits) of
+    // the values scaled by the power of two that puts max |x| in [1, 2) (exact;
+    // squares cannot overflow; t does not depend on the scale), the means and
+    // the statistic in FP64.
+    float amax = 0.0f;
+    for (int s = lane; s < n; s += 32) amax = fmaxf(amax, fabsf(x[s]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    int ex = int((__float_as_uint(amax) >> 23) & 0xffu) - 127;
+    ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
+    const float scale = __uint_as_float(uint32_t(127 - ex) << 23);
+    float s1h = 0.0f, s1l = 0.0f, s2h = 0.0f, s2l = 0.0f;
     for (int s = lane; s < n; s += 32) {
-      const double xs = double(x[s]);
-      if ((g1[s >> 5] >> (s & 31)) & 1u) s1 += xs;
-      else s2 += xs;
+      const float xs = x[s] * scale;
+      if ((g1[s >> 5] >> (s & 31)) & 1u) ff_acc(s1h, s1l, xs, 0.0f);
+      else ff_acc(s2h, s2l, xs, 0.0f);
+    }
+    for (int o = 16; o > 0; o >>= 1) {  // two-sum is exact, so every lane ends with the same sums
+      const float a = __shfl_xor_sync(0xffffffffu, s1h, o), b = __shfl_xor_sync(0xffffffffu, s1l, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, s2h, o), d = __shfl_xor_sync(0xffffffffu, s2l, o);
+      ff_acc(s1h, s1l, a, b);
+      ff_acc(s2h, s2l, c2, d);
+    }
+    const double m1 = ff_d(s1h, s1l) * rc[0], m2 = ff_d(s2h, s2l) * rc[1];
+    const float m1h = float(m1), m1l = float(m1 - double(m1h));
+    const float m2h = float(m2), m2l = float(m2 - double(m2h));
+    float ssh = 0.0f, ssl = 0.0f;
+    for (int s = lane; s < n; s += 32) {
+      const bool in1 = (g1[s >> 5] >> (s & 31)) & 1u;
+      float dh, dl;
+      two_sum(x[s] * scale, in1 ? -m1h : -m2h, dh, dl);
+      dl -= in1 ? m1l : m2l;
+      const float tt = dh + dl;
+      dl = dl - (tt - dh);
+      dh = tt;
+      const float p = dh * dh;
+      ff_acc(ssh, ssl, p, fmaf(2.0f * dh, dl, fmaf(dh, dh, -p)));
     }
     for (int o = 16; o > 0; o >>= 1) {
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      const float a = __shfl_xor_sync(0xffffffffu, ssh, o), b = __shfl_xor_sync(0xffffffffu, ssl, o);
+      ff_acc(ssh, ssl, a, b);
     }
-    // Reciprocals per block and a reciprocal square root: FP64 divides and
-    // square roots are long FP64 sequences, and every warp instruction
-    // occupies the (narrow) FP64 pipe whatever its active lanes.
-    const double m1 = s1 * rc[0], m2 = s2 * rc[1];
-    double ss = 0.0;
-    for (int s = lane; s < n; s += 32) {
-      const double d = double(x[s]) - (((g1[s >> 5] >> (s & 31)) & 1u) ? m1 : m2);
-      ss += d * d;
-    }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double ss = ff_d(ssh, ssl);
     if (lane == 0) {
       const double t = (m1 - m2) * rsqrt(ss * rc[2]);
       maxnull[i] = float(two_sided ? fabs(t) : t);

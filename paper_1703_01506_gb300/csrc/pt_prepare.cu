@@ -15,6 +15,7 @@
 #include <string>
 
 #include "pt_internal.h"
+#include "pt_kernels.h"
 
 namespace pt {
 namespace {
@@ -134,23 +135,6 @@ __global__ void iota64_kernel(int64_t* __restrict__ out, int64_t N) {
 constexpr int kMV = 32;  // voxels per CTA (one per lane)
 constexpr int kMW = 8;   // warps per CTA; warp w sums subjects s = w, w + 8, ...
 
-// s + e = a + b exactly (Knuth's branch-free two-sum).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-// (h, l) += (bh, bl), renormalised so that |l| <= ulp(h)/2.
-__device__ __forceinline__ void ff_acc(float& h, float& l, float bh, float bl) {
-  float s, e;
-  two_sum(h, bh, s, e);
-  e += l + bl;
-  h = s + e;
-  l = e - (h - s);
-}
-
-__device__ __forceinline__ double ff_d(float h, float l) { return double(h) + double(l); }
 
 // 1/n, 1/n_1, 1/n_2 and (1/n_1 + 1/n_2)/(n - 2), rounded once on the host.
 struct MomentRecips {
