@@ -696,53 +696,53 @@ __global__ void u0_kernel(float* __restrict__ U, int64_t V, int R, int RP, uint3
   }
 }
 
-// Partial Gram U^T U in FP64 over a contiguous row range per block: upper
-// triangle pairs, products of FP32 values accumulated in FP64.
-__global__ void __launch_bounds__(1024) gram64_kernel(const float* __restrict__ U, int64_t V,
-                                                      int R, int RP,
-                                                      double* __restrict__ partials) {
-  extern __shared__ float sm[];
-  float* stage = sm;  // 32 x RP
+// Partial Gram matrices U^T U over row ranges, for the QR of U: 4 x 4 tiles of
+// the upper triangle per thread, products exact as float pairs (FMA residual)
+// and sums in float-float (~44 bits; the FP32 pipes are many times the FP64
+// rate here); each (block, row group) writes its tile sums as FP64 partials
+// indexed like the pairs (c <= d) of the factorisation.
+constexpr int kGramThreads = 256;
+__global__ void __launch_bounds__(kGramThreads) gram_ff_kernel(const float* __restrict__ U,
+                                                               int64_t V, int R, int RP,
+                                                               int ngroups,
+                                                               double* __restrict__ partials) {
+  const int RT = RP / 4, ntile = RT * (RT + 1) / 2;
   const int npairs = R * (R + 1) / 2;
   const int64_t per = (V + gridDim.x - 1) / gridDim.x;
   const int64_t j0 = blockIdx.x * per, j1 = min(V, j0 + per);
-  double acc[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
-  int pc[9], pd[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int pi = threadIdx.x + k * blockDim.x;
-    int c = 0, rem = pi < npairs ? pi : 0;
-    while (rem >= R - c) {
-      rem -= R - c;
-      ++c;
+  for (int t = threadIdx.x; t < ntile * ngroups; t += blockDim.x) {
+    const int tile = t % ntile, g = t / ntile;
+    int ti = 0, rem = tile;
+    while (rem >= RT - ti) {
+      rem -= RT - ti;
+      ++ti;
     }
-    pc[k] = c;
-    pd[k] = c + rem;
-  }
-  for (int64_t q0 = j0; q0 < j1; q0 += 32) {
-    const int rows = int(j1 - q0 < 32 ? j1 - q0 : 32);
-    for (int e = threadIdx.x; e < 32 * RP; e += blockDim.x) {
-      const int rr = e / RP;
-      stage[e] = rr < rows ? U[(q0 + rr) * RP + (e - rr * RP)] : 0.0f;
-    }
-    __syncthreads();
+    const int tj = ti + rem;
+    float h[4][4], l[4][4];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      if (threadIdx.x + k * blockDim.x < npairs) {
-        double t = acc[k];
-        for (int rr = 0; rr < rows; ++rr)
-          t = fma(double(stage[rr * RP + pc[k]]), double(stage[rr * RP + pd[k]]), t);
-        acc[k] = t;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) h[a][b] = l[a][b] = 0.0f;
+    for (int64_t j = j0 + g; j < j1; j += ngroups) {
+      const float4 u = *reinterpret_cast<const float4*>(U + j * RP + 4 * ti);
+      const float4 v = *reinterpret_cast<const float4*>(U + j * RP + 4 * tj);
+      const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float p = uu[a] * vv[b];
+          ff_acc(h[a][b], l[a][b], p, fmaf(uu[a], vv[b], -p));
+        }
+    }
+    double* out = partials + (int64_t(blockIdx.x) * ngroups + g) * npairs;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int c = 4 * ti + a, d = 4 * tj + b;
+        if (c <= d && d < R) out[c * R - c * (c - 1) / 2 + (d - c)] = ff_d(h[a][b], l[a][b]);
       }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int pi = threadIdx.x + k * blockDim.x;
-    if (pi < npairs) partials[int64_t(blockIdx.x) * npairs + pi] = acc[k];
   }
 }
 
@@ -1137,20 +1137,28 @@ __global__ void pack_u_kernel(const float* __restrict__ Uin, int64_t V, int R, i
   }
 }
 
-// Calls f(std::integral_constant<int, RP>) for the padded rank RP (16..128).
+// Padded rank RP: the rank rounded up to 4 (to 8 above 64), so rows of U stay
+// 16-byte aligned without wasting HBM traffic on padding columns (U is
+// streamed by every geodesic update).
+constexpr int padded_rank(int rank) { return rank <= 64 ? (rank + 3) / 4 * 4 : (rank + 7) / 8 * 8; }
+
+template <int RP, class F>
+bool with_rp_tail(int rp, F&& f) {
+  if constexpr (RP > kMaxRank) {
+    return false;
+  } else {
+    if (rp == RP) {
+      f(std::integral_constant<int, RP>{});
+      return true;
+    }
+    return with_rp_tail<(RP < 64 ? RP + 4 : RP + 8)>(rp, f);
+  }
+}
+
+// Calls f(std::integral_constant<int, RP>) for the padded rank RP (4..128).
 template <class F>
 bool with_rp(int rp, F&& f) {
-  switch (rp) {
-    case 16: f(std::integral_constant<int, 16>{}); return true;
-    case 32: f(std::integral_constant<int, 32>{}); return true;
-    case 48: f(std::integral_constant<int, 48>{}); return true;
-    case 64: f(std::integral_constant<int, 64>{}); return true;
-    case 80: f(std::integral_constant<int, 80>{}); return true;
-    case 96: f(std::integral_constant<int, 96>{}); return true;
-    case 112: f(std::integral_constant<int, 112>{}); return true;
-    case 128: f(std::integral_constant<int, 128>{}); return true;
-    default: return false;
-  }
+  return with_rp_tail<4>(rp, f);
 }
 
 int grid_n(int64_t work, int threads, int cap = 152 * 16) {
@@ -1242,7 +1250,7 @@ pt_status check_rapid_args(pt_ctx* ctx, int32_t rank, double sample_rate, const 
     return PT_ERR_INVALID;
   }
   pl.R = rank;
-  pl.RP = (rank + 15) / 16 * 16;
+  pl.RP = padded_rank(rank);
   pl.V = ctx->v_valid;
   pl.m = int(std::ceil(sample_rate * double(pl.V)));
   if (pl.m < rank) {
@@ -1256,13 +1264,16 @@ pt_status check_rapid_args(pt_ctx* ctx, int32_t rank, double sample_rate, const 
 
 // Orthonormalise U (V x RP) in place: FP64 Gram and factorisation, FP32 apply.
 pt_status qr_inplace(pt_ctx* ctx, float* U, const RapidPlan& pl, Buf& part, Buf& rinv) {
-  const int nparts = 152 * 2;
+  const int nblocks = 152 * 2;
+  const int ntile = (pl.RP / 4) * (pl.RP / 4 + 1) / 2;
+  const int ngroups = std::max(1, kGramThreads / ntile);
+  const int nparts = nblocks * ngroups;
   const int npairs = pl.R * (pl.R + 1) / 2;
   if (!part.ensure(sizeof(double) * size_t(nparts) * npairs) ||
       !rinv.ensure(sizeof(float) * pl.RP * pl.RP))
     return nomem_r(ctx, "QR");
-  const int gsm = 32 * pl.RP * int(sizeof(float));
-  gram64_kernel<<<nparts, 1024, gsm, ctx->stream>>>(U, pl.V, pl.R, pl.RP, part.as<double>());
+  gram_ff_kernel<<<nblocks, kGramThreads, 0, ctx->stream>>>(U, pl.V, pl.R, pl.RP, ngroups,
+                                                            part.as<double>());
   PT_LAUNCH_CHECK(ctx);
   const int fsm = (pl.R * pl.R + pl.R) * int(sizeof(double));
   if (fsm > 48 * 1024)
