@@ -319,37 +319,102 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
   for (int e = tid; e < R * R; e += blockDim.x) f.Gi[e] = 0.0f;
   __syncthreads();
   for (int c = tid; c < R; c += blockDim.x) f.Gi[c * R + c] = 1.0f;
-  // --- G^-1 by Gauss-Jordan (no pivoting: G is symmetric positive definite).
-  // Pivot k: the scaled pivot row goes to rowk and the column to fac (phase
-  // 1), then every row is updated from them (phase 2): two barriers a pivot.
-  float* fac = f.red;       // R
-  float* rowk = f.red + R;  // 2R: scaled pivot row of [G | G^-1]
+  // --- G^-1 by block Gauss-Jordan on [G | I] with 4 x 4 pivot blocks (no
+  // pivoting: G is symmetric positive definite, so every pivot block is too).
+  // Round k: every thread inverts the pivot block P in registers; the scaled
+  // pivot rows P^-1 [G | G^-1]_k go to rowk and the pivot columns to fac
+  // (phase 1); then every row is updated from them (phase 2): two barriers per
+  // four pivots.
+  float* fac = f.red;           // R x 4: pivot columns of the other rows
+  float* rowk = f.red + 4 * R;  // 4 x 2R: scaled pivot rows
   constexpr int kRowsPerWarp = (RP + kCluWarps - 1) / kCluWarps;
-  for (int k = 0; k < R; ++k) {
+  for (int k = 0; k < R; k += 4) {
+    const int bk = R - k < 4 ? R - k : 4;
     __syncthreads();
-    const float inv = 1.0f / f.G[k * R + k];
-    for (int j = tid; j < 2 * R; j += blockDim.x)
-      rowk[j] = (j < R ? f.G[k * R + j] : f.Gi[k * R + (j - R)]) * inv;
-    for (int i = tid; i < R; i += blockDim.x) fac[i] = (i == k) ? 0.0f : f.G[i * R + k];
+    float pi[4][4];  // P^-1 (Gauss-Jordan on the b x b block, padded with I)
+    {
+      float pa[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          pa[r][c] = (r < bk && c < bk) ? f.G[(k + r) * R + k + c] : (r == c ? 1.0f : 0.0f);
+          pi[r][c] = r == c ? 1.0f : 0.0f;
+        }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float inv = 1.0f / pa[q][q];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          pa[q][c] *= inv;
+          pi[q][c] *= inv;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (r == q) continue;
+          const float fr = pa[r][q];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            pa[r][c] = fmaf(-fr, pa[q][c], pa[r][c]);
+            pi[r][c] = fmaf(-fr, pi[q][c], pi[r][c]);
+          }
+        }
+      }
+    }
+    for (int e = tid; e < 4 * 2 * R; e += blockDim.x) {
+      const int r = e / (2 * R), j = e - r * 2 * R;
+      float t = 0.0f;
+      if (r < bk)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < bk)
+            t = fmaf(pi[r][c], j < R ? f.G[(k + c) * R + j] : f.Gi[(k + c) * R + (j - R)], t);
+      rowk[e] = t;
+    }
+    for (int e = tid; e < 4 * R; e += blockDim.x) {
+      const int i = e >> 2, c = e & 3;
+      fac[e] = (c < bk && (i < k || i >= k + bk)) ? f.G[i * R + k + c] : 0.0f;
+    }
     __syncthreads();
     // all loads of a thread's entries before its stores (the compiler cannot
     // reorder loads past stores through these aliasing shared pointers)
     for (int j = lane; j < R; j += 32) {
-      const float rg = rowk[j], ri = rowk[R + j];
-      float gv[kRowsPerWarp], hv[kRowsPerWarp], fv[kRowsPerWarp];
+      float rg[4], ri[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        rg[c] = rowk[c * 2 * R + j];
+        ri[c] = rowk[c * 2 * R + R + j];
+      }
+      float gv[kRowsPerWarp], hv[kRowsPerWarp];
+      float4 fv[kRowsPerWarp];
 #pragma unroll
       for (int t = 0; t < kRowsPerWarp; ++t) {
         const int i = warp + kCluWarps * t;
         gv[t] = i < R ? f.G[i * R + j] : 0.0f;
         hv[t] = i < R ? f.Gi[i * R + j] : 0.0f;
-        fv[t] = i < R ? fac[i] : 0.0f;
+        fv[t] = i < R ? *reinterpret_cast<const float4*>(fac + 4 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int t = 0; t < kRowsPerWarp; ++t) {
         const int i = warp + kCluWarps * t;
         if (i < R) {
-          f.G[i * R + j] = i == k ? rg : fmaf(-fv[t], rg, gv[t]);
-          f.Gi[i * R + j] = i == k ? ri : fmaf(-fv[t], ri, hv[t]);
+          if (i >= k && i < k + bk) {
+            const int r = i - k;  // selected without indexing the register arrays
+            f.G[i * R + j] = r == 0 ? rg[0] : r == 1 ? rg[1] : r == 2 ? rg[2] : rg[3];
+            f.Gi[i * R + j] = r == 0 ? ri[0] : r == 1 ? ri[1] : r == 2 ? ri[2] : ri[3];
+          } else {
+            float g = gv[t], h = hv[t];
+            g = fmaf(-fv[t].x, rg[0], g);
+            h = fmaf(-fv[t].x, ri[0], h);
+            g = fmaf(-fv[t].y, rg[1], g);
+            h = fmaf(-fv[t].y, ri[1], h);
+            g = fmaf(-fv[t].z, rg[2], g);
+            h = fmaf(-fv[t].z, ri[2], h);
+            g = fmaf(-fv[t].w, rg[3], g);
+            h = fmaf(-fv[t].w, ri[3], h);
+            f.G[i * R + j] = g;
+            f.Gi[i * R + j] = h;
+          }
         }
       }
     }
