@@ -104,7 +104,7 @@ constexpr int kCluThreads = 512;  // 16 warps per CTA
 constexpr int kCluWarps = kCluThreads / 32;
 
 struct CluSmem {
-  float* A;      // mloc x RS, RS = RP + 4 (16-byte rows; row-wise float4 reads conflict-free)
+  float* A;      // mloc x clu_rs(RP)
   float* b;      // mloc each: b, s, y, x
   float* s;
   float* y;
@@ -123,9 +123,14 @@ struct CluSmem {
 };
 constexpr int kSlot = kMaxRank + 8;
 
+// Row stride of A in shared memory: 16-byte rows whose stride in 16-byte units
+// is odd, so a warp reading 32 different rows in float4 steps hits every bank
+// group once per four lanes (and column-wise reads stay conflict-free).
+__host__ __device__ constexpr int clu_rs(int RP) { return (RP / 4) % 2 == 0 ? RP + 4 : RP + 8; }
+
 __host__ __device__ inline size_t clu_carve(float* base, int mloc, int R, int RP, int n_pad,
                                             CluSmem* f) {
-  const int RS = RP + 4;
+  const int RS = clu_rs(RP);
   size_t o = 0;
   auto take = [&](size_t nfl) {
     float* p = base ? base + o : nullptr;
@@ -184,7 +189,7 @@ __device__ __forceinline__ void clu_sum(cg::cluster_group& cl, const CluSmem& f,
 template <int RP>
 __device__ __forceinline__ void clu_AtX(const CluSmem& f, int mloc, int R, const float* x,
                                         float* out) {
-  constexpr int RS = RP + 4, KC = (RP + 31) / 32;
+  constexpr int RS = clu_rs(RP), KC = (RP + 31) / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   float acc[KC];
 #pragma unroll
@@ -243,47 +248,58 @@ __device__ __forceinline__ float clu_row_dot(const float* row, const float* v) {
 
 // Gram G = A^T A over the cluster, then G^-1 (Gauss-Jordan, no pivoting: G is
 // symmetric positive definite), then ADMM; leaves w in f.wv (zero-padded to RP).
-// In the ADMM loop warp w owns the local rows q = w, w + 8, ... and lane l the
-// columns l + 32k: one pass over a warp's rows applies the s, y update of the
-// current iteration and accumulates A^T x of the next one, so an iteration
-// costs one block barrier and one cluster barrier.
+// An ADMM iteration: A^T x over the CTA's rows, one cluster barrier and a
+// rank-ordered gather of the R-vector, w = G^-1 v, then the s, y, x updates
+// with one thread per row.
 template <int RP>
 __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, int R, float rho,
                            int iters, int CL, int& par) {
-  constexpr int RS = RP + 4, KC = (RP + 31) / 32;
+  constexpr int RS = clu_rs(RP), KC = (RP + 31) / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int RG = (R + 3) / 4 * 4;
-  // --- local Gram partial by 4x4 register tiles of the upper triangle ---
+  // --- local Gram partial by 4x4 register tiles of the upper triangle; the
+  // rows are split over ngr thread groups whose sums are added in group order
   constexpr int RT = RP / 4;
   const int ntile = RT * (RT + 1) / 2;
-  for (int t = tid; t < ntile; t += blockDim.x) {
-    int ti = 0, rem = t;
-    while (rem >= RT - ti) {
-      rem -= RT - ti;
-      ++ti;
-    }
-    const int tj = ti + rem;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.0f;
-    for (int q = 0; q < mloc; ++q) {
-      const float4 u = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * ti);
-      const float4 v = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * tj);
-      const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+  const int ngr = ntile >= int(blockDim.x) ? 1 : int(blockDim.x) / ntile;
+  for (int g = 0; g < ngr; ++g) {
+    for (int t = tid; t < ntile * ngr; t += blockDim.x) {
+      const int tile = t % ntile, grp = t / ntile;
+      int ti = 0, rem = tile;
+      while (rem >= RT - ti) {
+        rem -= RT - ti;
+        ++ti;
+      }
+      const int tj = ti + rem;
+      float acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(uu[a], vv[b2], acc[a][b2]);
-    }
+        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.0f;
+      if (grp == g || ngr == 1) {
+        for (int q = (ngr == 1 ? 0 : grp); q < mloc; q += ngr) {
+          const float4 u = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * ti);
+          const float4 v = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * tj);
+          const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) {
-        const int c = 4 * ti + a, d = 4 * tj + b2;
-        if (c < R && d < RG) f.Gp[c * RG + d] = (c <= d && d < R) ? acc[a][b2] : 0.0f;
+            for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(uu[a], vv[b2], acc[a][b2]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b2 = 0; b2 < 4; ++b2) {
+            const int c = 4 * ti + a, d = 4 * tj + b2;
+            if (c < R && d < RG) {
+              const float val = (c <= d && d < R) ? acc[a][b2] : 0.0f;
+              f.Gp[c * RG + d] = g == 0 ? val : f.Gp[c * RG + d] + val;
+            }
+          }
       }
+    }
+    if (ngr == 1) break;
+    __syncthreads();
   }
   __syncthreads();
   cl.sync();
@@ -421,27 +437,28 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
   }
   __syncthreads();  // fac and rowk (in red) are read until here
   // --- ADMM on min ||s||_1 s.t. A w + s = b (s = y = 0 at the start, so x = b).
-  // Warp w owns the local rows q = w, w + 8, ... and lane l the columns
-  // l + 32k; one pass over a warp's rows (four at a time) applies the s, y
-  // update of the current iteration and accumulates A^T x of the next one.
+  // A^T x: warp w takes the local rows q = w, w + 16, ... and lane l the
+  // columns l + 32k. The s, y, x updates take one thread per row (its dot
+  // product with w in float4 steps), so no shuffles are needed there.
   const float irho = 1.0f / rho;
-  float acc[KC];
-#pragma unroll
-  for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
-  for (int q = warp; q < mloc; q += kCluWarps) {
-    const float xq = f.b[q];
-    if (lane == 0) {
-      f.s[q] = 0.0f;
-      f.y[q] = 0.0f;
-    }
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      const int c = lane + 32 * k;
-      if (c < RP) acc[k] = fmaf(f.A[q * RS + c], xq, acc[k]);
-    }
+  for (int q = tid; q < mloc; q += blockDim.x) {
+    f.s[q] = 0.0f;
+    f.y[q] = 0.0f;
+    f.x[q] = f.b[q];
   }
   for (int it = 0; it < iters; ++it) {
-    // A^T x: warps -> this CTA's slot -> cluster sum (threads c < R)
+    __syncthreads();
+    float acc[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
+    for (int q = warp; q < mloc; q += kCluWarps) {
+      const float xq = f.x[q];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        const int c = lane + 32 * k;
+        if (c < RP) acc[k] = fmaf(f.A[q * RS + c], xq, acc[k]);
+      }
+    }
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       const int c = lane + 32 * k;
@@ -462,7 +479,7 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
     // w = G^-1 v (G^-1 symmetric: column c read along d, conflict-free); the
     // d range is split over kCluWarps / KC groups, partials summed in order
     {
-      constexpr int NG = kCluWarps / KC;  // groups of KC warps: one column each per lane
+      constexpr int NG = kCluWarps / KC;
       const int g = warp / KC, c = lane + 32 * (warp % KC);
       const int per = (R + NG - 1) / NG, d0 = g * per, d1 = min(R, d0 + per);
       float t = 0.0f;
@@ -470,63 +487,29 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
         for (int d = d0; d < d1; ++d) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
       if (c < RP) f.red[g * RP + c] = t;
       __syncthreads();
-      for (int c2 = tid; c2 < R; c2 += blockDim.x) {
+      for (int c2 = tid; c2 < RP; c2 += blockDim.x) {
         float w = 0.0f;
+        if (c2 < R)
 #pragma unroll
-        for (int gg = 0; gg < NG; ++gg) w += f.red[gg * RP + c2];
+          for (int gg = 0; gg < NG; ++gg) w += f.red[gg * RP + c2];
         f.wv[c2] = w;
       }
       __syncthreads();
     }
-    float wc[KC];
-#pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      const int c = lane + 32 * k;
-      wc[k] = c < R ? f.wv[c] : 0.0f;
-      acc[k] = 0.0f;
-    }
-    // rows: s, y update of this iteration, then A^T x of the next
-    for (int q0 = warp; q0 < mloc; q0 += 4 * kCluWarps) {
-      float a[4][KC], p[4], bv[4], yv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + u * kCluWarps;
-        bv[u] = q < mloc ? f.b[q] : 0.0f;
-        yv[u] = q < mloc ? f.y[q] : 0.0f;
-        p[u] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-          const int c = lane + 32 * k;
-          a[u][k] = (q < mloc && c < RP) ? f.A[q * RS + c] : 0.0f;
-          p[u] = fmaf(a[u][k], wc[k], p[u]);
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) p[u] += __shfl_xor_sync(0xffffffffu, p[u], o);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = q0 + u * kCluWarps;
-        if (q >= mloc) break;
-        const float bq = bv[u], yq = yv[u];
-        const float e = bq - p[u] - yq * irho;
-        const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
-        const float yn = yq + rho * (p[u] + sq - bq);
-        const float xn = bq - sq - yn * irho;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) acc[k] = fmaf(a[u][k], xn, acc[k]);
-        __syncwarp();
-        if (lane == 0) {
-          f.s[q] = sq;
-          f.y[q] = yn;
-        }
-      }
+    // rows: s, y update of this iteration and x of the next
+    for (int q = tid; q < mloc; q += blockDim.x) {
+      const float aw = clu_row_dot<RP>(f.A + q * RS, f.wv);
+      const float bq = f.b[q], yq = f.y[q];
+      const float e = bq - aw - yq * irho;
+      const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
+      const float yn = yq + rho * (aw + sq - bq);
+      f.s[q] = sq;
+      f.y[q] = yn;
+      f.x[q] = bq - sq - yn * irho;
     }
   }
-  // f.wv holds the last iteration's w (entries c >= R are zero)
-  for (int c = R + tid; c < RP; c += blockDim.x) f.wv[c] = 0.0f;
   __syncthreads();
+  // f.wv holds the last iteration's w (entries c >= R are zero)
 }
 
 // Rows [q0, q0 + mloc) of the m sampled rows belong to cluster rank `rank`.
@@ -559,7 +542,7 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
   extern __shared__ __align__(16) float smc[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = int(cl.block_rank());
-  constexpr int RS = RP + 4;
+  constexpr int RS = clu_rs(RP);
   int q0, mloc;
   clu_rows(a.m, a.CL, rank, q0, mloc);
   CluSmem f;
@@ -713,7 +696,7 @@ __global__ void __launch_bounds__(kCluThreads, 1) recover_fit_cluster_kernel(Clu
   cg::cluster_group cl = cg::this_cluster();
   const int rank = int(cl.block_rank());
   const int64_t cid = blockIdx.x / a.CL, ncl = gridDim.x / a.CL;
-  constexpr int RS = RP + 4;
+  constexpr int RS = clu_rs(RP);
   int q0, mloc;
   clu_rows(a.m, a.CL, rank, q0, mloc);
   CluSmem f;
