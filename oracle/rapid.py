@@ -80,13 +80,17 @@ class draws:
 
     normal(tag, a, b)      z = sqrt(-2 ln u1) cos(2 pi u2) from words (x0, x1),
                            u1 = (x0 + 1) 2^-32, u2 = x1 2^-32   (counter (a, b, 0, tag))
+    voxel_normal(tag, j, b) both Box-Muller normals of one counter serve a pair
+                           of voxels: sqrt(-2 ln u1) cos(2 pi u2) for even j and
+                           sqrt(-2 ln u1) sin(2 pi u2) for odd j, with u1, u2 from
+                           counter (floor(j / 2), b, 0, tag)
     index(tag, q, i, p, v) floor((x1 2^32 + x0) v / 2^64)         (counter (q, i, p, tag))
 
     U0[j, c]            = normal(TAG_U0, j, c)
     training sample q   = index(TAG_TRAIN, q, i, pass, v)   of column i in a pass
     recovery sample q   = index(TAG_REC, q, i, 0, v)        of relabelling i
-    recovery noise      = normal(TAG_NOISE, j, i)           at voxel j, relabelling i
-    shift-estimate noise= normal(TAG_SHIFT, j, i)           at voxel j, training column i
+    recovery noise      = voxel_normal(TAG_NOISE, j, i)     at voxel j, relabelling i
+    shift-estimate noise= voxel_normal(TAG_SHIFT, j, i)     at voxel j, training column i
     """
 
     def __init__(self, seed):
@@ -100,6 +104,15 @@ class draws:
         u1 = (x0.astype(np.float64) + 1.0) * 2.0 ** -32
         u2 = x1.astype(np.float64) * 2.0 ** -32
         return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+    def voxel_normal(self, tag, j, b):
+        j = np.asarray(j, dtype=np.uint64)
+        x0, x1, _, _ = self.words(j >> np.uint64(1), b, 0, tag)
+        u1 = (x0.astype(np.float64) + 1.0) * 2.0 ** -32
+        u2 = x1.astype(np.float64) * 2.0 ** -32
+        r = np.sqrt(-2.0 * np.log(u1))
+        return np.where((j & np.uint64(1)) == 0, r * np.cos(2.0 * np.pi * u2),
+                        r * np.sin(2.0 * np.pi * u2))
 
     def index(self, tag, q, i, p, v):
         x0, x1, _, _ = self.words(q, i, p, tag)
@@ -234,7 +247,7 @@ def rapid_train(X, n1, perms, rank, sample_rate, n_train, opts=None):
     else:
         gaps = np.empty(ell)
         for i in range(ell):
-            z = dr.normal(TAG_SHIFT, np.arange(V), i)
+            z = dr.voxel_normal(TAG_SHIFT, np.arange(V), i)
             gaps[i] = np.max(T_ex[i]) - np.max(model[i] + sigma * z)
         mu = float(np.mean(gaps))
     T_obs = rows(np.arange(n, dtype=np.int32)[None, :])[0]
@@ -263,7 +276,7 @@ def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=F
         tt = entries(int(i), idx)
         w, _, _ = admm_l1(U[idx], tt, o.admm_rho, o.admm_iters)
         ws.append(w)
-        z = dr.normal(TAG_NOISE, np.arange(V), int(i))
+        z = dr.voxel_normal(TAG_NOISE, np.arange(V), int(i))
         out[k] = np.max(U @ w + sigma * z) + mu
     return (out, np.array(ws)) if return_w else out
 

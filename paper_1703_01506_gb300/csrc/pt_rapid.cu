@@ -84,6 +84,21 @@ __device__ __forceinline__ float draw_normal(uint32_t k0, uint32_t k1, uint32_t 
   return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
+// Both Box-Muller normals of one counter serve the voxel pair (2p, 2p + 1):
+// r cos(2 pi u2) for the even voxel, r sin(2 pi u2) for the odd one.
+__device__ __forceinline__ void draw_normal_pair(uint32_t k0, uint32_t k1, uint32_t tag,
+                                                 uint32_t pair, uint32_t b, float& z_even,
+                                                 float& z_odd) {
+  const uint4 o = philox(make_uint4(pair, b, 0u, tag), k0, k1);
+  const float u1 = fmaf(__uint2float_rn(o.x), 2.3283064365386963e-10f, 2.3283064365386963e-10f);
+  const float u2 = __uint2float_rn(o.y) * 2.3283064365386963e-10f;
+  const float r = sqrtf(-2.0f * logf(u1));
+  float sv, cv;
+  sincospif(2.0f * u2, &sv, &cv);
+  z_even = r * cv;
+  z_odd = r * sv;
+}
+
 __device__ __forceinline__ uint32_t draw_index(uint32_t k0, uint32_t k1, uint32_t tag, uint32_t q,
                                                uint32_t i, uint32_t p, uint32_t V) {
   const uint4 o = philox(make_uint4(q, i, p, tag), k0, k1);
@@ -1086,22 +1101,31 @@ __global__ void __launch_bounds__(256) reconstruct_max_kernel(ReconArgs a) {
       const int64_t row = r0 + ((p < 4) ? (ty * 4 + p) : (64 + ty * 4 + p - 4));
       if (row >= a.rows) continue;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      // columns in pairs (even, odd): one counter's two normals serve both
+      for (int q = 0; q < 8; q += 2) {
         const int64_t col = c0 + ((q < 4) ? (tx * 4 + q) : (64 + tx * 4 + q - 4));
-        if (col >= a.V) continue;
-        float val = acc[p][q];
-        if (a.mode == 1) {
-          val = a.Tex[row * a.V + col] - val;
-        } else {
-          if (val + bound < M[p]) continue;
-          val = fmaf(a.sigma, draw_normal(a.k0, a.k1, a.tag, uint32_t(col),
-                                          uint32_t(a.row_label0 + row)), val);
+        float z[2] = {0.0f, 0.0f};
+        if (a.mode == 0 && (acc[p][q] + bound >= M[p] || acc[p][q + 1] + bound >= M[p]) &&
+            col < a.V)
+          draw_normal_pair(a.k0, a.k1, a.tag, uint32_t(col >> 1), uint32_t(a.row_label0 + row),
+                           z[0], z[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t cc = col + h;
+          if (cc >= a.V) continue;
+          float val = acc[p][q + h];
+          if (a.mode == 1) {
+            val = a.Tex[row * a.V + cc] - val;
+          } else {
+            if (val + bound < M[p]) continue;
+            val = fmaf(a.sigma, z[h], val);
+          }
+          if (val > best[p] || (val == best[p] && uint32_t(cc) < bj[p])) {
+            best[p] = val;
+            bj[p] = uint32_t(cc);
+          }
+          M[p] = fmaxf(M[p], val);
         }
-        if (val > best[p] || (val == best[p] && uint32_t(col) < bj[p])) {
-          best[p] = val;
-          bj[p] = uint32_t(col);
-        }
-        M[p] = fmaxf(M[p], val);
       }
       // share the running maximum among the 16 threads of this row
       float mm = M[p];
