@@ -459,10 +459,11 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
   float* u_obs_m = reinterpret_cast<float*>(inv_norm + vv);
   uint8_t* valid = reinterpret_cast<uint8_t*>(u_obs_m + vv);
   if (v > 0) {
+    // dynamic tile plus ~7 KB of static partials: the opt-in is needed from
+    // well below 48 KB of dynamic memory, so it is always set
     const int smem = ctx->n * (kMV + 1) * int(sizeof(float));
-    if (smem > 48 * 1024)
-      PT_CUDA_TRY(ctx, cudaFuncSetAttribute(moments_kernel,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PT_CUDA_TRY(ctx, cudaFuncSetAttribute(moments_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     moments_kernel<<<unsigned((v + kMV - 1) / kMV), 32 * kMW, smem, st>>>(
         X, ctx->n_grid, ctx->n, ctx->n1, n_pad,
         MomentRecips{1.0 / ctx->n, 1.0 / ctx->n1, 1.0 / ctx->n2, ctx->k / (ctx->n - 2)},

@@ -75,7 +75,8 @@ def test_parity_gauss_n20_v2000(cuda_lib, precision, two_sided):
 
 @pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("n,n1,v,P", [(37, 15, 1007, 300), (100, 50, 3000, 1000),
-                                      (3, 1, 129, 5), (64, 63, 513, 129), (200, 100, 700, 260)])
+                                      (3, 1, 129, 5), (64, 63, 513, 129), (200, 100, 700, 260),
+                                      (360, 180, 700, 130)])
 def test_parity_ragged_shapes(cuda_lib, precision, n, n1, v, P):
     X = synth.two_group_gaussian(n1, n - n1, v, frac=0.02, effect=1.0, seed=n + v)
     perms = synth.perms_pcg32(n, P, seed=7)
