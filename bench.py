@@ -215,7 +215,7 @@ def hist_kl(p_samples, q_samples, bins=100):
     return float(np.sum(pp[m] * np.log(pp[m] / qq[m])))
 
 
-def rapid_leg(dev, B, synth, torch):
+def rapid_leg(dev, B, synth, torch, passes=10, rows=None):
     """RapidPT vs NaivePT max-null wall time on the RapidPT workload (n=200,
     500,000 voxels, 100,000 relabellings, r=50, 400 training rows, 0.35%
     sampling): each method's time from pt_prepare to the max-null vector, with
@@ -223,7 +223,7 @@ def rapid_leg(dev, B, synth, torch):
     name = "brain_n200_v500k"
     w = synth.workload(name, device=dev)
     X, mask, n1 = w["X"], w["mask"], w["n1"]
-    perms = torch.as_tensor(w["perms"]).to(dev)
+    perms = torch.as_tensor(w["perms"][:rows] if rows else w["perms"]).to(dev)
     P, r, ell, eta = perms.shape[0], w["rank"], w["n_train"], w["sample_rate"]
     stream = torch.cuda.current_stream(dev)
     mx_naive = torch.empty(P, dtype=torch.float32, device=dev)
@@ -237,7 +237,7 @@ def rapid_leg(dev, B, synth, torch):
         c.close()
         return v
 
-    opts = B.rapid_opts()
+    opts = B.rapid_opts(train_passes=passes)
     mx_rapid = torch.empty(P, dtype=torch.float32, device=dev)
     phase = {}
 
@@ -355,6 +355,16 @@ def batched_leg(dev, B, synth, torch, studies=64, P=10000):
 
 
 def run_ours(args):
+    if args.rapid_only:
+        import torch
+        from paper_1703_01506_gb300 import binding as B
+        from paper_1703_01506_gb300 import synth
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        B.load()
+        print(json.dumps({"rapidpt": rapid_leg(dev, B, synth, torch, args.rapid_passes,
+                                                args.rapid_rows)}), flush=True)
+        return
     import torch
     import torch.distributed as dist
     from paper_1703_01506_gb300 import binding as B
@@ -527,7 +537,7 @@ def run_ours(args):
         "maxnull_wall_ms": ms,
     }
     if ws == 1 and not args.no_rapid:
-        line["rapidpt"] = rapid_leg(dev, B, synth, torch)
+        line["rapidpt"] = rapid_leg(dev, B, synth, torch, args.rapid_passes, args.rapid_rows)
     if ws == 1 and not args.no_batched:
         line["batched"] = batched_leg(dev, B, synth, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -550,6 +560,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rapid-passes", type=int, default=10,
+                    help="RapidPT training passes in the RapidPT leg (default 10)")
+    ap.add_argument("--rapid-rows", type=int, default=0,
+                    help="relabellings of the RapidPT leg (default all 100,000)")
+    ap.add_argument("--rapid-only", action="store_true",
+                    help="run the RapidPT leg alone (profiling); prints only its object")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-study batched leg")
     ap.add_argument("--no-rapid", action="store_true",
