@@ -229,6 +229,20 @@ pt_status pt_sync(pt_ctx* ctx);
  * Enqueued on the context's stream. */
 pt_status pt_t_obs(pt_ctx* ctx, float* t_obs);
 
+/*
+ * pt_fwer_pvalues -- FWER-corrected p-value of every mask voxel from a
+ * max-null (Sec. 2: the share of the permutation distribution of the maximum
+ * statistic at or above the voxel's observed statistic; the observed
+ * labelling counts as one of the P + 1):
+ *   p_j = (1 + #{i : maxnull_i >= T_j}) / (P + 1),  T_j = t_obs_j (|t_obs_j| if two_sided),
+ * compared as float32 values.
+ *   maxnull : device, float32[P] (from pt_maxnull_naive / _rapid with the same sidedness).
+ *   p_out   : device, float32[v] in masked order; NaN where the voxel has no t.
+ * Asynchronous on the context's stream. The smallest attainable value is 1/(P + 1).
+ */
+pt_status pt_fwer_pvalues(pt_ctx* ctx, const float* maxnull, int64_t P, int32_t two_sided,
+                          float* p_out);
+
 /* grid_index: device int64[v]: grid column of each masked-order voxel. */
 pt_status pt_voxel_grid_index(pt_ctx* ctx, int64_t* grid_index);
 

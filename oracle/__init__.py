@@ -142,3 +142,24 @@ def t_entries(Xt, n1, perms, rows, idx):
     if rc != 0:
         raise ValueError("oracle_t_entries failed (rc=%d)" % rc)
     return out
+
+
+def fwer_pvalues(maxnull, t_obs, two_sided=False):
+    """FWER-corrected p-value of every voxel from a max-null (Sec. 2: the
+    fraction of the permutation distribution of the maximum at or above the
+    voxel's observed statistic), counting the observed labelling as one of
+    the P + 1 labellings: p_j = (1 + #{i : m_i >= T_j}) / (P + 1), with
+    T_j = t_obs_j (|t_obs_j| two-sided). The comparison is made on float32
+    values, as the library stores both. Voxels without a statistic get NaN.
+    Brute force over all (voxel, relabelling) pairs."""
+    m = np.asarray(maxnull, dtype=np.float32)
+    t = np.asarray(t_obs, dtype=np.float64).astype(np.float32)
+    T = np.abs(t) if two_sided else t
+    P = m.shape[0]
+    out = np.full(T.shape[0], np.nan)
+    ok = ~np.isnan(T)
+    ms = np.sort(m)
+    # #{i : m_i >= T_j} = P - #{i : m_i < T_j}
+    below = np.searchsorted(ms, T[ok], side="left")
+    out[ok] = (1.0 + (P - below)) / (P + 1.0)
+    return out

@@ -66,6 +66,7 @@ def load(path=None):
         "pt_maxnull_naive_batched": (ctypes.c_int, [_VP, i32, _VP, _VP,
                                                     ctypes.POINTER(pt_naive_opts), _VP, _VP,
                                                     _VP]),
+        "pt_fwer_pvalues": (ctypes.c_int, [_VP, _VP, i64, i32, _VP]),
         "pt_sync": (ctypes.c_int, [_VP]),
         "pt_t_obs": (ctypes.c_int, [_VP, _VP]),
         "pt_voxel_grid_index": (ctypes.c_int, [_VP, _VP]),
@@ -195,6 +196,11 @@ def pt_maxnull_naive_batched(ctxs, perms, opts, maxnull, argmax, counts=None):
 
 def pt_sync(ctx):
     _check(load().pt_sync(ctx.handle), ctx.handle)
+
+
+def pt_fwer_pvalues(ctx, maxnull, p_out, two_sided=False):
+    _check(load().pt_fwer_pvalues(ctx.handle, _ptr(maxnull), maxnull.shape[0], int(bool(two_sided)),
+                                  _ptr(p_out)), ctx.handle)
 
 
 def pt_t_obs(ctx, t_obs):

@@ -262,6 +262,28 @@ pt_status pt_maxnull_naive(pt_ctx* ctx, const int32_t* perms, int64_t P, float* 
   return pt_maxnull_naive_ex(ctx, perms, P, nullptr, maxnull, argmax, counts);
 }
 
+pt_status pt_fwer_pvalues(pt_ctx* ctx, const float* maxnull, int64_t P, int32_t two_sided,
+                          float* p_out) {
+  if (!ctx) {
+    pt::set_thread_error("pt_fwer_pvalues: ctx is NULL");
+    return PT_ERR_INVALID;
+  }
+  if (!maxnull || !p_out || P < 1 || two_sided < 0 || two_sided > 1) {
+    set_error(ctx, "pt_fwer_pvalues: need maxnull, p_out non-NULL, P >= 1, two_sided 0 or 1");
+    return PT_ERR_INVALID;
+  }
+  try {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) {
+      set_error(ctx, "pt_fwer_pvalues: cudaSetDevice failed");
+      return PT_ERR_CUDA;
+    }
+    return pt::fwer_pvalues_impl(ctx, maxnull, P, two_sided, p_out);
+  } catch (...) {
+    set_error(ctx, "pt_fwer_pvalues: internal error");
+    return PT_ERR_CUDA;
+  }
+}
+
 pt_status pt_sync(pt_ctx* ctx) {
   if (!ctx) {
     pt::set_thread_error("pt_sync: ctx is NULL");

@@ -105,6 +105,8 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
 pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
                              const int64_t* P, const pt_naive_opts& o, float* const* maxnull,
                              int32_t* const* argmax, uint32_t* const* counts);
+pt_status fwer_pvalues_impl(pt_ctx* ctx, const float* maxnull, int64_t P, int two_sided,
+                            float* p_out);
 // Drops a cached batched graph that names this context (from pt_destroy).
 void batch_forget(const pt_ctx* ctx);
 

@@ -342,6 +342,43 @@ __global__ void scatter_counts_kernel(const uint32_t* __restrict__ cnt, int64_t 
     counts[valid_map[c]] = cnt[c] + ties;
 }
 
+// FWER-corrected p-values: p_j = (1 + #{i : m_i >= T_j}) / (P + 1) over the
+// max-null, T_j the voxel's observed statistic (float32 on both sides of the
+// comparison). Brute force: each thread one voxel, the maxima streamed through
+// shared memory in tiles.
+constexpr int kPvalTile = 4096;
+__global__ void __launch_bounds__(256) fwer_pvalues_kernel(const float* __restrict__ maxnull,
+                                                           int64_t P,
+                                                           const double* __restrict__ t_obs64,
+                                                           int64_t v, int two_sided,
+                                                           float* __restrict__ p_out) {
+  __shared__ float tile[kPvalTile];
+  const int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  float T = NAN;
+  if (j < v) {
+    T = float(t_obs64[j]);
+    if (two_sided) T = fabsf(T);
+  }
+  uint32_t cnt = 0;
+  for (int64_t i0 = 0; i0 < P; i0 += kPvalTile) {
+    const int len = int(P - i0 < kPvalTile ? P - i0 : kPvalTile);
+    __syncthreads();
+    for (int k = threadIdx.x; k < len; k += blockDim.x) tile[k] = maxnull[i0 + k];
+    __syncthreads();
+    int k = 0;
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    for (; k + 3 < len; k += 4) {
+      c0 += tile[k] >= T;
+      c1 += tile[k + 1] >= T;
+      c2 += tile[k + 2] >= T;
+      c3 += tile[k + 3] >= T;
+    }
+    for (; k < len; ++k) c0 += tile[k] >= T;
+    cnt += c0 + c1 + c2 + c3;
+  }
+  if (j < v) p_out[j] = isnan(T) ? NAN : float((1.0 + double(cnt)) / (double(P) + 1.0));
+}
+
 static int grid_1d(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -431,6 +468,16 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
         ctx->cnt.as<uint32_t>(), ctx->v_valid, ctx->valid_map.as<int32_t>(), counts);
     PT_LAUNCH_CHECK(ctx);
   }
+  return PT_OK;
+}
+
+pt_status fwer_pvalues_impl(pt_ctx* ctx, const float* maxnull, int64_t P, int two_sided,
+                            float* p_out) {
+  if (ctx->v < 1) return PT_OK;
+  const int64_t blocks = (ctx->v + 255) / 256;
+  fwer_pvalues_kernel<<<unsigned(blocks), 256, 0, ctx->stream>>>(
+      maxnull, P, ctx->t_obs64.as<double>(), ctx->v, two_sided, p_out);
+  PT_LAUNCH_CHECK(ctx);
   return PT_OK;
 }
 

@@ -223,3 +223,25 @@ def test_prepare_from_pinned_host_memory(cuda_lib):
         ctx.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("two_sided", [False, True])
+def test_fwer_pvalues_match_oracle(cuda_lib, two_sided):
+    """Corrected p-values from the GPU max-null equal the oracle's definition
+    applied to the same float32 max-null and observed statistics."""
+    B = cuda_lib
+    n, n1, v, P = 30, 15, 3000, 5000
+    X = synth.two_group_gaussian(n1, n - n1, v, frac=0.02, effect=1.5, seed=4)
+    perms = synth.perms_pcg32(n, P, seed=2)
+    ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1)
+    pd = torch.as_tensor(perms).cuda()
+    mx, _, _ = B.maxnull_naive(ctx, pd, precision=2, two_sided=two_sided)
+    t = torch.empty(v, dtype=torch.float32, device="cuda")
+    B.pt_t_obs(ctx, t)
+    p = torch.empty(v, dtype=torch.float32, device="cuda")
+    B.pt_fwer_pvalues(ctx, mx, p, two_sided)
+    B.pt_sync(ctx)
+    ref = oracle.fwer_pvalues(mx.cpu().numpy(), t.cpu().numpy(), two_sided)
+    np.testing.assert_array_equal(p.cpu().numpy(), ref.astype(np.float32))
+    assert np.nanmin(p.cpu().numpy()) >= 1.0 / (P + 1) - 1e-9
+    ctx.close()

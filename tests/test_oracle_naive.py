@@ -177,3 +177,37 @@ def test_fisher_yates_rows_are_permutations():
     # uniformity of the first position over 500 rows (chi-square, loose)
     cnt = np.bincount(p[:, 0], minlength=37)
     assert st.chisquare(cnt).pvalue > 1e-4
+
+
+def test_fwer_pvalues_definition():
+    """Corrected p-values: brute-force counting on a tiny case, the smallest
+    attainable value 1/(P+1), monotone in t_obs, and the exact permutation
+    distribution of the maximum over all C(8,4) relabellings."""
+    rng = np.random.default_rng(5)
+    m = rng.standard_normal(50).astype(np.float32)
+    t = np.array([-1.0, 0.0, 0.3, 5.0, np.nan, float(m[7])])
+    p = oracle.fwer_pvalues(m, t)
+    for j, tj in enumerate(t):
+        if np.isnan(tj):
+            assert np.isnan(p[j])
+        else:
+            cnt = sum(1 for x in m if x >= np.float32(tj))
+            assert p[j] == (1 + cnt) / 51.0
+    assert p[3] == 1.0 / 51.0  # above every maximum
+    assert p[0] >= p[1] >= p[2]
+    p2 = oracle.fwer_pvalues(m, t, two_sided=True)
+    assert p2[0] == (1 + np.sum(m >= 1.0)) / 51.0
+    # exact: all C(8,4) relabellings (each group-1 set once, observed one included)
+    import itertools
+    n, n1, v = 8, 4, 30
+    X = rng.standard_normal((n, v))
+    X[:4, 3] += 3.0
+    sets = [c for c in itertools.combinations(range(n), n1) if c != (0, 1, 2, 3)]
+    perms = np.array([list(c) + [s for s in range(n) if s not in c] for c in sets],
+                     dtype=np.int32)
+    ref = oracle.naive(X, n1, perms)
+    p = oracle.fwer_pvalues(ref.maxnull, ref.t_obs)
+    allmax = np.concatenate([ref.maxnull, [np.max(ref.t_obs)]])
+    for j in range(v):
+        exact = np.mean(allmax.astype(np.float32) >= np.float32(ref.t_obs[j]))
+        assert abs(p[j] - exact) < 1e-12
