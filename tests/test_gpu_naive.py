@@ -245,3 +245,35 @@ def test_fwer_pvalues_match_oracle(cuda_lib, two_sided):
     np.testing.assert_array_equal(p.cpu().numpy(), ref.astype(np.float32))
     assert np.nanmin(p.cpu().numpy()) >= 1.0 / (P + 1) - 1e-9
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_largest_tensor_core_n(cuda_lib, precision):
+    """n = 544: the largest subject count whose BF16x3 data tile (64 voxels)
+    still fits in shared memory, on every path."""
+    n, n1, v, P = 544, 272, 300, 140
+    X = synth.gaussian_mean_shift(n, v, seed=9)
+    perms = synth.perms_pcg32(n, P, seed=8)
+    ref = oracle.naive(X, n1, perms, tie_rel=tie_rel(precision, n))
+    got = run_gpu(cuda_lib, X, n1, perms, precision)
+    check(ref, got, precision, "n544")
+
+
+def test_maximum_n_fp32_and_tensor_core_limit(cuda_lib):
+    """n = 1024 (the API maximum): the FP32 path matches the oracle; the BF16x3
+    path reports PT_ERR_UNSUPPORTED (its resident data tile cannot fit) and
+    leaves the context usable."""
+    B = cuda_lib
+    n, n1, v, P = 1024, 512, 257, 40
+    X = synth.gaussian_mean_shift(n, v, seed=10)
+    perms = synth.perms_pcg32(n, P, seed=11)
+    ref = oracle.naive(X, n1, perms, tie_rel=tie_rel(0, n))
+    ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1)
+    pd = torch.as_tensor(perms).cuda()
+    with pytest.raises(B.PtError) as e:
+        B.maxnull_naive(ctx, pd, precision=2)
+    assert e.value.status == B.PT_ERR_UNSUPPORTED
+    mx, am, ct = B.maxnull_naive(ctx, pd, precision=0)
+    check(ref, (mx.cpu().numpy().astype(np.float64), am.cpu().numpy().astype(np.int64),
+                ct.cpu().numpy().astype(np.int64)), 0, "n1024")
+    ctx.close()
