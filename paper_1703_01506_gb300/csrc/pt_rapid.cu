@@ -107,6 +107,49 @@ __device__ __forceinline__ uint32_t draw_index(uint32_t k0, uint32_t k1, uint32_
   return uint32_t(t >> 32);
 }
 
+// One row of the geodesic update of U (Sec. 4.1; GROUSE-style rank-one step):
+// U_j <- U_j + coef_j w^T/||w||, coef_j = alpha (U_j . w) + beta (lift_j - U_j . g2).
+// Shared by the whole-U update and by the next step's gather, which applies a
+// still-running update to the rows it samples: both give the same bits.
+// w, wh and g2 are shared-memory vectors (16-byte aligned); they are re-read
+// for every row (volatile loads), so a loop over rows holds only the row in
+// registers.
+__device__ __forceinline__ float4 lds4(const float* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(uint32_t(__cvta_generic_to_shared(p))));
+  return v;
+}
+
+template <int RP>
+__device__ __forceinline__ void geodesic_row(float4 (&x)[RP / 4], float lj, const float* w,
+                                             const float* wh, const float* g2, float alpha,
+                                             float beta) {
+  float p = 0.0f, g = 0.0f;
+#pragma unroll
+  for (int c4 = 0; c4 < RP / 4; ++c4) {
+    const float4 wc = lds4(w + 4 * c4), gc = lds4(g2 + 4 * c4);
+    p = fmaf(x[c4].x, wc.x, p);
+    p = fmaf(x[c4].y, wc.y, p);
+    p = fmaf(x[c4].z, wc.z, p);
+    p = fmaf(x[c4].w, wc.w, p);
+    g = fmaf(x[c4].x, gc.x, g);
+    g = fmaf(x[c4].y, gc.y, g);
+    g = fmaf(x[c4].z, gc.z, g);
+    g = fmaf(x[c4].w, gc.w, g);
+  }
+  const float coef = fmaf(alpha, p, beta * (lj - g));
+#pragma unroll
+  for (int c4 = 0; c4 < RP / 4; ++c4) {
+    const float4 hc = lds4(wh + 4 * c4);
+    x[c4].x = fmaf(coef, hc.x, x[c4].x);
+    x[c4].y = fmaf(coef, hc.y, x[c4].y);
+    x[c4].z = fmaf(coef, hc.z, x[c4].z);
+    x[c4].w = fmaf(coef, hc.w, x[c4].w);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Cluster l1 weight solve (Sec. 4.1 / 4.2, the Complete step). The m sampled
 // rows are split over the CL CTAs of a thread-block cluster: each CTA keeps
@@ -537,9 +580,13 @@ __device__ __forceinline__ void clu_rows(int m, int CL, int rank, int& q0, int& 
 
 // One training step (Sec. 4.1): sampled rows of the training column, l1
 // weights, residual lifted onto the sampled voxels, and the geodesic step's
-// coefficients (written to upd for geodesic_update_kernel).
+// coefficients (written to upd). The same launch applies the previous step's
+// geodesic update to all of U on its other clusters: the step's fit (cluster
+// 0, 16 SMs) and the update (bandwidth-bound, the rest of the GPU) overlap.
 struct CluStepArgs {
-  const float* U;     // V x RP
+  const float* U;     // V x RP: U of the previous step when pend_upd is set, else this step's
+  const float* pend_upd;   // nullable: coefficients of the previous step's update (not yet
+  const float* pend_lift;  // applied to U); the sampled rows are updated here on the fly
   const float* Trow;  // t of this training column (V values)
   uint32_t V;
   int R, m, CL;
@@ -547,14 +594,45 @@ struct CluStepArgs {
   int pass, col;
   float rho, step;
   int iters;
-  float* lift;    // V, zero on entry
+  float* lift;    // V: zero except at the draws of step (clear_pass, clear_col)
   float* upd;     // 3 RP + 4: w, w/||w||, g2, alpha, beta
   float* w_hist;  // nullable
+  int fit;        // 1: cluster 0 runs this step's fit; 0: every CTA runs the update
+  int clear_pass, clear_col;  // lift entries zeroed before the fit adds to it (-1: none)
+  const float* gu_src;        // nullable: U of the previous step ...
+  float* gu_dst;              // ... updated into this buffer (all V rows)
+  const float* gu_lift;       // that step's lift and coefficients
+  const float* gu_coef;
 };
+
+// U_next = U + coef w^T/||w|| over rows j = first.. of the grid (geodesic_row).
+template <int RP>
+__device__ __forceinline__ void geodesic_rows(const CluStepArgs& a, int first_cta, float* su) {
+  for (int e = threadIdx.x; e < 3 * RP + 2; e += blockDim.x) su[e] = a.gu_coef[e];
+  __syncthreads();
+  const float alpha = su[3 * RP], beta = su[3 * RP + 1];
+  const int64_t stride = int64_t(gridDim.x - first_cta) * blockDim.x;
+  for (int64_t j = int64_t(blockIdx.x - first_cta) * blockDim.x + threadIdx.x; j < a.V;
+       j += stride) {
+    const float4* u4 = reinterpret_cast<const float4*>(a.gu_src + j * RP);
+    float4 x[RP / 4];
+#pragma unroll
+    for (int c4 = 0; c4 < RP / 4; ++c4) x[c4] = __ldcs(u4 + c4);
+    geodesic_row<RP>(x, __ldcs(a.gu_lift + j), su, su + RP, su + 2 * RP, alpha, beta);
+    float4* o4 = reinterpret_cast<float4*>(a.gu_dst + j * RP);
+#pragma unroll
+    for (int c4 = 0; c4 < RP / 4; ++c4) o4[c4] = x[c4];
+  }
+}
 
 template <int RP>
 __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluStepArgs a) {
   extern __shared__ __align__(16) float smc[];
+  const int first = a.fit ? a.CL : 0;  // CTAs [0, CL) form cluster 0
+  if (int(blockIdx.x) >= first) {
+    if (a.gu_src) geodesic_rows<RP>(a, first, smc);
+    return;
+  }
   cg::cluster_group cl = cg::this_cluster();
   const int rank = int(cl.block_rank());
   constexpr int RS = clu_rs(RP);
@@ -563,15 +641,29 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
   CluSmem f;
   clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, &f);
   const int tid = threadIdx.x;
+  if (a.clear_pass >= 0)  // ordered before this step's lift adds by the fit's cluster barriers
+    for (int q = tid; q < mloc; q += blockDim.x)
+      a.lift[draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q0 + q), uint32_t(a.clear_col),
+                        uint32_t(a.clear_pass), a.V)] = 0.0f;
+  if (a.pend_upd) {  // the previous update's coefficients, staged in red (free here)
+    for (int e = tid; e < 3 * RP + 2; e += blockDim.x) f.red[e] = a.pend_upd[e];
+    __syncthreads();
+  }
   for (int q = tid; q < mloc; q += blockDim.x) {
     const uint32_t j = draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q0 + q), uint32_t(a.col),
                                   uint32_t(a.pass), a.V);
     f.idx[q] = int32_t(j);
     f.b[q] = a.Trow[j];
     const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
+    float4 x[RP / 4];
+#pragma unroll
+    for (int c4 = 0; c4 < RP / 4; ++c4) x[c4] = src[c4];
+    if (a.pend_upd)
+      geodesic_row<RP>(x, a.pend_lift[j], f.red, f.red + RP, f.red + 2 * RP, f.red[3 * RP],
+                       f.red[3 * RP + 1]);
     float4* dst = reinterpret_cast<float4*>(f.A + q * RS);
 #pragma unroll
-    for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
+    for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = x[c4];
   }
   __syncthreads();
   int par = 0;
@@ -880,48 +972,6 @@ __global__ void qr_apply_kernel(float* __restrict__ U, int64_t V, int R, int RP,
       float t = 0.0f;
       for (int k = 0; k <= c; ++k) t = fmaf(row[k], ri[k * RP + c], t);
       u[c] = t;
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Training step (one block) and geodesic update (whole grid)
-// ---------------------------------------------------------------------------
-// U_j += (alpha (U_j . w) + beta (lift_j - U_j . g2)) w^T/||w||; lift_j <- 0.
-template <int RP>
-__global__ void geodesic_update_kernel(float* __restrict__ U, int64_t V,
-                                       float* __restrict__ lift, const float* __restrict__ upd) {
-  extern __shared__ float su[];
-  for (int e = threadIdx.x; e < 3 * RP + 2; e += blockDim.x) su[e] = upd[e];
-  __syncthreads();
-  const float alpha = su[3 * RP], beta = su[3 * RP + 1];
-  const float* w = su;
-  const float* wh = su + RP;
-  const float* g2 = su + 2 * RP;
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < V;
-       j += int64_t(gridDim.x) * blockDim.x) {
-    float4* u4 = reinterpret_cast<float4*>(U + j * RP);
-    float4 x[RP / 4];
-#pragma unroll
-    for (int c4 = 0; c4 < RP / 4; ++c4) x[c4] = u4[c4];
-    const float lj = lift[j];
-    float p = 0.0f, g = 0.0f;
-#pragma unroll
-    for (int c4 = 0; c4 < RP / 4; ++c4) {
-      p = fmaf(x[c4].x, w[4 * c4], fmaf(x[c4].y, w[4 * c4 + 1], fmaf(x[c4].z, w[4 * c4 + 2], fmaf(x[c4].w, w[4 * c4 + 3], p))));
-      g = fmaf(x[c4].x, g2[4 * c4], fmaf(x[c4].y, g2[4 * c4 + 1], fmaf(x[c4].z, g2[4 * c4 + 2], fmaf(x[c4].w, g2[4 * c4 + 3], g))));
-    }
-    const float coef = alpha * p + beta * (lj - g);
-    if (lj != 0.0f) lift[j] = 0.0f;
-    if (coef != 0.0f) {
-#pragma unroll
-      for (int c4 = 0; c4 < RP / 4; ++c4) {
-        x[c4].x = fmaf(coef, wh[4 * c4], x[c4].x);
-        x[c4].y = fmaf(coef, wh[4 * c4 + 1], x[c4].y);
-        x[c4].z = fmaf(coef, wh[4 * c4 + 2], x[c4].z);
-        x[c4].w = fmaf(coef, wh[4 * c4 + 3], x[c4].w);
-        u4[c4] = x[c4];
-      }
     }
   }
 }
@@ -1255,29 +1305,51 @@ int choose_cluster(int m, int R, int RP, int n_pad, int first, size_t* smem) {
   return 0;
 }
 
-// Launches `kernel` as nclusters clusters of CL CTAs of kCluThreads threads;
-// nclusters <= 0 asks for as many clusters as can be resident at once.
+// Launch configuration of `kernel` as clusters of CL CTAs of kCluThreads threads.
 template <class Arg>
-cudaError_t launch_cluster(void (*kernel)(Arg), int nclusters, int CL, size_t smem,
-                           cudaStream_t st, const Arg& arg, int* used = nullptr) {
+cudaError_t cluster_config(void (*kernel)(Arg), int CL, size_t smem, cudaStream_t st,
+                           cudaLaunchConfig_t* cfg, cudaLaunchAttribute* at) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem));
   if (e == cudaSuccess && CL > 8)
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
-  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = unsigned(CL);
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kCluThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
+  *cfg = cudaLaunchConfig_t{};
+  cfg->blockDim = dim3(kCluThreads, 1, 1);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = st;
+  cfg->attrs = at;
+  cfg->numAttrs = 1;
+  cfg->gridDim = dim3(unsigned(CL) * 152u, 1, 1);
+  return cudaSuccess;
+}
+
+// How many clusters of `kernel` can be resident at once (>= 1 on success).
+template <class Arg>
+cudaError_t max_active_clusters(void (*kernel)(Arg), int CL, size_t smem, int* maxc) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  cudaError_t e = cluster_config(kernel, CL, smem, nullptr, &cfg, at);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(maxc, kernel, &cfg);
+  if (e == cudaSuccess && *maxc < 1) e = cudaErrorInvalidConfiguration;
+  return e;
+}
+
+// Launches `kernel` as nclusters clusters of CL CTAs of kCluThreads threads;
+// nclusters <= 0 asks for as many clusters as can be resident at once (at most
+// -nclusters when that is positive).
+template <class Arg>
+cudaError_t launch_cluster(void (*kernel)(Arg), int nclusters, int CL, size_t smem,
+                           cudaStream_t st, const Arg& arg, int* used = nullptr) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute at[1];
+  cudaError_t e = cluster_config(kernel, CL, smem, st, &cfg, at);
+  if (e != cudaSuccess) return e;
   if (nclusters <= 0) {
-    cfg.gridDim = dim3(unsigned(CL) * 152u, 1, 1);
     int maxc = 0;
     e = cudaOccupancyMaxActiveClusters(&maxc, kernel, &cfg);
     if (e != cudaSuccess) return e;
@@ -1417,16 +1489,18 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   cudaStream_t st = ctx->stream;
   const int64_t V = pl.V;
   const int ell = n_train;
-  Buf Ub, Tex, lift, upd, part, rinv, Wex, keys, sig, tmax;
+  Buf Ub, Ub2, Tex, lift, upd, part, rinv, Wex, keys, sig, tmax;
   struct G {
     std::vector<Buf*> v;
     ~G() {
       for (Buf* b : v) b->release();
     }
-  } guard{{&Ub, &Tex, &lift, &upd, &part, &rinv, &Wex, &keys, &sig, &tmax}};
-  if (!Ub.ensure(sizeof(float) * size_t(V) * pl.RP) || !Tex.ensure(sizeof(float) * size_t(ell) * V) ||
-      !lift.ensure(sizeof(float) * V) ||
-      !upd.ensure(sizeof(float) * (3 * pl.RP + 4)) || !Wex.ensure(sizeof(float) * size_t(ell) * pl.RP) ||
+  } guard{{&Ub, &Ub2, &Tex, &lift, &upd, &part, &rinv, &Wex, &keys, &sig, &tmax}};
+  const int updw = 3 * pl.RP + 4;  // floats per step's update coefficients
+  if (!Ub.ensure(sizeof(float) * size_t(V) * pl.RP) ||
+      !Ub2.ensure(sizeof(float) * size_t(V) * pl.RP) || !Tex.ensure(sizeof(float) * size_t(ell) * V) ||
+      !lift.ensure(sizeof(float) * 2 * V) ||
+      !upd.ensure(sizeof(float) * 2 * updw) || !Wex.ensure(sizeof(float) * size_t(ell) * pl.RP) ||
       !keys.ensure(sizeof(unsigned long long) * ell) || !tmax.ensure(sizeof(float) * ell))
     return nomem_r(ctx, "RapidPT training");
 
@@ -1493,18 +1567,25 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   PT_LAUNCH_CHECK(ctx);
   s = qr_inplace(ctx, U, pl, part, rinv);
   if (s != PT_OK) return s;
-  PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * V, st));
 
-  // 3. sequential subspace tracking over passes x columns: each step's l1
-  //    fit on one thread-block cluster, then the geodesic update over all of U
+  // 3. sequential subspace tracking over passes x columns, one launch per
+  //    step: cluster 0 fits step t on U_{t-1} with step t-1's update applied
+  //    to its sampled rows (geodesic_row, the same bits as the whole-U
+  //    update), while the other clusters write U_t = update_{t-1}(U_{t-1})
+  //    into the other buffer. lift and the coefficients alternate by step
+  //    parity; a step clears the lift entries of the step two before it.
   size_t csm = 0;
   const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 16, &csm);
   if (CL == 0) {
     set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
     return PT_ERR_UNSUPPORTED;
   }
+  float* ua = U;               // latest complete U (U_{t-1} while an update is pending)
+  float* ub = Ub2.as<float>();
+  float* liftb[2] = {lift.as<float>(), lift.as<float>() + V};
+  float* updb[2] = {upd.as<float>(), upd.as<float>() + updw};
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * 2 * V, st));
   CluStepArgs sa;
-  sa.U = U;
   sa.V = uint32_t(V);
   sa.R = pl.R;
   sa.m = pl.m;
@@ -1514,35 +1595,66 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   sa.rho = o.admm_rho;
   sa.iters = o.admm_iters;
   sa.step = o.step;
-  sa.lift = lift.as<float>();
-  sa.upd = upd.as<float>();
-  const int usm = (3 * pl.RP + 2) * int(sizeof(float));
   int64_t steps = 0;
+  int pend = -1;                          // parity of the step whose update is pending
+  int last_pc[2][2] = {{-1, -1}, {-1, -1}};  // (pass, col) of the last step per parity
+  int nclu = 0;                           // clusters of a launch that updates U (resident)
   cudaError_t lerr = cudaSuccess;
   with_rp(pl.RP, [&](auto rpc) {
     constexpr int RPc = decltype(rpc)::value;
+    auto launch = [&](bool fit) {
+      sa.fit = fit ? 1 : 0;
+      if (pend >= 0) {
+        sa.gu_src = ua;
+        sa.gu_dst = ub;
+        sa.gu_lift = liftb[pend];
+        sa.gu_coef = updb[pend];
+      } else {
+        sa.gu_src = nullptr;
+      }
+      lerr = launch_cluster(train_step_cluster_kernel<RPc>, pend >= 0 ? nclu : 1, CL, csm, st,
+                            sa);
+      count_launch();
+      if (pend >= 0) std::swap(ua, ub);
+    };
+    // the fused launch needs a second cluster for the update
+    lerr = max_active_clusters(train_step_cluster_kernel<RPc>, CL, csm, &nclu);
+    if (lerr == cudaSuccess && nclu < 2) lerr = cudaErrorInvalidConfiguration;
     for (int p = 0; p < o.train_passes && lerr == cudaSuccess && s == PT_OK; ++p) {
       for (int i = 0; i < ell; ++i) {
+        const int cur = int(steps & 1);
+        sa.U = ua;
+        sa.pend_upd = pend >= 0 ? updb[pend] : nullptr;
+        sa.pend_lift = pend >= 0 ? liftb[pend] : nullptr;
+        sa.clear_pass = last_pc[cur][0];
+        sa.clear_col = last_pc[cur][1];
+        sa.lift = liftb[cur];
+        sa.upd = updb[cur];
         sa.pass = p;
         sa.col = i;
         sa.Trow = Tex.as<float>() + int64_t(i) * V;
         sa.w_hist = w_hist ? w_hist + steps * pl.R : nullptr;
-        lerr = launch_cluster(train_step_cluster_kernel<RPc>, 1, CL, csm, st, sa);
+        launch(true);
         if (lerr != cudaSuccess) break;
-        geodesic_update_kernel<RPc><<<grid_n(V, 256, 152 * 8), 256, usm, st>>>(
-            U, V, lift.as<float>(), upd.as<float>());
-        lerr = cudaGetLastError();
-        if (lerr != cudaSuccess) break;
-        count_launch();
-        count_launch();
+        last_pc[cur][0] = p;
+        last_pc[cur][1] = i;
+        pend = cur;
         ++steps;
-        if (steps % o.qr_every == 0) {
-          s = qr_inplace(ctx, U, pl, part, rinv);
+        if (steps % o.qr_every == 0) {  // QR needs the whole U of this step
+          launch(false);
+          if (lerr != cudaSuccess) break;
+          pend = -1;
+          s = qr_inplace(ctx, ua, pl, part, rinv);
           if (s != PT_OK) break;
         }
       }
     }
+    if (lerr == cudaSuccess && s == PT_OK && pend >= 0) {
+      launch(false);
+      pend = -1;
+    }
   });
+  U = ua;
   if (lerr != cudaSuccess) {
     set_error(ctx, std::string("RapidPT training launch: ") + cudaGetErrorString(lerr));
     return PT_ERR_CUDA;
