@@ -80,10 +80,12 @@ class draws:
 
     normal(tag, a, b)      z = sqrt(-2 ln u1) cos(2 pi u2) from words (x0, x1),
                            u1 = (x0 + 1) 2^-32, u2 = x1 2^-32   (counter (a, b, 0, tag))
-    voxel_normal(tag, j, b) both Box-Muller normals of one counter serve a pair
-                           of voxels: sqrt(-2 ln u1) cos(2 pi u2) for even j and
-                           sqrt(-2 ln u1) sin(2 pi u2) for odd j, with u1, u2 from
-                           counter (floor(j / 2), b, 0, tag)
+    voxel_normal(tag, j, b) one counter (floor(j / 4), b, 0, tag) serves four
+                           voxels: words (x0, x1) give the Box-Muller pair of
+                           voxels 4p, 4p + 1 and words (x2, x3) that of 4p + 2,
+                           4p + 3; in each pair sqrt(-2 ln u1) cos(2 pi u2) for the
+                           even voxel and sqrt(-2 ln u1) sin(2 pi u2) for the odd
+                           one, u1 = (first word + 1) 2^-32, u2 = second word 2^-32
     index(tag, q, i, p, v) floor((x1 2^32 + x0) v / 2^64)         (counter (q, i, p, tag))
 
     U0[j, c]            = normal(TAG_U0, j, c)
@@ -107,9 +109,12 @@ class draws:
 
     def voxel_normal(self, tag, j, b):
         j = np.asarray(j, dtype=np.uint64)
-        x0, x1, _, _ = self.words(j >> np.uint64(1), b, 0, tag)
-        u1 = (x0.astype(np.float64) + 1.0) * 2.0 ** -32
-        u2 = x1.astype(np.float64) * 2.0 ** -32
+        x0, x1, x2, x3 = self.words(j >> np.uint64(2), b, 0, tag)
+        second = ((j >> np.uint64(1)) & np.uint64(1)) == 1  # voxels 4p + 2, 4p + 3
+        a = np.where(second, x2, x0)
+        c = np.where(second, x3, x1)
+        u1 = (a.astype(np.float64) + 1.0) * 2.0 ** -32
+        u2 = c.astype(np.float64) * 2.0 ** -32
         r = np.sqrt(-2.0 * np.log(u1))
         return np.where((j & np.uint64(1)) == 0, r * np.cos(2.0 * np.pi * u2),
                         r * np.sin(2.0 * np.pi * u2))

@@ -99,6 +99,14 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
                              const float* U_in, int32_t rank, double sample_rate, double sigma,
                              double mu, const pt_rapid_opts& o, float* maxnull, float* W_out);
 
+// ---- reconstruction with noise on the tensor cores (pt_recon_tc.cu) ----
+// keys[i] (zero or an earlier key on entry) <- max with the packed (value,
+// voxel) maximum over voxels j of (W_i . U_j) + sigma z(tag, j, label0 + i);
+// W rows x RP, U V x RP (FP32, padded columns zero), RP <= 128.
+pt_status recon_tc(pt_ctx* ctx, const float* W, int64_t rows, int64_t label0, const float* U,
+                   int64_t V, int RP, float sigma, uint32_t tag, uint32_t k0, uint32_t k1,
+                   unsigned long long* keys);
+
 // ---- naive path (pt_naive.cu) ----
 pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_opts& o,
                      float* maxnull, int32_t* argmax, uint32_t* counts);

@@ -2,6 +2,7 @@
 // host-side launchers shared between translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -203,6 +204,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
+
+// ---- TMA descriptors (pt_naive_tc.cu) ----
+// 2D view [rows][256] of a BF16 buffer, box [box_rows][256], no swizzle;
+// false if the driver entry point is missing or rejects the view.
+bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint32_t box_rows);
 
 // ---- launchers implemented in pt_naive_tc.cu ----
 pt_status tc_supported(pt_ctx* ctx);

@@ -21,9 +21,8 @@
 //   Gamma = lift(r) - U g2, theta = step * atan(||r|| / ||w||),
 //   U <- U + [(cos theta - 1) U w / ||w|| + sin theta Gamma / ||Gamma||] w^T / ||w||,
 //   with ||Gamma||^2 = ||lift||^2 - ||g2||^2 (U orthonormal).
-// Random numbers: Philox4x32-10 (Salmon et al., SC 2011) keyed by the seed,
-// counters (a, b, c, tag): normals by Box-Muller from the first two words,
-// voxel indices as floor((x1 2^32 + x0) v / 2^64).
+// Random numbers: Philox4x32-10 by counter (pt_draws.h). The reconstruction
+// with noise runs on the tensor cores (pt_recon_tc.cu).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -35,6 +34,7 @@
 #include <vector>
 
 #include "pt_internal.h"
+#include "pt_draws.h"
 #include "pt_kernels.h"
 
 namespace pt {
@@ -55,57 +55,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr uint32_t TAG_U0 = 1, TAG_TRAIN = 2, TAG_REC = 3, TAG_NOISE = 4, TAG_SHIFT = 5;
 constexpr int kMaxRank = 128;
-constexpr float kNoiseBound = 6.6604f;  // sqrt(-2 ln 2^-32) rounded up: |z| of every draw
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 and the draws built on it
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
-    const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
-
-__device__ __forceinline__ float draw_normal(uint32_t k0, uint32_t k1, uint32_t tag, uint32_t a,
-                                             uint32_t b) {
-  const uint4 o = philox(make_uint4(a, b, 0u, tag), k0, k1);
-  const float u1 = fmaf(__uint2float_rn(o.x), 2.3283064365386963e-10f, 2.3283064365386963e-10f);
-  const float u2 = __uint2float_rn(o.y) * 2.3283064365386963e-10f;
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-}
-
-// Both Box-Muller normals of one counter serve the voxel pair (2p, 2p + 1):
-// r cos(2 pi u2) for the even voxel, r sin(2 pi u2) for the odd one.
-__device__ __forceinline__ void draw_normal_pair(uint32_t k0, uint32_t k1, uint32_t tag,
-                                                 uint32_t pair, uint32_t b, float& z_even,
-                                                 float& z_odd) {
-  const uint4 o = philox(make_uint4(pair, b, 0u, tag), k0, k1);
-  const float u1 = fmaf(__uint2float_rn(o.x), 2.3283064365386963e-10f, 2.3283064365386963e-10f);
-  const float u2 = __uint2float_rn(o.y) * 2.3283064365386963e-10f;
-  const float r = sqrtf(-2.0f * logf(u1));
-  float sv, cv;
-  sincospif(2.0f * u2, &sv, &cv);
-  z_even = r * cv;
-  z_odd = r * sv;
-}
-
-__device__ __forceinline__ uint32_t draw_index(uint32_t k0, uint32_t k1, uint32_t tag, uint32_t q,
-                                               uint32_t i, uint32_t p, uint32_t V) {
-  const uint4 o = philox(make_uint4(q, i, p, tag), k0, k1);
-  const unsigned long long t =
-      (unsigned long long)o.y * V + (((unsigned long long)o.x * V) >> 32);
-  return uint32_t(t >> 32);
-}
 
 // One row of the geodesic update of U (Sec. 4.1; GROUSE-style rank-one step):
 // U_j <- U_j + coef_j w^T/||w||, coef_j = alpha (U_j . w) + beta (lift_j - U_j . g2).
@@ -1072,27 +1022,22 @@ __global__ void __launch_bounds__(256) sigma_partial_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Reconstruct + noise + max (Alg. 2 recovery): rows = relabellings (weights W),
-// columns = voxels (U). mode 0: value (U w)_j + sigma z_j; mode 1: residual
-// T_ex[i][j] - (U w)_j (literal shift of Alg. 2). Each CTA walks a range of
-// voxel tiles for one 128-row tile and keeps per-row running maxima.
+// Residual max (Alg. 2, the literal training shift): rows = training columns
+// (weights W_ex), columns = voxels; max_j (T_ex[i][j] - (U w_i)_j). Each CTA
+// walks a range of voxel tiles for one 128-row tile and keeps per-row maxima.
 // ---------------------------------------------------------------------------
-struct ReconArgs {
+struct ResidArgs {
   const float* W;  // rows x RP
   int64_t rows;
-  int64_t row_label0;  // relabelling index of row 0 (noise counter)
-  const float* U;      // V x RP
+  const float* U;  // V x RP
   int64_t V;
   int RP;
-  float sigma;
-  uint32_t tag, k0, k1;
-  int mode;
-  const float* Tex;  // mode 1
+  const float* Tex;  // rows x V
   int64_t tiles_per_cta;
   unsigned long long* maxkey;  // rows, zero on entry
 };
 
-__global__ void __launch_bounds__(256) reconstruct_max_kernel(ReconArgs a) {
+__global__ void __launch_bounds__(256) residual_max_kernel(ResidArgs a) {
   __shared__ __align__(16) float Ws[16][128];
   __shared__ __align__(16) float Us[16][128];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -1102,19 +1047,11 @@ __global__ void __launch_bounds__(256) reconstruct_max_kernel(ReconArgs a) {
   const int64_t vt1 = min(vtiles, vt0 + a.tiles_per_cta);
   float best[8];
   uint32_t bj[8];
-  float M[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     best[q] = -INFINITY;
     bj[q] = 0xffffffffu;
-    const int64_t row = r0 + ((q < 4) ? (ty * 4 + q) : (64 + ty * 4 + q - 4));
-    M[q] = -INFINITY;
-    if (row < a.rows) {
-      const unsigned long long k = __ldcg(&a.maxkey[row]);
-      if (k) M[q] = unpack_key_value(k);
-    }
   }
-  const float bound = a.mode == 0 ? a.sigma * kNoiseBound : 0.0f;
   for (int64_t vt = vt0; vt < vt1; ++vt) {
     const int64_t c0 = vt * 128;
     float acc[8][8];
@@ -1145,43 +1082,20 @@ __global__ void __launch_bounds__(256) reconstruct_max_kernel(ReconArgs a) {
           for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(wv[p], uv[q], acc[p][q]);
       }
     }
-    // epilogue: bounded-noise skip, running maxima
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       const int64_t row = r0 + ((p < 4) ? (ty * 4 + p) : (64 + ty * 4 + p - 4));
       if (row >= a.rows) continue;
 #pragma unroll
-      // columns in pairs (even, odd): one counter's two normals serve both
-      for (int q = 0; q < 8; q += 2) {
-        const int64_t col = c0 + ((q < 4) ? (tx * 4 + q) : (64 + tx * 4 + q - 4));
-        float z[2] = {0.0f, 0.0f};
-        if (a.mode == 0 && (acc[p][q] + bound >= M[p] || acc[p][q + 1] + bound >= M[p]) &&
-            col < a.V)
-          draw_normal_pair(a.k0, a.k1, a.tag, uint32_t(col >> 1), uint32_t(a.row_label0 + row),
-                           z[0], z[1]);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int64_t cc = col + h;
-          if (cc >= a.V) continue;
-          float val = acc[p][q + h];
-          if (a.mode == 1) {
-            val = a.Tex[row * a.V + cc] - val;
-          } else {
-            if (val + bound < M[p]) continue;
-            val = fmaf(a.sigma, z[h], val);
-          }
-          if (val > best[p] || (val == best[p] && uint32_t(cc) < bj[p])) {
-            best[p] = val;
-            bj[p] = uint32_t(cc);
-          }
-          M[p] = fmaxf(M[p], val);
+      for (int q = 0; q < 8; ++q) {
+        const int64_t cc = c0 + ((q < 4) ? (tx * 4 + q) : (64 + tx * 4 + q - 4));
+        if (cc >= a.V) continue;
+        const float val = a.Tex[row * a.V + cc] - acc[p][q];
+        if (val > best[p] || (val == best[p] && uint32_t(cc) < bj[p])) {
+          best[p] = val;
+          bj[p] = uint32_t(cc);
         }
       }
-      // share the running maximum among the 16 threads of this row
-      float mm = M[p];
-#pragma unroll
-      for (int o = 1; o < 16; o <<= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
-      M[p] = mm;
     }
   }
 #pragma unroll
@@ -1434,10 +1348,15 @@ pt_status qr_inplace(pt_ctx* ctx, float* U, const RapidPlan& pl, Buf& part, Buf&
 
 // Row maxima of (U w + sigma z) (mode 0) or of T_ex - U w (mode 1) for `rows`
 // rows of W; keys zeroed here.
+// Per-row maxima (packed keys) of the reconstructed rows: mode 0 adds the
+// noise sigma z(tag, voxel, label0 + row) on the tensor cores; mode 1 is the
+// residual T_ex - U W_ex.
 pt_status reconstruct(pt_ctx* ctx, const float* W, int64_t rows, int64_t label0, const float* U,
                       const RapidPlan& pl, float sigma, uint32_t tag, int mode, const float* Tex,
                       unsigned long long* keys) {
   PT_CUDA_TRY(ctx, cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * rows, ctx->stream));
+  if (mode == 0)
+    return recon_tc(ctx, W, rows, label0, U, pl.V, pl.RP, sigma, tag, pl.k0, pl.k1, keys);
   const int64_t rtiles = (rows + 127) / 128;
   const int64_t vtiles = (pl.V + 127) / 128;
   int64_t per = vtiles;
@@ -1447,25 +1366,17 @@ pt_status reconstruct(pt_ctx* ctx, const float* W, int64_t rows, int64_t label0,
     if (split > vtiles) split = vtiles;
     per = (vtiles + split - 1) / split;
   }
-  ReconArgs a;
+  ResidArgs a;
   a.W = W;
   a.rows = rows;
-  a.row_label0 = label0;
   a.U = U;
   a.V = pl.V;
   a.RP = pl.RP;
-  a.sigma = sigma;
-  a.tag = tag;
-  a.k0 = pl.k0;
-  a.k1 = pl.k1;
-  a.mode = mode;
   a.Tex = Tex;
   a.tiles_per_cta = per;
   a.maxkey = keys;
   const dim3 grid{unsigned((vtiles + per - 1) / per), unsigned(rtiles), 1u};
-  prof_begin(ctx);
-  reconstruct_max_kernel<<<grid, 256, 0, ctx->stream>>>(a);
-  prof_end(ctx);
+  residual_max_kernel<<<grid, 256, 0, ctx->stream>>>(a);
   PT_LAUNCH_CHECK(ctx);
   return PT_OK;
 }

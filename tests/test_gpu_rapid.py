@@ -54,6 +54,35 @@ def test_recovery_matches_oracle_given_basis(cuda_lib):
     ctx.close()
 
 
+def test_recovery_large_rank_given_basis(cuda_lib):
+    """Rank 70 (padded to 72; the reconstruction's K = 80 takes the 64-voxel
+    tensor-core tile) with a random orthonormal basis, and a ragged voxel count."""
+    B = cuda_lib
+    n, n1, P, r, eta, ell = 80, 40, 300, 70, 0.02, 60
+    X = smooth_field(n, n1, seed=9)
+    X = X[:, : X.shape[1] - 37]
+    V = X.shape[1]
+    perms = synth.perms_pcg32(n, P, seed=4)
+    U = np.linalg.qr(np.random.default_rng(5).standard_normal((V, r)))[0]
+    sigma, mu = 0.8, 0.1
+    o = R.RapidOpts(seed=13)
+    m = int(np.ceil(eta * V))
+    rows = np.arange(ell, P)
+    want, w_want = R.rapid_recover(X, n1, perms, rows, U, sigma, mu, m, o, return_w=True)
+    ctx = gpu_ctx(B, X, n1)
+    pd = torch.as_tensor(perms).cuda()
+    got = torch.empty(P - ell, dtype=torch.float32, device="cuda")
+    W = torch.empty((P - ell, r), dtype=torch.float32, device="cuda")
+    B.pt_rapid_recover(ctx, pd, ell, torch.as_tensor(U.astype(np.float32)).cuda(), r, eta, sigma,
+                       mu, B.rapid_opts(seed=13), got, W)
+    B.pt_sync(ctx)
+    W = W.cpu().numpy().astype(np.float64)
+    wrel = np.linalg.norm(W - w_want, axis=1) / np.linalg.norm(w_want, axis=1)
+    assert np.max(wrel) < 1e-3, np.max(wrel)
+    np.testing.assert_allclose(got.cpu().numpy().astype(np.float64), want, rtol=2e-4, atol=2e-4)
+    ctx.close()
+
+
 def test_training_matches_oracle(cuda_lib):
     B = cuda_lib
     n, n1, P, r, eta, ell = 40, 20, 200, 10, 0.03, 60
