@@ -121,7 +121,8 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
  * for (ctxs[i], perms[i], P[i]) into maxnull[i], argmax[i], counts[i]. The
  * paper runs one study at a time (Sec. 5); batching only packs the studies'
  * (relabelling block x voxel tile) work into one persistent tensor-core launch
- * per tile class, so small studies share the GPU instead of each leaving SMs idle.
+ * per launch class (voxel tile, k-steps per label stage; see pt_tc_config), so
+ * small studies share the GPU instead of each leaving SMs idle.
  *   ctxs      : host array of n_studies distinct contexts, all on one device.
  *               Work runs on ctxs[0]'s stream; every context's own stream is
  *               synchronised once when the batch is (re)planned.
@@ -242,6 +243,77 @@ pt_status pt_t_obs(pt_ctx* ctx, float* t_obs);
  */
 pt_status pt_fwer_pvalues(pt_ctx* ctx, const float* maxnull, int64_t P, int32_t two_sided,
                           float* p_out);
+
+/* ------------------------------------------------------------------------- */
+/* Launch configuration of the tensor-core NaivePT kernel and its autotuner.  */
+/* The paper has no GPU kernel; these entry points only choose how the fused  */
+/* contraction of Alg. 1 is cut into work: the outputs do not depend on the   */
+/* configuration (every T entry is summed over the same data pieces and       */
+/* subjects in the same order whatever the ring shape or the block split).    */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t voxel_tile;   /* voxels per work tile: 256, 128 or 64, fixed by n (the largest whose
+                           BF16 data pieces fit in shared memory; they stay there while the
+                           relabellings stream). It also fixes how the pieces' partial sums
+                           are combined, so a configuration must keep it. */
+  int32_t stages;       /* depth of the shared-memory ring of label stages, 2..32 (limited by
+                           what fits beside the data tile) */
+  int32_t ksteps_per_stage; /* k-steps (128 relabellings x 16 subjects, 4 KB) per stage and per
+                           ring wait: 1, 2, 4 or 8 */
+  int32_t items_per_sm; /* single-study launches split each voxel tile's relabelling blocks
+                           until there are at least this many work items per SM, 1..64 */
+} pt_tc_config;
+
+/*
+ * pt_autotune_naive -- times candidate launch configurations of the fused
+ * tensor-core kernel on this problem (ctx's data, these relabellings, the
+ * options' precision and sidedness): k-steps per stage (1, 2, 4, 8) x ring
+ * depths of 8, 16 and 32 k-steps at eight work items per SM, then block splits
+ * of 1, 2 and 4 items per SM for the best;
+ * each candidate runs twice and its faster run counts. The fastest is recorded
+ * in the process-wide table under the shape key (padded n, precision,
+ * sidedness, half-octave buckets of the voxel count and of P), where later
+ * pt_maxnull_naive(_ex) and pt_maxnull_naive_batched calls of the same key
+ * find it. Shapes without an entry use the default: the largest stage (8, 4, 2
+ * or 1 k-steps) of which two fit, a ring of about 16 k-steps, 8 items per SM.
+ *   perms, P : as pt_maxnull_naive (device). opts: precision BF16X2 or BF16X3
+ *              (PT_ERR_INVALID otherwise); NULL = defaults.
+ *   chosen   : host, or NULL: the recorded configuration.
+ *   chosen_ms: host, or NULL: its kernel time in ms (CUDA events).
+ * Synchronous; computes no outputs. Errors: PT_ERR_INVALID (bad arguments or a
+ * row that is not a permutation), PT_ERR_UNSUPPORTED, PT_ERR_NOMEM, PT_ERR_CUDA,
+ * PT_ERR_TIMEOUT.
+ */
+pt_status pt_autotune_naive(pt_ctx* ctx, const int32_t* perms, int64_t P,
+                            const pt_naive_opts* opts, pt_tc_config* chosen, double* chosen_ms);
+
+/* pt_autotune_naive for every distinct shape key among the studies of a
+ * batched call (arguments as pt_maxnull_naive_batched); a cached batched graph
+ * is dropped so that the next batched call plans with the new entries. */
+pt_status pt_autotune_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
+                                    const int32_t* const* perms, const int64_t* P,
+                                    const pt_naive_opts* opts);
+
+/* The configuration a reduce call would use for n subjects, v voxels with a
+ * defined t and P relabellings (host only, no CUDA call): returns 1 when the
+ * table has an entry (copied to *out), 0 when it has none (*out = the
+ * default), -1 for bad arguments or an n no tile fits. */
+int32_t pt_tune_lookup(int32_t n, int32_t precision, int32_t two_sided, int64_t v, int64_t P,
+                       pt_tc_config* out);
+
+/* Records cfg for the shape key of (n, precision, two_sided, v, P) without
+ * timing. PT_ERR_INVALID if the configuration does not fit that n or names
+ * another voxel tile than the one n fixes. */
+pt_status pt_tune_set(int32_t n, int32_t precision, int32_t two_sided, int64_t v, int64_t P,
+                      const pt_tc_config* cfg);
+
+/* Writes the table to a text file (a header line, then one line per key with
+ * its configuration and measured ms), or merges such a file into the table;
+ * a malformed file or an entry that does not fit its n leaves the table as
+ * it was and returns PT_ERR_INVALID. pt_tune_clear empties the table. */
+pt_status pt_tune_save(const char* path);
+pt_status pt_tune_load(const char* path);
+void pt_tune_clear(void);
 
 /* grid_index: device int64[v]: grid column of each masked-order voxel. */
 pt_status pt_voxel_grid_index(pt_ctx* ctx, int64_t* grid_index);

@@ -31,6 +31,14 @@ class pt_naive_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("two_sided", ctypes.c_int32)]
 
 
+class pt_tc_config(ctypes.Structure):
+    _fields_ = [("voxel_tile", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("ksteps_per_stage", ctypes.c_int32), ("items_per_sm", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.voxel_tile, self.stages, self.ksteps_per_stage, self.items_per_sm)
+
+
 class pt_rapid_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("train_passes", ctypes.c_int32),
                 ("qr_every", ctypes.c_int32), ("admm_iters", ctypes.c_int32),
@@ -91,6 +99,16 @@ def load(path=None):
         "pt_rapid_recover": (ctypes.c_int, [_VP, _VP, i64, i64, _VP, i32, ctypes.c_double,
                                             ctypes.c_double, ctypes.c_double,
                                             ctypes.POINTER(pt_rapid_opts), _VP, _VP]),
+        "pt_autotune_naive": (ctypes.c_int, [_VP, _VP, i64, ctypes.POINTER(pt_naive_opts),
+                                             ctypes.POINTER(pt_tc_config),
+                                             ctypes.POINTER(ctypes.c_double)]),
+        "pt_autotune_naive_batched": (ctypes.c_int, [_VP, i32, _VP, _VP,
+                                                     ctypes.POINTER(pt_naive_opts)]),
+        "pt_tune_lookup": (i32, [i32, i32, i32, i64, i64, ctypes.POINTER(pt_tc_config)]),
+        "pt_tune_set": (ctypes.c_int, [i32, i32, i32, i64, i64, ctypes.POINTER(pt_tc_config)]),
+        "pt_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+        "pt_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+        "pt_tune_clear": (None, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -192,6 +210,57 @@ def pt_maxnull_naive_batched(ctxs, perms, opts, maxnull, argmax, counts=None):
     cn = None if counts is None else (_VP * m)(*[_ptr(t) for t in counts])
     st = lib.pt_maxnull_naive_batched(h, m, pp, P, ctypes.byref(opts), mx, am, cn)
     _check(st, None)
+
+
+def pt_autotune_naive(ctx, perms, opts):
+    """Times the fused kernel's launch configurations on this problem and
+    records the fastest; returns (pt_tc_config, ms)."""
+    lib = load()
+    assert perms.dtype == torch.int32
+    cfg = pt_tc_config()
+    ms = ctypes.c_double()
+    st = lib.pt_autotune_naive(ctx.handle, _ptr(perms), perms.shape[0], ctypes.byref(opts),
+                               ctypes.byref(cfg), ctypes.byref(ms))
+    _check(st, ctx.handle)
+    return cfg, ms.value
+
+
+def pt_autotune_naive_batched(ctxs, perms, opts):
+    lib = load()
+    m = len(ctxs)
+    if len(perms) != m:
+        raise ValueError("one relabelling tensor per context")
+    h = (_VP * m)(*[c.handle for c in ctxs])
+    pp = (_VP * m)(*[_ptr(p) for p in perms])
+    P = (ctypes.c_int64 * m)(*[p.shape[0] for p in perms])
+    _check(lib.pt_autotune_naive_batched(h, m, pp, P, ctypes.byref(opts)), None)
+
+
+def pt_tune_lookup(n, precision, two_sided, v, P):
+    """Returns (found, pt_tc_config); found is 1 (tuned entry), 0 (default) or -1 (bad)."""
+    cfg = pt_tc_config()
+    r = load().pt_tune_lookup(int(n), int(precision), int(two_sided), int(v), int(P),
+                              ctypes.byref(cfg))
+    return int(r), cfg
+
+
+def pt_tune_set(n, precision, two_sided, v, P, voxel_tile, stages, ksteps_per_stage=1,
+                items_per_sm=2):
+    cfg = pt_tc_config(int(voxel_tile), int(stages), int(ksteps_per_stage), int(items_per_sm))
+    _check(load().pt_tune_set(int(n), int(precision), int(two_sided), int(v), int(P),
+                              ctypes.byref(cfg)), None)
+
+
+def pt_tune_save(path):
+    _check(load().pt_tune_save(os.fsencode(path)), None)
+
+
+def pt_tune_load(path):
+    _check(load().pt_tune_load(os.fsencode(path)), None)
+
+
+def pt_tune_clear():
+    load().pt_tune_clear()
 
 
 def pt_sync(ctx):

@@ -117,6 +117,8 @@ pt_status fwer_pvalues_impl(pt_ctx* ctx, const float* maxnull, int64_t P, int tw
                             float* p_out);
 // Drops a cached batched graph that names this context (from pt_destroy).
 void batch_forget(const pt_ctx* ctx);
+// Drops the cached batched graph (the tuned configurations changed).
+void batch_drop_graph();
 
 }  // namespace pt
 

@@ -228,12 +228,35 @@ pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int wri
 struct TcGroup {
   int NT, first, count, n_pad_max;
   int64_t items;
+  int stages, kps;  // label ring: stages of kps k-steps
 };
 pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int n,
-                        int precision, Buf& descbuf, std::vector<char>& host_desc,
+                        const pt_naive_opts& o, Buf& descbuf, std::vector<char>& host_desc,
                         std::vector<TcGroup>& groups);
 pt_status tc_batch_launch(pt_ctx* lead, const Buf& descbuf, const std::vector<TcGroup>& groups,
                           int precision, int two_sided);
+
+// ---- launch configuration of the fused kernel (pt_naive_tc.cu) ----
+// Label-ring stages of kps k-steps that fit beside a resident tile of NT voxels (0: none).
+int tc_max_stages(int NT, int n_pad, int pieces, int kps);
+// Configuration used when none is recorded: the largest voxel tile that fits,
+// the largest stage of which two fit (8, 4, 2 or 1 k-steps), a ring of about
+// 16 k-steps, 8 work items per SM. false if no tile fits.
+bool tc_default_config(int n_pad, int pieces, pt_tc_config* out);
+bool tc_config_valid(const pt_tc_config& c, int n_pad, int pieces);
+struct TcTrial {
+  pt_tc_config cfg;
+  double ms;
+};
+// Times the candidate configurations of the reduce-only launch on ctx's
+// problem (labels in Lb, operand pieces built, maxkey/cnt sized for P).
+pt_status tc_autotune(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int two_sided,
+                      pt_tc_config* best, double* best_ms, std::vector<TcTrial>* trials);
+
+// ---- table of tuned configurations (pt_tune.cu) ----
+// Overwrites *cfg and returns true when a configuration is recorded for this
+// shape (padded n, precision, sidedness, voxel and relabelling counts).
+bool tune_find(int n_pad, int precision, int two_sided, int64_t v, int64_t P, pt_tc_config* cfg);
 
 // ---- shared with pt_naive.cu ----
 pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout,

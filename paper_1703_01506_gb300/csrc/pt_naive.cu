@@ -510,6 +510,12 @@ void drop_graph_locked() {
 }
 }  // namespace
 
+// Called when the tuned configurations change: the next batched call replans.
+void batch_drop_graph() {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  drop_graph_locked();
+}
+
 // Called by pt_destroy: a cached graph must not outlive the buffers it names.
 void batch_forget(const pt_ctx* ctx) {
   std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -619,8 +625,7 @@ pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* p
     }
     PT_CUDA_TRY(lead, cudaStreamSynchronize(c->stream));
   }
-  s = tc_batch_plan(lead, ctxs, P, n, o.precision, g_batch.desc, g_batch.host_desc,
-                    g_batch.groups);
+  s = tc_batch_plan(lead, ctxs, P, n, o, g_batch.desc, g_batch.host_desc, g_batch.groups);
   if (s != PT_OK) return s;
   if (g_batch.device != lead->device) {
     if (g_batch.capture) cudaStreamDestroy(g_batch.capture);

@@ -66,9 +66,11 @@ namespace {
 
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;  // 576
-constexpr int kStageBytes = 4096;  // 128 relabellings x 16 subjects x BF16
+constexpr int kStepBytes = 4096;  // one k-step of labels: 128 relabellings x 16 subjects x BF16
 constexpr int kSmemLimit = 232448;
 constexpr int kMaxBlocksPerItem = 255;  // per-thread 8-bit exceedance counters
+constexpr int kMaxStages = 32;          // label ring stages (4 KB each)
+constexpr int kDefaultItemsPerSm = 8;
 
 // One study (one prepared context and its relabellings) of a launch. Launches
 // with several studies (pt_maxnull_naive_batched) walk the concatenation of
@@ -89,7 +91,7 @@ struct TcStudy {  // CUtensorMap members carry their own alignment
 
 struct TcArgs {
   const TcStudy* studies;
-  int n_studies, stages;
+  int n_studies, stages, kps;  // ring stages, k-steps per stage
   int n_pad_max;
   int64_t n_items;
   int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
@@ -200,15 +202,25 @@ template <int NT, bool TWO, int PIECES, bool WRITE>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_contract_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int CW = NT / 4;                 // accumulator columns per epilogue thread
-  constexpr int CHK = CW < 32 ? CW : 32;     // columns per TMEM load
+  // Accumulators per block (NACC), summed in the epilogue. The data pieces'
+  // tiles are adjacent in shared memory, so one MMA of width q NT covers q of
+  // them: NT = 256 accumulates every piece in one accumulator (one MMA per
+  // piece); NT = 128 keeps hi and mid(+lo) apart (one MMA of width 256 for
+  // hi and mid, one for lo); NT = 64 keeps every piece apart (one MMA of
+  // width PIECES x 64 per k-step, so the label operand is read once).
+  constexpr int NACC = NT == 256 ? 1 : (NT == 128 ? 2 : PIECES);
+  constexpr int ACC = NACC * NT;             // accumulator columns per buffer
+  constexpr int CW = NT / 4;                 // voxel columns per epilogue thread
+  constexpr int CHK = NACC > 1 ? (CW < 16 ? CW : 16) : (CW < 32 ? CW : 32);  // per load
   constexpr int NCH = CW / CHK;              // loads per block
   const bool do_reduce = !WRITE || a.do_reduce;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int S = a.stages;
+  const int KPS = a.kps;
+  const uint32_t stage_bytes = uint32_t(KPS) * kStepBytes;
   uint8_t* xs = smem;
   uint8_t* ls = smem + PIECES * uint32_t(NT) * a.n_pad_max * 2;
-  float* su = reinterpret_cast<float*>(ls + S * kStageBytes);
+  float* su = reinterpret_cast<float*>(ls + S * stage_bytes);
   uint8_t* sbf = reinterpret_cast<uint8_t*>(su + NT);  // block flags of the current item
   uint64_t* bars = reinterpret_cast<uint64_t*>(sbf + kMaxBlocksPerItem + 1);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7 + 2 * S);
@@ -234,7 +246,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(smem_addr(tmem_slot), 2 * NT);
+  constexpr uint32_t kTmemCols = 2 * ACC <= 256 ? (2 * ACC <= 128 ? 128 : 256) : 512;
+  if (warp == 1) tmem_alloc(smem_addr(tmem_slot), kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -268,14 +281,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t nb = b1 - b0, rot = (int64_t(blockIdx.x) * 17) % nb;
         for (int64_t kb = 0; kb < nb && ok; ++kb) {
           const int64_t b = b0 + (kb + rot) % nb;
-          for (int ks = 0; ks < st.ksteps; ++ks, ++it) {
+          // One stage = KPS consecutive k-steps of the block (one box); the
+          // block's last stage may hold fewer, the rest of its box is unused.
+          for (int ks = 0; ks < st.ksteps; ks += KPS, ++it) {
             if (!mbar_wait(LEMPTY(ps), pph ^ 1u, a.status, abort_flag)) {
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(LFULL(ps), kStageBytes);
+            mbar_arrive_expect_tx(LFULL(ps), stage_bytes);
             const int64_t row = b * (n_pad / 2) + ks * 8;
-            tma_load_2d(smem_addr(ls + ps * kStageBytes), &st.tmL, 0, int32_t(row), LFULL(ps));
+            tma_load_2d(smem_addr(ls + ps * stage_bytes), &st.tmL, 0, int32_t(row), LFULL(ps));
             if (++ps == uint32_t(S)) {
               ps = 0;
               pph ^= 1u;
@@ -299,6 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t j = 0, ms = 0, mph = 0;  // block counter; ring stage and phase
       int w = 0;
       const uint32_t idesc = idesc_bf16_f32(128, NT);
+      const uint32_t idesc_w = idesc_bf16_f32(128, (NACC == 2 ? 2 : PIECES) * NT);
       // L stage: k-group major (k-groups 2 KB apart, 8-row groups adjacent);
       // Xn tile: row-group major (k-groups adjacent, 8-row groups n_pad/8 x 128 B apart).
       const uint64_t adesc0 = smem_desc(smem_addr(ls), 16 * 128, 128);
@@ -326,17 +342,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem + abuf * NT;
-          for (int ks = 0; ks < ksteps; ++ks) {
+          const uint32_t d = tmem + abuf * ACC;
+          for (int ks0 = 0; ks0 < ksteps; ks0 += KPS) {
             if (!mbar_wait(LFULL(ms), mph, a.status, abort_flag)) {
               ok = false;
               break;
             }
+            const int nk = ksteps - ks0 < KPS ? ksteps - ks0 : KPS;
             // descriptor start addresses advance in 16-byte units
-            const uint64_t adesc = adesc0 + uint64_t(ms * (kStageBytes >> 4));
+            uint64_t adesc = adesc0 + uint64_t(ms * uint32_t(KPS) * (kStepBytes >> 4));
+            for (int kk = 0; kk < nk; ++kk, adesc += kStepBytes >> 4) {
+              const int ks = ks0 + kk;
+              if constexpr (NACC == PIECES && NACC > 1) {
+                // piece q -> columns [q NT, (q + 1) NT)
+                tc_mma_f16(d, adesc, bdesc0[0] + uint64_t(ks * 16), idesc_w, ks != 0 ? 1u : 0u);
+              } else if constexpr (NACC == 2) {
+                // hi -> columns [0, NT), mid -> [NT, 2 NT); lo joins mid's accumulator
+                tc_mma_f16(d, adesc, bdesc0[0] + uint64_t(ks * 16), idesc_w, ks != 0 ? 1u : 0u);
+                tc_mma_f16(d + NT, adesc, bdesc0[2] + uint64_t(ks * 16), idesc, 1u);
+              } else {
 #pragma unroll
-            for (int q = 0; q < PIECES; ++q)
-              tc_mma_f16(d, adesc, bdesc0[q] + uint64_t(ks * 16), idesc, (ks | q) != 0 ? 1u : 0u);
+                for (int q = 0; q < PIECES; ++q)
+                  tc_mma_f16(d, adesc, bdesc0[q] + uint64_t(ks * 16), idesc,
+                             (ks | q) != 0 ? 1u : 0u);
+              }
+            }
             tc_commit(LEMPTY(ms));
             if (++ms == uint32_t(S)) {
               ms = 0;
@@ -420,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) continue;
         tc_fence_after();
-        const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * NT + colbase;
+        const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * ACC + colbase;
         const bool row_ok = row < Pn;
         const bool cnt_ok = row_ok && !(ragged && do_reduce && rowflag[row]);
         // Running row maximum over the chunks and, for a maximum that can beat
@@ -433,7 +463,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < NCH; ++c) {
           uint32_t r[CHK];
           tc_ld_cols<CHK>(taddr + c * CHK, r);
-          tc_wait_ld();
+          if constexpr (NACC == 2) {
+            uint32_t r2[CHK];
+            tc_ld_cols<CHK>(taddr + NT + c * CHK, r2);
+            tc_wait_ld();
+#pragma unroll
+            for (int jj = 0; jj < CHK; ++jj)
+              r[jj] = __float_as_uint(__uint_as_float(r[jj]) + __uint_as_float(r2[jj]));
+          } else if constexpr (NACC == 3) {
+            uint32_t r2[CHK], r3[CHK];
+            tc_ld_cols<CHK>(taddr + NT + c * CHK, r2);
+            tc_ld_cols<CHK>(taddr + 2 * NT + c * CHK, r3);
+            tc_wait_ld();
+#pragma unroll
+            for (int jj = 0; jj < CHK; ++jj)  // hi + (mid + lo)
+              r[jj] = __float_as_uint(__uint_as_float(r[jj]) +
+                                      (__uint_as_float(r2[jj]) + __uint_as_float(r3[jj])));
+          } else {
+            tc_wait_ld();
+          }
           const int64_t g0 = gcol0 + c * CHK;
           if (WRITE && a.write_mode && row_ok) {
             float* dst = st.uout + row * V;
@@ -491,14 +539,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, 2 * NT);
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-int smem_bytes(int NT, int n_pad, int pieces, int stages) {
-  return pieces * NT * n_pad * 2 + stages * kStageBytes + NT * 4 + (kMaxBlocksPerItem + 1) +
+int smem_bytes(int NT, int n_pad, int pieces, int stages, int kps) {
+  return pieces * NT * n_pad * 2 + stages * kps * kStepBytes + NT * 4 + (kMaxBlocksPerItem + 1) +
          (7 + 2 * stages) * 8 + 16;
 }
 
@@ -522,15 +570,21 @@ pt_status launch_nt(pt_ctx* ctx, const TcArgs& a, int pieces, int grid, int smem
   return PT_OK;
 }
 
-// Largest voxel tile NT (and its stage count) whose resident data tile fits.
-bool choose_tile(int n_pad, int pieces, int* NT, int* stages) {
+// Label-ring stages of kps k-steps each that fit beside the resident data
+// tile of NT voxels (0 when fewer than 2 fit or the tile exceeds one TMA box).
+int max_stages_fit(int NT, int n_pad, int pieces, int kps) {
+  if (int64_t(NT) * n_pad / 256 > 256) return 0;
+  int s = kMaxStages;
+  while (s >= 2 && smem_bytes(NT, n_pad, pieces, s, kps) > kSmemLimit - 1024) --s;
+  return s >= 2 ? s : 0;
+}
+
+// Largest voxel tile NT whose resident data tile fits beside at least 4
+// one-k-step label stages.
+bool choose_tile(int n_pad, int pieces, int* NT) {
   for (int cand : {256, 128, 64}) {
-    if (int64_t(cand) * n_pad / 256 > 256) continue;
-    int s = 12;
-    while (s >= 4 && smem_bytes(cand, n_pad, pieces, s) > kSmemLimit - 1024) --s;
-    if (s >= 4) {
+    if (max_stages_fit(cand, n_pad, pieces, 1) >= 4) {
       *NT = cand;
-      *stages = s;
       return true;
     }
   }
@@ -539,7 +593,7 @@ bool choose_tile(int n_pad, int pieces, int* NT, int* stages) {
 
 // Work split of one study into items (voxel tile x block range) and its
 // descriptor; target_items spreads small studies over more block ranges.
-bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int64_t target_items,
+bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int kps, int64_t target_items,
                 int64_t item_begin, const float* u_obs, unsigned long long* maxkey, uint32_t* cnt,
                 float* uout, TcStudy* st) {
   memset(st, 0, sizeof(*st));
@@ -567,18 +621,20 @@ bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int64_t target_ite
   st->cnt = cnt;
   st->uout = uout;
   const int64_t P_pad = st->nblocks * 128;
-  return make_map(&st->tmL, Lb, uint64_t(P_pad) * c->n_pad / 256, 8) &&
+  // Label box: kps k-steps of one 128-row block (8 view rows per k-step); a
+  // box that runs past the last block reads zero fill.
+  return make_map(&st->tmL, Lb, uint64_t(P_pad) * c->n_pad / 256, uint32_t(8 * kps)) &&
          make_map(&st->tmX, c->Xnb.p, uint64_t(3) * c->v_pad * c->n_pad / 256,
                   uint32_t(NT * c->n_pad / 256));
 }
 
-// Launch the fused kernel over n studies sharing tile NT and piece count.
-// descs: device copy of the descriptors (filled by the caller).
+// Launch the fused kernel over n studies sharing tile NT, ring shape and piece
+// count. descs: device copy of the descriptors (filled by the caller).
 pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_items, int NT,
-                         int pieces, int n_pad_max, int do_reduce, int write_mode, int two_sided,
-                         float kf, float ctf) {
-  int NTc = 0, stages = 0;
-  if (!choose_tile(n_pad_max, pieces, &NTc, &stages) || NTc < NT) {
+                         int stages, int kps, int pieces, int n_pad_max, int do_reduce,
+                         int write_mode, int two_sided, float kf, float ctf) {
+  const int fit = max_stages_fit(NT, n_pad_max, pieces, kps);
+  if (!fit || stages < 2 || stages > fit) {
     set_error(ctx, "tensor-core path: n too large for the resident data tile");
     return PT_ERR_UNSUPPORTED;
   }
@@ -586,6 +642,7 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   a.studies = descs;
   a.n_studies = n;
   a.stages = stages;
+  a.kps = kps;
   a.n_pad_max = n_pad_max;
   a.n_items = n_items;
   a.do_reduce = do_reduce;
@@ -595,7 +652,7 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   a.status = ctx->status.as<uint32_t>();
   const int sms = num_sms(ctx->device);
   const int grid = int(n_items < sms ? n_items : sms);
-  const int smem = smem_bytes(NT, n_pad_max, pieces, stages);
+  const int smem = smem_bytes(NT, n_pad_max, pieces, stages, kps);
   if (two_sided) {
     if (NT == 256) return launch_nt<256, true>(ctx, a, pieces, grid, smem);
     if (NT == 128) return launch_nt<128, true>(ctx, a, pieces, grid, smem);
@@ -606,17 +663,16 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   return launch_nt<64, false>(ctx, a, pieces, grid, smem);
 }
 
-pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
-                    int write_mode, int two_sided, const float* u_obs,
-                    unsigned long long* maxkey, uint32_t* cnt, float* uout) {
-  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
-  int NT = 0, stages = 0;
-  if (!choose_tile(ctx->n_pad, pieces, &NT, &stages)) {
-    set_error(ctx, "tensor-core path: n too large for the resident data tile");
-    return PT_ERR_UNSUPPORTED;
-  }
+// One study with an explicit launch configuration (already validated).
+pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int do_reduce,
+                        int write_mode, int two_sided, const float* u_obs,
+                        unsigned long long* maxkey, uint32_t* cnt, float* uout,
+                        const pt_tc_config& cfg) {
+  const int NT = cfg.voxel_tile;
   TcStudy st;
-  if (!fill_study(ctx, Lb, P, NT, 2 * num_sms(ctx->device), 0, u_obs, maxkey, cnt, uout, &st)) {
+  if (!fill_study(ctx, Lb, P, NT, cfg.ksteps_per_stage,
+                  int64_t(cfg.items_per_sm) * num_sms(ctx->device), 0, u_obs, maxkey, cnt, uout,
+                  &st)) {
     set_error(ctx, "cuTensorMapEncodeTiled failed");
     return PT_ERR_CUDA;
   }
@@ -627,8 +683,25 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
   PT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->tcdesc.p, &st, sizeof(TcStudy), cudaMemcpyHostToDevice,
                                    ctx->stream));
   const int64_t items = ((st.v + NT - 1) / NT) * st.n_chunks;
-  return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, pieces, ctx->n_pad,
-                        do_reduce, write_mode, two_sided, float(ctx->k), float(ctx->c_t));
+  return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, cfg.stages,
+                        cfg.ksteps_per_stage, pieces, ctx->n_pad, do_reduce, write_mode,
+                        two_sided, float(ctx->k), float(ctx->c_t));
+}
+
+pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
+                    int write_mode, int two_sided, const float* u_obs,
+                    unsigned long long* maxkey, uint32_t* cnt, float* uout) {
+  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  pt_tc_config cfg;
+  if (!tc_default_config(ctx->n_pad, pieces, &cfg)) {
+    set_error(ctx, "tensor-core path: n too large for the resident data tile");
+    return PT_ERR_UNSUPPORTED;
+  }
+  // The reduce-only launch (NaivePT) takes a tuned configuration when one is
+  // recorded for this shape; row-writing launches keep the default.
+  if (do_reduce && !write_mode) tune_find(ctx->n_pad, precision, two_sided, ctx->v_valid, P, &cfg);
+  return tc_launch_cfg(ctx, Lb, P, pieces, do_reduce, write_mode, two_sided, u_obs, maxkey, cnt,
+                       uout, cfg);
 }
 
 }  // namespace
@@ -665,38 +738,60 @@ pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int wri
 // Several prepared studies in one persistent launch per tile class
 // ---------------------------------------------------------------------------
 pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int n,
-                        int precision, Buf& descbuf, std::vector<char>& host_desc,
+                        const pt_naive_opts& o, Buf& descbuf, std::vector<char>& host_desc,
                         std::vector<TcGroup>& groups) {
-  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
-  std::vector<int> nt(n);
+  const int pieces = o.precision == PT_PREC_BF16X2 ? 2 : 3;
+  std::vector<pt_tc_config> cfg(n);
   for (int i = 0; i < n; ++i) {
-    int stages = 0;
-    if (!choose_tile(ctxs[i]->n_pad, pieces, &nt[i], &stages)) {
+    if (!tc_default_config(ctxs[i]->n_pad, pieces, &cfg[i])) {
       set_error(lead, "tensor-core path: a study's n is too large for the resident data tile");
       return PT_ERR_UNSUPPORTED;
     }
+    tune_find(ctxs[i]->n_pad, o.precision, o.two_sided, ctxs[i]->v_valid, P[i], &cfg[i]);
   }
   host_desc.assign(sizeof(TcStudy) * size_t(n), 0);
   TcStudy* hd = reinterpret_cast<TcStudy*>(host_desc.data());
   groups.clear();
+  // One launch per (voxel tile, k-steps per stage) among the studies: the ring
+  // is as deep (in k-steps) as its members ask for and fits the largest n of
+  // the launch, and every study's blocks are split so that the launch holds
+  // about items_per_sm work items per SM, each study by its share of voxels.
+  const int sms = num_sms(lead->device);
   int filled = 0;
   for (int NT : {256, 128, 64}) {
-    TcGroup g{NT, filled, 0, 16, 0};
-    for (int i = 0; i < n; ++i) {
-      pt_ctx* c = ctxs[i];
-      if (nt[i] != NT || c->v_valid < 1) continue;  // nothing to contract
-      if (!fill_study(c, c->labels.p, P[i], NT, 0, g.items, c->u_obs.as<float>(),
-                      c->maxkey.as<unsigned long long>(), c->cnt.as<uint32_t>(), nullptr,
-                      &hd[filled])) {
-        set_error(lead, "cuTensorMapEncodeTiled failed");
-        return PT_ERR_CUDA;
+    for (int kps : {8, 4, 2, 1}) {
+      TcGroup g{NT, filled, 0, 16, 0, 0, kps};
+      int ring = 1 << 30, items_per_sm = 1;
+      int64_t vsum = 0;
+      for (int i = 0; i < n; ++i) {
+        if (cfg[i].voxel_tile != NT || cfg[i].ksteps_per_stage != kps || ctxs[i]->v_valid < 1)
+          continue;
+        ring = std::min(ring, cfg[i].stages * kps);
+        items_per_sm = std::max(items_per_sm, cfg[i].items_per_sm);
+        g.n_pad_max = std::max(g.n_pad_max, ctxs[i]->n_pad);
+        vsum += ctxs[i]->v_valid;
       }
-      g.items += ((hd[filled].v + NT - 1) / NT) * hd[filled].n_chunks;
-      g.n_pad_max = std::max(g.n_pad_max, c->n_pad);
-      ++filled;
-      ++g.count;
+      if (!vsum) continue;
+      const int fit = max_stages_fit(NT, g.n_pad_max, pieces, kps);
+      g.stages = std::max(2, std::min(fit, ring / kps));
+      const double want = double(items_per_sm) * sms;
+      for (int i = 0; i < n; ++i) {
+        pt_ctx* c = ctxs[i];
+        if (cfg[i].voxel_tile != NT || cfg[i].ksteps_per_stage != kps || c->v_valid < 1)
+          continue;  // another launch, or nothing to contract
+        const int64_t target = int64_t(std::ceil(want * double(c->v_valid) / double(vsum)));
+        if (!fill_study(c, c->labels.p, P[i], NT, kps, target, g.items, c->u_obs.as<float>(),
+                        c->maxkey.as<unsigned long long>(), c->cnt.as<uint32_t>(), nullptr,
+                        &hd[filled])) {
+          set_error(lead, "cuTensorMapEncodeTiled failed");
+          return PT_ERR_CUDA;
+        }
+        g.items += ((hd[filled].v + NT - 1) / NT) * hd[filled].n_chunks;
+        ++filled;
+        ++g.count;
+      }
+      groups.push_back(g);
     }
-    if (g.count) groups.push_back(g);
   }
   if (!filled) return PT_OK;
   if (!descbuf.ensure(sizeof(TcStudy) * size_t(filled))) {
@@ -714,9 +809,145 @@ pt_status tc_batch_launch(pt_ctx* lead, const Buf& descbuf, const std::vector<Tc
   const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
   for (const TcGroup& g : groups) {
     pt_status s = launch_studies(lead, static_cast<const TcStudy*>(descbuf.p) + g.first, g.count,
-                                 g.items, g.NT, pieces, g.n_pad_max, 1, 0, two_sided, 0.0f, 0.0f);
+                                 g.items, g.NT, g.stages, g.kps, pieces, g.n_pad_max, 1, 0,
+                                 two_sided, 0.0f, 0.0f);
     if (s != PT_OK) return s;
   }
+  return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch configurations and the autotuner's timing loop
+// ---------------------------------------------------------------------------
+int tc_max_stages(int NT, int n_pad, int pieces, int kps) {
+  return max_stages_fit(NT, n_pad, pieces, kps);
+}
+
+bool tc_default_config(int n_pad, int pieces, pt_tc_config* out) {
+  int NT = 0;
+  if (!choose_tile(n_pad, pieces, &NT)) return false;
+  // Fewest ring waits: the largest stage (in k-steps) of which two fit, and a
+  // ring of about 16 k-steps.
+  int kps = 1;
+  for (int k : {8, 4, 2})
+    if (max_stages_fit(NT, n_pad, pieces, k) >= 2) {
+      kps = k;
+      break;
+    }
+  const int fit = max_stages_fit(NT, n_pad, pieces, kps);
+  out->voxel_tile = NT;
+  out->ksteps_per_stage = kps;
+  out->stages = std::max(2, std::min(fit, 16 / kps));
+  out->items_per_sm = kDefaultItemsPerSm;
+  return true;
+}
+
+// The voxel tile fixes how the data pieces' partial sums are combined (one,
+// two or three accumulators), so a configuration keeps the default tile for
+// its n: the outputs never depend on the configuration.
+bool tc_config_valid(const pt_tc_config& c, int n_pad, int pieces) {
+  pt_tc_config d;
+  if (!tc_default_config(n_pad, pieces, &d)) return false;
+  if (c.voxel_tile != d.voxel_tile) return false;
+  const int k = c.ksteps_per_stage;
+  if (k != 1 && k != 2 && k != 4 && k != 8) return false;
+  const int fit = max_stages_fit(c.voxel_tile, n_pad, pieces, k);
+  return fit >= 2 && c.stages >= 2 && c.stages <= fit && c.items_per_sm >= 1 &&
+         c.items_per_sm <= 64;
+}
+
+// Times the reduce-only launch of every candidate configuration on this
+// problem (labels already built, operand pieces ready): each candidate runs
+// twice after the workspaces are cleared, and its faster run counts.
+pt_status tc_autotune(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int two_sided,
+                      pt_tc_config* best, double* best_ms, std::vector<TcTrial>* trials) {
+  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  std::vector<pt_tc_config> cand;
+  pt_tc_config d;
+  if (!tc_default_config(ctx->n_pad, pieces, &d)) {
+    set_error(ctx, "tensor-core path: n too large for the resident data tile");
+    return PT_ERR_UNSUPPORTED;
+  }
+  for (int NT : {d.voxel_tile}) {
+    for (int kps : {1, 2, 4, 8}) {
+      const int fit = max_stages_fit(NT, ctx->n_pad, pieces, kps);
+      for (int ring : {8, 16, 32}) {  // ring depth in k-steps
+        const int st = std::min(fit, std::max(2, ring / kps));
+        const pt_tc_config c{NT, st, kps, kDefaultItemsPerSm};
+        if (!tc_config_valid(c, ctx->n_pad, pieces)) continue;
+        bool dup = false;
+        for (const auto& e : cand)
+          dup = dup || (e.voxel_tile == NT && e.stages == st && e.ksteps_per_stage == kps);
+        if (!dup) cand.push_back(c);
+      }
+    }
+  }
+  if (cand.empty()) {
+    set_error(ctx, "tensor-core path: n too large for the resident data tile");
+    return PT_ERR_UNSUPPORTED;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PT_CUDA_TRY(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error(ctx, "cudaEventCreate failed");
+    return PT_ERR_CUDA;
+  }
+  const bool prof = ctx->profile;
+  ctx->profile = false;
+  pt_status s = PT_OK;
+  double bms = 0.0;
+  pt_tc_config b{};
+  auto time_one = [&](const pt_tc_config& c, double* ms_out) -> pt_status {
+    double bestrun = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {
+      PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->maxkey.p, 0, sizeof(unsigned long long) * P,
+                                       ctx->stream));
+      PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(uint32_t) * (ctx->v_valid + 1),
+                                       ctx->stream));
+      PT_CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
+      pt_status r = tc_launch_cfg(ctx, Lb, P, pieces, 1, 0, two_sided, ctx->u_obs.as<float>(),
+                                  ctx->maxkey.as<unsigned long long>(), ctx->cnt.as<uint32_t>(),
+                                  nullptr, c);
+      if (r != PT_OK) return r;
+      PT_CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
+      PT_CUDA_TRY(ctx, cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      PT_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 0 || ms < bestrun) bestrun = ms;
+    }
+    *ms_out = bestrun;
+    if (trials) trials->push_back({c, bestrun});
+    return PT_OK;
+  };
+  // Phase 1: tile and ring shape at the default block split.
+  for (size_t i = 0; i < cand.size() && s == PT_OK; ++i) {
+    double ms = 0.0;
+    s = time_one(cand[i], &ms);
+    if (s == PT_OK && (i == 0 || ms < bms)) {
+      bms = ms;
+      b = cand[i];
+    }
+  }
+  // Phase 2: how finely the relabelling blocks of a voxel tile are split.
+  for (int items : {1, 2, 4, 8}) {
+    if (s != PT_OK) break;
+    if (items == kDefaultItemsPerSm) continue;
+    pt_tc_config c = b;
+    c.items_per_sm = items;
+    double ms = 0.0;
+    s = time_one(c, &ms);
+    if (s == PT_OK && ms < bms) {
+      bms = ms;
+      b = c;
+    }
+  }
+  ctx->profile = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != PT_OK) return s;
+  *best = b;
+  *best_ms = bms;
   return PT_OK;
 }
 
