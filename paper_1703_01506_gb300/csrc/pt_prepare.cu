@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cmath>
 #include <string>
 
@@ -161,19 +163,25 @@ __global__ void __launch_bounds__(32 * kMW)
   const float x0f = g >= 0 ? X[g] : 0.0f;
   float amax = 0.0f;
   uint32_t fl = 0u;  // bit 0: non-finite seen, bit 1: a value differs from x_0
-  for (int s = warp; s < n; s += kMW) {
-    const float xf = g >= 0 ? X[int64_t(s) * n_grid + g] : 0.0f;
-    tile[s * LD + lane] = xf;
-    if (!isfinite(xf)) fl |= 1u;
-    if (xf != x0f) fl |= 2u;
-    amax = fmaxf(amax, fabsf(xf));
+  {
+    const float* xp = X + (g >= 0 ? g : 0) + int64_t(warp) * n_grid;
+    const int64_t step = int64_t(kMW) * n_grid;
+    for (int s = warp; s < n; s += kMW, xp += step) {
+      const float xf = g >= 0 ? *xp : 0.0f;
+      tile[s * LD + lane] = xf;
+      if (!isfinite(xf)) fl |= 1u;
+      if (xf != x0f) fl |= 2u;
+      amax = fmaxf(amax, fabsf(xf));
+    }
   }
   part[warp][0][lane] = amax;
   flags[warp][lane] = fl;
   __syncthreads();
-  for (int idx = tid; idx < kMV * n_pad; idx += blockDim.x) {
-    const int l = idx / n_pad, s = idx - l * n_pad;
-    if (j0 + l < v) Xraw[(j0 + l) * n_pad + s] = s < n ? tile[s * LD + l] : 0.0f;
+  // Voxel-major copy: warp w writes rows l = w, w + 8, ... (lane = subject;
+  // tile reads at stride LD = 33 words fall in distinct banks).
+  for (int l = warp; l < kMV && j0 + l < v; l += kMW) {
+    float* dst = Xraw + (j0 + l) * n_pad;
+    for (int s = lane; s < n_pad; s += 32) dst[s] = s < n ? tile[s * LD + l] : 0.0f;
   }
   fl = 0u;
   amax = 0.0f;
@@ -338,18 +346,19 @@ __global__ void build_xn32_kernel(const float* __restrict__ Xraw, int n, int n_p
 
 // BF16 pieces: hi = bf16(y), mid = bf16(y - hi), lo = bf16(y - hi - mid)
 // (each residual exact in FP32), stored as 8x8 core matrices, row-group major.
-// One thread per core-matrix row (8 consecutive subjects): 16-byte stores.
+// A CTA takes one row group (8 consecutive compact voxels); a thread builds one
+// core-matrix row (8 consecutive subjects of one voxel), so the 8 threads of a
+// core matrix store its 128 contiguous bytes together (16-byte stores).
 __global__ void build_xnb_kernel(const float* __restrict__ Xraw, int n, int n_pad,
                                  const int32_t* __restrict__ valid_map, int64_t v_valid,
                                  int64_t v_pad, const float4* __restrict__ vstat,
                                  __nv_bfloat16* __restrict__ Xnb) {
   const int kg_n = n_pad >> 3;
-  const int64_t total = v_pad * kg_n;
   const int64_t piece = v_pad * n_pad;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t c = e / kg_n;
-    const int kg = int(e - c * kg_n);
+  const int64_t cg = blockIdx.x;  // row group
+  for (int idx = threadIdx.x; idx < kg_n * 8; idx += blockDim.x) {
+    const int r = idx & 7, kg = idx >> 3;
+    const int64_t c = cg * 8 + r;
     float y[8];
     if (c < v_valid) {
       const float4 st = vstat[c];
@@ -371,7 +380,7 @@ __global__ void build_xnb_kernel(const float* __restrict__ Xraw, int n, int n_pa
       mid[q] = __float2bfloat16_rn(r1);
       lo[q] = __float2bfloat16_rn(r1 - __bfloat162float(mid[q]));
     }
-    const int64_t off = ((c >> 3) * kg_n + kg) * 64 + (c & 7) * 8;
+    const int64_t off = (cg * kg_n + kg) * 64 + r * 8;
     *reinterpret_cast<uint4*>(Xnb + off) = *reinterpret_cast<const uint4*>(hi);
     *reinterpret_cast<uint4*>(Xnb + piece + off) = *reinterpret_cast<const uint4*>(mid);
     *reinterpret_cast<uint4*>(Xnb + 2 * piece + off) = *reinterpret_cast<const uint4*>(lo);
@@ -523,7 +532,8 @@ pt_status ensure_xnb(pt_ctx* ctx) {
   if (ctx->have_xnb) return PT_OK;
   const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
   if (!ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) return nomem(ctx, "Xnb");
-  build_xnb_kernel<<<grid_for(int64_t(elems / 8), 256), 256, 0, ctx->stream>>>(
+  const int xnb_threads = std::min(256, (ctx->n_pad + 31) / 32 * 32);
+  build_xnb_kernel<<<unsigned(ctx->v_pad / 8), xnb_threads, 0, ctx->stream>>>(
       ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,
       ctx->v_pad, ctx->vstat.as<float4>(), ctx->Xnb.as<__nv_bfloat16>());
   PT_LAUNCH_CHECK(ctx);
