@@ -176,28 +176,34 @@ def test_deterministic_repeat(cuda_lib):
             np.testing.assert_array_equal(x, y)
 
 
-def test_full_brain_n100_sampled(cuda_lib):
-    """The benchmark workload (n=100, ~232k voxels, 10k relabellings, split-BF16x3)
-    in the launch configuration bench.py times: sampled rows against the oracle's
-    full-row maxima, sampled voxels against the oracle's counts over all rows."""
+@pytest.mark.parametrize("name", ["brain_n100_v232k", "brain_n200_v500k", "brain_n400_v600k"])
+def test_full_size_sampled(cuda_lib, name):
+    """The full-size workloads (n=100 / 232k voxels / 10k relabellings, n=200 /
+    500k / 100k, n=400 / 600k / 100k; split-BF16x3) in the launch configuration
+    bench.py times (autotuned): sampled rows against the oracle's full-row
+    maxima, sampled voxels against the oracle's counts over all rows."""
     B = cuda_lib
-    w = synth.workload("brain_n100_v232k", device="cuda")
+    w = synth.workload(name, device="cuda")
     X, mask, n1, perms = w["X"], w["mask"], w["n1"], w["perms"]
     ctx = B.pt_prepare(X, n1, mask)
     v = B.pt_num_voxels(ctx)
     pd = torch.as_tensor(perms).cuda()
+    B.pt_tune_clear()
+    B.pt_autotune_naive(ctx, pd, B.naive_opts(B.PT_PREC_BF16X3))
     mx, am, ct = B.maxnull_naive(ctx, pd, precision=B.PT_PREC_BF16X3)
+    B.pt_tune_clear()
     mx = mx.cpu().numpy().astype(np.float64)
     am = am.cpu().numpy()
     ct = ct.cpu().numpy().astype(np.int64)
     Xm = X[:, mask.bool()].cpu().numpy()
+    del X
     assert Xm.shape[1] == v
     rng = np.random.default_rng(0)
-    rows = np.sort(rng.choice(perms.shape[0], 12, replace=False))
+    rows = np.sort(rng.choice(perms.shape[0], 8, replace=False))
     n = Xm.shape[0]
     ref = oracle.naive(Xm, n1, perms[rows], tie_rel=tie_rel(2, n))
-    check(ref, (mx[rows], am[rows], np.zeros(0, np.int64)), 2, "rows")
-    vox = np.sort(rng.choice(v, 48, replace=False))
+    check(ref, (mx[rows], am[rows], np.zeros(0, np.int64)), 2, name + " rows")
+    vox = np.sort(rng.choice(v, 32, replace=False))
     refc = oracle.naive(Xm[:, vox], n1, perms, tie_rel=tie_rel(2, n))
     dc = np.abs(ct[vox] - refc.counts.astype(np.int64))
     assert np.all(dc <= refc.near.astype(np.int64)), dc
