@@ -63,6 +63,9 @@ typedef enum {
 typedef struct {
   int32_t precision; /* pt_precision; default PT_PREC_BF16X3 */
   int32_t two_sided; /* 0 (default): statistic t; 1: statistic |t| (max |t|, counts |t|>=|t_obs|) */
+  int32_t accumulate_counts; /* 0 (default): counts = this call's exceedances; 1: counts +=
+                                this call's (a run split into relabelling chunks, resumed
+                                from a checkpoint or sharded, sums its counts in place) */
 } pt_naive_opts;
 
 /* Fills *o with the defaults above. */

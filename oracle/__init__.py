@@ -163,3 +163,22 @@ def fwer_pvalues(maxnull, t_obs, two_sided=False):
     below = np.searchsorted(ms, T[ok], side="left")
     out[ok] = (1.0 + (P - below)) / (P + 1.0)
     return out
+
+
+def resampling_risk(reject1, reject2):
+    """Resampling risk of two methods' voxel-wise decisions (Sec. 5.5, Eq. (6)):
+    with v1 and v2 the numbers of voxels whose null hypothesis method 1 and
+    method 2 reject, and vc the number both reject,
+        risk = ((v1 - vc) / v1 + (v2 - vc) / v2) / 2.
+    The paper leaves v1 = 0 or v2 = 0 open; reading taken here: a method that
+    rejects nothing contributes 0 for its own term (none of its rejections is
+    missed by the other), so two empty sets give 0 and one empty set against
+    a non-empty one gives 1/2. Returns (risk, v1, v2, vc)."""
+    a = np.asarray(reject1, dtype=bool)
+    b = np.asarray(reject2, dtype=bool)
+    v1 = int(a.sum())
+    v2 = int(b.sum())
+    vc = int(np.logical_and(a, b).sum())
+    t1 = (v1 - vc) / v1 if v1 else 0.0
+    t2 = (v2 - vc) / v2 if v2 else 0.0
+    return (t1 + t2) / 2.0, v1, v2, vc

@@ -28,7 +28,8 @@ class PtError(RuntimeError):
 
 
 class pt_naive_opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int32), ("two_sided", ctypes.c_int32)]
+    _fields_ = [("precision", ctypes.c_int32), ("two_sided", ctypes.c_int32),
+                ("accumulate_counts", ctypes.c_int32)]
 
 
 class pt_tc_config(ctypes.Structure):
@@ -301,11 +302,12 @@ def pt_release_cached_memory():
     load().pt_release_cached_memory()
 
 
-def naive_opts(precision=PT_PREC_BF16X3, two_sided=False):
+def naive_opts(precision=PT_PREC_BF16X3, two_sided=False, accumulate_counts=False):
     o = pt_naive_opts()
     load().pt_naive_opts_default(ctypes.byref(o))
     o.precision = int(precision)
     o.two_sided = int(bool(two_sided))
+    o.accumulate_counts = int(bool(accumulate_counts))
     return o
 
 

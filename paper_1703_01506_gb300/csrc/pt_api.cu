@@ -140,6 +140,7 @@ void pt_naive_opts_default(pt_naive_opts* o) {
   if (!o) return;
   o->precision = PT_PREC_BF16X3;
   o->two_sided = 0;
+  o->accumulate_counts = 0;
 }
 
 pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* mask, int32_t n1,
@@ -197,7 +198,7 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
       return PT_ERR_INVALID;
     }
     if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_BF16X3 || o.two_sided < 0 ||
-        o.two_sided > 1) {
+        o.two_sided > 1 || o.accumulate_counts < 0 || o.accumulate_counts > 1) {
       set_error(ctx, "pt_maxnull_naive: bad options");
       return PT_ERR_INVALID;
     }
@@ -227,7 +228,7 @@ pt_status pt_maxnull_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
     pt_naive_opts_default(&o);
     if (opts) o = *opts;
     if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_BF16X3 || o.two_sided < 0 ||
-        o.two_sided > 1) {
+        o.two_sided > 1 || o.accumulate_counts < 0 || o.accumulate_counts > 1) {
       pt::set_thread_error("pt_maxnull_naive_batched: bad options");
       return PT_ERR_INVALID;
     }

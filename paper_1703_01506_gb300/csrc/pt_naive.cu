@@ -335,11 +335,13 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
 // whose group-1 set equals the observed one (cnt[v_valid]).
 __global__ void scatter_counts_kernel(const uint32_t* __restrict__ cnt, int64_t v_valid,
                                       const int32_t* __restrict__ valid_map,
-                                      uint32_t* __restrict__ counts) {
+                                      uint32_t* __restrict__ counts, int accumulate) {
   const uint32_t ties = cnt[v_valid];
   for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < v_valid;
-       c += int64_t(gridDim.x) * blockDim.x)
-    counts[valid_map[c]] = cnt[c] + ties;
+       c += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t j = valid_map[c];
+    counts[j] = (accumulate ? counts[j] : 0u) + cnt[c] + ties;
+  }
 }
 
 // FWER-corrected p-values: p_j = (1 + #{i : m_i >= T_j}) / (P + 1) over the
@@ -441,7 +443,8 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
   }
   PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->maxkey.p, 0, sizeof(unsigned long long) * P, st));
   PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(uint32_t) * (ctx->v_valid + 1), st));
-  if (counts) PT_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ctx->v, st));
+  if (counts && !o.accumulate_counts)
+    PT_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ctx->v, st));
   int64_t P_pad = 0;
   s = build_labels(ctx, perms, P, tc ? 1 : 0, &P_pad);
   if (s != PT_OK) return s;
@@ -465,7 +468,8 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
   PT_LAUNCH_CHECK(ctx);
   if (counts && ctx->v_valid > 0) {
     scatter_counts_kernel<<<grid_1d(ctx->v_valid, 256), 256, 0, st>>>(
-        ctx->cnt.as<uint32_t>(), ctx->v_valid, ctx->valid_map.as<int32_t>(), counts);
+        ctx->cnt.as<uint32_t>(), ctx->v_valid, ctx->valid_map.as<int32_t>(), counts,
+        o.accumulate_counts);
     PT_LAUNCH_CHECK(ctx);
   }
   return PT_OK;
@@ -535,7 +539,7 @@ static pt_status batched_enqueue(pt_ctx* lead, pt_ctx* const* ctxs, int n,
     pt_ctx* c = ctxs[i];
     PT_CUDA_TRY(lead, cudaMemsetAsync(c->maxkey.p, 0, sizeof(unsigned long long) * P[i], st));
     PT_CUDA_TRY(lead, cudaMemsetAsync(c->cnt.p, 0, sizeof(uint32_t) * (c->v_valid + 1), st));
-    if (counts && counts[i])
+    if (counts && counts[i] && !o.accumulate_counts)
       PT_CUDA_TRY(lead, cudaMemsetAsync(counts[i], 0, sizeof(uint32_t) * c->v, st));
     int64_t P_pad = 0;
     pt_status s = build_labels(c, perms[i], P[i], 1, &P_pad);
@@ -551,7 +555,8 @@ static pt_status batched_enqueue(pt_ctx* lead, pt_ctx* const* ctxs, int n,
     PT_LAUNCH_CHECK(lead);
     if (counts && counts[i] && c->v_valid > 0) {
       scatter_counts_kernel<<<grid_1d(c->v_valid, 256), 256, 0, st>>>(
-          c->cnt.as<uint32_t>(), c->v_valid, c->valid_map.as<int32_t>(), counts[i]);
+          c->cnt.as<uint32_t>(), c->v_valid, c->valid_map.as<int32_t>(), counts[i],
+          o.accumulate_counts);
       PT_LAUNCH_CHECK(lead);
     }
   }
@@ -565,7 +570,9 @@ static std::vector<const void*> batch_key(pt_ctx* const* ctxs, int n, const int3
                                           uint32_t* const* counts) {
   std::vector<const void*> key;
   key.push_back(reinterpret_cast<const void*>(intptr_t(n)));
-  key.push_back(reinterpret_cast<const void*>(intptr_t(o.precision * 2 + o.two_sided)));
+  key.push_back(
+      reinterpret_cast<const void*>(intptr_t((o.precision * 2 + o.two_sided) * 2 +
+                                             o.accumulate_counts)));
   key.push_back(reinterpret_cast<const void*>(intptr_t(ctxs[0]->device)));
   for (int i = 0; i < n; ++i) {
     key.push_back(ctxs[i]);

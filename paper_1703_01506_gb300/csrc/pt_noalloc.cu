@@ -38,7 +38,8 @@ __global__ void finalize_max_kernel(const unsigned long long* maxkey, int64_t P,
                                     int n_pad, const int32_t* perms, int two_sided,
                                     float* maxnull, int32_t* argmax);
 __global__ void scatter_counts_kernel(const uint32_t* cnt, int64_t v_valid,
-                                      const int32_t* valid_map, uint32_t* counts);
+                                      const int32_t* valid_map, uint32_t* counts,
+                                      int accumulate);
 
 namespace {
 
@@ -312,7 +313,7 @@ extern "C" pt_status pt_maxnull_naive_noalloc(const float* X, int32_t n, int64_t
       maxkey, P, valid_map, Xraw, n, n1, n_pad, perms, two_sided, maxnull, argmax);
   if (counts && v_valid > 0)
     scatter_counts_kernel<<<blocks_for(v_valid, 256), 256, 0, st>>>(cnt, v_valid, valid_map,
-                                                                    counts);
+                                                                    counts, 0);
   NA_TRY(cudaGetLastError());
   uint32_t bits = 0;
   NA_TRY(cudaMemcpyAsync(&bits, status, sizeof(bits), cudaMemcpyDeviceToHost, st));

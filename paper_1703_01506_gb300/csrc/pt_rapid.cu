@@ -45,7 +45,8 @@ __global__ void finalize_max_kernel(const unsigned long long* maxkey, int64_t P,
                                     int n_pad, const int32_t* perms, int two_sided,
                                     float* maxnull, int32_t* argmax);
 __global__ void scatter_counts_kernel(const uint32_t* cnt, int64_t v_valid,
-                                      const int32_t* valid_map, uint32_t* counts);
+                                      const int32_t* valid_map, uint32_t* counts,
+                                      int accumulate);
 __global__ void simt_contract_kernel(const float* L, const float* Xn, int n_pad, int64_t P,
                                      int64_t v, int tiles_per_cta, int mode, int two_sided,
                                      const float* u_obs, const uint8_t* rowflag,
@@ -1464,7 +1465,7 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
     PT_LAUNCH_CHECK(ctx);
     if (counts) {
       scatter_counts_kernel<<<grid_n(V, 256), 256, 0, st>>>(
-          ctx->cnt.as<uint32_t>(), V, ctx->valid_map.as<int32_t>(), counts);
+          ctx->cnt.as<uint32_t>(), V, ctx->valid_map.as<int32_t>(), counts, 0);
       PT_LAUNCH_CHECK(ctx);
     }
     if (train_max)

@@ -211,3 +211,48 @@ def test_fwer_pvalues_definition():
     for j in range(v):
         exact = np.mean(allmax.astype(np.float32) >= np.float32(ref.t_obs[j]))
         assert abs(p[j] - exact) < 1e-12
+
+
+def test_resampling_risk_paper_examples():
+    """Eq. (6) against the two worked values of Sec. 6: RapidPT rejecting 59 and
+    SnPM 71 voxels (the 59 among the 71) gives 8.45%; 2158 among 2241 gives 1.85%."""
+    for a, b, want in [(59, 71, 0.0845), (2158, 2241, 0.0185)]:
+        v = 600000
+        r_small = np.zeros(v, bool)
+        r_small[:a] = True
+        r_large = np.zeros(v, bool)
+        r_large[:b] = True
+        risk, v1, v2, vc = oracle.resampling_risk(r_small, r_large)
+        assert (v1, v2, vc) == (a, b, a)
+        assert round(100 * risk, 2) == round(100 * want, 2)
+        assert oracle.resampling_risk(r_large, r_small)[0] == risk  # symmetric
+
+
+def test_resampling_risk_special_cases():
+    rng = np.random.default_rng(3)
+    r = rng.random(1000) < 0.1
+    assert oracle.resampling_risk(r, r)[0] == 0.0            # same decisions
+    assert oracle.resampling_risk(r, ~r)[0] == 1.0           # disjoint rejections
+    none = np.zeros(1000, bool)
+    assert oracle.resampling_risk(none, none)[0] == 0.0
+    assert oracle.resampling_risk(none, r)[0] == 0.5
+    # brute force over a small case: the fraction of each method's rejections
+    # that the other method does not reject, averaged
+    a = rng.random(50) < 0.3
+    b = rng.random(50) < 0.3
+    miss_a = sum(1 for i in range(50) if a[i] and not b[i]) / max(1, a.sum())
+    miss_b = sum(1 for i in range(50) if b[i] and not a[i]) / max(1, b.sum())
+    assert abs(oracle.resampling_risk(a, b)[0] - (miss_a + miss_b) / 2) < 1e-15
+
+
+def test_package_resampling_risk_matches_oracle():
+    from paper_1703_01506_gb300 import metrics
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        p1 = rng.random(5000)
+        p2 = np.clip(p1 + rng.normal(0, 0.02, 5000), 0, 1)
+        p1[rng.random(5000) < 0.01] = np.nan
+        for alpha in (0.01, 0.05, 0.2):
+            got = metrics.resampling_risk(p1, p2, alpha)
+            want = oracle.resampling_risk(p1 <= alpha, p2 <= alpha)  # NaN <= alpha is False
+            assert got["risk"] == want[0] and (got["v1"], got["v2"], got["vc"]) == want[1:]
