@@ -14,7 +14,11 @@ sampling): each method's max-null wall time, and RapidPT's accuracy against
 the exhaustive max-null (KL divergence, FWER 0.05/0.01 thresholds).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision bf16x3|bf16x2|fp32] [--no-rapid] [--no-cpu-baseline]
+                  [--precision bf16x3|bf16x2|fp32] [--no-tune] [--no-rapid] [--no-batched]
+                  [--no-cpu-baseline] [--quick]
+
+Default K = 500 steps (about 0.7 s of timed work at one GPU, so that several
+nvidia-smi clock samples fall inside the timed region).
 
 With N > 1 it runs under torch.distributed.run, one rank per GPU: every rank
 takes its own 10,000 relabellings of the same study (weak scaling, no data
@@ -54,7 +58,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms; stop() reports the
+    samples taken inside [t0, t1] (the timed region), or all samples, flagged, when
+    the region held none."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -82,9 +88,9 @@ class ClockSampler:
         for line in self.proc.stdout:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
-                self.rows.append(f)
+                self.rows.append((time.time(), f))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -97,7 +103,9 @@ class ClockSampler:
         mx = None
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for f in self.rows:
+        inside = [f for t, f in self.rows if t0 is not None and t0 <= t <= t1]
+        rows = inside if inside else [f for _, f in self.rows]
+        for f in rows:
             try:
                 sm.append(float(f[1]))
                 mx = float(f[2])
@@ -107,7 +115,9 @@ class ClockSampler:
                 if val.strip().lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window": "timed region" if inside else "whole sampling (no sample fell "
+                          "inside the timed region)"}
 
 
 def dist_env():
@@ -175,9 +185,11 @@ def run_reference(args):
     oracle.build()
     Xt = oracle.voxel_major(Xm)
     cores = cpu_cores()
-    # size one step to ~5 s of CPU work
+    # size one step so that the warm-up and timed steps take about 90 s in all
+    # (at most 5 s of CPU work per step)
+    step_s = max(0.05, min(5.0, 90.0 / max(1, args.steps + args.warmup)))
     rate, rows, dt, _ = oracle_sample(Xm, w["n1"], w["perms"], seconds_target=4.0)
-    step_rows = max(1, int(round(rows * 5.0 / max(dt, 1e-6))))
+    step_rows = max(1, int(round(rows * step_s / max(dt, 1e-6))))
     step_rows = min(step_rows, w["perms"].shape[0])
     for i in range(args.warmup):
         _oracle_rows(Xt, w["n1"], w["perms"][:step_rows], cores)
@@ -446,6 +458,7 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
         ctx = step(profile=True)
@@ -456,8 +469,9 @@ def run_ours(args):
         ctx.close()  # workspaces go back to the library's cache for the next step
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    t_wall1 = time.time()
     launches = B.pt_kernel_launch_count() - launches0
-    clk = clocks.stop()
+    clk = clocks.stop(t_wall0, t_wall1)
     ms = ev0.elapsed_time(ev1) / args.steps
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -583,7 +597,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
