@@ -230,7 +230,7 @@ def hist_kl(p_samples, q_samples, bins=100):
     return float(np.sum(pp[m] * np.log(pp[m] / qq[m])))
 
 
-def rapid_leg(dev, B, synth, torch, passes=10, rows=None):
+def rapid_leg(dev, B, synth, torch, passes=1, rows=None):
     """RapidPT vs NaivePT max-null wall time on the RapidPT workload (n=200,
     500,000 voxels, 100,000 relabellings, r=50, 400 training rows, 0.35%
     sampling): each method's time from pt_prepare to the max-null vector, with
@@ -602,8 +602,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--rapid-passes", type=int, default=10,
-                    help="RapidPT training passes in the RapidPT leg (default 10)")
+    ap.add_argument("--rapid-passes", type=int, default=1,
+                    help="RapidPT training passes in the RapidPT leg (default 1, Alg. 2)")
     ap.add_argument("--rapid-rows", type=int, default=0,
                     help="relabellings of the RapidPT leg (default all 100,000)")
     ap.add_argument("--rapid-only", action="store_true",

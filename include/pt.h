@@ -155,8 +155,8 @@ pt_status pt_maxnull_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
 /* ------------------------------------------------------------------------- */
 typedef struct {
   int32_t precision;    /* contraction of the training rows (pt_precision); default BF16X3 */
-  int32_t train_passes; /* passes over the training columns (Sec. 4.1 "multiple passes");
-                           default 10 */
+  int32_t train_passes; /* passes over the training columns; default 1 (Alg. 2's single
+                           loop; Sec. 4.1 allows "multiple passes") */
   int32_t qr_every;     /* re-orthonormalise U (FP64-factorised QR) every this many steps;
                            default 100 */
   int32_t admm_iters;   /* iterations of each l1 weight solve; default 30 */

@@ -172,7 +172,7 @@ def geodesic_step(U, idx, b, w, step):
 
 
 class RapidOpts:
-    def __init__(self, train_passes=10, qr_every=100, admm_iters=30, admm_rho=2.0, step=1.0,
+    def __init__(self, train_passes=1, qr_every=100, admm_iters=30, admm_rho=2.0, step=1.0,
                  shift_mode=1, seed=1, stat="t"):
         self.train_passes, self.qr_every = train_passes, qr_every
         self.admm_iters, self.admm_rho, self.step = admm_iters, admm_rho, step

@@ -1760,7 +1760,7 @@ extern "C" {
 void pt_rapid_opts_default(pt_rapid_opts* o) {
   if (!o) return;
   o->precision = PT_PREC_BF16X3;
-  o->train_passes = 10;
+  o->train_passes = 1;
   o->qr_every = 100;
   o->admm_iters = 30;
   o->admm_rho = 2.0f;
