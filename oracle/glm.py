@@ -34,6 +34,7 @@ def glm_t_rows(X, Z, n1, perms):
     C = design_base(Z, n)
     perms = np.asarray(perms)
     T = np.empty((perms.shape[0], v))
+    dead = degenerate_voxels(X, C)
     for i, row in enumerate(perms):
         lab = np.zeros(n)
         lab[row[:n1]] = 1.0
@@ -47,7 +48,22 @@ def glm_t_rows(X, Z, n1, perms):
         g00 = np.linalg.inv(D.T @ D)[0, 0]
         with np.errstate(divide="ignore", invalid="ignore"):
             T[i] = beta[0] / np.sqrt(rss / df * g00)
+        T[i, dead] = np.nan
     return T
+
+
+def degenerate_voxels(X, C):
+    """Voxels without a statistic: all n values equal, or values in the span of
+    [1, Z] (residual sum of squares at most 1e-24 of the centred one, decided
+    in FP64)."""
+    X = np.asarray(X, dtype=np.float64)
+    const = np.all(X == X[0], axis=0)
+    Q, _ = np.linalg.qr(C)
+    R = X - Q @ (Q.T @ X)
+    Xc = X - X.mean(axis=0)
+    ss_r = np.einsum("sj,sj->j", R, R)
+    ss_c = np.einsum("sj,sj->j", Xc, Xc)
+    return const | (ss_r <= 1e-24 * ss_c)
 
 
 def glm_t_obs(X, Z, n1):
