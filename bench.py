@@ -15,7 +15,7 @@ the exhaustive max-null (KL divergence, FWER 0.05/0.01 thresholds).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision bf16x3|bf16x2|fp32] [--no-tune] [--no-rapid] [--no-batched]
-                  [--no-cpu-baseline] [--quick]
+                  [--no-glm] [--no-cpu-baseline] [--quick]
 
 Default K = 500 steps (about 0.7 s of timed work at one GPU, so that several
 nvidia-smi clock samples fall inside the timed region).
@@ -385,6 +385,47 @@ def batched_leg(dev, B, synth, torch, studies=64, P=10000):
             "timing": "device events over 5 graph replays / 3 loops of per-study calls"}
 
 
+def glm_leg(dev, B, synth, torch, q=2, reps=20):
+    """NaivePT with q nuisance covariates (pt_prepare_glm) on the benchmark
+    workload (n=100, 231,719 voxels, 10,000 relabellings): the covariate-adjusted
+    t of the group column; covariates are seeded N(0,1) values per subject."""
+    w = synth.workload(WORKLOAD, device=dev)
+    X, mask, n1 = w["X"], w["mask"], w["n1"]
+    n = X.shape[0]
+    Z = np.random.default_rng(5).standard_normal((n, q))
+    perms = torch.as_tensor(w["perms"]).to(dev)
+    P = perms.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    ctx = B.pt_prepare_glm(X, n1, Z, mask, stream=stream)
+    v = B.pt_num_voxels(ctx)
+    mx = torch.empty(P, dtype=torch.float32, device=dev)
+    am = torch.empty(P, dtype=torch.int32, device=dev)
+    ct = torch.empty(v, dtype=torch.int32, device=dev)
+    opts = B.naive_opts(2)
+    B.pt_autotune_naive(ctx, perms, opts)
+    for _ in range(3):
+        B.pt_maxnull_naive_ex(ctx, perms, opts, mx, am, ct)
+    B.pt_sync(ctx)
+    B.pt_profile_enable(ctx, True)
+    B.pt_profile_read(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        B.pt_maxnull_naive_ex(ctx, perms, opts, mx, am, ct)
+    e1.record(stream)
+    B.pt_sync(ctx)
+    kern_ms, k = B.pt_profile_read(ctx)
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    return {"workload": "%s with %d covariates (N(0,1), seeded): group t adjusted by least "
+                        "squares, %d voxels, P=%d" % (WORKLOAD, q, v, P),
+            "maxnull_ms": ms, "kernel_ms": kern_ms / max(k, 1),
+            "entries_per_s": float(P) * v / (ms * 1e-3),
+            "timing": "device events over %d calls of pt_maxnull_naive_ex (context prepared "
+                      "once)" % reps}
+
+
 def run_ours(args):
     if args.rapid_only:
         import torch
@@ -582,6 +623,8 @@ def run_ours(args):
         line["rapidpt"] = rapid_leg(dev, B, synth, torch, args.rapid_passes, args.rapid_rows)
     if ws == 1 and not args.no_batched:
         line["batched"] = batched_leg(dev, B, synth, torch)
+    if ws == 1 and not args.no_glm:
+        line["glm"] = glm_leg(dev, B, synth, torch)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         Xm = X[:, mask.bool()].cpu().numpy()
         rate, rows, dt, cores = oracle_sample(Xm, n1, perms_np, seconds_target=15.0)
@@ -612,6 +655,8 @@ def main():
                     help="skip the 64-study batched leg")
     ap.add_argument("--no-rapid", action="store_true",
                     help="skip the RapidPT vs NaivePT leg (n=200, 500k voxels, 1e5 relabellings)")
+    ap.add_argument("--no-glm", action="store_true",
+                    help="skip the covariate-adjusted NaivePT leg")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default launch configurations)")
     ap.add_argument("--quick", action="store_true",

@@ -100,6 +100,30 @@ pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* m
                      int32_t n1, void* stream, pt_ctx** out);
 
 /*
+ * pt_prepare_glm -- pt_prepare for the two-group statistic with nuisance
+ * covariates (the general-contrast form of the per-voxel statistic that Alg. 1
+ * takes as input; Sec. 3.2 instantiates it as the two-sample t of Eq. (5)).
+ * For a relabelling with group-1 indicator l the statistic is the least-squares
+ * t of beta in  y = beta l + [1, Z] gamma + e  (intercept always added): the
+ * group column is relabelled, every subject keeps its covariate values. With
+ * q = 0 it is the pooled t of pt_prepare.
+ *   X, n, n_grid, mask, n1, stream, out : as pt_prepare.
+ *   Z : host, float64, n x q row-major (subject s's covariates in row s); NULL if q = 0.
+ *   q : 0 <= q <= 16 and q <= n - 3 (the fit keeps n - q - 2 >= 1 degrees of freedom).
+ * Computes in FP64 an orthonormal basis of [1, Z], each voxel's residual on it
+ * (a voxel whose residual vanishes, e.g. constant, has no statistic), and the
+ * observed statistic (pt_t_obs). Contexts from here run pt_maxnull_naive(_ex)
+ * and pt_autotune_naive on the tensor-core precisions (PT_PREC_FP32, RapidPT
+ * and the batched call return PT_ERR_UNSUPPORTED), pt_fwer_pvalues and pt_t_obs.
+ * A relabelling whose group column lies in the span of [1, Z] makes the next
+ * pt_sync return PT_ERR_INVALID.
+ * Errors: as pt_prepare, and PT_ERR_INVALID for NaN/Inf in Z, [1, Z] without
+ * full column rank, or an observed group column in its span.
+ */
+pt_status pt_prepare_glm(const float* X, int32_t n, int64_t n_grid, const uint8_t* mask,
+                         int32_t n1, const double* Z, int32_t q, void* stream, pt_ctx** out);
+
+/*
  * pt_maxnull_naive -- NaivePT (Alg. 1) with default options.
  *   perms   : device, int32, P x n row-major; each row a permutation of 0..n-1.
  *   P       : relabellings, 1 <= P <= 2^31 - 1.

@@ -69,6 +69,8 @@ def load(path=None):
     sig = {
         "pt_naive_opts_default": (None, [ctypes.POINTER(pt_naive_opts)]),
         "pt_prepare": (ctypes.c_int, [_VP, i32, i64, _VP, i32, _VP, ctypes.POINTER(_VP)]),
+        "pt_prepare_glm": (ctypes.c_int, [_VP, i32, i64, _VP, i32, _VP, i32, _VP,
+                                          ctypes.POINTER(_VP)]),
         "pt_maxnull_naive": (ctypes.c_int, [_VP, _VP, i64, _VP, _VP, _VP]),
         "pt_maxnull_naive_ex": (ctypes.c_int, [_VP, _VP, i64, ctypes.POINTER(pt_naive_opts),
                                                _VP, _VP, _VP]),
@@ -173,6 +175,28 @@ def pt_prepare(X, n1, mask=None, stream=None):
     out = ctypes.c_void_p()
     st = lib.pt_prepare(_ptr(X, True), X.shape[0], X.shape[1], _ptr(mask, True), int(n1),
                         _stream_ptr(stream), ctypes.byref(out))
+    _check(st, None)
+    return Ctx(out)
+
+
+def pt_prepare_glm(X, n1, Z=None, mask=None, stream=None):
+    """pt_prepare with nuisance covariates: Z is an (n, q) array (host, float64)
+    or None; the statistic is the least-squares t of the group column."""
+    import numpy as np
+    lib = load()
+    assert X.dtype == torch.float32 and X.dim() == 2
+    n = X.shape[0]
+    if mask is not None:
+        assert mask.dtype == torch.uint8 and mask.numel() == X.shape[1]
+    if Z is None:
+        Zc, q, zp = None, 0, None
+    else:
+        Zc = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(n, -1))
+        q = Zc.shape[1]
+        zp = ctypes.c_void_p(Zc.ctypes.data) if q > 0 else None
+    out = ctypes.c_void_p()
+    st = lib.pt_prepare_glm(_ptr(X, True), n, X.shape[1], _ptr(mask, True), int(n1), zp, int(q),
+                            _stream_ptr(stream), ctypes.byref(out))
     _check(st, None)
     return Ctx(out)
 

@@ -182,6 +182,48 @@ pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* m
   }
 }
 
+pt_status pt_prepare_glm(const float* X, int32_t n, int64_t n_grid, const uint8_t* mask,
+                         int32_t n1, const double* Z, int32_t q, void* stream, pt_ctx** out) {
+  try {
+    if (!out || !X || q < 0 || q > pt::kGlmMaxQ1 - 1 || (q > 0 && !Z)) {
+      pt::set_thread_error("pt_prepare_glm: need X, out non-NULL, 0 <= q <= 16, Z non-NULL if q > 0");
+      return PT_ERR_INVALID;
+    }
+    if (n < 3 || n > 1024 || n1 < 1 || n1 > n - 1 || n_grid < 1 || n_grid >= (int64_t(1) << 31) ||
+        n - q - 2 < 1) {
+      pt::set_thread_error(
+          "pt_prepare_glm: need 3 <= n <= 1024, 1 <= n1 <= n-1, 1 <= n_grid < 2^31, q <= n - 3");
+      return PT_ERR_INVALID;
+    }
+    pt_ctx* ctx = new (std::nothrow) pt_ctx();
+    if (!ctx) {
+      pt::set_thread_error("pt_prepare_glm: out of host memory");
+      return PT_ERR_NOMEM;
+    }
+    cudaGetDevice(&ctx->device);
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->n = n;
+    ctx->n1 = n1;
+    ctx->n2 = n - n1;
+    ctx->n_pad = (n + 15) / 16 * 16;
+    ctx->n_grid = n_grid;
+    ctx->k = 1.0 / n1 + 1.0 / (n - n1);
+    ctx->c_t = std::sqrt(ctx->k * (n - 2));
+    pt_status st = pt::glm_setup(ctx, Z, q);
+    if (st == PT_OK) st = pt::prepare_impl(ctx, X, mask);
+    if (st != PT_OK) {
+      pt::set_thread_error(ctx->last_error);
+      pt_destroy(ctx);
+      return st;
+    }
+    *out = ctx;
+    return PT_OK;
+  } catch (...) {
+    pt::set_thread_error("pt_prepare_glm: internal error");
+    return PT_ERR_CUDA;
+  }
+}
+
 pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
                               const pt_naive_opts* opts, float* maxnull, int32_t* argmax,
                               uint32_t* counts) {
@@ -304,6 +346,10 @@ pt_status pt_sync(pt_ctx* ctx) {
       set_error(ctx, "a relabelling row is not a permutation of 0..n-1");
       return PT_ERR_INVALID;
     }
+    if (bits & pt::kErrGlmSpan) {
+      set_error(ctx, "a relabelled group column lies in the span of the covariates");
+      return PT_ERR_INVALID;
+    }
     set_error(ctx, "invalid input data (NaN or Inf)");
     return PT_ERR_INVALID;
   }
@@ -375,7 +421,8 @@ void pt_destroy(pt_ctx* ctx) {
                      &ctx->Xraw,    &ctx->vstat,    &ctx->u_obs,     &ctx->Xn32,
                      &ctx->Xnb,     &ctx->labels,   &ctx->rowflag,   &ctx->blockflag,
                      &ctx->maxkey,  &ctx->cnt,      &ctx->scratch,   &ctx->tcdesc,
-                     &ctx->moments};
+                     &ctx->moments, &ctx->glmQ,     &ctx->glm_coef,  &ctx->glm_inv,
+                     &ctx->rowscale};
   for (pt::Buf* b : bufs) b->release();
   delete ctx;
 }

@@ -16,7 +16,11 @@ enum : uint32_t {
   kErrBadPerm = 1u,   // a relabelling row is not a permutation of 0..n-1
   kErrTimeout = 2u,   // a bounded spin-wait expired
   kErrBadData = 4u,   // NaN / Inf in the input data
+  kErrGlmSpan = 8u,   // a relabelled group column lies in the span of the covariates
 };
+
+// Covariate-adjusted statistic: at most this many columns in [1, Z].
+constexpr int kGlmMaxQ1 = 17;
 
 // Caching device allocator: blocks are keyed by (device, rounded size) and
 // recycled, so steady-state calls never reach cudaMalloc.
@@ -68,6 +72,14 @@ struct pt_ctx {
   pt::Buf moments;      // pt_prepare's per-voxel FP64 moments (read by kernels it enqueues)
   pt::Buf tcdesc;       // device copy of the tensor-core launch descriptor
 
+  // Covariate-adjusted statistic (pt_prepare_glm); glm_q1 = 0 for the plain t.
+  int32_t glm_q1 = 0;   // columns of [1, Z]
+  double glm_a_obs = 0.0, glm_df = 0.0;
+  pt::Buf glmQ;         // double[n][q1]: orthonormal basis of [1, Z]
+  pt::Buf glm_coef;     // double[v][q1]: Q^T x per masked voxel
+  pt::Buf glm_inv;      // double[v]: 1 / ||x - Q Q^T x||
+  pt::Buf rowscale;     // float[P_pad]: sqrt(a_obs / a(l)) per relabelling
+
   // Profiling of the dominant kernel (events on `stream`).
   bool profile = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_pool;
@@ -86,6 +98,14 @@ void set_thread_error(const std::string& msg);
 
 // ---- prepare (pt_prepare.cu) ----
 pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask);
+
+// ---- covariate-adjusted statistic (pt_glm.cu) ----
+pt_status glm_setup(pt_ctx* ctx, const double* Z, int q);      // host basis, before prepare
+pt_status glm_moments(pt_ctx* ctx, uint8_t* valid, float* u_obs_m);
+pt_status glm_build_xnb(pt_ctx* ctx);
+pt_status glm_rowscale(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t P_pad);
+pt_status glm_finalize(pt_ctx* ctx, const int32_t* perms, int64_t P, int two_sided,
+                       float* maxnull, int32_t* argmax);
 // Operand layouts built from Xraw on first use (FP32 rows / BF16 pieces).
 pt_status ensure_xn32(pt_ctx* ctx);
 pt_status ensure_xnb(pt_ctx* ctx);

@@ -276,7 +276,7 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
     const int32_t* row = perms + i * n;
     for (int q = lane; q < n1; q += 32) {
       const int32_t e = row[q];
-      atomicOr(&g1[e >> 5], 1u << (e & 31));
+      if (e >= 0 && e < n) atomicOr(&g1[e >> 5], 1u << (e & 31));  // others: reported by labels
     }
     __syncwarp();
     const float* x = Xraw + int64_t(valid_map[c]) * n_pad;  // Xraw is in masked order
@@ -404,6 +404,10 @@ pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout,
       ctx->rowflag.as<uint8_t>(), ctx->blockflag.as<uint8_t>(),
       ctx->cnt.as<uint32_t>() + ctx->v_valid, ctx->status.as<uint32_t>());
   PT_LAUNCH_CHECK(ctx);
+  if (ctx->glm_q1 && layout == 1) {
+    pt_status s = glm_rowscale(ctx, perms, P, P_pad);
+    if (s != PT_OK) return s;
+  }
   *P_pad_out = P_pad;
   return PT_OK;
 }
@@ -434,6 +438,10 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
                      float* maxnull, int32_t* argmax, uint32_t* counts) {
   cudaStream_t st = ctx->stream;
   const bool tc = o.precision != PT_PREC_FP32;
+  if (ctx->glm_q1 && !tc) {
+    set_error(ctx, "the covariate-adjusted statistic runs on the tensor-core path (BF16X2/X3)");
+    return PT_ERR_UNSUPPORTED;
+  }
   pt_status s = tc ? tc_supported(ctx) : PT_OK;
   if (s != PT_OK) return s;
   if (!ctx->maxkey.ensure(sizeof(unsigned long long) * P) ||
@@ -462,10 +470,15 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
     }
     if (s != PT_OK) return s;
   }
-  finalize_max_kernel<<<grid_1d((P + 7) / 8, 1), 256, 0, st>>>(
-      ctx->maxkey.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(),
-      ctx->Xraw.as<float>(), ctx->n, ctx->n1, ctx->n_pad, perms, o.two_sided, maxnull, argmax);
-  PT_LAUNCH_CHECK(ctx);
+  if (ctx->glm_q1) {
+    s = glm_finalize(ctx, perms, P, o.two_sided, maxnull, argmax);
+    if (s != PT_OK) return s;
+  } else {
+    finalize_max_kernel<<<grid_1d((P + 7) / 8, 1), 256, 0, st>>>(
+        ctx->maxkey.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(),
+        ctx->Xraw.as<float>(), ctx->n, ctx->n1, ctx->n_pad, perms, o.two_sided, maxnull, argmax);
+    PT_LAUNCH_CHECK(ctx);
+  }
   if (counts && ctx->v_valid > 0) {
     scatter_counts_kernel<<<grid_1d(ctx->v_valid, 256), 256, 0, st>>>(
         ctx->cnt.as<uint32_t>(), ctx->v_valid, ctx->valid_map.as<int32_t>(), counts,
@@ -601,6 +614,11 @@ pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* p
   }
   pt_status s = tc_supported(lead);
   if (s != PT_OK) return s;
+  for (int i = 0; i < n; ++i)
+    if (ctxs[i]->glm_q1) {
+      set_error(lead, "pt_maxnull_naive_batched: covariate-adjusted contexts run one at a time");
+      return PT_ERR_UNSUPPORTED;
+    }
 
   const std::vector<const void*> key = batch_key(ctxs, n, perms, P, o, maxnull, argmax, counts);
   std::lock_guard<std::mutex> lk(g_batch_mu);

@@ -87,6 +87,8 @@ struct TcStudy {  // CUtensorMap members carry their own alignment
   unsigned long long* maxkey;
   uint32_t* cnt;
   float* uout;  // row writes (single-study launches only)
+  const float* rowscale;  // covariate-adjusted statistic: per-row factor of the
+                          // exceedance test (u * f >= u_obs); NULL for the plain t
 };
 
 struct TcArgs {
@@ -95,6 +97,7 @@ struct TcArgs {
   int n_pad_max;
   int64_t n_items;
   int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
+  int scaled;                 // the studies carry per-row factors (covariate-adjusted t)
   float k_f, ct_f;
   uint32_t* status;
 };
@@ -170,10 +173,10 @@ __device__ __forceinline__ void tc_ld_cols(uint32_t taddr, uint32_t (&r)[CW]) {
 // with the observed group-1 set. Padded entries take the value -inf (never
 // counted, never a maximum); an observed-set row still competes for the
 // maximum but is not compared (its count is added exactly elsewhere).
-template <int CW, bool TWO, bool RAGGED>
+template <int CW, bool TWO, bool RAGGED, bool SCALE = false>
 __device__ __forceinline__ float cols_reduce(const uint32_t (&r)[CW], const float* su_cols,
                                              int64_t gcol0, int64_t v, bool row_ok, bool cnt_ok,
-                                             uint32_t (&c8)[CW / 4]) {
+                                             uint32_t (&c8)[CW / 4], float fr = 1.0f) {
   float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
   const float4* s4 = reinterpret_cast<const float4*>(su_cols);
 #pragma unroll
@@ -190,15 +193,17 @@ __device__ __forceinline__ float cols_reduce(const uint32_t (&r)[CW], const floa
       if (e == 1) m1 = fmaxf(m1, s);
       if (e == 2) m2 = fmaxf(m2, s);
       if (e == 3) m3 = fmaxf(m3, s);
-      if (s >= ov[e] && (!RAGGED || cnt_ok)) c8[g] += 1u << (8 * e);
+      if ((SCALE ? s * fr : s) >= ov[e] && (!RAGGED || cnt_ok)) c8[g] += 1u << (8 * e);
     }
   }
   return fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
 }
 
 // WRITE = false: reduce only (the NaivePT path); true: rows of u or t are
-// written (training rows of Alg. 2), optionally also reduced.
-template <int NT, bool TWO, int PIECES, bool WRITE>
+// written (training rows of Alg. 2), optionally also reduced. SCALED: the
+// covariate-adjusted statistic (per-row factor in the exceedance test; the
+// launch's studies carry rowscale).
+template <int NT, bool TWO, int PIECES, bool WRITE, bool SCALED = false>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_contract_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -453,6 +458,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * ACC + colbase;
         const bool row_ok = row < Pn;
         const bool cnt_ok = row_ok && !(ragged && do_reduce && rowflag[row]);
+        const float fr = SCALED && row_ok ? st.rowscale[row] : 1.0f;
         // Running row maximum over the chunks and, for a maximum that can beat
         // the row's current global key, its first column (found while the
         // chunk is still in registers).
@@ -501,10 +507,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (do_reduce) {
             uint32_t(&cc)[CHK / 4] = *reinterpret_cast<uint32_t(*)[CHK / 4]>(&c8[c * (CHK / 4)]);
             const float cm =
-                ragged ? cols_reduce<CHK, TWO, true>(r, su + colbase + c * CHK, g0, V, row_ok,
-                                                     cnt_ok, cc)
-                       : cols_reduce<CHK, TWO, false>(r, su + colbase + c * CHK, g0, V, true,
-                                                      true, cc);
+                ragged ? cols_reduce<CHK, TWO, true, SCALED>(r, su + colbase + c * CHK, g0, V,
+                                                             row_ok, cnt_ok, cc, fr)
+                       : cols_reduce<CHK, TWO, false, SCALED>(r, su + colbase + c * CHK, g0, V,
+                                                              true, true, cc, fr);
             const bool cand = row_ok && cm > best && cm >= gval && cm > -INFINITY;
             if (cm > best) {
               best = cm;
@@ -560,6 +566,8 @@ template <int NT, bool TWO>
 pt_status launch_nt(pt_ctx* ctx, const TcArgs& a, int pieces, int grid, int smem) {
   auto kern = a.write_mode ? (pieces == 2 ? tc_contract_kernel<NT, TWO, 2, true>
                                           : tc_contract_kernel<NT, TWO, 3, true>)
+              : a.scaled   ? (pieces == 2 ? tc_contract_kernel<NT, TWO, 2, false, true>
+                                          : tc_contract_kernel<NT, TWO, 3, false, true>)
                            : (pieces == 2 ? tc_contract_kernel<NT, TWO, 2, false>
                                           : tc_contract_kernel<NT, TWO, 3, false>);
   PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -620,6 +628,7 @@ bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int kps, int64_t t
   st->maxkey = maxkey;
   st->cnt = cnt;
   st->uout = uout;
+  st->rowscale = c->glm_q1 ? c->rowscale.as<float>() : nullptr;
   const int64_t P_pad = st->nblocks * 128;
   // Label box: kps k-steps of one 128-row block (8 view rows per k-step); a
   // box that runs past the last block reads zero fill.
@@ -632,7 +641,11 @@ bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int kps, int64_t t
 // count. descs: device copy of the descriptors (filled by the caller).
 pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_items, int NT,
                          int stages, int kps, int pieces, int n_pad_max, int do_reduce,
-                         int write_mode, int two_sided, float kf, float ctf) {
+                         int write_mode, int two_sided, float kf, float ctf, int scaled = 0) {
+  if (scaled && (write_mode || !do_reduce)) {
+    set_error(ctx, "covariate-adjusted statistic: reduce-only launches");
+    return PT_ERR_UNSUPPORTED;
+  }
   const int fit = max_stages_fit(NT, n_pad_max, pieces, kps);
   if (!fit || stages < 2 || stages > fit) {
     set_error(ctx, "tensor-core path: n too large for the resident data tile");
@@ -649,6 +662,7 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   a.write_mode = write_mode;
   a.k_f = kf;
   a.ct_f = ctf;
+  a.scaled = scaled;
   a.status = ctx->status.as<uint32_t>();
   const int sms = num_sms(ctx->device);
   const int grid = int(n_items < sms ? n_items : sms);
@@ -685,7 +699,7 @@ pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int 
   const int64_t items = ((st.v + NT - 1) / NT) * st.n_chunks;
   return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, cfg.stages,
                         cfg.ksteps_per_stage, pieces, ctx->n_pad, do_reduce, write_mode,
-                        two_sided, float(ctx->k), float(ctx->c_t));
+                        two_sided, float(ctx->k), float(ctx->c_t), ctx->glm_q1 ? 1 : 0);
 }
 
 pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,

@@ -480,6 +480,10 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
         ctx->t_obs64.as<double>(), u_obs_m, valid, ctx->Xraw.as<float>(),
         ctx->status.as<uint32_t>());
     PT_LAUNCH_CHECK(ctx);
+    if (ctx->glm_q1) {  // covariate-adjusted statistic: residual fit, validity, u/t_obs
+      pt_status s = glm_moments(ctx, valid, u_obs_m);
+      if (s != PT_OK) return s;
+    }
   }
 
   // 3. compact list of voxels with a defined t (sized by v; the count is read
@@ -532,6 +536,11 @@ pt_status ensure_xnb(pt_ctx* ctx) {
   if (ctx->have_xnb) return PT_OK;
   const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
   if (!ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) return nomem(ctx, "Xnb");
+  if (ctx->glm_q1) {
+    pt_status s = glm_build_xnb(ctx);
+    if (s == PT_OK) ctx->have_xnb = true;
+    return s;
+  }
   const int xnb_threads = std::min(256, (ctx->n_pad + 31) / 32 * 32);
   build_xnb_kernel<<<unsigned(ctx->v_pad / 8), xnb_threads, 0, ctx->stream>>>(
       ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,

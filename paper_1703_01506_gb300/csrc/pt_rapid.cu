@@ -1290,6 +1290,10 @@ struct RapidPlan {
 
 pt_status check_rapid_args(pt_ctx* ctx, int32_t rank, double sample_rate, const pt_rapid_opts& o,
                            RapidPlan& pl) {
+  if (ctx->glm_q1) {
+    set_error(ctx, "RapidPT runs the plain two-sample t (context prepared with covariates)");
+    return PT_ERR_UNSUPPORTED;
+  }
   if (rank < 1 || rank > kMaxRank || rank > ctx->n) {
     set_error(ctx, "RapidPT: need 1 <= rank <= min(n, 128)");
     return PT_ERR_INVALID;
