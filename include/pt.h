@@ -366,6 +366,28 @@ pt_status pt_profile_read(pt_ctx* ctx, double* total_ms, int64_t* launches);
 /* Number of kernels this library has launched in this process (all contexts). */
 int64_t pt_kernel_launch_count(void);
 
+/* ------------------------------------------------------------------------- */
+/* Failure handling checks (no counterpart in the paper). Failures are made on */
+/* the host or by a wait that runs out of time; nothing here faults the GPU.  */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * pt_debug_fail_allocations -- after `after` more device allocations by this
+ * library (its caching allocator's requests, cache hits included) every later
+ * one fails, so the calls that need memory return PT_ERR_NOMEM; after < 0
+ * switches the injection off. Process-wide; for tests of the error paths.
+ */
+void pt_debug_fail_allocations(int64_t after);
+
+/*
+ * pt_selftest_bounded_wait -- runs, on ctx's stream, the library's bounded
+ * device-side wait on an mbarrier phase that nothing completes, with a limit of
+ * limit_ms (1 <= limit_ms <= 2000): the kernel gives up, records the timeout in
+ * ctx's status word and returns. The next pt_sync returns PT_ERR_TIMEOUT and
+ * clears it; the context stays usable. Asynchronous.
+ */
+pt_status pt_selftest_bounded_wait(pt_ctx* ctx, int32_t limit_ms);
+
 /*
  * pt_maxnull_naive_noalloc -- NaivePT (FP32 CUDA-core contraction) for callers
  * that cannot allocate device memory. The paper has no counterpart: this entry

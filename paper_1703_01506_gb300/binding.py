@@ -112,6 +112,8 @@ def load(path=None):
         "pt_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
         "pt_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
         "pt_tune_clear": (None, []),
+        "pt_debug_fail_allocations": (None, [i64]),
+        "pt_selftest_bounded_wait": (ctypes.c_int, [_VP, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -286,6 +288,15 @@ def pt_tune_load(path):
 
 def pt_tune_clear():
     load().pt_tune_clear()
+
+
+def pt_debug_fail_allocations(after):
+    """After ``after`` more device allocations every later one fails (< 0: off)."""
+    load().pt_debug_fail_allocations(int(after))
+
+
+def pt_selftest_bounded_wait(ctx, limit_ms):
+    _check(load().pt_selftest_bounded_wait(ctx.handle, int(limit_ms)), ctx.handle)
 
 
 def pt_sync(ctx):

@@ -31,7 +31,17 @@ size_t round_size(size_t b) {
 }
 }  // namespace
 
+namespace {
+// Allocation-failure injection (pt_debug_fail_allocations): allocations left
+// before every later one fails; negative = off.
+std::atomic<int64_t> g_fail_after{-1};
+}  // namespace
+
 void* dev_alloc(size_t bytes) {
+  for (int64_t left = g_fail_after.load(); left >= 0;) {
+    if (left == 0) return nullptr;
+    if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   const size_t sz = round_size(bytes);
@@ -406,6 +416,8 @@ pt_status pt_profile_read(pt_ctx* ctx, double* total_ms, int64_t* launches) {
 }
 
 int64_t pt_kernel_launch_count(void) { return pt::g_launches.load(); }
+
+void pt_debug_fail_allocations(int64_t after) { pt::g_fail_after.store(after < 0 ? -1 : after); }
 
 void pt_destroy(pt_ctx* ctx) {
   if (!ctx) return;
