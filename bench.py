@@ -41,8 +41,8 @@ import numpy as np  # noqa: E402
 
 METRIC = "T entries/s (perm x voxel t) & max-null wall time, RapidPT vs NaivePT, 1 GB300"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one tuned launch of the
-# fused kernel on brain_n100_v232k (160.23 MB read + 4.05 MB written).
-TRAFFIC_BYTES = 164.28e6
+# fused kernel on brain_n100_v232k (160.21 MB read + 4.67 MB written).
+TRAFFIC_BYTES = 164.89e6
 WORKLOAD = "brain_n100_v232k"
 PREC = {"fp32": 0, "bf16x2": 1, "bf16x3": 2}
 
