@@ -50,7 +50,7 @@ typedef enum {
   PT_ERR_NOMEM = 2,       /* device allocation failed */
   PT_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
   PT_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired */
-  PT_ERR_UNSUPPORTED = 5  /* valid request this build cannot run (e.g. no sm_103 device) */
+  PT_ERR_UNSUPPORTED = 5  /* valid request the library cannot serve here (e.g. no sm_103 device) */
 } pt_status;
 
 /* Arithmetic of the contraction S1 = L . Xn (labels exact in every mode). */
