@@ -155,6 +155,7 @@ void pt_naive_opts_default(pt_naive_opts* o) {
 
 pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* mask, int32_t n1,
                      void* stream, pt_ctx** out) {
+  pt::NvtxRange nvtx_range("pt_prepare");
   try {
     if (!out || !X) {
       pt::set_thread_error("pt_prepare: X and out must be non-NULL");
@@ -194,6 +195,7 @@ pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* m
 
 pt_status pt_prepare_glm(const float* X, int32_t n, int64_t n_grid, const uint8_t* mask,
                          int32_t n1, const double* Z, int32_t q, void* stream, pt_ctx** out) {
+  pt::NvtxRange nvtx_range("pt_prepare_glm");
   try {
     if (!out || !X || q < 0 || q > pt::kGlmMaxQ1 - 1 || (q > 0 && !Z)) {
       pt::set_thread_error("pt_prepare_glm: need X, out non-NULL, 0 <= q <= 16, Z non-NULL if q > 0");
@@ -237,6 +239,7 @@ pt_status pt_prepare_glm(const float* X, int32_t n, int64_t n_grid, const uint8_
 pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
                               const pt_naive_opts* opts, float* maxnull, int32_t* argmax,
                               uint32_t* counts) {
+  pt::NvtxRange nvtx_range("pt_maxnull_naive");
   if (!ctx) {
     pt::set_thread_error("pt_maxnull_naive: ctx is NULL");
     return PT_ERR_INVALID;
@@ -269,6 +272,7 @@ pt_status pt_maxnull_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
                                    const int32_t* const* perms, const int64_t* P,
                                    const pt_naive_opts* opts, float* const* maxnull,
                                    int32_t* const* argmax, uint32_t* const* counts) {
+  pt::NvtxRange nvtx_range("pt_maxnull_naive_batched");
   if (!ctxs || n_studies < 1 || n_studies > 4096 || !perms || !P || !maxnull || !argmax) {
     pt::set_thread_error(
         "pt_maxnull_naive_batched: need 1 <= n_studies <= 4096 and non-NULL arrays");
@@ -317,6 +321,7 @@ pt_status pt_maxnull_naive(pt_ctx* ctx, const int32_t* perms, int64_t P, float* 
 
 pt_status pt_fwer_pvalues(pt_ctx* ctx, const float* maxnull, int64_t P, int32_t two_sided,
                           float* p_out) {
+  pt::NvtxRange nvtx_range("pt_fwer_pvalues");
   if (!ctx) {
     pt::set_thread_error("pt_fwer_pvalues: ctx is NULL");
     return PT_ERR_INVALID;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -86,6 +87,15 @@ struct pt_ctx {
 };
 
 namespace pt {
+
+// NVTX range over a host-side phase (prepare, max-null, training, recovery,
+// tuning): shows in profilers' timelines, free when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 void set_error(pt_ctx* ctx, const std::string& msg);
 void count_launch();

@@ -1777,6 +1777,7 @@ pt_status pt_rapid_train(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int
                          double sample_rate, const pt_rapid_opts* opts, float* U_out,
                          float* train_max, uint32_t* counts, float* w_hist,
                          pt_rapid_info* info) {
+  pt::NvtxRange nvtx_range("pt_rapid_train");
   if (!ctx || !perms) {
     pt::set_error(ctx, "pt_rapid_train: NULL argument");
     return PT_ERR_INVALID;
@@ -1797,6 +1798,7 @@ pt_status pt_rapid_train(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int
 pt_status pt_rapid_recover(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t first_row,
                            const float* U, int32_t rank, double sample_rate, double sigma,
                            double mu, const pt_rapid_opts* opts, float* maxnull, float* W_out) {
+  pt::NvtxRange nvtx_range("pt_rapid_recover");
   if (!ctx || !perms || !U || !maxnull) {
     pt::set_error(ctx, "pt_rapid_recover: NULL argument");
     return PT_ERR_INVALID;
@@ -1817,6 +1819,7 @@ pt_status pt_rapid_recover(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t
 pt_status pt_maxnull_rapid(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t rank,
                            double sample_rate, int32_t n_train, const pt_rapid_opts* opts,
                            float* maxnull, uint32_t* counts, pt_rapid_info* info) {
+  pt::NvtxRange nvtx_range("pt_maxnull_rapid");
   if (!ctx || !perms || !maxnull) {
     pt::set_error(ctx, "pt_maxnull_rapid: NULL argument");
     return PT_ERR_INVALID;

@@ -110,6 +110,7 @@ extern "C" {
 
 pt_status pt_autotune_naive(pt_ctx* ctx, const int32_t* perms, int64_t P,
                             const pt_naive_opts* opts, pt_tc_config* chosen, double* chosen_ms) {
+  pt::NvtxRange nvtx_range("pt_autotune_naive");
   if (!ctx) {
     pt::set_thread_error("pt_autotune_naive: ctx is NULL");
     return PT_ERR_INVALID;
@@ -138,6 +139,7 @@ pt_status pt_autotune_naive(pt_ctx* ctx, const int32_t* perms, int64_t P,
 pt_status pt_autotune_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
                                     const int32_t* const* perms, const int64_t* P,
                                     const pt_naive_opts* opts) {
+  pt::NvtxRange nvtx_range("pt_autotune_naive_batched");
   if (!ctxs || n_studies < 1 || n_studies > 4096 || !perms || !P) {
     pt::set_thread_error("pt_autotune_naive_batched: need 1 <= n_studies <= 4096 and arrays");
     return PT_ERR_INVALID;
