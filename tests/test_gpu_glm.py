@@ -167,3 +167,66 @@ def test_glm_errors(cuda_lib):
         B.pt_maxnull_naive_batched([ctx], [pd], B.naive_opts(2), [mx], [am])
     assert e.value.status == B.PT_ERR_UNSUPPORTED
     ctx.close()
+
+
+def test_glm_masked_field_from_pinned_host_memory(cuda_lib):
+    """A masked brain-shaped field with covariates, X and the mask read from
+    page-locked host memory: outputs equal the device-memory run and match the
+    oracle on the mask voxels (masked-order argmax and counts)."""
+    B = cuda_lib
+    n, n1, P, q = 28, 14, 300, 2
+    X, mask = synth.brain_field(n, n1, grid=(20, 24, 20), center=(10, 12, 10),
+                                semi_axes=(8, 10, 8), fwhm=4.0, effect=0.5, effect_radius=3.0,
+                                seed=8, device="cpu")
+    Z = np.random.default_rng(8).standard_normal((n, q))
+    perms = synth.perms_pcg32(n, P, seed=8)
+    pd = torch.as_tensor(perms).cuda()
+    outs = []
+    for host in (False, True):
+        Xa = X.contiguous().pin_memory() if host else X.cuda()
+        ma = mask.to(torch.uint8).contiguous()
+        ma = ma.pin_memory() if host else ma.cuda()
+        ctx = B.pt_prepare_glm(Xa, n1, Z, ma)
+        mx, am, ct = B.maxnull_naive(ctx, pd, precision=2)
+        t_obs = torch.empty(B.pt_num_voxels(ctx), dtype=torch.float32, device="cuda")
+        B.pt_t_obs(ctx, t_obs)
+        B.pt_sync(ctx)
+        outs.append([t.cpu() for t in (mx, am, ct, t_obs)])
+        ctx.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    Xm = X[:, mask.bool()].numpy()
+    ref = glm.glm_naive(Xm, Z, n1, perms)
+    mx, am, ct, t_obs = outs[1]
+    check(ref, (mx.numpy().astype(np.float64), am.numpy().astype(np.int64),
+                ct.numpy().astype(np.int64), t_obs.numpy().astype(np.float64)),
+          Xm, Z, 2, False, "masked field")
+
+
+@pytest.mark.parametrize("two_sided", [False, True])
+def test_glm_fwer_pvalues_match_oracle(cuda_lib, two_sided):
+    """FWER-corrected p-values (Sec. 2) from the covariate-adjusted max-null and
+    t_obs (pt_fwer_pvalues) against the oracle's definition applied to the
+    oracle's own max-null and t_obs."""
+    import oracle
+    B = cuda_lib
+    n, n1, v, P, q = 36, 18, 1200, 400, 3
+    rng = np.random.default_rng(21)
+    X = synth.two_group_gaussian(n1, n - n1, v, frac=0.05, effect=1.5, seed=21)
+    Z = rng.standard_normal((n, q))
+    perms = synth.perms_pcg32(n, P, seed=21)
+    ctx = B.pt_prepare_glm(torch.as_tensor(X).cuda(), n1, Z)
+    pd = torch.as_tensor(perms).cuda()
+    mx, am, ct = B.maxnull_naive(ctx, pd, precision=2, two_sided=two_sided)
+    p = torch.empty(v, dtype=torch.float32, device="cuda")
+    B.pt_fwer_pvalues(ctx, mx, p, two_sided=two_sided)
+    B.pt_sync(ctx)
+    ref = glm.glm_naive(X, Z, n1, perms, two_sided=two_sided)
+    want = oracle.fwer_pvalues(ref.maxnull, ref.t_obs, two_sided=two_sided)
+    got = p.cpu().numpy().astype(np.float64)
+    # both sides compare float32 values: a p differs only where an FP64 maximum or
+    # statistic rounds to a different float32 on the two sides, or at a near-tie row
+    diff = np.abs(got - np.asarray(want, dtype=np.float32).astype(np.float64))
+    assert np.mean(diff > 0) <= 0.01, np.flatnonzero(diff > 0)[:10]
+    assert np.all(diff <= 3.0 / (P + 1)), diff.max()
+    ctx.close()

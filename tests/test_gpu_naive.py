@@ -233,8 +233,11 @@ def test_prepare_from_pinned_host_memory(cuda_lib):
 
 @pytest.mark.parametrize("two_sided", [False, True])
 def test_fwer_pvalues_match_oracle(cuda_lib, two_sided):
-    """Corrected p-values from the GPU max-null equal the oracle's definition
-    applied to the same float32 max-null and observed statistics."""
+    """Corrected p-values (Sec. 2) from the GPU max-null and observed statistics
+    against the oracle's definition applied to the oracle's own max-null and
+    observed statistics. Both sides compare float32 values; a voxel's p can
+    differ only where an FP64 maximum or statistic rounds to a different float32
+    on the two sides, or at a near-tie row whose winner differs."""
     B = cuda_lib
     n, n1, v, P = 30, 15, 3000, 5000
     X = synth.two_group_gaussian(n1, n - n1, v, frac=0.02, effect=1.5, seed=4)
@@ -242,14 +245,16 @@ def test_fwer_pvalues_match_oracle(cuda_lib, two_sided):
     ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1)
     pd = torch.as_tensor(perms).cuda()
     mx, _, _ = B.maxnull_naive(ctx, pd, precision=2, two_sided=two_sided)
-    t = torch.empty(v, dtype=torch.float32, device="cuda")
-    B.pt_t_obs(ctx, t)
     p = torch.empty(v, dtype=torch.float32, device="cuda")
     B.pt_fwer_pvalues(ctx, mx, p, two_sided)
     B.pt_sync(ctx)
-    ref = oracle.fwer_pvalues(mx.cpu().numpy(), t.cpu().numpy(), two_sided)
-    np.testing.assert_array_equal(p.cpu().numpy(), ref.astype(np.float32))
-    assert np.nanmin(p.cpu().numpy()) >= 1.0 / (P + 1) - 1e-9
+    ref = oracle.naive(X, n1, perms, two_sided=two_sided, tie_rel=tie_rel(2, n))
+    want = oracle.fwer_pvalues(ref.maxnull, ref.t_obs, two_sided).astype(np.float32)
+    got = p.cpu().numpy()
+    diff = np.abs(got.astype(np.float64) - want.astype(np.float64))
+    assert np.mean(diff > 0) <= 0.005, np.flatnonzero(diff > 0)[:10]
+    assert np.all(diff <= 3.0 / (P + 1)), diff.max()
+    assert np.nanmin(got) >= 1.0 / (P + 1) - 1e-9
     ctx.close()
 
 
