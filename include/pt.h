@@ -198,6 +198,8 @@ typedef struct {
   int64_t train_steps;  /* subspace-tracking steps taken (train_passes * n_train) */
 } pt_rapid_info;
 
+/* Fills *o with the defaults above (one training pass, QR every 100 steps,
+ * 30 ADMM iterations at rho = 2, step 1, shift_mode 1, seed 1, BF16X3). */
 void pt_rapid_opts_default(pt_rapid_opts* o);
 
 /*
@@ -345,7 +347,8 @@ void pt_tune_clear(void);
 /* grid_index: device int64[v]: grid column of each masked-order voxel. */
 pt_status pt_voxel_grid_index(pt_ctx* ctx, int64_t* grid_index);
 
-/* v (mask voxels), number of voxels with a defined t, n, n1; -1 if ctx NULL. */
+/* Number of mask voxels (v, the length of counts and of the masked-order maps),
+ * and of those with a defined statistic; -1 if ctx is NULL. */
 int64_t pt_num_voxels(const pt_ctx* ctx);
 int64_t pt_num_valid_voxels(const pt_ctx* ctx);
 
