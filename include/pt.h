@@ -383,6 +383,15 @@ int64_t pt_kernel_launch_count(void);
 void pt_debug_fail_allocations(int64_t after);
 
 /*
+ * pt_debug_device_reset -- cudaDeviceReset() on the calling thread's current
+ * device, through the library's own CUDA runtime: every allocation and module
+ * of this process on that device is released and the primary context starts
+ * afresh at its next use. Only for tests that check a call still works after
+ * such a reset; no pt_ctx may be alive. Returns PT_ERR_CUDA on failure.
+ */
+pt_status pt_debug_device_reset(void);
+
+/*
  * pt_selftest_bounded_wait -- runs, on ctx's stream, the library's bounded
  * device-side wait on an mbarrier phase that nothing completes, with a limit of
  * limit_ms (1 <= limit_ms <= 2000): the kernel gives up, records the timeout in
@@ -395,23 +404,26 @@ pt_status pt_selftest_bounded_wait(pt_ctx* ctx, int32_t limit_ms);
  * pt_maxnull_naive_noalloc -- NaivePT (FP32 CUDA-core contraction) for callers
  * that cannot allocate device memory. The paper has no counterpart: this entry
  * point exists for callers that must not call cudaMalloc (code running inside
- * another runtime's memory pool or a host callback, or under a fixed memory
- * budget after start-up). It allocates nothing: all intermediate buffers live
- * in one static device array of 64 MiB that every GPU loading this library
- * holds until the process exits.
+ * another runtime's memory pool, or under a fixed memory budget after
+ * start-up). It allocates nothing: all intermediate buffers live in one static
+ * device array of 64 MiB that every GPU loading this library holds until the
+ * process exits.
  *   X       : device, float32, n x v row-major (every column is a voxel; no mask).
  *   n, n1   : as pt_prepare (3 <= n <= 1024, 1 <= n1 <= n-1); v >= 1.
  *   perms, P, maxnull, argmax, counts : as pt_maxnull_naive (argmax is the
- *             column of X; counts may be NULL).
+ *             column of X; counts may be NULL). perms holds P x n entries,
+ *             maxnull and argmax P each, counts v.
  *   two_sided: 0 statistic t, 1 statistic |t|.
  *   stream  : cudaStream_t to run on (NULL = legacy default stream).
- * Synchronous: returns after the stream has finished the work, with
- * PT_ERR_INVALID for a bad argument, NaN/Inf in X, a row that is not a
- * permutation, or a problem whose buffers exceed the 64 MiB array (the message
- * gives the bytes needed). The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make it
- * before any stream capture. Calls share the array: calls that overlap on the
- * GPU race and must be serialised by the caller.
+ * Synchronous: it reads two status words back to the host and waits on the
+ * stream during the work and at its end, so it cannot be recorded by stream
+ * capture. Returns PT_ERR_INVALID for a bad argument, NaN/Inf in X, a row that
+ * is not a permutation, or a problem whose buffers exceed the 64 MiB array
+ * (the message gives the bytes needed). Each call looks up the array's device
+ * address (cudaGetSymbolAddress) in the context current at the call, so it is
+ * valid in any context on the device, including the primary context after
+ * cudaDeviceReset. Calls share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller.
  */
 pt_status pt_maxnull_naive_noalloc(const float* X, int32_t n, int64_t v, int32_t n1,
                                    const int32_t* perms, int64_t P, int32_t two_sided,

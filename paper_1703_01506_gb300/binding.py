@@ -113,6 +113,7 @@ def load(path=None):
         "pt_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
         "pt_tune_clear": (None, []),
         "pt_debug_fail_allocations": (None, [i64]),
+        "pt_debug_device_reset": (ctypes.c_int, []),
         "pt_selftest_bounded_wait": (ctypes.c_int, [_VP, i32]),
     }
     for name, (res, args) in sig.items():
@@ -380,13 +381,33 @@ def pt_kernel_launch_count():
 def pt_maxnull_naive_noalloc(X, n1, perms, maxnull, argmax, counts=None, two_sided=False,
                              stream=None):
     """NaivePT without any device allocation (see include/pt.h). X: (n, v)
-    float32 CUDA tensor, every column a voxel. Synchronous."""
+    float32 CUDA tensor, every column a voxel; perms (P, n) int32; maxnull
+    (>= P) float32, argmax (>= P) int32, counts (>= v) int32/uint32 or None.
+    Shapes are checked here, before the library is called: the kernels read
+    perms row by row and write P maxima and v counts. Synchronous."""
+    if X.dtype != torch.float32 or X.dim() != 2:
+        raise ValueError("X must be a 2-D float32 tensor (n x v)")
+    n, v = X.shape
+    if perms.dtype != torch.int32 or perms.dim() != 2 or perms.shape[1] != n:
+        raise ValueError("perms must be a 2-D int32 tensor with X.shape[0] = %d columns" % n)
+    P = perms.shape[0]
+    if maxnull.dtype != torch.float32 or maxnull.numel() < P:
+        raise ValueError("maxnull must be float32 with at least P = %d elements" % P)
+    if argmax.dtype != torch.int32 or argmax.numel() < P:
+        raise ValueError("argmax must be int32 with at least P = %d elements" % P)
+    if counts is not None and (counts.dtype not in (torch.int32, torch.uint32)
+                               or counts.numel() < v):
+        raise ValueError("counts must be int32/uint32 with at least v = %d elements" % v)
     lib = load()
-    assert X.dtype == torch.float32 and X.dim() == 2 and perms.dtype == torch.int32
-    st = lib.pt_maxnull_naive_noalloc(_ptr(X), X.shape[0], X.shape[1], int(n1), _ptr(perms),
-                                      perms.shape[0], int(bool(two_sided)), _ptr(maxnull),
-                                      _ptr(argmax), _ptr(counts), _stream_ptr(stream))
+    st = lib.pt_maxnull_naive_noalloc(_ptr(X), n, v, int(n1), _ptr(perms), P,
+                                      int(bool(two_sided)), _ptr(maxnull), _ptr(argmax),
+                                      _ptr(counts), _stream_ptr(stream))
     _check(st, None)
+
+
+def pt_debug_device_reset():
+    """cudaDeviceReset on the current device through the library's runtime (tests only)."""
+    _check(load().pt_debug_device_reset(), None)
 
 
 def rapid_opts(**kw):

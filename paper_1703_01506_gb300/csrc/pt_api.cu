@@ -424,6 +424,15 @@ int64_t pt_kernel_launch_count(void) { return pt::g_launches.load(); }
 
 void pt_debug_fail_allocations(int64_t after) { pt::g_fail_after.store(after < 0 ? -1 : after); }
 
+pt_status pt_debug_device_reset(void) {
+  const cudaError_t e = cudaDeviceReset();
+  if (e != cudaSuccess) {
+    pt::set_thread_error(std::string("cudaDeviceReset: ") + cudaGetErrorString(e));
+    return PT_ERR_CUDA;
+  }
+  return PT_OK;
+}
+
 void pt_destroy(pt_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);

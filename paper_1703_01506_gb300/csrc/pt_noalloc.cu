@@ -1,24 +1,31 @@
 // pt_maxnull_naive_noalloc: the NaivePT path (FP32 CUDA-core contraction) for
 // callers that cannot allocate device memory. Some callers run where
-// cudaMalloc is not available to them: inside a host callback or a memory
-// pool that another runtime owns, in code that must not change the device's
-// memory footprint after start-up, or under allocation-free real-time rules.
-// This entry point needs no allocation at all: every intermediate buffer lives
-// in one file-scope static device array of fixed size, which every GPU that
-// loads this library holds until the process exits.
+// cudaMalloc is not available to them: inside a memory pool that another
+// runtime owns, in code that must not change the device's memory footprint
+// after start-up, or under allocation-free real-time rules. This entry point
+// needs no allocation at all: every intermediate buffer lives in one
+// file-scope static device array of fixed size, which every GPU that loads
+// this library holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, not a device
 // address, so the host asks the runtime for its device address
-// (cudaGetSymbolAddress) once per device, with that device current, on the
-// first call made on that device. Make that first call before any stream
-// capture. Every call shares the array and it keeps the previous call's
-// contents; calls that overlap on the GPU (two streams, two host threads)
-// race on it and must be serialised by the caller.
+// (cudaGetSymbolAddress) with the caller's device and context current. An
+// address is valid only in the context it was looked up in: another context
+// on the same device (one the caller made with cuCtxCreate, or the primary
+// context again after cudaDeviceReset) holds its own copy of the array. So
+// the lookup is made on every call; it is a host-side table lookup once the
+// module is loaded in that context.
+//
+// The call is synchronous: it copies two status words to host memory and
+// waits on the stream in the middle of the work and at its end, so it cannot
+// be recorded into a CUDA graph by stream capture. Every call shares the
+// array and it keeps the previous call's contents; calls that overlap on the
+// GPU (two streams, two host threads) race on it and must be serialised by
+// the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "pt_internal.h"
@@ -46,14 +53,16 @@ namespace {
 constexpr size_t kNoallocScratchBytes = size_t(64) << 20;  // 64 MiB per device
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::mutex g_sym_mu;
-void* g_sym_ptr[128] = {};
-
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Same arithmetic, in the same order, as the regular moments step: per voxel,
-// eight partial shifted sums over subjects s = w, w + 8, ... (w = 0..7), added
-// in order w = 0..7.
+// Per-voxel moments in one FP64 pass over values shifted by the voxel's first
+// value x_0 (which keeps the sums of squares well conditioned): eight partial
+// sums over subjects s = w, w + 8, ... (w = 0..7), added in order w = 0..7.
+// The validity rule is the regular path's (finite values, not all equal,
+// positive centred sum of squares). The regular moments step is a different
+// two-pass float-float computation, so mean, 1/sqrt(SS) and the observed u
+// agree with it to rounding, not bit for bit; the outputs agree with the
+// regular path within its tolerances.
 __global__ void noalloc_moments_kernel(const float* __restrict__ X, int n, int n1, int n_pad,
                                        int64_t v, float* __restrict__ Xraw,
                                        double* __restrict__ mean, double* __restrict__ inv_norm,
@@ -234,21 +243,14 @@ extern "C" pt_status pt_maxnull_naive_noalloc(const float* X, int32_t n, int64_t
     return fail(PT_ERR_INVALID, "problem needs " + std::to_string(need) +
                                     " bytes of scratch; the static limit is " +
                                     std::to_string(kNoallocScratchBytes) + " bytes");
-  int dev = 0;
-  NA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return fail(PT_ERR_UNSUPPORTED, "device index out of range");
-  unsigned char* base = nullptr;
+  // The array's device address in the current context (see the file comment).
+  void* sym = nullptr;
   {
-    std::lock_guard<std::mutex> lk(g_sym_mu);
-    if (!g_sym_ptr[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p)
-        return fail(PT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_sym_ptr[dev] = p;
-    }
-    base = static_cast<unsigned char*>(g_sym_ptr[dev]);
+    const cudaError_t e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+    if (e != cudaSuccess || !sym)
+      return fail(PT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   }
+  unsigned char* base = static_cast<unsigned char*>(sym);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int n_pad = (n + 15) / 16 * 16;
   const int64_t v_pad = (v + 255) / 256 * 256;

@@ -76,3 +76,32 @@ def test_oracle_and_product_share_no_code():
         if f.endswith((".py", ".c")):
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "binding" not in txt and "libpt" not in txt, f
+
+
+def test_noalloc_binding_rejects_wrong_shapes_before_any_call():
+    """The allocation-free wrapper checks perms against X and the output sizes
+    against P and v before it loads or calls the library (CPU tensors suffice:
+    the checks come first)."""
+    import torch
+    from paper_1703_01506_gb300 import binding as B
+    n, v, P = 12, 50, 8
+    X = torch.zeros((n, v), dtype=torch.float32)
+    perms = torch.zeros((P, n), dtype=torch.int32)
+    mx = torch.zeros(P, dtype=torch.float32)
+    am = torch.zeros(P, dtype=torch.int32)
+    ct = torch.zeros(v, dtype=torch.int32)
+    bad = [
+        dict(perms=torch.zeros((P, n + 1), dtype=torch.int32)),   # row length != n
+        dict(perms=torch.zeros(P * n, dtype=torch.int32)),        # not 2-D
+        dict(perms=torch.zeros((P, n), dtype=torch.int64)),       # wrong dtype
+        dict(maxnull=torch.zeros(P - 1, dtype=torch.float32)),    # too short
+        dict(argmax=torch.zeros(P - 1, dtype=torch.int32)),
+        dict(argmax=torch.zeros(P, dtype=torch.int64)),
+        dict(counts=torch.zeros(v - 1, dtype=torch.int32)),
+        dict(X=torch.zeros((n, v), dtype=torch.float64)),
+    ]
+    for kw in bad:
+        args = dict(X=X, n1=6, perms=perms, maxnull=mx, argmax=am, counts=ct)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            B.pt_maxnull_naive_noalloc(**args)
