@@ -174,6 +174,8 @@ def geodesic_step(U, idx, b, w, step):
 class RapidOpts:
     def __init__(self, train_passes=1, qr_every=100, admm_iters=30, admm_rho=2.0, step=1.0,
                  shift_mode=1, seed=1, stat="t"):
+        """stat: the statistic whose permutation matrix is modelled, "t" or "u"
+        (see _stat_fns); maxima are reported as t either way."""
         self.train_passes, self.qr_every = train_passes, qr_every
         self.admm_iters, self.admm_rho, self.step = admm_iters, admm_rho, step
         self.shift_mode, self.seed, self.stat = shift_mode, seed, stat
@@ -189,15 +191,42 @@ def valid_voxels(X):
 
 
 def _stat_fns(X, n1, perms, o):
+    """The modelled statistic: rows(sel) gives its rows for relabellings sel,
+    entries(i, idx) its values at voxels idx under relabelling i, and to_t maps
+    a (maximum) value of it to the t statistic.
+      "t"        -- Eq. 5's pooled t itself (to_t = identity);
+      "u"        -- the group-1 share of the unit-norm centred voxel,
+                    u = t / sqrt(k (n-2) + k t^2), k = 1/n1 + 1/n2: linear in
+                    the relabelling, so its matrix has rank <= n - 1 exactly
+                    (the low-rank structure of Sec. 3.2 without the t
+                    non-linearity); t = sqrt(k (n-2)) u / sqrt(1 - k u^2) is
+                    strictly increasing and the same at every voxel, so the
+                    maximum of t over voxels is t(maximum of u);
+      "meandiff" -- mean(group 1) - mean(group 2), linear (test statistic).
+    """
     n = X.shape[0]
     valid = valid_voxels(X)
     Xt = voxel_major(X[:, valid])
-    if o.stat == "t":
+    k = 1.0 / n1 + 1.0 / (n - n1)
+
+    def to_t(u):
+        u = np.asarray(u, dtype=np.float64)
+        ku2 = k * u * u
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = math.sqrt(k * (n - 2)) * u / np.sqrt(1.0 - ku2)
+        return np.where(ku2 >= 1.0, np.sign(u) * np.inf, t)
+
+    def u_of(t):
+        return t / np.sqrt(k * (n - 2) + k * t * t)
+
+    if o.stat in ("t", "u"):
+        f = u_of if o.stat == "u" else (lambda t: t)
+
         def rows(sel):
-            return t_rows(None, n1, sel, Xt=Xt)
+            return f(t_rows(None, n1, sel, Xt=Xt))
 
         def entries(i, idx):
-            return t_entries(Xt, n1, perms, np.full(idx.size, i), idx)
+            return f(t_entries(Xt, n1, perms, np.full(idx.size, i), idx))
     else:  # "meandiff": mean(group 1) - mean(group 2), a linear statistic (T has rank <= n-1)
         def rows(sel):
             Lm = np.full(sel.shape, -1.0 / (n - n1))
@@ -208,7 +237,39 @@ def _stat_fns(X, n1, perms, o):
 
         def entries(i, idx):
             return rows(perms[i:i + 1])[0, idx]
-    return valid, Xt, rows, entries
+    if o.stat != "u":
+        to_t = lambda x: np.asarray(x, dtype=np.float64)  # noqa: E731
+    return valid, Xt, rows, entries, to_t
+
+
+def training_summary(T_ex, U, last_idx, shift_mode, dr):
+    """What Alg. 2 computes once the basis is trained (Sec. 4.1): the training
+    weights by least squares, W_ex = U^T T_ex (U orthonormal); the residual
+    R = T_ex - U W_ex; sigma = population standard deviation of R over the
+    entries Omega sampled in the last pass (last_idx[i] = the voxels drawn for
+    column i, repeats counted as drawn); and the shift mu:
+      shift_mode 0 -- as Alg. 2 prints it, the largest residual over every
+                      training entry: sup_i max_j R[i, j];
+      shift_mode 1 -- the amount the maximum moves (Sec. 4.1, "Bias-variance
+                      trade-off"): mean over training columns i of
+                      max_j T_ex[i, j] - max_j (U W_ex[:, i] + sigma z_ij)_j,
+                      z_ij = voxel_normal(TAG_SHIFT, j, i).
+    T_ex is (ell x V), U (V x r). Returns (W_ex (r x ell), sigma, mu)."""
+    ell, V = T_ex.shape
+    W_ex = U.T @ T_ex.T                       # r x ell
+    model = (U @ W_ex).T                      # ell x V
+    R = T_ex - model
+    sampled = np.concatenate([R[i, last_idx[i]] for i in range(ell)])
+    sigma = float(np.std(sampled))
+    if shift_mode == 0:
+        mu = float(np.max(R))
+    else:
+        gaps = np.empty(ell)
+        for i in range(ell):
+            z = dr.voxel_normal(TAG_SHIFT, np.arange(V), i)
+            gaps[i] = np.max(T_ex[i]) - np.max(model[i] + sigma * z)
+        mu = float(np.mean(gaps))
+    return W_ex, sigma, mu
 
 
 def rapid_train(X, n1, perms, rank, sample_rate, n_train, opts=None):
@@ -218,7 +279,7 @@ def rapid_train(X, n1, perms, rank, sample_rate, n_train, opts=None):
     o = opts or RapidOpts()
     X = np.asarray(X)
     n = X.shape[0]
-    valid, Xt, rows, _ = _stat_fns(X, n1, perms, o)
+    valid, Xt, rows, _, to_t = _stat_fns(X, n1, perms, o)
     V = Xt.shape[0]
     m = int(math.ceil(sample_rate * V))
     dr = draws(o.seed)
@@ -242,36 +303,25 @@ def rapid_train(X, n1, perms, rank, sample_rate, n_train, opts=None):
                 U = qr_posdiag(U)
             last_idx[i] = idx
     U = qr_posdiag(U)
-    W_ex = U.T @ T_ex.T                       # r x ell
-    model = (U @ W_ex).T                      # ell x V
-    R = T_ex - model
-    sampled = np.concatenate([R[i, last_idx[i]] for i in range(ell)])
-    sigma = float(np.std(sampled))
-    if o.shift_mode == 0:
-        mu = float(np.max(R))
-    else:
-        gaps = np.empty(ell)
-        for i in range(ell):
-            z = dr.voxel_normal(TAG_SHIFT, np.arange(V), i)
-            gaps[i] = np.max(T_ex[i]) - np.max(model[i] + sigma * z)
-        mu = float(np.mean(gaps))
+    W_ex, sigma, mu = training_summary(T_ex, U, last_idx, o.shift_mode, dr)
     T_obs = rows(np.arange(n, dtype=np.int32)[None, :])[0]
     counts = np.zeros(X.shape[1], dtype=np.int64)
     counts[np.flatnonzero(valid)] = (T_ex >= T_obs[None, :]).sum(axis=0)
     res = RapidResult()
     res.U, res.W_ex, res.T_ex, res.sigma, res.mu, res.m = U, W_ex, T_ex, sigma, mu, m
     res.steps, res.w_hist, res.counts = steps, w_hist, counts
-    res.train_max = T_ex.max(axis=1)
+    res.train_max = to_t(T_ex.max(axis=1))
     return res
 
 
 def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=False):
     """Recovery phase (Sec. 4.2, Alg. 2 RECOVERY) for relabellings rows_sel with
     U frozen: exact statistic at the m sampled voxels, w = Complete(U, t, Omega),
-    m_i = max_j (U w + sigma z)_j + mu."""
+    m_i = max_j (U w + sigma z)_j + mu (mapped to t when the modelled
+    statistic is u)."""
     o = opts or RapidOpts()
     X = np.asarray(X)
-    _, Xt, _, entries = _stat_fns(X, n1, perms, o)
+    _, Xt, _, entries, to_t = _stat_fns(X, n1, perms, o)
     V = Xt.shape[0]
     dr = draws(o.seed)
     out = np.empty(len(rows_sel))
@@ -282,7 +332,7 @@ def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=F
         w, _, _ = admm_l1(U[idx], tt, o.admm_rho, o.admm_iters)
         ws.append(w)
         z = dr.voxel_normal(TAG_NOISE, np.arange(V), int(i))
-        out[k] = np.max(U @ w + sigma * z) + mu
+        out[k] = to_t(np.max(U @ w + sigma * z) + mu)
     return (out, np.array(ws)) if return_w else out
 
 

@@ -7,6 +7,8 @@ in FP64; sequential training lets the difference grow slowly, so training is
 compared over a short run (per-step weights) and by principal angles, and
 recovery is compared given the same basis U, sigma and mu.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -16,6 +18,8 @@ from oracle import rapid as R
 from paper_1703_01506_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def smooth_field(n, n1, seed=3, grid=(30, 36, 30), axes=(12, 15, 12), fwhm=6.0):
@@ -121,22 +125,35 @@ def test_training_matches_oracle(cuda_lib):
         ctx.close()
 
 
+def _oracle_seed_spread():
+    """Per-seed KL and FWER 0.05 / 0.01 threshold errors of the FP64 RapidPT
+    oracle on this fixture (written by tests/golden/make_rapid_seed_spread.py)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "rapid_seed_spread_smooth_n40.txt"))
+            if l.strip() and not l.startswith("#")]
+    a = np.array([[float(x) for x in r[1:]] for r in rows])
+    return a[:, 0], {0.05: a[:, 1], 0.01: a[:, 2]}
+
+
 def test_maxnull_rapid_end_to_end(cuda_lib):
     """Full RapidPT on the GPU: training rows exact, counts over them exact, and
-    the recovered max-null close to the exhaustive one (KL per run; FWER
-    thresholds as the median over three seeds: the 0.01 threshold of a
-    3000-relabelling max-null rests on its top 30 values, and the FP32 training
-    trajectory, which separates from the FP64 one after a few dozen steps, makes
-    each seed's threshold one draw of the method's spread)."""
+    every seed's recovered max-null as close to the exhaustive one as the FP64
+    oracle's own seeds come. RapidPT is randomised (basis start, samples,
+    residual draws) and the FP32 training trajectory separates from the FP64
+    one after a few dozen steps, so a GPU seed is one more draw of the method's
+    spread, not a copy of the oracle's draw with the same seed. Bound per seed:
+    KL <= 1.5 x the oracle's largest KL over eight seeds, and each threshold's
+    relative error <= 1.5 x the oracle's largest over those seeds."""
     B = cuda_lib
     n, n1, P, r, eta, ell = 40, 20, 3000, 20, 0.02, 80
     X = smooth_field(n, n1)
     perms = synth.perms_pcg32(n, P, seed=1)
     ref = oracle.naive(X, n1, perms)
     ref_train = oracle.naive(X, n1, perms[:ell])
+    kl_or, err_or = _oracle_seed_spread()
+    kl_bound = 1.5 * kl_or.max()
+    thr_bound = {a: 1.5 * np.abs(e).max() for a, e in err_or.items()}
     pd = torch.as_tensor(perms).cuda()
-    errs = {0.05: [], 0.01: []}
-    for seed in (1, 2, 3):
+    for seed in (1, 2, 3, 4):
         ctx = gpu_ctx(B, X, n1)
         mx = torch.empty(P, dtype=torch.float32, device="cuda")
         ct = torch.empty(X.shape[1], dtype=torch.int32, device="cuda")
@@ -147,14 +164,12 @@ def test_maxnull_rapid_end_to_end(cuda_lib):
         np.testing.assert_allclose(mx[:ell], ref.maxnull[:ell], rtol=1e-6)
         np.testing.assert_array_equal(ct.cpu().numpy(), ref_train.counts.astype(np.int32))
         kl = R.kl_divergence(ref.maxnull, mx)
-        assert kl < 0.6, (seed, kl)
-        for a in errs:
+        assert kl <= kl_bound, (seed, kl, kl_bound)
+        for a, bound in thr_bound.items():
             t_ref, t_rap = R.fwer_threshold(ref.maxnull, a), R.fwer_threshold(mx, a)
-            errs[a].append(abs(t_rap - t_ref) / t_ref)
+            assert abs(t_rap - t_ref) / t_ref <= bound, (seed, a, t_rap / t_ref - 1, bound)
         assert info.sigma > 0 and info.m_per_perm == int(np.ceil(eta * X.shape[1]))
         ctx.close()
-    for a, e in errs.items():
-        assert np.median(e) < 0.15, (a, e)
 
 
 def test_rapid_rejects_bad_arguments(cuda_lib):

@@ -172,3 +172,110 @@ def test_rapid_tracks_naive_max_null_on_smooth_field():
     for a in (0.05, 0.01):
         t_ref, t_rap = R.fwer_threshold(ref.maxnull, a), R.fwer_threshold(res.maxnull, a)
         assert abs(t_rap - t_ref) / t_ref < 0.15, (a, t_ref, t_rap)
+
+
+def _planted(ell=12, V=400, r=5, m=30, c=0.3, with_region=True, zero_model=False, seed=8):
+    """Training columns T_ex = U* W* + R with everything known in closed form.
+    U* = the unit vectors of voxels 0..r-1 (orthonormal); R is zero on those
+    voxels, so U*^T R = 0 and the least-squares weights are W* exactly. R holds
+    the constant c on voxels 100..199 (optional) and one spike h_i per column
+    at a voxel of 300..399 that the column's sampled set Omega_i never draws.
+    Omega_i (repeats allowed) draws two thirds of its entries from 100..199, so
+    the sampled share of the c-region differs from its share of all voxels."""
+    rng = np.random.default_rng(seed)
+    U = np.zeros((V, r))
+    U[np.arange(r), np.arange(r)] = 1.0
+    W = np.zeros((r, ell)) if zero_model else rng.uniform(-1.0, 1.0, (r, ell))
+    if not zero_model:
+        W[:, 3] = -np.abs(W[:, 3]) - 0.1    # a column whose model maximum is a zero voxel
+    Rm = np.zeros((ell, V))
+    if with_region:
+        Rm[:, 100:200] = c
+    last_idx, spikes, h = [], [], 5.0 + 0.25 * np.arange(ell)
+    for i in range(ell):
+        k = 2 * m // 3
+        idx = np.concatenate([rng.integers(100, 200, k), rng.integers(0, 100, m - k)])
+        idx[1] = idx[0]                     # a repeated draw counts twice
+        spike = 300 + int(rng.integers(0, 100))
+        Rm[i, spike] = h[i]
+        last_idx.append(idx)
+        spikes.append(spike)
+    T_ex = (U @ W).T + Rm
+    return T_ex, U, W, Rm, last_idx, h
+
+
+def test_training_summary_planted_residual_mode0():
+    """W_ex = W*, sigma = the population std of R over the last pass's sampled
+    entries (a two-valued sample: c * sqrt(p (1 - p)), p = share of sampled
+    entries in the c-region, repeats counted), mu = the largest residual over
+    all training entries (the spikes, never sampled)."""
+    T_ex, U, W, Rres, last_idx, h = _planted()
+    W_ex, sigma, mu = R_training_summary(T_ex, U, last_idx, 0)
+    np.testing.assert_allclose(W_ex, W, rtol=0, atol=1e-15)
+    hits = sum(int(np.sum((ix >= 100) & (ix < 200))) for ix in last_idx)
+    N = sum(ix.size for ix in last_idx)
+    p = hits / N
+    assert abs(p - 0.25) > 0.2                      # sampled share != share of all voxels
+    assert sigma == pytest.approx(0.3 * math.sqrt(p * (1.0 - p)), rel=1e-12)
+    assert mu == pytest.approx(float(h.max()), rel=1e-15)
+
+
+def test_training_summary_planted_residual_mode1_no_noise():
+    """With R zero on every sampled entry, sigma = 0 and the shift is the mean
+    over training columns of (column maximum of T_ex) - (column maximum of the
+    model U W_ex): h_i - max(max_k W*[k, i], 0), the model being zero off
+    voxels 0..r-1."""
+    T_ex, U, W, Rres, last_idx, h = _planted(with_region=False)
+    W_ex, sigma, mu = R_training_summary(T_ex, U, last_idx, 1)
+    assert sigma == 0.0
+    expect = np.mean(h - np.maximum(W.max(axis=0), 0.0))
+    assert mu == pytest.approx(float(expect), rel=1e-14)
+    assert W[:, 3].max() < 0.0                      # that column's model maximum is 0
+
+
+def test_training_summary_planted_residual_mode1_zero_model():
+    """With W* = 0 the model vanishes, so the shift is the mean over columns of
+    h_i - sigma * max_j z_ij, z_ij the shift-estimate normals of column i."""
+    T_ex, U, W, Rres, last_idx, h = _planted(zero_model=True)
+    W_ex, sigma, mu = R_training_summary(T_ex, U, last_idx, 1)
+    np.testing.assert_allclose(W_ex, 0.0, atol=0)
+    hits = sum(int(np.sum((ix >= 100) & (ix < 200))) for ix in last_idx)
+    p = hits / sum(ix.size for ix in last_idx)
+    s = 0.3 * math.sqrt(p * (1.0 - p))
+    assert sigma == pytest.approx(s, rel=1e-12)
+    d = R.draws(1)
+    zmax = np.array([d.voxel_normal(R.TAG_SHIFT, np.arange(T_ex.shape[1]), i).max()
+                     for i in range(T_ex.shape[0])])
+    assert mu == pytest.approx(float(np.mean(h - s * zmax)), rel=1e-12)
+
+
+def test_training_weights_are_least_squares():
+    """W_ex is the least-squares fit of every training column on U (Sec. 4.1):
+    equal to LAPACK's lstsq for an orthonormal U and arbitrary columns."""
+    rng = np.random.default_rng(9)
+    U = R.qr_posdiag(rng.standard_normal((300, 7)))
+    T_ex = rng.standard_normal((10, 300))
+    W_ex, _, _ = R_training_summary(T_ex, U, [np.arange(5)] * 10, 0)
+    ls = np.linalg.lstsq(U, T_ex.T, rcond=None)[0]
+    np.testing.assert_allclose(W_ex, ls, atol=1e-12)
+
+
+def R_training_summary(T_ex, U, last_idx, shift_mode):
+    return R.training_summary(T_ex, U, last_idx, shift_mode, R.draws(1))
+
+
+def test_u_statistic_exact_recovery_at_full_rank():
+    """Modelling u (the group-1 share of the unit-norm centred voxel, linear in
+    the relabelling, so its matrix has rank <= n - 1) instead of t: with
+    r = n - 1 and a converged basis the residual vanishes (sigma, mu -> 0) and
+    the recovered t maxima, t(max u), equal the exhaustive ones, because t(u)
+    is strictly increasing and the same at every voxel."""
+    n, n1, v, P = 10, 5, 400, 150
+    X = synth.gaussian_mean_shift(n, v, seed=4)
+    perms = synth.perms_pcg32(n, P, seed=2)
+    ref = oracle.naive(X, n1, perms)
+    o = R.RapidOpts(train_passes=60, stat="u", admm_iters=300, qr_every=50)
+    res = R.rapid(X, n1, perms, n - 1, 0.3, 40, o)
+    assert res.sigma < 1e-8 and abs(res.mu) < 1e-8
+    np.testing.assert_allclose(res.maxnull, ref.maxnull, rtol=1e-7)
+    np.testing.assert_array_equal(res.counts, oracle.naive(X, n1, perms[:40]).counts)
