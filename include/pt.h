@@ -255,6 +255,21 @@ pt_status pt_rapid_recover(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t
  */
 pt_status pt_sync(pt_ctx* ctx);
 
+/*
+ * pt_t_rows -- rows of the permutation testing matrix T (Sec. 2.1): the pooled
+ * t of Eq. 5 at every mask voxel under each of P relabellings, written out
+ * (NaivePT never forms T; this call is for inspection and for RapidPT's
+ * training rows, whose kernels it shares).
+ *   perms     : device, int32, P x n (as pt_maxnull_naive), 1 <= P <= 2^31 - 1.
+ *   precision : PT_PREC_FP32 (CUDA cores) or PT_PREC_BF16X2 / _BF16X3 (tensor cores).
+ *   T         : device, float32, P x v row-major in masked order; NaN where the
+ *               voxel has no statistic. P * v * 4 bytes, caller-owned.
+ * t is formed in FP32 from the FP32 accumulator u as sqrt(k(n-2)) u / sqrt(1 - k u^2).
+ * Asynchronous on the context's stream; invalid rows make the next pt_sync
+ * return PT_ERR_INVALID. PT_ERR_UNSUPPORTED for a context with covariates.
+ */
+pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precision, float* T);
+
 /* t_obs: device float32[v]: observed statistic per voxel (NaN where undefined).
  * Enqueued on the context's stream. */
 pt_status pt_t_obs(pt_ctx* ctx, float* t_obs);

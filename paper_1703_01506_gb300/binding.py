@@ -80,6 +80,7 @@ def load(path=None):
         "pt_fwer_pvalues": (ctypes.c_int, [_VP, _VP, i64, i32, _VP]),
         "pt_sync": (ctypes.c_int, [_VP]),
         "pt_t_obs": (ctypes.c_int, [_VP, _VP]),
+        "pt_t_rows": (ctypes.c_int, [_VP, _VP, i64, i32, _VP]),
         "pt_voxel_grid_index": (ctypes.c_int, [_VP, _VP]),
         "pt_num_voxels": (i64, [_VP]),
         "pt_num_valid_voxels": (i64, [_VP]),
@@ -360,6 +361,20 @@ def maxnull_naive(ctx, perms, precision=PT_PREC_BF16X3, two_sided=False, counts=
     if sync:
         pt_sync(ctx)
     return mx, am, ct
+
+
+def pt_t_rows(ctx, perms, precision=PT_PREC_BF16X3, out=None):
+    """Rows of T: (P, v) float32 CUDA tensor, NaN where a voxel has no t."""
+    P = perms.shape[0]
+    v = int(load().pt_num_voxels(ctx.handle))
+    if perms.dim() != 2 or perms.dtype != torch.int32:
+        raise ValueError("perms must be a 2-D int32 tensor")
+    if out is None:
+        out = torch.empty((P, v), dtype=torch.float32, device=perms.device)
+    elif out.dtype != torch.float32 or out.numel() < P * v:
+        raise ValueError("out must be float32 with at least P * v elements")
+    _check(load().pt_t_rows(ctx.handle, _ptr(perms), P, int(precision), _ptr(out)), ctx.handle)
+    return out
 
 
 def pt_profile_enable(ctx, on=True):

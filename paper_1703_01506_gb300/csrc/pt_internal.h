@@ -125,6 +125,7 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
                            double sample_rate, const pt_rapid_opts& o, float* U_out,
                            float* train_max, uint32_t* counts, float* w_hist,
                            pt_rapid_info* info);
+pt_status t_rows_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int precision, float* T);
 pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t first_row,
                              const float* U_in, int32_t rank, double sample_rate, double sigma,
                              double mu, const pt_rapid_opts& o, float* maxnull, float* W_out);

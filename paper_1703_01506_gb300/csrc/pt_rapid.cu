@@ -1162,6 +1162,19 @@ __global__ void u_to_t_kernel(float* __restrict__ T, int64_t total, float kf, fl
   }
 }
 
+// Rows of t in compact (valid-voxel) order -> rows in mask order; voxels
+// without a statistic keep the NaN the destination was filled with.
+__global__ void scatter_rows_kernel(const float* __restrict__ src, int64_t P, int64_t V,
+                                    const int32_t* __restrict__ valid_map, int64_t v,
+                                    float* __restrict__ dst) {
+  const int64_t total = P * V;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / V, c = e - i * V;
+    dst[i * v + valid_map[c]] = src[e];
+  }
+}
+
 __global__ void pack_u_kernel(const float* __restrict__ Uin, int64_t V, int R, int RP,
                               float* __restrict__ Uout, int to_padded) {
   const int64_t total = V * RP;
@@ -1754,6 +1767,63 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
   return PT_OK;
 }
 
+// Rows of T (Sec. 2.1): t of every mask voxel under each of P relabellings,
+// from the contraction RapidPT uses for its training rows T_ex: the tensor-core
+// kernel writing t from its accumulator (BF16 pieces), or the FP32 CUDA-core
+// kernel writing u followed by the same u -> t map.
+pt_status t_rows_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int precision, float* T) {
+  if (ctx->glm_q1) {
+    set_error(ctx, "pt_t_rows: rows of the plain two-sample t only (context has covariates)");
+    return PT_ERR_UNSUPPORTED;
+  }
+  cudaStream_t st = ctx->stream;
+  const int64_t V = ctx->v_valid, v = ctx->v;
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(T, 0xFF, sizeof(float) * size_t(P) * v, st));  // NaN
+  if (V == 0) return PT_OK;
+  Buf comp;
+  struct G {
+    Buf* b;
+    ~G() { b->release(); }
+  } guard{&comp};
+  float* out = T;
+  if (V != v) {
+    if (!comp.ensure(sizeof(float) * size_t(P) * V)) {
+      set_error(ctx, "pt_t_rows: out of device memory");
+      return PT_ERR_NOMEM;
+    }
+    out = comp.as<float>();
+  }
+  int64_t P_pad = 0;
+  pt_status s;
+  if (precision != PT_PREC_FP32) {
+    s = tc_supported(ctx);
+    if (s == PT_OK) s = ensure_xnb(ctx);
+    if (s == PT_OK) s = build_labels(ctx, perms, P, 1, &P_pad);
+    if (s == PT_OK)
+      s = tc_rows(ctx, ctx->labels.p, P, precision, 2, out, 0, 0, nullptr, nullptr, nullptr);
+  } else {
+    s = ensure_xn32(ctx);
+    if (s == PT_OK) s = build_labels(ctx, perms, P, 0, &P_pad);
+    if (s == PT_OK) {
+      const dim3 grid{unsigned((V + 127) / 128), unsigned((P + 127) / 128), 1u};
+      simt_contract_kernel<<<grid, 256, 0, st>>>(ctx->labels.as<float>(), ctx->Xn32.as<float>(),
+                                                 ctx->n_pad, P, V, 1, 1, 0, nullptr,
+                                                 ctx->rowflag.as<uint8_t>(), nullptr, nullptr, out);
+      PT_LAUNCH_CHECK(ctx);
+      u_to_t_kernel<<<grid_n(P * V, 256), 256, 0, st>>>(out, P * V, float(ctx->k),
+                                                         float(ctx->c_t));
+      PT_LAUNCH_CHECK(ctx);
+    }
+  }
+  if (s != PT_OK) return s;
+  if (V != v) {
+    scatter_rows_kernel<<<grid_n(P * V, 256), 256, 0, st>>>(out, P, V, ctx->valid_map.as<int32_t>(),
+                                                            v, T);
+    PT_LAUNCH_CHECK(ctx);
+  }
+  return PT_OK;
+}
+
 }  // namespace pt
 
 // ---------------------------------------------------------------------------
@@ -1771,6 +1841,25 @@ void pt_rapid_opts_default(pt_rapid_opts* o) {
   o->step = 1.0f;
   o->shift_mode = 1;
   o->seed = 1;
+}
+
+pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precision, float* T) {
+  pt::NvtxRange nvtx_range("pt_t_rows");
+  if (!ctx || !perms || !T) {
+    pt::set_error(ctx, "pt_t_rows: NULL argument");
+    return PT_ERR_INVALID;
+  }
+  if (P < 1 || P > INT32_MAX || precision < PT_PREC_FP32 || precision > PT_PREC_BF16X3) {
+    pt::set_error(ctx, "pt_t_rows: need 1 <= P <= 2^31-1 and a valid precision");
+    return PT_ERR_INVALID;
+  }
+  try {
+    cudaSetDevice(ctx->device);
+    return pt::t_rows_impl(ctx, perms, P, precision, T);
+  } catch (...) {
+    pt::set_error(ctx, "pt_t_rows: internal error");
+    return PT_ERR_CUDA;
+  }
 }
 
 pt_status pt_rapid_train(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int32_t rank,
