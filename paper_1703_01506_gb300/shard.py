@@ -20,10 +20,12 @@ def shard_rows(P, world, rank):
 
 
 def merge_maxnull(local, P, group=None):
-    """Concatenate every rank's maxima (its rows of shard_rows) into a P-vector."""
+    """Concatenate every rank's per-relabelling outputs (maxima or argmax; its
+    rows of shard_rows) into a P-vector."""
     world = dist.get_world_size(group)
     size = max(shard_rows(P, world, r)[1] - shard_rows(P, world, r)[0] for r in range(world))
-    buf = torch.full((size,), float("-inf"), dtype=local.dtype, device=local.device)
+    fill = float("-inf") if local.dtype.is_floating_point else -1
+    buf = torch.full((size,), fill, dtype=local.dtype, device=local.device)
     buf[:local.numel()] = local
     parts = [torch.empty_like(buf) for _ in range(world)]
     dist.all_gather(parts, buf, group=group)

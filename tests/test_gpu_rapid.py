@@ -58,11 +58,15 @@ def test_recovery_matches_oracle_given_basis(cuda_lib):
     ctx.close()
 
 
-def test_recovery_large_rank_given_basis(cuda_lib):
+@pytest.mark.parametrize("n,r,eta", [(80, 70, 0.02), (120, 100, 0.235)])
+def test_recovery_large_rank_given_basis(cuda_lib, n, r, eta):
     """Rank 70 (padded to 72; the reconstruction's K = 80 takes the 64-voxel
-    tensor-core tile) with a random orthonormal basis, and a ragged voxel count."""
+    tensor-core tile) and rank 100 with about 2,100 sampled voxels per
+    relabelling (the n=400, 600k-voxel workload's r and m: the fit's rows span
+    a larger cluster), each with a random orthonormal basis and a ragged voxel
+    count."""
     B = cuda_lib
-    n, n1, P, r, eta, ell = 80, 40, 300, 70, 0.02, 60
+    n1, P, ell = n // 2, 300, 60
     X = smooth_field(n, n1, seed=9)
     X = X[:, : X.shape[1] - 37]
     V = X.shape[1]
@@ -170,6 +174,29 @@ def test_maxnull_rapid_end_to_end(cuda_lib):
             assert abs(t_rap - t_ref) / t_ref <= bound, (seed, a, t_rap / t_ref - 1, bound)
         assert info.sigma > 0 and info.m_per_perm == int(np.ceil(eta * X.shape[1]))
         ctx.close()
+
+
+def test_rapid_rank100_training_runs_exact_rows(cuda_lib):
+    """Training and recovery at rank 100 with m = 2,100 samples per column (the
+    sizes of the n=400 workload) on a small field: training maxima and counts
+    are the exhaustive ones and every recovered maximum is finite."""
+    B = cuda_lib
+    n, n1, P, r, ell = 120, 60, 400, 100, 150
+    X = smooth_field(n, n1, seed=11)
+    eta = 2100.0 / X.shape[1]
+    perms = synth.perms_pcg32(n, P, seed=6)
+    ref_train = oracle.naive(X, n1, perms[:ell])
+    ctx = gpu_ctx(B, X, n1)
+    mx = torch.empty(P, dtype=torch.float32, device="cuda")
+    ct = torch.empty(X.shape[1], dtype=torch.int32, device="cuda")
+    info = B.pt_maxnull_rapid(ctx, torch.as_tensor(perms).cuda(), r, eta, ell,
+                              B.rapid_opts(seed=3), mx, ct)
+    B.pt_sync(ctx)
+    mx = mx.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(mx[:ell], ref_train.maxnull, rtol=1e-6)
+    np.testing.assert_array_equal(ct.cpu().numpy(), ref_train.counts.astype(np.int32))
+    assert np.all(np.isfinite(mx)) and info.m_per_perm == int(np.ceil(eta * X.shape[1]))
+    ctx.close()
 
 
 def test_rapid_rejects_bad_arguments(cuda_lib):

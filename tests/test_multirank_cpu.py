@@ -34,9 +34,11 @@ def _worker(rank, world, port, out_dir):
     a, b = shard.shard_rows(P, world, rank)
     r = oracle.naive(X, n1, perms[a:b])
     mx = shard.merge_maxnull(torch.tensor(r.maxnull), P)
-    ct = shard.merge_counts(torch.tensor(r.counts.astype(np.int64)))
+    am = shard.merge_maxnull(torch.tensor(r.argmax.astype(np.int32)), P)
+    ct = shard.merge_counts(torch.tensor(r.counts.astype(np.int32)))
     if rank == 0:
         np.save(os.path.join(out_dir, "mx.npy"), mx.numpy())
+        np.save(os.path.join(out_dir, "am.npy"), am.numpy())
         np.save(os.path.join(out_dir, "ct.npy"), ct.numpy())
     dist.destroy_process_group()
 
@@ -60,4 +62,5 @@ def test_two_rank_gloo_merge_equals_single(tmp_path):
     perms = synth.perms_pcg32(n, P, seed=1)
     ref = oracle.naive(X, n1, perms)
     np.testing.assert_array_equal(np.load(tmp_path / "mx.npy"), ref.maxnull)
+    np.testing.assert_array_equal(np.load(tmp_path / "am.npy"), ref.argmax.astype(np.int32))
     np.testing.assert_array_equal(np.load(tmp_path / "ct.npy"), ref.counts.astype(np.int64))
