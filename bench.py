@@ -53,10 +53,14 @@ import numpy as np  # noqa: E402
 
 METRIC = "T entries/s (perm x voxel t) & max-null wall time, RapidPT vs NaivePT, 1 GB300"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one tuned launch of the
-# fused kernel on brain_n100_v232k (160.21 MB read + 4.67 MB written).
-TRAFFIC_BYTES = 164.89e6
+# fused kernel on brain_n100_v232k, per precision (BF16x3: 160.21 MB read +
+# 4.67 MB written); None where no capture of the current kernel exists.
+TRAFFIC_BYTES = {2: 164.89e6, 3: None}
 WORKLOAD = "brain_n100_v232k"
-PREC = {"fp32": 0, "bf16x2": 1, "bf16x3": 2}
+# NaivePT arithmetic of the RapidPT-vs-NaivePT and large legs: FP16x2 (two FP16
+# pieces of 2^15 Xn), the fastest path that meets the FP32-class tolerances.
+NAIVE_PREC = 3
+PREC = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "fp16x2": 3}
 
 
 def peaks():
@@ -261,7 +265,7 @@ def rapid_vs_naive(dev, B, torch, X, mask, n1, perms, r, ell, eta, passes=1):
 
     def naive_run():
         c = B.pt_prepare(X, n1, mask, stream=stream)
-        B.pt_maxnull_naive_ex(c, perms, B.naive_opts(2), mx_naive, am, None)
+        B.pt_maxnull_naive_ex(c, perms, B.naive_opts(NAIVE_PREC), mx_naive, am, None)
         B.pt_sync(c)
         v = B.pt_num_valid_voxels(c)
         c.close()
@@ -301,7 +305,7 @@ def rapid_vs_naive(dev, B, torch, X, mask, n1, perms, r, ell, eta, passes=1):
 
     v = naive_run()
     c = B.pt_prepare(X, n1, mask, stream=stream)
-    B.pt_autotune_naive(c, perms, B.naive_opts(2))
+    B.pt_autotune_naive(c, perms, B.naive_opts(NAIVE_PREC))
     c.close()
     naive_ms = timed(naive_run, 3)
     rapid_run()
@@ -333,7 +337,8 @@ def rapid_vs_naive(dev, B, torch, X, mask, n1, perms, r, ell, eta, passes=1):
         "rapid_info": {k: phase[k] for k in ("sigma", "mu", "train_steps", "m_per_perm")},
         "opts": {"train_passes": opts.train_passes, "qr_every": opts.qr_every,
                  "admm_iters": opts.admm_iters, "admm_rho": opts.admm_rho,
-                 "shift_mode": opts.shift_mode, "precision": "bf16x3"},
+                 "shift_mode": opts.shift_mode, "training_rows_precision": "bf16x3",
+                 "naive_precision": "fp16x2"},
         "accuracy_vs_naive": {
             "kl": hist_kl(a, b), **thr, "resampling_risk_fwer0.05": risk,
             # the estimator's own floor: two exhaustive max-nulls over disjoint halves
@@ -391,7 +396,7 @@ def precision_leg(dev, B, torch, X, mask, n1, perms, t_rows_sel, reps=20):
     stream = torch.cuda.current_stream(dev)
     P = perms.shape[0]
     out = {}
-    for name, prec in (("fp32", 0), ("bf16x2", 1), ("bf16x3", 2)):
+    for name, prec in (("fp32", 0), ("bf16x2", 1), ("bf16x3", 2), ("fp16x2", 3)):
         ctx = B.pt_prepare(X, n1, mask, stream=stream)
         opts = B.naive_opts(prec)
         if prec:
@@ -447,6 +452,7 @@ def precision_summary(paths, ref_rows, ref_max, ref_argmax, ref_t):
             "thr_err_bound_vs_oracle": float(np.max(np.abs(m - ref_max)))}
     res["speedup_bf16x3_over_fp32_kernel"] = paths["fp32"]["kernel_ms"] / paths["bf16x3"]["kernel_ms"]
     res["speedup_bf16x2_over_fp32_kernel"] = paths["fp32"]["kernel_ms"] / paths["bf16x2"]["kernel_ms"]
+    res["speedup_fp16x2_over_fp32_kernel"] = paths["fp32"]["kernel_ms"] / paths["fp16x2"]["kernel_ms"]
     res["reference"] = ("FP64 oracle (oracle/naive_fp64.c), %d sampled relabelling rows x all "
                         "voxels for maxima, %d rows for t entries, computed in the CPU leg"
                         % (len(ref_rows), ref_t.shape[0]))
@@ -457,7 +463,7 @@ def batched_leg(dev, B, synth, torch, studies=64, P=10000):
     """Many independent studies of uneven shape in one call: 64 studies with
     n ~ U{24..400} (n1 = n/2) and v ~ U{50k..600k} voxels (PCG32 seeded 1000 + k),
     10,000 relabellings each, BF16x3. Values are Gaussian (mean ~ U(0,1) per voxel,
-    unit noise; the contraction's cost does not depend on smoothness). Compares
+    unit noise; the contraction's cost does not depend on smoothness), FP16x2. Compares
     pt_maxnull_naive_batched (one persistent launch per tile class, replayed as a
     CUDA graph) with one pt_maxnull_naive_ex call per study on the same stream."""
     shapes = synth.uneven_study_shapes(studies)
@@ -474,7 +480,7 @@ def batched_leg(dev, B, synth, torch, studies=64, P=10000):
         mx.append(torch.empty(P, dtype=torch.float32, device=dev))
         am.append(torch.empty(P, dtype=torch.int32, device=dev))
     entries = float(P) * sum(v for _, _, v in shapes)
-    opts = B.naive_opts(2)
+    opts = B.naive_opts(NAIVE_PREC)
 
     def batched():
         B.pt_maxnull_naive_batched(ctxs, perms, opts, mx, am)
@@ -768,12 +774,12 @@ def run_ours(args):
         peak_key = "bf16_tflops" if timed_s < 2.0 else "bf16_tflops_sustained"
         peak = pk.get(peak_key, pk.get("bf16_tflops"))
         ach = flops / (avg_kern_ms * 1e-3) / 1e12
-        pieces = 2 if prec == 1 else 3
+        pieces = 3 if prec == 2 else 2
         n_pad = (n + 15) // 16 * 16
         hw = 2.0 * pieces * n_pad * entries / (avg_kern_ms * 1e-3) / 1e12
         # DRAM bytes per launch of this kernel from the ncu capture summarised in
         # profiles/tc_contract_kernel_brain_n100_v232k.md (BF16x3, tuned launch).
-        traffic = TRAFFIC_BYTES if prec == 2 and tuned is not None else None
+        traffic = TRAFFIC_BYTES.get(prec) if tuned is not None else None
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
@@ -784,14 +790,15 @@ def run_ours(args):
                 "kernel": "tc_contract_kernel<256>", "kernel_ms": avg_kern_ms,
                 "launch_config": tuned,
                 "hw_tflops": hw, "hw_frac": hw / peak,
-                "algorithmic": "2n flops per T entry (n=%d); hardware issues %d BF16 pieces x "
+                "algorithmic": "2n flops per T entry (n=%d); hardware issues %d data pieces x "
                                "n_pad=%d" % (n, pieces, n_pad)}
 
     line = {
         "metric": METRIC, "value": value, "unit": "T entries/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "f32", 1: "bf16x2/f32acc", 2: "bf16x3/f32acc"}[prec], "data": "synthetic",
+        "dtype": {0: "f32", 1: "bf16x2/f32acc", 2: "bf16x3/f32acc", 3: "fp16x2/f32acc"}[prec],
+        "data": "synthetic",
         "config": {"workload": "%s: n=100 (50/50), 91x109x91 grid, ellipsoid mask %d voxels, "
                                "FWHM 8 smoothing, +0.3 SD effect r=10, P=%d relabellings per "
                                "GPU (PCG32 Fisher-Yates)" % (WORKLOAD, v, P),
@@ -847,7 +854,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
+    ap.add_argument("--precision", default="fp16x2", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rapid-passes", type=int, default=1,
                     help="RapidPT training passes in the RapidPT leg (default 1, Alg. 2)")

@@ -57,7 +57,9 @@ typedef enum {
 typedef enum {
   PT_PREC_FP32 = 0,    /* plain FP32 CUDA-core (SIMT) kernel */
   PT_PREC_BF16X2 = 1,  /* tcgen05 tensor cores, data split hi+lo in BF16, FP32 accumulate */
-  PT_PREC_BF16X3 = 2   /* tcgen05 tensor cores, data split hi+mid+lo in BF16, FP32 accumulate */
+  PT_PREC_BF16X3 = 2,  /* tcgen05 tensor cores, data split hi+mid+lo in BF16, FP32 accumulate */
+  PT_PREC_FP16X2 = 3   /* tcgen05 tensor cores, data scaled by 2^15 and split hi+lo in FP16
+                          (~22 significant bits), labels in FP16, FP32 accumulate */
 } pt_precision;
 
 typedef struct {
@@ -157,8 +159,8 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
  *   perms, P, maxnull, argmax, counts : host arrays of n_studies entries with
  *               the meaning of pt_maxnull_naive's arguments (device buffers);
  *               counts may be NULL, as may any counts[i].
- *   opts      : precision must be PT_PREC_BF16X2 or PT_PREC_BF16X3
- *               (PT_ERR_UNSUPPORTED for FP32); two_sided applies to all.
+ *   opts      : precision must be a tensor-core one (PT_PREC_BF16X2, _BF16X3 or
+ *               _FP16X2; PT_ERR_UNSUPPORTED for FP32); two_sided applies to all.
  * The first call with a given set of arguments plans the launch (host work and
  * one synchronisation), captures it in a CUDA graph and runs the graph; a
  * later call with the same contexts, buffers and sizes replays that graph
@@ -261,7 +263,8 @@ pt_status pt_sync(pt_ctx* ctx);
  * (NaivePT never forms T; this call is for inspection and for RapidPT's
  * training rows, whose kernels it shares).
  *   perms     : device, int32, P x n (as pt_maxnull_naive), 1 <= P <= 2^31 - 1.
- *   precision : PT_PREC_FP32 (CUDA cores) or PT_PREC_BF16X2 / _BF16X3 (tensor cores).
+ *   precision : PT_PREC_FP32 (CUDA cores) or PT_PREC_BF16X2 / _BF16X3 / _FP16X2
+ *               (tensor cores).
  *   T         : device, float32, P x v row-major in masked order; NaN where the
  *               voxel has no statistic. P * v * 4 bytes, caller-owned.
  * t is formed in FP32 from the FP32 accumulator u as sqrt(k(n-2)) u / sqrt(1 - k u^2).

@@ -16,7 +16,7 @@ import torch
 from .build import LIB
 
 PT_OK, PT_ERR_INVALID, PT_ERR_NOMEM, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_UNSUPPORTED = range(6)
-PT_PREC_FP32, PT_PREC_BF16X2, PT_PREC_BF16X3 = 0, 1, 2
+PT_PREC_FP32, PT_PREC_BF16X2, PT_PREC_BF16X3, PT_PREC_FP16X2 = 0, 1, 2, 3
 _STATUS = {0: "PT_OK", 1: "PT_ERR_INVALID", 2: "PT_ERR_NOMEM", 3: "PT_ERR_CUDA",
            4: "PT_ERR_TIMEOUT", 5: "PT_ERR_UNSUPPORTED"}
 

@@ -252,7 +252,7 @@ pt_status pt_maxnull_naive_ex(pt_ctx* ctx, const int32_t* perms, int64_t P,
       set_error(ctx, "pt_maxnull_naive: need perms, maxnull, argmax non-NULL and 1 <= P < 2^31");
       return PT_ERR_INVALID;
     }
-    if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_BF16X3 || o.two_sided < 0 ||
+    if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_FP16X2 || o.two_sided < 0 ||
         o.two_sided > 1 || o.accumulate_counts < 0 || o.accumulate_counts > 1) {
       set_error(ctx, "pt_maxnull_naive: bad options");
       return PT_ERR_INVALID;
@@ -283,7 +283,7 @@ pt_status pt_maxnull_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
     pt_naive_opts o;
     pt_naive_opts_default(&o);
     if (opts) o = *opts;
-    if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_BF16X3 || o.two_sided < 0 ||
+    if (o.precision < PT_PREC_FP32 || o.precision > PT_PREC_FP16X2 || o.two_sided < 0 ||
         o.two_sided > 1 || o.accumulate_counts < 0 || o.accumulate_counts > 1) {
       pt::set_thread_error("pt_maxnull_naive_batched: bad options");
       return PT_ERR_INVALID;

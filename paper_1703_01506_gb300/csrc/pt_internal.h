@@ -62,6 +62,7 @@ struct pt_ctx {
   pt::Buf Xn32;         // float[v_pad][n_pad]: unit-norm centred data (built on first FP32 use)
   pt::Buf Xnb;          // bf16 pieces 3 x [v_pad/8][n_pad/8][8][8] (built on first tensor-core use)
   bool have_xn32 = false, have_xnb = false;
+  bool xnb_f16 = false;  // Xnb holds the FP16 pieces (PT_PREC_FP16X2), else BF16 pieces
 
   // Per-call workspaces (grown on demand).
   pt::Buf labels;       // float or bf16 labels
@@ -118,7 +119,17 @@ pt_status glm_finalize(pt_ctx* ctx, const int32_t* perms, int64_t P, int two_sid
                        float* maxnull, int32_t* argmax);
 // Operand layouts built from Xraw on first use (FP32 rows / BF16 pieces).
 pt_status ensure_xn32(pt_ctx* ctx);
-pt_status ensure_xnb(pt_ctx* ctx);
+pt_status ensure_xnb(pt_ctx* ctx, int precision);
+
+// Tensor-core operand forms of each precision: data pieces per k-step, label
+// layout (0 FP32 rows, 1 BF16 core matrices, 2 FP16 core matrices), and the
+// power-of-two scale of the FP16 data pieces (|Xn| < 1, so 2^15 Xn < 32768 is
+// in FP16 range and the low piece stays a normal FP16 number for |Xn| >= 2^-18).
+inline int prec_pieces(int precision) { return precision == PT_PREC_BF16X3 ? 3 : 2; }
+inline int prec_label_layout(int precision) {
+  return precision == PT_PREC_FP32 ? 0 : (precision == PT_PREC_FP16X2 ? 2 : 1);
+}
+constexpr float kF16Scale = 32768.0f;
 
 // ---- RapidPT (pt_rapid.cu) ----
 pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int32_t rank,

@@ -205,6 +205,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
+// Same with A = B = F16 (type fields 0): both operands of one MMA share a type.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
 // ---- TMA descriptors (pt_naive_tc.cu) ----
 // 2D view [rows][256] of a BF16 buffer, box [box_rows][256], no swizzle;
 // false if the driver entry point is missing or rejects the view.

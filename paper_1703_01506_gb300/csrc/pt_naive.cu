@@ -7,6 +7,7 @@
 // t_ij >= t_obs_j  <=>  u_ij >= u_obs_j. The kernels therefore reduce u and
 // convert only the P row maxima to t (in FP64) at the end.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -80,7 +81,10 @@ __global__ void labels_kernel(const int32_t* __restrict__ perms, int64_t P, int6
       // subjects is a contiguous 4 KB slab (one TMA stage).
       const int64_t off = (i >> 7) * int64_t(128) * n_pad +
                           ((s >> 3) * 16 + ((i & 127) >> 3)) * 64 + (i & 7) * 8 + (s & 7);
-      static_cast<__nv_bfloat16*>(Lout)[off] = __float2bfloat16(in ? 1.0f : 0.0f);
+      if (layout == 1)
+        static_cast<__nv_bfloat16*>(Lout)[off] = __float2bfloat16(in ? 1.0f : 0.0f);
+      else  // layout 2: FP16 labels for the FP16 data pieces
+        static_cast<__half*>(Lout)[off] = __float2half(in ? 1.0f : 0.0f);
     }
   }
 }
@@ -392,7 +396,7 @@ static int grid_1d(int64_t work, int threads) {
 // observed-set flags; ctx->cnt must already hold v_valid + 1 zeroed words.
 pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout, int64_t* P_pad_out) {
   const int64_t P_pad = (P + 127) / 128 * 128;
-  const size_t elem = layout == 0 ? sizeof(float) : sizeof(__nv_bfloat16);
+  const size_t elem = layout == 0 ? sizeof(float) : sizeof(__nv_bfloat16);  // BF16 / FP16: 2 B
   if (!ctx->labels.ensure(elem * size_t(P_pad) * ctx->n_pad) || !ctx->rowflag.ensure(P_pad) ||
       !ctx->blockflag.ensure(P_pad / 128)) {
     set_error(ctx, "out of device memory (labels)");
@@ -404,7 +408,7 @@ pt_status build_labels(pt_ctx* ctx, const int32_t* perms, int64_t P, int layout,
       ctx->rowflag.as<uint8_t>(), ctx->blockflag.as<uint8_t>(),
       ctx->cnt.as<uint32_t>() + ctx->v_valid, ctx->status.as<uint32_t>());
   PT_LAUNCH_CHECK(ctx);
-  if (ctx->glm_q1 && layout == 1) {
+  if (ctx->glm_q1 && layout != 0) {
     pt_status s = glm_rowscale(ctx, perms, P, P_pad);
     if (s != PT_OK) return s;
   }
@@ -454,7 +458,7 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
   if (counts && !o.accumulate_counts)
     PT_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ctx->v, st));
   int64_t P_pad = 0;
-  s = build_labels(ctx, perms, P, tc ? 1 : 0, &P_pad);
+  s = build_labels(ctx, perms, P, prec_label_layout(o.precision), &P_pad);
   if (s != PT_OK) return s;
   if (ctx->v_valid > 0) {
     if (!tc) {
@@ -463,7 +467,7 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
         s = launch_simt(ctx, ctx->labels.as<float>(), P, 0, o.two_sided, ctx->u_obs.as<float>(),
                         ctx->maxkey.as<unsigned long long>(), ctx->cnt.as<uint32_t>(), nullptr);
     } else {
-      s = ensure_xnb(ctx);
+      s = ensure_xnb(ctx, o.precision);
       if (s == PT_OK)
         s = tc_reduce(ctx, ctx->labels.p, P, o.precision, o.two_sided, ctx->u_obs.as<float>(),
                       ctx->maxkey.as<unsigned long long>(), ctx->cnt.as<uint32_t>());
@@ -555,7 +559,7 @@ static pt_status batched_enqueue(pt_ctx* lead, pt_ctx* const* ctxs, int n,
     if (counts && counts[i] && !o.accumulate_counts)
       PT_CUDA_TRY(lead, cudaMemsetAsync(counts[i], 0, sizeof(uint32_t) * c->v, st));
     int64_t P_pad = 0;
-    pt_status s = build_labels(c, perms[i], P[i], 1, &P_pad);
+    pt_status s = build_labels(c, perms[i], P[i], prec_label_layout(o.precision), &P_pad);
     if (s != PT_OK) return s;
   }
   pt_status s = tc_batch_launch(lead, g_batch.desc, g_batch.groups, o.precision, o.two_sided);
@@ -609,7 +613,7 @@ pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* p
                              int32_t* const* argmax, uint32_t* const* counts) {
   pt_ctx* lead = ctxs[0];
   if (o.precision == PT_PREC_FP32) {
-    set_error(lead, "pt_maxnull_naive_batched runs the tensor-core path (BF16x2 or BF16x3)");
+    set_error(lead, "pt_maxnull_naive_batched runs the tensor-core path (BF16x2/x3, FP16x2)");
     return PT_ERR_UNSUPPORTED;
   }
   pt_status s = tc_supported(lead);
@@ -637,7 +641,7 @@ pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* p
       return PT_ERR_INVALID;
     }
     if (c->v_valid > 0) {
-      s = ensure_xnb(c);
+      s = ensure_xnb(c, o.precision);
       if (s != PT_OK) return s;
     }
     const int64_t P_pad = (P[i] + 127) / 128 * 128;

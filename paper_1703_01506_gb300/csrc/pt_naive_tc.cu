@@ -12,8 +12,10 @@
 //               column = voxel), row max -> packed (u, voxel) atomics, per-voxel
 //               exceedance counts in packed 8-bit registers, optional row writes.
 //
-// Labels are exact in BF16; the data enter as hi + mid (+ lo) BF16 pieces of
-// the FP64 unit-norm value, so the FP32 accumulator carries ~16 or ~24 bits.
+// Labels are exact in BF16 and FP16; the data enter as hi + mid (+ lo) BF16
+// pieces of the unit-norm value (~16 or ~24 bits), or as hi + lo FP16 pieces of
+// 2^15 times it (~22 bits; the accumulator then holds 2^15 u, and the observed
+// values and written rows are scaled by that power of two, exactly).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -98,6 +100,8 @@ struct TcArgs {
   int64_t n_items;
   int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
   int scaled;                 // the studies carry per-row factors (covariate-adjusted t)
+  int f16;                    // FP16 operands (labels and 2^15-scaled data pieces)
+  float uscale, inv_uscale;   // accumulator = uscale * u (2^15 for FP16 pieces, else 1)
   float k_f, ct_f;
   uint32_t* status;
 };
@@ -318,8 +322,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       uint32_t j = 0, ms = 0, mph = 0;  // block counter; ring stage and phase
       int w = 0;
-      const uint32_t idesc = idesc_bf16_f32(128, NT);
-      const uint32_t idesc_w = idesc_bf16_f32(128, (NACC == 2 ? 2 : PIECES) * NT);
+      const uint32_t idesc = a.f16 ? idesc_f16_f32(128, NT) : idesc_bf16_f32(128, NT);
+      const int nw = (NACC == 2 ? 2 : PIECES) * NT;
+      const uint32_t idesc_w = a.f16 ? idesc_f16_f32(128, nw) : idesc_bf16_f32(128, nw);
       // L stage: k-group major (k-groups 2 KB apart, 8-row groups adjacent);
       // Xn tile: row-group major (k-groups adjacent, 8-row groups n_pad/8 x 128 B apart).
       const uint64_t adesc0 = smem_desc(smem_addr(ls), 16 * 128, 128);
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = etid; c < NT; c += 32 * kEpiWarps) {
         float x = INFINITY;
         if (do_reduce && v0 + c < V) {
-          x = u_obs[v0 + c];
+          x = u_obs[v0 + c] * a.uscale;  // power of two: exact
           if (TWO) x = fabsf(x);
         }
         su[c] = x;
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int jj = 0; jj < CHK; ++jj) {
               if (g0 + jj < V) {
-                const float u = __uint_as_float(r[jj]);
+                const float u = __uint_as_float(r[jj]) * a.inv_uscale;  // exact
                 float val = u;
                 if (a.write_mode == 2) {
                   const float den = 1.0f - a.k_f * u * u;
@@ -641,7 +646,8 @@ bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int kps, int64_t t
 // count. descs: device copy of the descriptors (filled by the caller).
 pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_items, int NT,
                          int stages, int kps, int pieces, int n_pad_max, int do_reduce,
-                         int write_mode, int two_sided, float kf, float ctf, int scaled = 0) {
+                         int write_mode, int two_sided, float kf, float ctf, int scaled = 0,
+                         int f16 = 0) {
   if (scaled && (write_mode || !do_reduce)) {
     set_error(ctx, "covariate-adjusted statistic: reduce-only launches");
     return PT_ERR_UNSUPPORTED;
@@ -663,6 +669,9 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   a.k_f = kf;
   a.ct_f = ctf;
   a.scaled = scaled;
+  a.f16 = f16;
+  a.uscale = f16 ? kF16Scale : 1.0f;
+  a.inv_uscale = f16 ? 1.0f / kF16Scale : 1.0f;
   a.status = ctx->status.as<uint32_t>();
   const int sms = num_sms(ctx->device);
   const int grid = int(n_items < sms ? n_items : sms);
@@ -681,7 +690,7 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
 pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int do_reduce,
                         int write_mode, int two_sided, const float* u_obs,
                         unsigned long long* maxkey, uint32_t* cnt, float* uout,
-                        const pt_tc_config& cfg) {
+                        const pt_tc_config& cfg, int f16) {
   const int NT = cfg.voxel_tile;
   TcStudy st;
   if (!fill_study(ctx, Lb, P, NT, cfg.ksteps_per_stage,
@@ -699,13 +708,13 @@ pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int 
   const int64_t items = ((st.v + NT - 1) / NT) * st.n_chunks;
   return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, cfg.stages,
                         cfg.ksteps_per_stage, pieces, ctx->n_pad, do_reduce, write_mode,
-                        two_sided, float(ctx->k), float(ctx->c_t), ctx->glm_q1 ? 1 : 0);
+                        two_sided, float(ctx->k), float(ctx->c_t), ctx->glm_q1 ? 1 : 0, f16);
 }
 
 pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
                     int write_mode, int two_sided, const float* u_obs,
                     unsigned long long* maxkey, uint32_t* cnt, float* uout) {
-  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int pieces = prec_pieces(precision);
   pt_tc_config cfg;
   if (!tc_default_config(ctx->n_pad, pieces, &cfg)) {
     set_error(ctx, "tensor-core path: n too large for the resident data tile");
@@ -715,7 +724,7 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
   // recorded for this shape; row-writing launches keep the default.
   if (do_reduce && !write_mode) tune_find(ctx->n_pad, precision, two_sided, ctx->v_valid, P, &cfg);
   return tc_launch_cfg(ctx, Lb, P, pieces, do_reduce, write_mode, two_sided, u_obs, maxkey, cnt,
-                       uout, cfg);
+                       uout, cfg, precision == PT_PREC_FP16X2 ? 1 : 0);
 }
 
 }  // namespace
@@ -754,7 +763,7 @@ pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int wri
 pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int n,
                         const pt_naive_opts& o, Buf& descbuf, std::vector<char>& host_desc,
                         std::vector<TcGroup>& groups) {
-  const int pieces = o.precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int pieces = prec_pieces(o.precision);
   std::vector<pt_tc_config> cfg(n);
   for (int i = 0; i < n; ++i) {
     if (!tc_default_config(ctxs[i]->n_pad, pieces, &cfg[i])) {
@@ -820,11 +829,11 @@ pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int
 
 pt_status tc_batch_launch(pt_ctx* lead, const Buf& descbuf, const std::vector<TcGroup>& groups,
                           int precision, int two_sided) {
-  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int pieces = prec_pieces(precision);
   for (const TcGroup& g : groups) {
     pt_status s = launch_studies(lead, static_cast<const TcStudy*>(descbuf.p) + g.first, g.count,
                                  g.items, g.NT, g.stages, g.kps, pieces, g.n_pad_max, 1, 0,
-                                 two_sided, 0.0f, 0.0f);
+                                 two_sided, 0.0f, 0.0f, 0, precision == PT_PREC_FP16X2 ? 1 : 0);
     if (s != PT_OK) return s;
   }
   return PT_OK;
@@ -875,7 +884,7 @@ bool tc_config_valid(const pt_tc_config& c, int n_pad, int pieces) {
 // twice after the workspaces are cleared, and its faster run counts.
 pt_status tc_autotune(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int two_sided,
                       pt_tc_config* best, double* best_ms, std::vector<TcTrial>* trials) {
-  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int pieces = prec_pieces(precision);
   std::vector<pt_tc_config> cand;
   pt_tc_config d;
   if (!tc_default_config(ctx->n_pad, pieces, &d)) {
@@ -922,7 +931,7 @@ pt_status tc_autotune(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int
       PT_CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
       pt_status r = tc_launch_cfg(ctx, Lb, P, pieces, 1, 0, two_sided, ctx->u_obs.as<float>(),
                                   ctx->maxkey.as<unsigned long long>(), ctx->cnt.as<uint32_t>(),
-                                  nullptr, c);
+                                  nullptr, c, precision == PT_PREC_FP16X2 ? 1 : 0);
       if (r != PT_OK) return r;
       PT_CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
       PT_CUDA_TRY(ctx, cudaEventSynchronize(e1));

@@ -9,6 +9,7 @@
 // Eq. (5) is t = sqrt(k (n-2)) u / sqrt(1 - k u^2), k = 1/n1 + 1/n2, because
 // mean1 - mean2 = k s1 and the within-group SS = SS - k s1^2 with s1 = u sqrt(SS).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -387,6 +388,45 @@ __global__ void build_xnb_kernel(const float* __restrict__ Xraw, int n, int n_pa
   }
 }
 
+// FP16 pieces of the scaled value ys = 2^15 y: hi = fp16(ys), lo = fp16(ys - hi)
+// (the residual is exact in FP32), same core-matrix layout as the BF16 pieces.
+// |y| < 1, so |ys| < 32768 lies in FP16 range; lo carries the next 11 bits.
+__global__ void build_xnh_kernel(const float* __restrict__ Xraw, int n, int n_pad,
+                                 const int32_t* __restrict__ valid_map, int64_t v_valid,
+                                 int64_t v_pad, const float4* __restrict__ vstat,
+                                 __half* __restrict__ Xnh) {
+  const int kg_n = n_pad >> 3;
+  const int64_t piece = v_pad * n_pad;
+  const int64_t cg = blockIdx.x;  // row group
+  for (int idx = threadIdx.x; idx < kg_n * 8; idx += blockDim.x) {
+    const int r = idx & 7, kg = idx >> 3;
+    const int64_t c = cg * 8 + r;
+    float y[8];
+    if (c < v_valid) {
+      const float4 st = vstat[c];
+      const float4* src =
+          reinterpret_cast<const float4*>(Xraw + int64_t(valid_map[c]) * n_pad + kg * 8);
+      const float4 a = src[0], b = src[1];
+      const float xv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        y[q] = (kg * 8 + q < n) ? unit_centre(xv[q], st) * kF16Scale : 0.0f;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) y[q] = 0.0f;
+    }
+    __align__(16) __half hi[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      hi[q] = __float2half_rn(y[q]);
+      lo[q] = __float2half_rn(y[q] - __half2float(hi[q]));
+    }
+    const int64_t off = (cg * kg_n + kg) * 64 + r * 8;
+    *reinterpret_cast<uint4*>(Xnh + off) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(Xnh + piece + off) = *reinterpret_cast<const uint4*>(lo);
+  }
+}
+
 __global__ void t_obs_to_float_kernel(const double* __restrict__ t64, float* __restrict__ out,
                                       int64_t v) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < v;
@@ -532,16 +572,31 @@ pt_status ensure_xn32(pt_ctx* ctx) {
   return PT_OK;
 }
 
-pt_status ensure_xnb(pt_ctx* ctx) {
-  if (ctx->have_xnb) return PT_OK;
+pt_status ensure_xnb(pt_ctx* ctx, int precision) {
+  const bool f16 = precision == PT_PREC_FP16X2;
+  if (ctx->have_xnb && ctx->xnb_f16 == f16) return PT_OK;
+  ctx->have_xnb = false;
   const size_t elems = size_t(ctx->v_pad) * ctx->n_pad;
   if (!ctx->Xnb.ensure(sizeof(__nv_bfloat16) * 3 * elems)) return nomem(ctx, "Xnb");
+  const int xnb_threads = std::min(256, (ctx->n_pad + 31) / 32 * 32);
+  if (f16) {
+    if (ctx->glm_q1) {
+      set_error(ctx, "PT_PREC_FP16X2 is not available with covariates (use BF16X2/X3)");
+      return PT_ERR_UNSUPPORTED;
+    }
+    build_xnh_kernel<<<unsigned(ctx->v_pad / 8), xnb_threads, 0, ctx->stream>>>(
+        ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,
+        ctx->v_pad, ctx->vstat.as<float4>(), ctx->Xnb.as<__half>());
+    PT_LAUNCH_CHECK(ctx);
+    ctx->have_xnb = ctx->xnb_f16 = true;
+    return PT_OK;
+  }
+  ctx->xnb_f16 = false;
   if (ctx->glm_q1) {
     pt_status s = glm_build_xnb(ctx);
     if (s == PT_OK) ctx->have_xnb = true;
     return s;
   }
-  const int xnb_threads = std::min(256, (ctx->n_pad + 31) / 32 * 32);
   build_xnb_kernel<<<unsigned(ctx->v_pad / 8), xnb_threads, 0, ctx->stream>>>(
       ctx->Xraw.as<float>(), ctx->n, ctx->n_pad, ctx->valid_map.as<int32_t>(), ctx->v_valid,
       ctx->v_pad, ctx->vstat.as<float4>(), ctx->Xnb.as<__nv_bfloat16>());

@@ -1317,7 +1317,7 @@ pt_status check_rapid_args(pt_ctx* ctx, int32_t rank, double sample_rate, const 
   }
   if (o.train_passes < 1 || o.qr_every < 1 || o.admm_iters < 1 || !(o.admm_rho > 0.0f) ||
       !(o.step > 0.0f) || o.shift_mode < 0 || o.shift_mode > 1 || o.precision < 0 ||
-      o.precision > 2) {
+      o.precision > PT_PREC_FP16X2) {
     set_error(ctx, "RapidPT: bad options");
     return PT_ERR_INVALID;
   }
@@ -1446,8 +1446,8 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
     const bool tc = o.precision != PT_PREC_FP32;
     if (tc) {
       s = tc_supported(ctx);
-      if (s == PT_OK) s = ensure_xnb(ctx);
-      if (s == PT_OK) s = build_labels(ctx, perms, ell, 1, &P_pad);
+      if (s == PT_OK) s = ensure_xnb(ctx, o.precision);
+      if (s == PT_OK) s = build_labels(ctx, perms, ell, prec_label_layout(o.precision), &P_pad);
       if (s == PT_OK)
         s = tc_rows(ctx, ctx->labels.p, ell, o.precision, 2, Tex.as<float>(), 1, 0,
                     ctx->u_obs.as<float>(), ctx->maxkey.as<unsigned long long>(),
@@ -1797,8 +1797,8 @@ pt_status t_rows_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int precisio
   pt_status s;
   if (precision != PT_PREC_FP32) {
     s = tc_supported(ctx);
-    if (s == PT_OK) s = ensure_xnb(ctx);
-    if (s == PT_OK) s = build_labels(ctx, perms, P, 1, &P_pad);
+    if (s == PT_OK) s = ensure_xnb(ctx, precision);
+    if (s == PT_OK) s = build_labels(ctx, perms, P, prec_label_layout(precision), &P_pad);
     if (s == PT_OK)
       s = tc_rows(ctx, ctx->labels.p, P, precision, 2, out, 0, 0, nullptr, nullptr, nullptr);
   } else {
@@ -1849,7 +1849,7 @@ pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precis
     pt::set_error(ctx, "pt_t_rows: NULL argument");
     return PT_ERR_INVALID;
   }
-  if (P < 1 || P > INT32_MAX || precision < PT_PREC_FP32 || precision > PT_PREC_BF16X3) {
+  if (P < 1 || P > INT32_MAX || precision < PT_PREC_FP32 || precision > PT_PREC_FP16X2) {
     pt::set_error(ctx, "pt_t_rows: need 1 <= P <= 2^31-1 and a valid precision");
     return PT_ERR_INVALID;
   }

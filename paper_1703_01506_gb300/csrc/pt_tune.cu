@@ -59,7 +59,7 @@ pt_status tune_one(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_
                    pt_tc_config* chosen, double* chosen_ms) {
   pt_status s = tc_supported(ctx);
   if (s != PT_OK) return s;
-  const int pieces = o.precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int pieces = prec_pieces(o.precision);
   pt_tc_config best;
   if (!tc_default_config(ctx->n_pad, pieces, &best)) {
     set_error(ctx, "tensor-core path: n too large for the resident data tile");
@@ -75,8 +75,8 @@ pt_status tune_one(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_
     PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->cnt.p, 0, sizeof(uint32_t) * (ctx->v_valid + 1),
                                      ctx->stream));
     int64_t P_pad = 0;
-    s = build_labels(ctx, perms, P, 1, &P_pad);
-    if (s == PT_OK) s = ensure_xnb(ctx);
+    s = build_labels(ctx, perms, P, prec_label_layout(o.precision), &P_pad);
+    if (s == PT_OK) s = ensure_xnb(ctx, o.precision);
     if (s == PT_OK) s = tc_autotune(ctx, ctx->labels.p, P, o.precision, o.two_sided, &best,
                                     &best_ms, nullptr);
     if (s != PT_OK) return s;
@@ -90,7 +90,8 @@ pt_status tune_one(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naive_
 }
 
 bool opts_ok(const pt_naive_opts& o) {
-  return (o.precision == PT_PREC_BF16X2 || o.precision == PT_PREC_BF16X3) &&
+  return (o.precision == PT_PREC_BF16X2 || o.precision == PT_PREC_BF16X3 ||
+          o.precision == PT_PREC_FP16X2) &&
          (o.two_sided == 0 || o.two_sided == 1);
 }
 
@@ -122,7 +123,7 @@ pt_status pt_autotune_naive(pt_ctx* ctx, const int32_t* perms, int64_t P,
     if (!perms || P < 1 || P > INT32_MAX || !pt::opts_ok(o)) {
       pt::set_error(ctx,
                     "pt_autotune_naive: need perms non-NULL, 1 <= P < 2^31 and a tensor-core "
-                    "precision (BF16X2 or BF16X3)");
+                    "precision (BF16X2, BF16X3 or FP16X2)");
       return PT_ERR_INVALID;
     }
     if (cudaSetDevice(ctx->device) != cudaSuccess) {
@@ -187,10 +188,10 @@ pt_status pt_autotune_naive_batched(pt_ctx* const* ctxs, int32_t n_studies,
 int32_t pt_tune_lookup(int32_t n, int32_t precision, int32_t two_sided, int64_t v, int64_t P,
                        pt_tc_config* out) {
   if (!out || n < 3 || n > 1024 || v < 1 || P < 1 || precision < PT_PREC_BF16X2 ||
-      precision > PT_PREC_BF16X3 || two_sided < 0 || two_sided > 1)
+      precision > PT_PREC_FP16X2 || two_sided < 0 || two_sided > 1)
     return -1;
   const int n_pad = pt::pad16(n);
-  const int pieces = precision == PT_PREC_BF16X2 ? 2 : 3;
+  const int pieces = pt::prec_pieces(precision);
   if (!pt::tc_default_config(n_pad, pieces, out)) return -1;
   return pt::tune_find(n_pad, precision, two_sided, v, P, out) ? 1 : 0;
 }
@@ -198,12 +199,12 @@ int32_t pt_tune_lookup(int32_t n, int32_t precision, int32_t two_sided, int64_t 
 pt_status pt_tune_set(int32_t n, int32_t precision, int32_t two_sided, int64_t v, int64_t P,
                       const pt_tc_config* cfg) {
   if (!cfg || n < 3 || n > 1024 || v < 1 || P < 1 || precision < PT_PREC_BF16X2 ||
-      precision > PT_PREC_BF16X3 || two_sided < 0 || two_sided > 1) {
+      precision > PT_PREC_FP16X2 || two_sided < 0 || two_sided > 1) {
     pt::set_thread_error("pt_tune_set: bad shape or options");
     return PT_ERR_INVALID;
   }
   const int n_pad = pt::pad16(n);
-  if (!pt::tc_config_valid(*cfg, n_pad, precision == PT_PREC_BF16X2 ? 2 : 3)) {
+  if (!pt::tc_config_valid(*cfg, n_pad, pt::prec_pieces(precision))) {
     pt::set_thread_error("pt_tune_set: configuration does not fit this n (voxel_tile as n "
                          "fixes it, ksteps_per_stage 1/2/4/8, 2 <= stages <= what fits, "
                          "1 <= items_per_sm <= 64)");
@@ -276,8 +277,8 @@ pt_status pt_tune_load(const char* path) {
                     &k.two_sided, &k.vb, &k.pb, &e.cfg.voxel_tile, &e.cfg.stages,
                     &e.cfg.ksteps_per_stage, &e.cfg.items_per_sm, &e.ms) != 10 ||
         k.n_pad < 16 || k.n_pad % 16 != 0 || k.n_pad > 1024 || k.precision < PT_PREC_BF16X2 ||
-        k.precision > PT_PREC_BF16X3 || k.two_sided < 0 || k.two_sided > 1 ||
-        !pt::tc_config_valid(e.cfg, k.n_pad, k.precision == PT_PREC_BF16X2 ? 2 : 3)) {
+        k.precision > PT_PREC_FP16X2 || k.two_sided < 0 || k.two_sided > 1 ||
+        !pt::tc_config_valid(e.cfg, k.n_pad, pt::prec_pieces(k.precision))) {
       err = "malformed or invalid entry on line " + std::to_string(lineno);
       break;
     }

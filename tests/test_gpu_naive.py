@@ -14,16 +14,19 @@ from paper_1703_01506_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-PRECS = [0, 1, 2]  # PT_PREC_FP32, PT_PREC_BF16X2, PT_PREC_BF16X3
+PRECS = [0, 1, 2, 3]  # PT_PREC_FP32, PT_PREC_BF16X2, PT_PREC_BF16X3, PT_PREC_FP16X2
 
 
 def tie_rel(precision, n):
     """Bound on |error of u - u_obs| per unit l1 norm of the unit-norm voxel:
-    FP32 data and accumulation (FP32, BF16x3) or 16-bit data pieces (BF16x2),
-    for both the relabelled and the observed group sum."""
+    FP32 data and accumulation (FP32, BF16x3), 16-bit data pieces (BF16x2) or
+    22-bit FP16 pieces (FP16x2: |2^15 y - hi - lo| <= 2^-22 |2^15 y|), for both
+    the relabelled and the observed group sum."""
     eps24 = 2.0 ** -24
     if precision == 1:
         return 2.0 * (2.0 ** -17 + (n + 4) * eps24)
+    if precision == 3:
+        return 2.0 * (2.0 ** -22 + (n + 4) * eps24)
     return 2.0 * (n + 4) * eps24
 
 
@@ -176,10 +179,11 @@ def test_deterministic_repeat(cuda_lib):
             np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("precision", [2, 3])
 @pytest.mark.parametrize("name", ["brain_n100_v232k", "brain_n200_v500k", "brain_n400_v600k"])
-def test_full_size_sampled(cuda_lib, name):
+def test_full_size_sampled(cuda_lib, name, precision):
     """The full-size workloads (n=100 / 232k voxels / 10k relabellings, n=200 /
-    500k / 100k, n=400 / 600k / 100k; split-BF16x3) in the launch configuration
+    500k / 100k, n=400 / 600k / 100k; split BF16x3 and FP16x2) in the launch configuration
     bench.py times (autotuned): sampled rows against the oracle's full-row
     maxima, sampled voxels against the oracle's counts over all rows."""
     B = cuda_lib
@@ -189,8 +193,8 @@ def test_full_size_sampled(cuda_lib, name):
     v = B.pt_num_voxels(ctx)
     pd = torch.as_tensor(perms).cuda()
     B.pt_tune_clear()
-    B.pt_autotune_naive(ctx, pd, B.naive_opts(B.PT_PREC_BF16X3))
-    mx, am, ct = B.maxnull_naive(ctx, pd, precision=B.PT_PREC_BF16X3)
+    B.pt_autotune_naive(ctx, pd, B.naive_opts(precision))
+    mx, am, ct = B.maxnull_naive(ctx, pd, precision=precision)
     B.pt_tune_clear()
     mx = mx.cpu().numpy().astype(np.float64)
     am = am.cpu().numpy()
@@ -201,10 +205,10 @@ def test_full_size_sampled(cuda_lib, name):
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(perms.shape[0], 8, replace=False))
     n = Xm.shape[0]
-    ref = oracle.naive(Xm, n1, perms[rows], tie_rel=tie_rel(2, n))
-    check(ref, (mx[rows], am[rows], np.zeros(0, np.int64)), 2, name + " rows")
+    ref = oracle.naive(Xm, n1, perms[rows], tie_rel=tie_rel(precision, n))
+    check(ref, (mx[rows], am[rows], np.zeros(0, np.int64)), precision, name + " rows")
     vox = np.sort(rng.choice(v, 32, replace=False))
-    refc = oracle.naive(Xm[:, vox], n1, perms, tie_rel=tie_rel(2, n))
+    refc = oracle.naive(Xm[:, vox], n1, perms, tie_rel=tie_rel(precision, n))
     dc = np.abs(ct[vox] - refc.counts.astype(np.int64))
     assert np.all(dc <= refc.near.astype(np.int64)), dc
     ctx.close()

@@ -6,8 +6,9 @@ sqrt(1 - k u^2) in FP32; the oracle computes Eq. 5 per entry in FP64. These
 are RapidPT's training-row kernels (T_ex).
 
 Tolerances:
-* FP32 and BF16x3 (FP32-class): |t_gpu - t| <= 1e-5 max(|t|, 1) (1e-5
-  relative, absolute floor 1e-5 near t = 0).
+* FP32, BF16x3 and FP16x2 (FP32-class; FP16x2 keeps ~22 bits of each
+  value): |t_gpu - t| <= 1e-5 max(|t|, 1) (1e-5 relative, absolute floor
+  1e-5 near t = 0).
 * BF16x2 keeps 16 bits of each data value, so its u carries up to
   tau_j = (2^-17 + (n+4) 2^-24) ||Xn_j||_1 of error; through the map that is
   |dt/du| tau_j = sqrt(k(n-2)) (1 - k u^2)^(-3/2) tau_j, plus FP32 rounding of t.
@@ -43,7 +44,7 @@ def check_rows(X, n1, perms, T, precision):
     assert np.all(np.isnan(T[:, ~valid]))
     ref, T = ref[:, valid], T[:, valid]
     err = np.abs(T - ref)
-    if precision in (0, 2):
+    if precision in (0, 2, 3):
         bound = 1e-5 * np.maximum(np.abs(ref), 1.0)
     else:
         k = 1.0 / n1 + 1.0 / (n - n1)
@@ -59,7 +60,7 @@ def check_rows(X, n1, perms, T, precision):
     return float(np.max(err / np.maximum(np.abs(ref), 1.0)))
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 @pytest.mark.parametrize("n,n1,v,P", [(20, 10, 2000, 300), (37, 15, 3001, 257),
                                       (100, 50, 1500, 130), (200, 100, 700, 129)])
 def test_t_rows_match_oracle(cuda_lib, precision, n, n1, v, P):
@@ -72,7 +73,7 @@ def test_t_rows_match_oracle(cuda_lib, precision, n, n1, v, P):
     print("n=%d v=%d P=%d precision=%d: max |dt|/max(|t|,1) = %.3g" % (n, v, P, precision, rel))
 
 
-@pytest.mark.parametrize("precision", [0, 2])
+@pytest.mark.parametrize("precision", [0, 2, 3])
 def test_t_rows_masked_brain_field(cuda_lib, precision):
     """A masked smoothed field in [0, 1] (gray-matter-like values): rows come
     back in masked order."""
