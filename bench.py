@@ -54,8 +54,9 @@ import numpy as np  # noqa: E402
 METRIC = "T entries/s (perm x voxel t) & max-null wall time, RapidPT vs NaivePT, 1 GB300"
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one tuned launch of the
 # fused kernel on brain_n100_v232k, per precision (BF16x3: 160.21 MB read +
-# 4.67 MB written); None where no capture of the current kernel exists.
-TRAFFIC_BYTES = {2: 164.89e6, 3: None}
+# 4.67 MB written; FP16x2: 108.21 MB read + 3.54 MB written); None where no
+# capture of the current kernel exists.
+TRAFFIC_BYTES = {2: 164.89e6, 3: 111.75e6}
 WORKLOAD = "brain_n100_v232k"
 # NaivePT arithmetic of the RapidPT-vs-NaivePT and large legs: FP16x2 (two FP16
 # pieces of 2^15 Xn), the fastest path that meets the FP32-class tolerances.
