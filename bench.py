@@ -779,7 +779,7 @@ def run_ours(args):
         n_pad = (n + 15) // 16 * 16
         hw = 2.0 * pieces * n_pad * entries / (avg_kern_ms * 1e-3) / 1e12
         # DRAM bytes per launch of this kernel from the ncu capture summarised in
-        # profiles/tc_contract_kernel_brain_n100_v232k.md (BF16x3, tuned launch).
+        # profiles/tc_contract_kernel_bf16x3_brain_n100_v232k.md (BF16x3, tuned launch).
         traffic = TRAFFIC_BYTES.get(prec) if tuned is not None else None
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": traffic,
