@@ -362,10 +362,48 @@ def rapid_leg(dev, B, synth, torch, passes=1, rows=None):
     X, mask, n1 = w["X"], w["mask"], w["n1"]
     perms = torch.as_tensor(w["perms"][:rows] if rows else w["perms"]).to(dev)
     P, r, ell, eta = perms.shape[0], w["rank"], w["n_train"], w["sample_rate"]
-    out, v, _, _ = rapid_vs_naive(dev, B, torch, X, mask, n1, perms, r, ell, eta, passes)
+    out, v, a_naive, _ = rapid_vs_naive(dev, B, torch, X, mask, n1, perms, r, ell, eta, passes)
     out = {"workload": "%s: n=200 (100/100), %d voxels, no signal, P=%d, r=%d, n_train=%d, "
                        "sample_rate=%g" % (name, v, P, r, ell, eta), **out}
+    out["recovery_updates"] = recovery_updates_study(dev, B, torch, X, mask, n1, perms, r, ell,
+                                                     eta, a_naive, passes)
     return out
+
+
+def recovery_updates_study(dev, B, torch, X, mask, n1, perms, r, ell, eta, a_naive, passes,
+                           rows=2000):
+    """U updates during recovery (pt_rapid_opts.rec_step = 1, sequential) against
+    the frozen U of Alg. 2, on the first `rows` recovery relabellings after the
+    same training: accuracy of each against NaivePT's maxima of those rows, and
+    the time of each recovery."""
+    stream = torch.cuda.current_stream(dev)
+    c = B.pt_prepare(X, n1, mask, stream=stream)
+    V = B.pt_num_valid_voxels(c)
+    U = torch.empty((V, r), dtype=torch.float32, device=dev)
+    opts = B.rapid_opts(train_passes=passes)
+    sub = perms[:ell + rows]
+    tmax = torch.empty(ell, dtype=torch.float32, device=dev)
+    info = B.pt_rapid_train(c, sub, ell, r, eta, opts, U, tmax)
+    res = {}
+    ref = a_naive[ell:ell + rows]
+    for name, step in (("frozen", 0.0), ("updates", 1.0)):
+        o = B.rapid_opts(train_passes=passes, rec_step=step)
+        mx = torch.empty(rows, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        B.pt_rapid_recover(c, sub, ell, U, r, eta, info.sigma, info.mu, o, mx)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        b = mx.cpu().numpy().astype(np.float64)
+        res[name] = {"recover_ms": dt * 1e3, "kl": hist_kl(ref, b),
+                     "sd_ratio": float(b.std() / ref.std()),
+                     "mean_diff": float(b.mean() - ref.mean()),
+                     **{"fwer%g" % al: fwer_thr(b, al) / fwer_thr(ref, al) - 1.0
+                        for al in (0.05, 0.01)}}
+    c.close()
+    res["rows"] = "recovery relabellings %d..%d of the same workload and training" % (
+        ell, ell + rows - 1)
+    return res
 
 
 def large_leg(dev, B, synth, torch, passes=1):

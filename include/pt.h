@@ -191,6 +191,12 @@ typedef struct {
   int32_t shift_mode;   /* 0: mu = largest training residual (Alg. 2 as printed);
                            1 (default): mu = mean shift of the maximum (Sec. 4.1) */
   uint64_t seed;        /* key of the Philox4x32-10 draws; default 1 */
+  float rec_step;       /* U during recovery: 0 (default) frozen, as Alg. 2 prints it;
+                           > 0: after each recovery relabelling's maximum is formed, U takes
+                           the training step (geodesic, theta = rec_step * atan(||r||/||w||))
+                           towards that relabelling's fit residual on its samples, in row
+                           order, with QR every qr_every such steps (recovery becomes
+                           sequential: one step and one reconstruction per relabelling) */
 } pt_rapid_opts;
 
 typedef struct {
@@ -201,7 +207,8 @@ typedef struct {
 } pt_rapid_info;
 
 /* Fills *o with the defaults above (one training pass, QR every 100 steps,
- * 30 ADMM iterations at rho = 2, step 1, shift_mode 1, seed 1, BF16X3). */
+ * 30 ADMM iterations at rho = 2, step 1, shift_mode 1, seed 1, BF16X3, U frozen
+ * during recovery). */
 void pt_rapid_opts_default(pt_rapid_opts* o);
 
 /*
@@ -242,7 +249,8 @@ pt_status pt_rapid_train(pt_ctx* ctx, const int32_t* perms, int32_t n_train, int
  * pt_rapid_recover -- the recovery phase alone (Sec. 4.2) for rows
  * first_row..P-1 of perms with a given basis U (v_valid x rank, device), sigma and
  * mu. Draws are keyed by the row index, so ranges can be split across calls or
- * devices with identical results.
+ * devices with identical results (with opts->rec_step = 0; with U updates the
+ * rows depend on the rows before them and the given U is the state at first_row).
  *   maxnull: device float32[P - first_row].  W_out: device float32[P - first_row][rank]
  *   or NULL (weights). Synchronises the stream.
  */

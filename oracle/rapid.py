@@ -173,12 +173,16 @@ def geodesic_step(U, idx, b, w, step):
 
 class RapidOpts:
     def __init__(self, train_passes=1, qr_every=100, admm_iters=30, admm_rho=2.0, step=1.0,
-                 shift_mode=1, seed=1, stat="t"):
+                 shift_mode=1, seed=1, stat="t", rec_step=0.0):
         """stat: the statistic whose permutation matrix is modelled, "t" or "u"
-        (see _stat_fns); maxima are reported as t either way."""
+        (see _stat_fns); maxima are reported as t either way. rec_step: 0 keeps
+        U frozen during recovery (Alg. 2 as printed); > 0 takes a geodesic
+        step of that size after every recovery fit (sequential updates, the
+        training step applied to the recovery samples)."""
         self.train_passes, self.qr_every = train_passes, qr_every
         self.admm_iters, self.admm_rho, self.step = admm_iters, admm_rho, step
         self.shift_mode, self.seed, self.stat = shift_mode, seed, stat
+        self.rec_step = rec_step
 
 
 class RapidResult:
@@ -318,7 +322,13 @@ def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=F
     """Recovery phase (Sec. 4.2, Alg. 2 RECOVERY) for relabellings rows_sel with
     U frozen: exact statistic at the m sampled voxels, w = Complete(U, t, Omega),
     m_i = max_j (U w + sigma z)_j + mu (mapped to t when the modelled
-    statistic is u)."""
+    statistic is u).
+
+    With opts.rec_step > 0 the relabellings are taken in order and, after
+    each one's maximum is formed with the current U, U takes the training
+    step (geodesic_step with step rec_step) towards that relabelling's fit
+    residual on its samples; QR every qr_every recovery steps. The rows then
+    depend on the ones before them."""
     o = opts or RapidOpts()
     X = np.asarray(X)
     _, Xt, _, entries, to_t = _stat_fns(X, n1, perms, o)
@@ -326,6 +336,7 @@ def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=F
     dr = draws(o.seed)
     out = np.empty(len(rows_sel))
     ws = []
+    steps = 0
     for k, i in enumerate(rows_sel):
         idx = dr.index(TAG_REC, np.arange(m), int(i), 0, V)
         tt = entries(int(i), idx)
@@ -333,6 +344,11 @@ def rapid_recover(X, n1, perms, rows_sel, U, sigma, mu, m, opts=None, return_w=F
         ws.append(w)
         z = dr.voxel_normal(TAG_NOISE, np.arange(V), int(i))
         out[k] = to_t(np.max(U @ w + sigma * z) + mu)
+        if o.rec_step > 0.0:
+            U = geodesic_step(U, idx, tt, w, o.rec_step)
+            steps += 1
+            if steps % o.qr_every == 0:
+                U = qr_posdiag(U)
     return (out, np.array(ws)) if return_w else out
 
 

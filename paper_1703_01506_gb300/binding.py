@@ -44,7 +44,8 @@ class pt_rapid_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("train_passes", ctypes.c_int32),
                 ("qr_every", ctypes.c_int32), ("admm_iters", ctypes.c_int32),
                 ("admm_rho", ctypes.c_float), ("step", ctypes.c_float),
-                ("shift_mode", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("shift_mode", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("rec_step", ctypes.c_float)]
 
 
 class pt_rapid_info(ctypes.Structure):

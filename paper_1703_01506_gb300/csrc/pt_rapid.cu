@@ -539,6 +539,8 @@ struct CluStepArgs {
   const float* pend_upd;   // nullable: coefficients of the previous step's update (not yet
   const float* pend_lift;  // applied to U); the sampled rows are updated here on the fly
   const float* Trow;  // t of this training column (V values)
+  const float* samp;  // nullable: t at the step's draws (recovery rows), else Trow[draw]
+  uint32_t tag;       // draw tag of the step's samples (training or recovery)
   uint32_t V;
   int R, m, CL;
   uint32_t k0, k1;
@@ -594,17 +596,17 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
   const int tid = threadIdx.x;
   if (a.clear_pass >= 0)  // ordered before this step's lift adds by the fit's cluster barriers
     for (int q = tid; q < mloc; q += blockDim.x)
-      a.lift[draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q0 + q), uint32_t(a.clear_col),
+      a.lift[draw_index(a.k0, a.k1, a.tag, uint32_t(q0 + q), uint32_t(a.clear_col),
                         uint32_t(a.clear_pass), a.V)] = 0.0f;
   if (a.pend_upd) {  // the previous update's coefficients, staged in red (free here)
     for (int e = tid; e < 3 * RP + 2; e += blockDim.x) f.red[e] = a.pend_upd[e];
     __syncthreads();
   }
   for (int q = tid; q < mloc; q += blockDim.x) {
-    const uint32_t j = draw_index(a.k0, a.k1, TAG_TRAIN, uint32_t(q0 + q), uint32_t(a.col),
+    const uint32_t j = draw_index(a.k0, a.k1, a.tag, uint32_t(q0 + q), uint32_t(a.col),
                                   uint32_t(a.pass), a.V);
     f.idx[q] = int32_t(j);
-    f.b[q] = a.Trow[j];
+    f.b[q] = a.samp ? a.samp[q0 + q] : a.Trow[j];
     const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
     float4 x[RP / 4];
 #pragma unroll
@@ -1317,7 +1319,7 @@ pt_status check_rapid_args(pt_ctx* ctx, int32_t rank, double sample_rate, const 
   }
   if (o.train_passes < 1 || o.qr_every < 1 || o.admm_iters < 1 || !(o.admm_rho > 0.0f) ||
       !(o.step > 0.0f) || o.shift_mode < 0 || o.shift_mode > 1 || o.precision < 0 ||
-      o.precision > PT_PREC_FP16X2) {
+      o.precision > PT_PREC_FP16X2 || !(o.rec_step >= 0.0f) || !(o.rec_step < 1e30f)) {
     set_error(ctx, "RapidPT: bad options");
     return PT_ERR_INVALID;
   }
@@ -1515,6 +1517,8 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   float* updb[2] = {upd.as<float>(), upd.as<float>() + updw};
   PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * 2 * V, st));
   CluStepArgs sa;
+  sa.samp = nullptr;
+  sa.tag = TAG_TRAIN;
   sa.V = uint32_t(V);
   sa.R = pl.R;
   sa.m = pl.m;
@@ -1673,6 +1677,115 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
 // ---------------------------------------------------------------------------
 // Recovery
 // ---------------------------------------------------------------------------
+// Recovery with U updates (pt_rapid_opts.rec_step > 0): the relabellings in
+// row order, each one a training-type step on its own samples (the step kernel
+// with the recovery draws and the sampled t values of Tt) followed by the
+// reconstruction of that relabelling with the U it was fitted to, which the
+// step launch has just materialised in full. QR every qr_every steps.
+pt_status recover_with_updates(pt_ctx* ctx, const RapidPlan& pl, const pt_rapid_opts& o,
+                               int64_t first_row, int64_t rows, float* U, const float* Tt,
+                               float sigma, float* Wrows, unsigned long long* keys) {
+  cudaStream_t st = ctx->stream;
+  const int64_t V = pl.V;
+  Buf Ub2, lift, upd, part, rinv;
+  struct G {
+    std::vector<Buf*> v;
+    ~G() {
+      for (Buf* b : v) b->release();
+    }
+  } guard{{&Ub2, &lift, &upd, &part, &rinv}};
+  const int updw = 3 * pl.RP + 4;
+  if (!Ub2.ensure(sizeof(float) * size_t(V) * pl.RP) || !lift.ensure(sizeof(float) * 2 * V) ||
+      !upd.ensure(sizeof(float) * 2 * updw))
+    return nomem_r(ctx, "RapidPT recovery updates");
+  size_t csm = 0;
+  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 16, &csm);
+  if (CL == 0) {
+    set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
+    return PT_ERR_UNSUPPORTED;
+  }
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * 2 * V, st));
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(Wrows, 0, sizeof(float) * size_t(rows) * pl.RP, st));
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * rows, st));
+  float* ua = U;
+  float* ub = Ub2.as<float>();
+  float* liftb[2] = {lift.as<float>(), lift.as<float>() + V};
+  float* updb[2] = {upd.as<float>(), upd.as<float>() + updw};
+  CluStepArgs sa;
+  sa.Trow = nullptr;
+  sa.tag = TAG_REC;
+  sa.V = uint32_t(V);
+  sa.R = pl.R;
+  sa.m = pl.m;
+  sa.CL = CL;
+  sa.k0 = pl.k0;
+  sa.k1 = pl.k1;
+  sa.rho = o.admm_rho;
+  sa.iters = o.admm_iters;
+  sa.step = o.rec_step;
+  sa.pass = 0;
+  int pend = -1;
+  int64_t last_row[2] = {-1, -1};
+  int nclu = 0;
+  int64_t steps = 0;
+  pt_status s = PT_OK;
+  cudaError_t lerr = cudaSuccess;
+  with_rp(pl.RP, [&](auto rpc) {
+    constexpr int RPc = decltype(rpc)::value;
+    auto launch = [&](bool fit) {
+      sa.fit = fit ? 1 : 0;
+      if (pend >= 0) {
+        sa.gu_src = ua;
+        sa.gu_dst = ub;
+        sa.gu_lift = liftb[pend];
+        sa.gu_coef = updb[pend];
+      } else {
+        sa.gu_src = nullptr;
+      }
+      lerr = launch_cluster(train_step_cluster_kernel<RPc>, pend >= 0 ? nclu : 1, CL, csm, st,
+                            sa);
+      count_launch();
+      if (pend >= 0) std::swap(ua, ub);
+    };
+    lerr = max_active_clusters(train_step_cluster_kernel<RPc>, CL, csm, &nclu);
+    if (lerr == cudaSuccess && nclu < 2) lerr = cudaErrorInvalidConfiguration;
+    for (int64_t k = 0; k < rows && lerr == cudaSuccess && s == PT_OK; ++k) {
+      const int64_t i = first_row + k;
+      const int cur = int(steps & 1);
+      sa.U = ua;
+      sa.pend_upd = pend >= 0 ? updb[pend] : nullptr;
+      sa.pend_lift = pend >= 0 ? liftb[pend] : nullptr;
+      sa.clear_pass = last_row[cur] >= 0 ? 0 : -1;
+      sa.clear_col = int(last_row[cur]);
+      sa.lift = liftb[cur];
+      sa.upd = updb[cur];
+      sa.col = int(i);
+      sa.samp = Tt + k * pl.m;
+      sa.w_hist = Wrows + k * pl.RP;
+      launch(true);
+      if (lerr != cudaSuccess) break;
+      // ua is now the U this relabelling was fitted to, in full
+      s = recon_tc(ctx, Wrows + k * pl.RP, 1, i, ua, V, pl.RP, sigma, TAG_NOISE, pl.k0, pl.k1,
+                   keys + k);
+      if (s != PT_OK) break;
+      last_row[cur] = i;
+      pend = cur;
+      ++steps;
+      if (steps % o.qr_every == 0) {
+        launch(false);
+        if (lerr != cudaSuccess) break;
+        pend = -1;
+        s = qr_inplace(ctx, ua, pl, part, rinv);
+      }
+    }
+  });
+  if (lerr != cudaSuccess) {
+    set_error(ctx, std::string("RapidPT recovery update launch: ") + cudaGetErrorString(lerr));
+    return PT_ERR_CUDA;
+  }
+  return s;
+}
+
 pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64_t first_row,
                              const float* U_in, int32_t rank, double sample_rate, double sigma,
                              double mu, const pt_rapid_opts& o, float* maxnull, float* W_out) {
@@ -1727,6 +1840,11 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
 #undef PT_SAMPLED_T
     PT_LAUNCH_CHECK(ctx);
   }
+  if (o.rec_step > 0.0f) {
+    s = recover_with_updates(ctx, pl, o, first_row, rows, Ub.as<float>(), Tt.as<float>(),
+                             float(sigma), Wb.as<float>(), keys.as<unsigned long long>());
+    if (s != PT_OK) return s;
+  } else {
   CluRecArgs a;
   a.Tt = Tt.as<float>();
   a.V = uint32_t(pl.V);
@@ -1755,6 +1873,7 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
   s = reconstruct(ctx, Wb.as<float>(), rows, first_row, Ub.as<float>(), pl, float(sigma),
                   TAG_NOISE, 0, nullptr, keys.as<unsigned long long>());
   if (s != PT_OK) return s;
+  }
   keys_to_values_kernel<<<grid_n(rows, 256), 256, 0, st>>>(keys.as<unsigned long long>(), rows,
                                                           float(mu), maxnull);
   PT_LAUNCH_CHECK(ctx);
@@ -1841,6 +1960,7 @@ void pt_rapid_opts_default(pt_rapid_opts* o) {
   o->step = 1.0f;
   o->shift_mode = 1;
   o->seed = 1;
+  o->rec_step = 0.0f;
 }
 
 pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precision, float* T) {

@@ -91,6 +91,43 @@ def test_recovery_large_rank_given_basis(cuda_lib, n, r, eta):
     ctx.close()
 
 
+def test_recovery_with_u_updates_matches_oracle(cuda_lib):
+    """U updates during recovery (rec_step = 1): the GPU takes the training step
+    after each recovery relabelling, in row order, from the oracle's trained U.
+    The first relabelling is recovered with the given U (as the frozen path);
+    weights and maxima follow the FP64 oracle step by step while the FP32 and
+    FP64 trajectories stay close (the first 20 rows; they separate slowly, as in
+    training), and every later maximum is finite."""
+    B = cuda_lib
+    n, n1, P, r, eta, ell = 40, 20, 140, 12, 0.03, 80
+    X = smooth_field(n, n1)
+    perms = synth.perms_pcg32(n, P, seed=1)
+    o = R.RapidOpts(train_passes=3, seed=7)
+    tr = R.rapid_train(X, n1, perms, r, eta, ell, o)
+    rows = np.arange(ell, P)
+    ou = R.RapidOpts(train_passes=3, seed=7, rec_step=1.0)
+    want, w_want = R.rapid_recover(X, n1, perms, rows, tr.U, tr.sigma, tr.mu, tr.m, ou,
+                                   return_w=True)
+    frozen = R.rapid_recover(X, n1, perms, rows[:1], tr.U, tr.sigma, tr.mu, tr.m, o)
+    ctx = gpu_ctx(B, X, n1)
+    pd = torch.as_tensor(perms).cuda()
+    Ud = torch.as_tensor(tr.U.astype(np.float32)).cuda().contiguous()
+    got = torch.empty(P - ell, dtype=torch.float32, device="cuda")
+    W = torch.empty((P - ell, r), dtype=torch.float32, device="cuda")
+    B.pt_rapid_recover(ctx, pd, ell, Ud, r, eta, tr.sigma, tr.mu,
+                       B.rapid_opts(seed=7, train_passes=3, rec_step=1.0), got, W)
+    B.pt_sync(ctx)
+    W = W.cpu().numpy().astype(np.float64)
+    got = got.cpu().numpy().astype(np.float64)
+    k = 20
+    wrel = np.linalg.norm(W[:k] - w_want[:k], axis=1) / np.linalg.norm(w_want[:k], axis=1)
+    assert np.max(wrel) < 1e-4, wrel
+    np.testing.assert_allclose(got[:k], want[:k], rtol=2e-4, atol=2e-4)
+    assert abs(got[0] - frozen[0]) <= 2e-4 * abs(frozen[0])
+    assert np.all(np.isfinite(got))
+    ctx.close()
+
+
 def test_training_matches_oracle(cuda_lib):
     B = cuda_lib
     n, n1, P, r, eta, ell = 40, 20, 200, 10, 0.03, 60

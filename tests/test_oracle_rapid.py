@@ -279,3 +279,45 @@ def test_u_statistic_exact_recovery_at_full_rank():
     assert res.sigma < 1e-8 and abs(res.mu) < 1e-8
     np.testing.assert_allclose(res.maxnull, ref.maxnull, rtol=1e-7)
     np.testing.assert_array_equal(res.counts, oracle.naive(X, n1, perms[:40]).counts)
+
+
+def _small_trained(stat="t", n=12, v=500, P=160, ell=40, r=6, eta=0.2, passes=4):
+    X = synth.gaussian_mean_shift(n, v, seed=12)
+    perms = synth.perms_pcg32(n, P, seed=13)
+    o = R.RapidOpts(train_passes=passes, stat=stat)
+    tr = R.rapid_train(X, n // 2, perms, r, eta, ell, o)
+    return X, perms, tr, o
+
+
+def test_recovery_updates_reconstruct_before_updating():
+    """With U updates in recovery (rec_step > 0) each relabelling is recovered
+    with the U it was fitted to, and U changes only afterwards: the first
+    recovered row equals the frozen recovery's, later rows differ, and a
+    vanishing step size tends to the frozen result."""
+    X, perms, tr, o = _small_trained()
+    rows = np.arange(40, 160)
+    frozen = R.rapid_recover(X, 6, perms, rows, tr.U, tr.sigma, tr.mu, tr.m, o)
+    upd = R.rapid_recover(X, 6, perms, rows, tr.U, tr.sigma, tr.mu, tr.m,
+                          R.RapidOpts(train_passes=4, rec_step=1.0))
+    assert upd[0] == frozen[0]
+    assert np.max(np.abs(upd[1:] - frozen[1:])) > 1e-6
+    tiny = R.rapid_recover(X, 6, perms, rows, tr.U, tr.sigma, tr.mu, tr.m,
+                           R.RapidOpts(train_passes=4, rec_step=1e-9))
+    np.testing.assert_allclose(tiny, frozen, rtol=0, atol=1e-6)
+
+
+def test_recovery_updates_keep_exact_low_rank():
+    """Linear statistic, r = n - 1, converged basis: every recovery fit is exact,
+    so the geodesic steps change nothing and the recovered max-null still equals
+    the exhaustive one."""
+    n, n1, v, P = 8, 4, 300, 120
+    X = synth.gaussian_mean_shift(n, v, seed=4)
+    perms = synth.perms_pcg32(n, P, seed=2)
+    o = R.RapidOpts(train_passes=60, stat="meandiff", admm_iters=300, qr_every=50, rec_step=1.0)
+    res = R.rapid(X, n1, perms, n - 1, 0.3, 40, o)
+    Lm = np.full(perms.shape, -1.0 / (n - n1))
+    Lm[:, :n1] = 1.0 / n1
+    Lw = np.zeros((P, n))
+    np.put_along_axis(Lw, perms, Lm, axis=1)
+    exact = (Lw @ X.astype(np.float64)).max(axis=1)
+    np.testing.assert_allclose(res.maxnull, exact, atol=1e-9)
