@@ -10,6 +10,8 @@ method's arithmetic.
   (``naive_fp64.c``) behind ctypes.
 * ``rapid``  -- RapidPT (Alg. 2, Sec. 4.1-4.2) in numpy FP64, with the
   counter-based generator (Philox4x32-10) both sides implement.
+* ``cluster`` -- clusters of thresholded maps (Sec. 6 cluster tables) and the
+  largest cluster per relabelling, with scipy's connected-component labelling.
 """
 
 import ctypes
