@@ -281,6 +281,33 @@ pt_status pt_sync(pt_ctx* ctx);
  */
 pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precision, float* T);
 
+/*
+ * Cluster-level summaries (the cluster tables of Sec. 6, Figs. 8-9, and the
+ * permutation distribution of the largest cluster, the cluster-level
+ * counterpart of the max-null of Sec. 2). A mask voxel is active when its t
+ * reaches tau; clusters are connected sets of active voxels on the grid.
+ *   tau          : cluster-forming threshold on t (finite).
+ *   dims         : host int32[3] (d0, d1, d2), d0 * d1 * d2 = n_grid; grid index
+ *                  g = (i0 * d1 + i1) * d2 + i2 (C order, as X's columns).
+ *   connectivity : 6 (faces), 18 (faces, edges) or 26 (faces, edges, corners).
+ * The plain two-sample t only (PT_ERR_UNSUPPORTED with covariates).
+ *
+ * pt_cluster_maxnull -- maxsize[i] (device int32[P]) = size of the largest
+ *   cluster of relabelling i (0 when no voxel is active). perms as
+ *   pt_maxnull_naive; precision as pt_naive_opts. Rows of u are formed a batch
+ *   of relabellings at a time (about 1 GB of device workspace). Synchronous.
+ * pt_cluster_observed -- the observed map's clusters, in masked order:
+ *   label[j] (device int32[v]) = masked index of the smallest voxel of j's
+ *   cluster, or -1; size[j] (device int32[v]) = that cluster's size, or 0.
+ *   The cluster-level FWER p-value of a cluster of size k is
+ *   (1 + #{i : maxsize[i] >= k}) / (P + 1). Synchronous.
+ */
+pt_status pt_cluster_maxnull(pt_ctx* ctx, const int32_t* perms, int64_t P, double tau,
+                             const int32_t* dims, int32_t connectivity, int32_t precision,
+                             int32_t* maxsize);
+pt_status pt_cluster_observed(pt_ctx* ctx, double tau, const int32_t* dims, int32_t connectivity,
+                              int32_t* label, int32_t* size);
+
 /* t_obs: device float32[v]: observed statistic per voxel (NaN where undefined).
  * Enqueued on the context's stream. */
 pt_status pt_t_obs(pt_ctx* ctx, float* t_obs);

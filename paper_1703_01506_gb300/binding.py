@@ -82,6 +82,9 @@ def load(path=None):
         "pt_sync": (ctypes.c_int, [_VP]),
         "pt_t_obs": (ctypes.c_int, [_VP, _VP]),
         "pt_t_rows": (ctypes.c_int, [_VP, _VP, i64, i32, _VP]),
+        "pt_cluster_maxnull": (ctypes.c_int, [_VP, _VP, i64, ctypes.c_double, _VP, i32, i32,
+                                              _VP]),
+        "pt_cluster_observed": (ctypes.c_int, [_VP, ctypes.c_double, _VP, i32, _VP, _VP]),
         "pt_voxel_grid_index": (ctypes.c_int, [_VP, _VP]),
         "pt_num_voxels": (i64, [_VP]),
         "pt_num_valid_voxels": (i64, [_VP]),
@@ -376,6 +379,37 @@ def pt_t_rows(ctx, perms, precision=PT_PREC_BF16X3, out=None):
         raise ValueError("out must be float32 with at least P * v elements")
     _check(load().pt_t_rows(ctx.handle, _ptr(perms), P, int(precision), _ptr(out)), ctx.handle)
     return out
+
+
+def _dims(dims):
+    if len(dims) != 3:
+        raise ValueError("dims must be (d0, d1, d2)")
+    return (ctypes.c_int32 * 3)(*[int(d) for d in dims])
+
+
+def pt_cluster_maxnull(ctx, perms, tau, dims, connectivity=6, precision=PT_PREC_FP16X2,
+                       out=None):
+    """Largest cluster of {t >= tau} per relabelling: (P,) int32 CUDA tensor."""
+    if perms.dim() != 2 or perms.dtype != torch.int32:
+        raise ValueError("perms must be a 2-D int32 tensor")
+    P = perms.shape[0]
+    if out is None:
+        out = torch.empty(P, dtype=torch.int32, device=perms.device)
+    elif out.dtype != torch.int32 or out.numel() < P:
+        raise ValueError("out must be int32 with at least P elements")
+    _check(load().pt_cluster_maxnull(ctx.handle, _ptr(perms), P, float(tau), _dims(dims),
+                                     int(connectivity), int(precision), _ptr(out)), ctx.handle)
+    return out
+
+
+def pt_cluster_observed(ctx, tau, dims, connectivity=6, device="cuda"):
+    """Observed map's clusters of {t >= tau}: (label, size), (v,) int32 tensors."""
+    v = int(load().pt_num_voxels(ctx.handle))
+    label = torch.empty(v, dtype=torch.int32, device=device)
+    size = torch.empty(v, dtype=torch.int32, device=device)
+    _check(load().pt_cluster_observed(ctx.handle, float(tau), _dims(dims), int(connectivity),
+                                      _ptr(label), _ptr(size)), ctx.handle)
+    return label, size
 
 
 def pt_profile_enable(ctx, on=True):

@@ -448,7 +448,7 @@ void pt_destroy(pt_ctx* ctx) {
                      &ctx->Xnb,     &ctx->labels,   &ctx->rowflag,   &ctx->blockflag,
                      &ctx->maxkey,  &ctx->cnt,      &ctx->scratch,   &ctx->tcdesc,
                      &ctx->moments, &ctx->glmQ,     &ctx->glm_coef,  &ctx->glm_inv,
-                     &ctx->rowscale};
+                     &ctx->rowscale, &ctx->grid_inv};
   for (pt::Buf* b : bufs) b->release();
   delete ctx;
 }

@@ -82,6 +82,11 @@ struct pt_ctx {
   pt::Buf glm_inv;      // double[v]: 1 / ||x - Q Q^T x||
   pt::Buf rowscale;     // float[P_pad]: sqrt(a_obs / a(l)) per relabelling
 
+  // Cluster-level summaries: grid index -> compact voxel (-1 outside the mask or
+  // without a statistic), built on first use for the grid shape in grid_dims.
+  pt::Buf grid_inv;
+  int64_t grid_dims[3] = {0, 0, 0};
+
   // Profiling of the dominant kernel (events on `stream`).
   bool profile = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_pool;
@@ -155,6 +160,11 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
 pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
                              const int64_t* P, const pt_naive_opts& o, float* const* maxnull,
                              int32_t* const* argmax, uint32_t* const* counts);
+pt_status cluster_maxnull_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, double tau,
+                               const int32_t* dims, int connectivity, int precision,
+                               int32_t* maxsize);
+pt_status cluster_observed_impl(pt_ctx* ctx, double tau, const int32_t* dims, int connectivity,
+                                int32_t* label, int32_t* size);
 pt_status fwer_pvalues_impl(pt_ctx* ctx, const float* maxnull, int64_t P, int two_sided,
                             float* p_out);
 // Drops a cached batched graph that names this context (from pt_destroy).

@@ -1912,6 +1912,10 @@ pt_status t_rows_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int precisio
     }
     out = comp.as<float>();
   }
+  if (!ctx->cnt.ensure(sizeof(uint32_t) * (V + 1))) {  // the labels kernel counts observed-set rows
+    set_error(ctx, "pt_t_rows: out of device memory");
+    return PT_ERR_NOMEM;
+  }
   int64_t P_pad = 0;
   pt_status s;
   if (precision != PT_PREC_FP32) {
