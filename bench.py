@@ -21,7 +21,9 @@ At one GPU the line also carries:
 * "large": the same comparison on n=400, 600,000 voxels, 100,000 relabellings
   (RapidPT r=100, 800 training rows), with NaivePT checked against the oracle
   on sampled rows;
-* "batched" (64 uneven studies in one call) and "glm" (two covariates);
+* "batched" (64 uneven studies in one call), "glm" (two covariates), "anova"
+  (one-way F of three groups) and "cluster" (largest cluster of {t >= 3.2}
+  per relabelling, the observed map's clusters and their p-values);
 * "cpu_baseline": the FP64 oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -635,6 +637,80 @@ def cpu_leg(Xm, n1, perms_np, t_rows_sel, large_host=None, large_rows=32):
     return base, ref, large
 
 
+def anova_leg(dev, B, synth, torch, sizes=(33, 33, 34), reps=3):
+    """One-way F of three groups as the voxel statistic (pt_maxnull_anova) on the
+    benchmark workload (n=100, 231,719 voxels, 10,000 relabellings): the two
+    group sums per relabelling from the FP16x2 contraction, B and its maxima and
+    counts, the winner's F in FP64."""
+    w = synth.workload(WORKLOAD, device=dev)
+    X, mask = w["X"], w["mask"]
+    perms = torch.as_tensor(w["perms"]).to(dev)
+    P = perms.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    ctx = B.pt_prepare(X, sizes[0], mask, stream=stream)
+    v = B.pt_num_voxels(ctx)
+    mx, _, _ = B.pt_maxnull_anova(ctx, perms, list(sizes), NAIVE_PREC)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        mx, _, _ = B.pt_maxnull_anova(ctx, perms, list(sizes), NAIVE_PREC)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    m = mx.cpu().numpy().astype(np.float64)
+    return {"workload": "%s, groups %s (one-way F), %d voxels, P=%d" % (WORKLOAD, list(sizes), v, P),
+            "ms_per_call": ms, "entries_per_s": P * v / (ms * 1e-3),
+            "fwer_thr": {"%g" % a: fwer_thr(m, a) for a in (0.05, 0.01)},
+            "timing": "device events over %d calls" % reps}
+
+
+def cluster_leg(dev, B, synth, torch, tau=3.2, conn=18, reps=3):
+    """Cluster-level inference on the benchmark workload (n=100, 231,719 voxels,
+    10,000 relabellings): the largest cluster of {t >= tau} per relabelling
+    (pt_cluster_maxnull, FP16x2 rows of u, union-find on the 91x109x91 grid)
+    and the observed map's clusters with their cluster-level FWER p-values."""
+    w = synth.workload(WORKLOAD, device=dev)
+    X, mask, n1 = w["X"], w["mask"], w["n1"]
+    perms = torch.as_tensor(w["perms"]).to(dev)
+    P = perms.shape[0]
+    dims = (91, 109, 91)
+    stream = torch.cuda.current_stream(dev)
+    ctx = B.pt_prepare(X, n1, mask, stream=stream)
+    ms = B.pt_cluster_maxnull(ctx, perms, tau, dims, conn, NAIVE_PREC)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        B.pt_cluster_maxnull(ctx, perms, tau, dims, conn, NAIVE_PREC, out=ms)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_call = e0.elapsed_time(e1) / reps
+    label, size = B.pt_cluster_observed(ctx, tau, dims, conn)
+    B.pt_sync(ctx)
+    v = B.pt_num_voxels(ctx)
+    ctx.close()
+    m = np.sort(ms.cpu().numpy())
+    lab = label.cpu().numpy()
+    sz = size.cpu().numpy()
+    reps_ = np.unique(lab[lab >= 0])
+    ks = np.sort(np.array([sz[r] for r in reps_], dtype=np.int64))[::-1]
+    pv = [(1.0 + (P - np.searchsorted(m, k, side="left"))) / (P + 1.0) for k in ks[:5]]
+    return {"workload": "%s: n=100, %d voxels, P=%d, tau=%g (t), %d-connectivity"
+                        % (WORKLOAD, v, P, tau, conn),
+            "ms_per_call": ms_call, "entries_per_s": P * v / (ms_call * 1e-3),
+            "max_cluster_null": {"median": float(np.median(m)), "p95": float(m[int(0.95 * P)]),
+                                 "max": int(m[-1])},
+            "observed_clusters": int(reps_.size),
+            "largest_observed": [{"k": int(k), "p_fwe_cluster": float(p)}
+                                 for k, p in zip(ks[:5], pv)],
+            "timing": "device events over %d calls (rows of u in batches, union-find, max)"
+                      % reps}
+
+
 def run_ours(args):
     if args.rapid_only:
         import torch
@@ -866,6 +942,9 @@ def run_ours(args):
         line["batched"] = batched_leg(dev, B, synth, torch)
     if ws == 1 and not args.no_glm:
         line["glm"] = glm_leg(dev, B, synth, torch)
+    if ws == 1 and not args.no_cluster:
+        line["cluster"] = cluster_leg(dev, B, synth, torch)
+        line["anova"] = anova_leg(dev, B, synth, torch)
     large_host = None
     if ws == 1 and not args.no_large:
         line["large"], large_host = large_leg(dev, B, synth, torch, args.rapid_passes)
@@ -907,6 +986,8 @@ def main():
                     help="skip the RapidPT vs NaivePT leg (n=200, 500k voxels, 1e5 relabellings)")
     ap.add_argument("--no-glm", action="store_true",
                     help="skip the covariate-adjusted NaivePT leg")
+    ap.add_argument("--no-cluster", action="store_true",
+                    help="skip the cluster-level leg (largest cluster per relabelling)")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the n=400, 600k-voxel NaivePT/RapidPT leg")
     ap.add_argument("--no-precision", action="store_true",

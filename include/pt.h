@@ -282,6 +282,24 @@ pt_status pt_sync(pt_ctx* ctx);
 pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precision, float* T);
 
 /*
+ * pt_maxnull_anova -- NaivePT (Alg. 1) with the one-way F of g groups as the
+ * voxel statistic (Alg. 1's "stat" input with several group columns; g = 2 gives
+ * F = t^2 of Eq. 5): F = (SS_between / (g-1)) / (SS_within / (n-g)).
+ *   perms       : device int32 P x n; positions [0, n_1) of a row form group 1,
+ *                 [n_1, n_1 + n_2) group 2, ...; the observed labelling is the identity.
+ *   group_sizes : host int32[g], each >= 1, summing to the context's n; 2 <= g <= 16, n > g.
+ *   precision   : as pt_naive_opts (the g - 1 group sums come from the same contraction).
+ *   maxnull, argmax : device float32[P] / int32[P]: max over voxels of F (the winner's F
+ *                 recomputed in FP64 from the input values) and its masked voxel index.
+ *   counts      : device uint32[v] or NULL: #{i : F_ij >= F_obs_j}.
+ * The context's n1 plays no part. Synchronous; a bad relabelling row makes the next
+ * pt_sync return PT_ERR_INVALID. PT_ERR_UNSUPPORTED with covariates.
+ */
+pt_status pt_maxnull_anova(pt_ctx* ctx, const int32_t* perms, int64_t P,
+                           const int32_t* group_sizes, int32_t g, int32_t precision,
+                           float* maxnull, int32_t* argmax, uint32_t* counts);
+
+/*
  * Cluster-level summaries (the cluster tables of Sec. 6, Figs. 8-9, and the
  * permutation distribution of the largest cluster, the cluster-level
  * counterpart of the max-null of Sec. 2). A mask voxel is active when its t

@@ -85,6 +85,7 @@ def load(path=None):
         "pt_cluster_maxnull": (ctypes.c_int, [_VP, _VP, i64, ctypes.c_double, _VP, i32, i32,
                                               _VP]),
         "pt_cluster_observed": (ctypes.c_int, [_VP, ctypes.c_double, _VP, i32, _VP, _VP]),
+        "pt_maxnull_anova": (ctypes.c_int, [_VP, _VP, i64, _VP, i32, i32, _VP, _VP, _VP]),
         "pt_voxel_grid_index": (ctypes.c_int, [_VP, _VP]),
         "pt_num_voxels": (i64, [_VP]),
         "pt_num_valid_voxels": (i64, [_VP]),
@@ -379,6 +380,25 @@ def pt_t_rows(ctx, perms, precision=PT_PREC_BF16X3, out=None):
         raise ValueError("out must be float32 with at least P * v elements")
     _check(load().pt_t_rows(ctx.handle, _ptr(perms), P, int(precision), _ptr(out)), ctx.handle)
     return out
+
+
+def pt_maxnull_anova(ctx, perms, group_sizes, precision=PT_PREC_FP16X2, counts=True):
+    """One-way F max-null over g groups: (maxnull float32[P], argmax int32[P],
+    counts int32[v] or None) CUDA tensors."""
+    if perms.dim() != 2 or perms.dtype != torch.int32:
+        raise ValueError("perms must be a 2-D int32 tensor")
+    P = perms.shape[0]
+    g = len(group_sizes)
+    sz = (ctypes.c_int32 * g)(*[int(x) for x in group_sizes])
+    mx = torch.empty(P, dtype=torch.float32, device=perms.device)
+    am = torch.empty(P, dtype=torch.int32, device=perms.device)
+    ct = None
+    if counts:
+        ct = torch.empty(int(load().pt_num_voxels(ctx.handle)), dtype=torch.int32,
+                         device=perms.device)
+    _check(load().pt_maxnull_anova(ctx.handle, _ptr(perms), P, sz, g, int(precision), _ptr(mx),
+                                   _ptr(am), _ptr(ct)), ctx.handle)
+    return mx, am, ct
 
 
 def _dims(dims):

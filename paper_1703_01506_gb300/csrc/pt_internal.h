@@ -160,6 +160,8 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
 pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
                              const int64_t* P, const pt_naive_opts& o, float* const* maxnull,
                              int32_t* const* argmax, uint32_t* const* counts);
+pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t* sizes, int g,
+                     int precision, float* maxnull, int32_t* argmax, uint32_t* counts);
 pt_status cluster_maxnull_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, double tau,
                                const int32_t* dims, int connectivity, int precision,
                                int32_t* maxsize);
