@@ -135,7 +135,7 @@ constexpr int kSlot = kMaxRank + 8;
 // Row stride of A in shared memory: 16-byte rows whose stride in 16-byte units
 // is odd, so a warp reading 32 different rows in float4 steps hits every bank
 // group once per four lanes (and column-wise reads stay conflict-free).
-__host__ __device__ constexpr int clu_rs(int RP) { return (RP / 4) % 2 == 0 ? RP + 4 : RP + 8; }
+__host__ __device__ constexpr int clu_rs(int RP) { return (RP / 4) % 2 == 0 ? RP + 4 : RP; }
 
 __host__ __device__ inline size_t clu_carve(float* base, int mloc, int R, int RP, int n_pad,
                                             CluSmem* f) {
@@ -155,7 +155,11 @@ __host__ __device__ inline size_t clu_carve(float* base, int mloc, int R, int RP
   t.idx = reinterpret_cast<int32_t*>(take(mloc));
   t.G = take(size_t(R) * R);
   t.Gi = take(size_t(R) * R);
-  t.Gp = take(size_t(R) * ((R + 3) / 4 * 4));
+  // The Gram partial is dead once the cluster has summed it (a cluster barrier
+  // follows the sum), before s, y and x are first written: it shares their
+  // space when it fits there (contiguous: s, y, x are taken in a row).
+  const size_t gp = size_t(R) * ((R + 3) / 4 * 4);
+  t.Gp = gp <= 3 * ((size_t(mloc) + 3) / 4 * 4) ? t.s : take(gp);
   t.slot = take(2 * kSlot);
   t.red = take(size_t(kCluWarps) * RP);
   t.vec = take(kSlot);
@@ -341,6 +345,7 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
       }
     }
   }
+  cl.sync();  // every CTA has read every Gram partial (their space is reused)
   for (int e = tid; e < R * R; e += blockDim.x) f.Gi[e] = 0.0f;
   __syncthreads();
   for (int c = tid; c < R; c += blockDim.x) f.Gi[c * R + c] = 1.0f;
@@ -446,76 +451,81 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
   }
   __syncthreads();  // fac and rowk (in red) are read until here
   // --- ADMM on min ||s||_1 s.t. A w + s = b (s = y = 0 at the start, so x = b).
-  // A^T x: warp w takes the local rows q = w, w + 16, ... and lane l the
-  // columns l + 32k. The s, y, x updates take one thread per row (its dot
-  // product with w in float4 steps), so no shuffles are needed there.
+  // Rows belong to warps in groups of 32: thread t handles rows t, t + 512, ...,
+  // so a warp's rows form whole groups. Per group the warp first updates each
+  // row with the current w (thread = row: A_q . w in float4 steps, then s, y, x)
+  // and then adds the group's rows into A^T x (lane = column, x_q passed by
+  // shuffle from its row's thread), so no block barrier separates the two.
+  // Then: the warps' partial sums (one barrier), this CTA's sum (one barrier),
+  // its share of the next w, G^-1 (this CTA's A^T x), summed over the cluster
+  // in rank order (one cluster barrier), the sum (one barrier). G^-1 is the
+  // same in every CTA and the rank-ordered sum is too, so every CTA holds the
+  // same w. An iteration: three block barriers and one cluster barrier.
   const float irho = 1.0f / rho;
-  for (int q = tid; q < mloc; q += blockDim.x) {
-    f.s[q] = 0.0f;
-    f.y[q] = 0.0f;
-    f.x[q] = f.b[q];
-  }
-  for (int it = 0; it < iters; ++it) {
-    __syncthreads();
-    float acc[KC];
+  float acc[KC];
+  auto rows_pass = [&](bool update) {
 #pragma unroll
     for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
-    for (int q = warp; q < mloc; q += kCluWarps) {
-      const float xq = f.x[q];
+    for (int base = warp * 32; base < mloc; base += int(blockDim.x)) {
+      const int q = base + lane;
+      float xq = 0.0f;
+      if (q < mloc) {
+        const float bq = f.b[q];
+        if (update) {
+          const float aw = clu_row_dot<RP>(f.A + q * RS, f.wv);
+          const float yq = f.y[q];
+          const float e = bq - aw - yq * irho;
+          const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
+          const float yn = yq + rho * (aw + sq - bq);
+          f.s[q] = sq;
+          f.y[q] = yn;
+          xq = bq - sq - yn * irho;
+        } else {
+          f.s[q] = 0.0f;
+          f.y[q] = 0.0f;
+          xq = bq;
+        }
+        f.x[q] = xq;
+      }
+      const int rows_here = mloc - base < 32 ? mloc - base : 32;
+      for (int jq = 0; jq < rows_here; ++jq) {
+        const float xj = __shfl_sync(0xffffffffu, xq, jq);
+        const float* row = f.A + (base + jq) * RS;
 #pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        const int c = lane + 32 * k;
-        if (c < RP) acc[k] = fmaf(f.A[q * RS + c], xq, acc[k]);
+        for (int k = 0; k < KC; ++k) {
+          const int c = lane + 32 * k;
+          if (c < RP) acc[k] = fmaf(row[c], xj, acc[k]);
+        }
       }
     }
+  };
+  rows_pass(false);  // A^T b
+  for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
       const int c = lane + 32 * k;
       if (c < RP) f.red[warp * RP + c] = acc[k];
     }
     __syncthreads();
-    float* mine = f.slot + par * kSlot;
     for (int c = tid; c < R; c += blockDim.x) {
       float t = 0.0f;
 #pragma unroll
       for (int ww = 0; ww < kCluWarps; ++ww) t += f.red[ww * RP + c];
+      f.vec[c] = t;  // this CTA's A^T x
+    }
+    __syncthreads();
+    float* mine = f.slot + par * kSlot;
+    for (int c = tid; c < R; c += blockDim.x) {  // this CTA's share of w: G^-1 (A^T x)_local
+      float t = 0.0f;
+      for (int d = 0; d < R; ++d) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
       mine[c] = t;
     }
     cl.sync();
-    for (int c = tid; c < R; c += blockDim.x) f.vec[c] = clu_gather_sum(cl, mine, c, CL);
+    for (int c = tid; c < RP; c += blockDim.x)
+      f.wv[c] = c < R ? clu_gather_sum(cl, mine, c, CL) : 0.0f;
     par ^= 1;
     __syncthreads();
-    // w = G^-1 v (G^-1 symmetric: column c read along d, conflict-free); the
-    // d range is split over kCluWarps / KC groups, partials summed in order
-    {
-      constexpr int NG = kCluWarps / KC;
-      const int g = warp / KC, c = lane + 32 * (warp % KC);
-      const int per = (R + NG - 1) / NG, d0 = g * per, d1 = min(R, d0 + per);
-      float t = 0.0f;
-      if (c < R)
-        for (int d = d0; d < d1; ++d) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
-      if (c < RP) f.red[g * RP + c] = t;
-      __syncthreads();
-      for (int c2 = tid; c2 < RP; c2 += blockDim.x) {
-        float w = 0.0f;
-        if (c2 < R)
-#pragma unroll
-          for (int gg = 0; gg < NG; ++gg) w += f.red[gg * RP + c2];
-        f.wv[c2] = w;
-      }
-      __syncthreads();
-    }
-    // rows: s, y update of this iteration and x of the next
-    for (int q = tid; q < mloc; q += blockDim.x) {
-      const float aw = clu_row_dot<RP>(f.A + q * RS, f.wv);
-      const float bq = f.b[q], yq = f.y[q];
-      const float e = bq - aw - yq * irho;
-      const float sq = copysignf(fmaxf(fabsf(e) - irho, 0.0f), e);
-      const float yn = yq + rho * (aw + sq - bq);
-      f.s[q] = sq;
-      f.y[q] = yn;
-      f.x[q] = bq - sq - yn * irho;
-    }
+    rows_pass(true);
   }
   __syncthreads();
   // f.wv holds the last iteration's w (entries c >= R are zero)
@@ -1808,7 +1818,7 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
     }
   } guard{{&Ub, &Wb, &keys, &Tt}};
   size_t csm = 0;
-  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 4, &csm);
+  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 2, &csm);
   if (CL == 0) {
     set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
     return PT_ERR_UNSUPPORTED;
