@@ -245,16 +245,18 @@ __device__ __forceinline__ void clu_block_sum_to(float v, const CluSmem& f, floa
 template <int RP>
 __device__ __forceinline__ float clu_row_dot(const float* row, const float* v) {
   const float4* r4 = reinterpret_cast<const float4*>(row);
+  const float4* v4 = reinterpret_cast<const float4*>(v);  // v: 16-byte aligned
   float4 a[RP / 4];
 #pragma unroll
   for (int c4 = 0; c4 < RP / 4; ++c4) a[c4] = r4[c4];
   float t0 = 0.0f, t1 = 0.0f;
 #pragma unroll
   for (int c4 = 0; c4 < RP / 4; ++c4) {
-    t0 = fmaf(a[c4].x, v[4 * c4], t0);
-    t1 = fmaf(a[c4].y, v[4 * c4 + 1], t1);
-    t0 = fmaf(a[c4].z, v[4 * c4 + 2], t0);
-    t1 = fmaf(a[c4].w, v[4 * c4 + 3], t1);
+    const float4 w = v4[c4];
+    t0 = fmaf(a[c4].x, w.x, t0);
+    t1 = fmaf(a[c4].y, w.y, t1);
+    t0 = fmaf(a[c4].z, w.z, t0);
+    t1 = fmaf(a[c4].w, w.w, t1);
   }
   return t0 + t1;
 }
@@ -267,7 +269,7 @@ __device__ __forceinline__ float clu_row_dot(const float* row, const float* v) {
 template <int RP>
 __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, int R, float rho,
                            int iters, int CL, int& par) {
-  constexpr int RS = clu_rs(RP), KC = (RP + 31) / 32;
+  constexpr int RS = clu_rs(RP);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int RG = (R + 3) / 4 * 4;
   // --- local Gram partial by 4x4 register tiles of the upper triangle; the
@@ -356,7 +358,7 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
   // (phase 1); then every row is updated from them (phase 2): two barriers per
   // four pivots.
   float* fac = f.red;           // R x 4: pivot columns of the other rows
-  float* rowk = f.red + 4 * R;  // 4 x 2R: scaled pivot rows
+  float* rowk = f.red + 4 * R;  // 4 x R: scaled pivot rows (the round's R columns)
   constexpr int kRowsPerWarp = (RP + kCluWarps - 1) / kCluWarps;
   for (int k = 0; k < R; k += 4) {
     const int bk = R - k < 4 ? R - k : 4;
@@ -391,14 +393,20 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
         }
       }
     }
-    for (int e = tid; e < 4 * 2 * R; e += blockDim.x) {
-      const int r = e / (2 * R), j = e - r * 2 * R;
+    // Only R of the 2R columns of [G | G^-1] can change in this round: the G
+    // columns right of the pivot block (those left of it are eliminated and
+    // never read again) and the G^-1 columns up to the pivot block's end (those
+    // right of it are still identity columns, which the round leaves alone).
+    // Column index jc < nG: G column kb + jc; else G^-1 column jc - nG.
+    const int kb = k + bk, nG = R - kb;
+    for (int e = tid; e < 4 * R; e += blockDim.x) {
+      const int r = e / R, jc = e - r * R;
+      const float* M = jc < nG ? f.G + kb + jc : f.Gi + (jc - nG);
       float t = 0.0f;
       if (r < bk)
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (c < bk)
-            t = fmaf(pi[r][c], j < R ? f.G[(k + c) * R + j] : f.Gi[(k + c) * R + (j - R)], t);
+          if (c < bk) t = fmaf(pi[r][c], M[(k + c) * R], t);
       rowk[e] = t;
     }
     for (int e = tid; e < 4 * R; e += blockDim.x) {
@@ -408,42 +416,33 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
     __syncthreads();
     // all loads of a thread's entries before its stores (the compiler cannot
     // reorder loads past stores through these aliasing shared pointers)
-    for (int j = lane; j < R; j += 32) {
-      float rg[4], ri[4];
+    for (int jc = lane; jc < R; jc += 32) {
+      float* M = jc < nG ? f.G + kb + jc : f.Gi + (jc - nG);
+      float rg[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        rg[c] = rowk[c * 2 * R + j];
-        ri[c] = rowk[c * 2 * R + R + j];
-      }
-      float gv[kRowsPerWarp], hv[kRowsPerWarp];
+      for (int c = 0; c < 4; ++c) rg[c] = rowk[c * R + jc];
+      float gv[kRowsPerWarp];
       float4 fv[kRowsPerWarp];
 #pragma unroll
       for (int t = 0; t < kRowsPerWarp; ++t) {
         const int i = warp + kCluWarps * t;
-        gv[t] = i < R ? f.G[i * R + j] : 0.0f;
-        hv[t] = i < R ? f.Gi[i * R + j] : 0.0f;
+        gv[t] = i < R ? M[i * R] : 0.0f;
         fv[t] = i < R ? *reinterpret_cast<const float4*>(fac + 4 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int t = 0; t < kRowsPerWarp; ++t) {
         const int i = warp + kCluWarps * t;
         if (i < R) {
-          if (i >= k && i < k + bk) {
+          if (i >= k && i < kb) {
             const int r = i - k;  // selected without indexing the register arrays
-            f.G[i * R + j] = r == 0 ? rg[0] : r == 1 ? rg[1] : r == 2 ? rg[2] : rg[3];
-            f.Gi[i * R + j] = r == 0 ? ri[0] : r == 1 ? ri[1] : r == 2 ? ri[2] : ri[3];
+            M[i * R] = r == 0 ? rg[0] : r == 1 ? rg[1] : r == 2 ? rg[2] : rg[3];
           } else {
-            float g = gv[t], h = hv[t];
+            float g = gv[t];
             g = fmaf(-fv[t].x, rg[0], g);
-            h = fmaf(-fv[t].x, ri[0], h);
             g = fmaf(-fv[t].y, rg[1], g);
-            h = fmaf(-fv[t].y, ri[1], h);
             g = fmaf(-fv[t].z, rg[2], g);
-            h = fmaf(-fv[t].z, ri[2], h);
             g = fmaf(-fv[t].w, rg[3], g);
-            h = fmaf(-fv[t].w, ri[3], h);
-            f.G[i * R + j] = g;
-            f.Gi[i * R + j] = h;
+            M[i * R] = g;
           }
         }
       }
@@ -462,10 +461,30 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
   // same in every CTA and the rank-ordered sum is too, so every CTA holds the
   // same w. An iteration: three block barriers and one cluster barrier.
   const float irho = 1.0f / rho;
-  float acc[KC];
+  // A^T x pass: lane l takes the VW adjacent columns VW l .. VW l + VW - 1
+  // (one 8- or 16-byte load per row), four rows per step.
+  constexpr int VW = RP <= 64 ? 2 : 4;
+  constexpr int NLANE = RP / VW;
+  static_assert(RP % 4 == 0 && NLANE <= 32, "columns per lane");
+  const bool lane_on = lane < NLANE;
+  float acc[VW] = {};
+  auto add_row = [&](int row, float xj) {
+    const float* src = f.A + row * RS + VW * lane;
+    if constexpr (VW == 2) {
+      const float2 a2 = *reinterpret_cast<const float2*>(src);
+      acc[0] = fmaf(a2.x, xj, acc[0]);
+      acc[1] = fmaf(a2.y, xj, acc[1]);
+    } else {
+      const float4 a4 = *reinterpret_cast<const float4*>(src);
+      acc[0] = fmaf(a4.x, xj, acc[0]);
+      acc[1] = fmaf(a4.y, xj, acc[1]);
+      acc[2] = fmaf(a4.z, xj, acc[2]);
+      acc[3] = fmaf(a4.w, xj, acc[3]);
+    }
+  };
   auto rows_pass = [&](bool update) {
 #pragma unroll
-    for (int k = 0; k < KC; ++k) acc[k] = 0.0f;
+    for (int k = 0; k < VW; ++k) acc[k] = 0.0f;
     for (int base = warp * 32; base < mloc; base += int(blockDim.x)) {
       const int q = base + lane;
       float xq = 0.0f;
@@ -488,23 +507,30 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
         f.x[q] = xq;
       }
       const int rows_here = mloc - base < 32 ? mloc - base : 32;
-      for (int jq = 0; jq < rows_here; ++jq) {
-        const float xj = __shfl_sync(0xffffffffu, xq, jq);
-        const float* row = f.A + (base + jq) * RS;
-#pragma unroll
-        for (int k = 0; k < KC; ++k) {
-          const int c = lane + 32 * k;
-          if (c < RP) acc[k] = fmaf(row[c], xj, acc[k]);
+      int jq = 0;
+      for (; jq + 4 <= rows_here; jq += 4) {
+        const float x0 = __shfl_sync(0xffffffffu, xq, jq);
+        const float x1 = __shfl_sync(0xffffffffu, xq, jq + 1);
+        const float x2 = __shfl_sync(0xffffffffu, xq, jq + 2);
+        const float x3 = __shfl_sync(0xffffffffu, xq, jq + 3);
+        if (lane_on) {
+          add_row(base + jq, x0);
+          add_row(base + jq + 1, x1);
+          add_row(base + jq + 2, x2);
+          add_row(base + jq + 3, x3);
         }
+      }
+      for (; jq < rows_here; ++jq) {
+        const float xj = __shfl_sync(0xffffffffu, xq, jq);
+        if (lane_on) add_row(base + jq, xj);
       }
     }
   };
   rows_pass(false);  // A^T b
   for (int it = 0; it < iters; ++it) {
+    if (lane_on) {
 #pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      const int c = lane + 32 * k;
-      if (c < RP) f.red[warp * RP + c] = acc[k];
+      for (int k = 0; k < VW; ++k) f.red[warp * RP + VW * lane + k] = acc[k];
     }
     __syncthreads();
     for (int c = tid; c < R; c += blockDim.x) {
