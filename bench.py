@@ -1,11 +1,13 @@
 """Benchmark: max-null permutation testing, NaivePT and RapidPT, on GB300s.
 
 One step = the whole NaivePT hot path on one batch: pt_prepare (per-voxel
-moments, unit-norm centring, BF16 split) + pt_maxnull_naive (labels, fused
-tensor-core contraction + max-null + exceedance counts, finalise) for the
-brain-shaped workload n=100 (50/50), 91x109x91 grid masked to 231,719 voxels,
-10,000 relabellings. Metric: T entries (relabelling x voxel t statistics) per
-second. Inputs (X 361 MB, BF16 data pieces 156 MB) are larger than L2.
+moments, unit-norm centring) + pt_maxnull_naive (split of the data into two
+FP16 pieces, labels, fused tensor-core contraction + max-null + exceedance
+counts, finalise) for the brain-shaped workload n=100 (50/50), 91x109x91 grid
+masked to 231,719 voxels, 10,000 relabellings. Metric: T entries (relabelling
+x voxel t statistics) per second. Inputs (X 361 MB, FP16 data pieces 104 MB)
+are larger than L2. Steps follow one another on one stream; the only host wait
+inside a step is pt_prepare's (it sizes the launches by the voxel counts).
 
 At one GPU the line also carries:
 * "precision": each arithmetic path of the fused kernel (FP32 CUDA cores,
@@ -503,20 +505,21 @@ def precision_summary(paths, ref_rows, ref_max, ref_argmax, ref_t):
 def batched_leg(dev, B, synth, torch, studies=64, P=10000):
     """Many independent studies of uneven shape in one call: 64 studies with
     n ~ U{24..400} (n1 = n/2) and v ~ U{50k..600k} voxels (PCG32 seeded 1000 + k),
-    10,000 relabellings each, BF16x3. Values are Gaussian (mean ~ U(0,1) per voxel,
-    unit noise; the contraction's cost does not depend on smoothness), FP16x2. Compares
-    pt_maxnull_naive_batched (one persistent launch per tile class, replayed as a
-    CUDA graph) with one pt_maxnull_naive_ex call per study on the same stream."""
+    10,000 relabellings each, FP16x2. Each study is a smoothed brain-shaped field
+    in [0, 1] (FWHM 8 voxels, the first v voxels of an ellipsoid mask on a
+    121x145x121 grid, seeded 1000 + k). Compares pt_maxnull_naive_batched (one
+    persistent launch per launch class, replayed as a CUDA graph) with one
+    pt_maxnull_naive_ex call per study on the same stream, and times each
+    study's fused kernel alone (the library's event pair)."""
     shapes = synth.uneven_study_shapes(studies)
     stream = torch.cuda.current_stream(dev)
     ctxs, perms, mx, am = [], [], [], []
+    sa = tuple(a * 1.4 for a in (34, 44, 37))
     for k, (n, n1, v) in enumerate(shapes):
-        g = torch.Generator(device=dev)
-        g.manual_seed(1000 + k)
-        X = torch.randn(n, v, device=dev, generator=g)
-        X += torch.rand(1, v, device=dev, generator=g)
-        ctxs.append(B.pt_prepare(X, n1, stream=stream))
-        del X
+        X, mask = synth.brain_field(n, n1, grid=synth.BIG_GRID, center=synth.BIG_CENTER,
+                                    semi_axes=sa, seed=1000 + k, device=dev, v_limit=v)
+        ctxs.append(B.pt_prepare(X, n1, mask, stream=stream))
+        del X, mask
         perms.append(torch.as_tensor(synth.perms_pcg32(n, P, seed=1000 + k)).to(dev))
         mx.append(torch.empty(P, dtype=torch.float32, device=dev))
         am.append(torch.empty(P, dtype=torch.int32, device=dev))
@@ -546,17 +549,48 @@ def batched_leg(dev, B, synth, torch, studies=64, P=10000):
     batched()  # plans and captures the graph
     b_ms = timed(batched, 5)
     s_ms = timed(sequential, 3)
+    # each study's fused kernel alone (the library's event pair around it)
+    per = []
+    for c, p_, m_, a_ in zip(ctxs, perms, mx, am):
+        B.pt_profile_enable(c, True)
+        B.pt_profile_read(c)
+        B.pt_maxnull_naive_ex(c, p_, opts, m_, a_, None)
+        ms_k, nk = B.pt_profile_read(c)
+        B.pt_profile_enable(c, False)
+        per.append(ms_k / max(nk, 1))
     for c in ctxs:
         B.pt_sync(c)
         c.close()
     ns = [n for n, _, _ in shapes]
+    pk, _ = peaks()
+    flops = sum(2.0 * n * P * v for n, _, v in shapes)
+    hw = sum(2.0 * 2 * ((n + 15) // 16 * 16) * P * v for n, _, v in shapes)
+    order = np.argsort(per)
+
+    def study(i):
+        n, _, v = shapes[i]
+        return {"n": n, "v": v, "kernel_ms": per[i],
+                "entries_per_s": P * v / (per[i] * 1e-3),
+                "issued_tflops": 4.0 * ((n + 15) // 16 * 16) * P * v / (per[i] * 1e-3) / 1e12}
     return {"workload": "%d studies, n ~ U{24..400} (here %d..%d), v ~ U{50k..600k} "
-                        "(total %d voxels), P=%d each, Gaussian values"
+                        "(total %d voxels), P=%d each, smoothed [0,1] fields (FWHM 8)"
                         % (studies, min(ns), max(ns), sum(v for _, _, v in shapes), P),
             "entries": entries, "batched_ms": b_ms, "sequential_ms": s_ms,
+            "batched_over_sequential": s_ms / b_ms,
             "batched_entries_per_s": entries / (b_ms * 1e-3),
             "sequential_entries_per_s": entries / (s_ms * 1e-3),
-            "timing": "device events over 5 graph replays / 3 loops of per-study calls"}
+            "roofline": {"algorithmic_tflops": flops / (b_ms * 1e-3) / 1e12,
+                         "frac_of_burst_peak": flops / (b_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                         "issued_tflops": hw / (b_ms * 1e-3) / 1e12,
+                         "hw_frac_of_burst_peak": hw / (b_ms * 1e-3) / 1e12 / pk["bf16_tflops"],
+                         "flops": "algorithmic 2 n P v per study; issued 2 FP16 pieces x "
+                                  "2 n_pad P v (n_pad = n rounded up to 16)"},
+            "sequential_kernel_ms_sum": float(sum(per)),
+            "sequential_outside_kernels_ms": s_ms - float(sum(per)),
+            "fastest_studies": [study(i) for i in order[:3]],
+            "slowest_studies": [study(i) for i in order[-4:]],
+            "timing": "device events over 5 graph replays / 3 loops of per-study calls; "
+                      "per-study kernel times from one profiled call each"}
 
 
 def glm_leg(dev, B, synth, torch, q=2, reps=20):
@@ -760,8 +794,7 @@ def run_ours(args):
         return (shard.merge_maxnull(maxnull, P_all), shard.merge_maxnull(argmax, P_all),
                 shard.merge_counts(step.counts))
 
-    def step(profile=False):
-        ctx = B.pt_prepare(X, n1, mask, stream=stream)
+    def launch(ctx, profile=False):
         if profile:
             B.pt_profile_enable(ctx, True)
         counts = step.counts
@@ -770,6 +803,9 @@ def run_ours(args):
         B.pt_maxnull_naive_ex(ctx, perms, B.naive_opts(prec), maxnull, argmax, counts)
         step.merged = merge()
         return ctx
+
+    def step(profile=False):
+        return launch(B.pt_prepare(X, n1, mask, stream=stream), profile)
     step.counts = None
 
     ctx = step()
@@ -802,16 +838,27 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     t_wall0 = time.time()
     ev0.record(stream)
+    prev = None
     for _ in range(args.steps):
-        ctx = step(profile=True)
-        B.pt_sync(ctx)
-        ms_k, n_k = B.pt_profile_read(ctx)
-        kern_ms += ms_k
-        kern_n += n_k
-        ctx.close()  # workspaces go back to the library's cache for the next step
+        # pt_prepare waits for the stream once (it sizes the launches by the
+        # count of voxels with a defined t), which also finishes the previous
+        # step; that step's kernel time is read and its context closed (its
+        # workspaces go back to the library's cache) before this step launches.
+        ctx = B.pt_prepare(X, n1, mask, stream=stream)
+        if prev is not None:
+            ms_k, n_k = B.pt_profile_read(prev)
+            kern_ms += ms_k
+            kern_n += n_k
+            prev.close()
+        prev = launch(ctx, profile=True)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     t_wall1 = time.time()
+    B.pt_sync(prev)  # error bits (every warm-up step was checked the same way)
+    ms_k, n_k = B.pt_profile_read(prev)
+    kern_ms += ms_k
+    kern_n += n_k
+    prev.close()
     launches = B.pt_kernel_launch_count() - launches0
     clk = clocks.stop(t_wall0, t_wall1)
     ms = ev0.elapsed_time(ev1) / args.steps

@@ -430,9 +430,10 @@ const char* pt_last_error(const pt_ctx* ctx);
 /*
  * Profiling of the dominant kernel. When enabled, every compute call records a
  * pair of CUDA events on the context's stream around the launch of its main
- * contraction kernel. pt_profile_read synchronises the stream and returns (host
- * outputs) the summed device time in ms and the number of timed launches since
- * the previous read, then resets both.
+ * contraction kernel. pt_profile_read waits for the last timed launch (not for
+ * later work on the stream) and returns (host outputs) the summed device time
+ * in ms and the number of timed launches since the previous read, then resets
+ * both.
  */
 pt_status pt_profile_enable(pt_ctx* ctx, int32_t on);
 pt_status pt_profile_read(pt_ctx* ctx, double* total_ms, int64_t* launches);
@@ -501,11 +502,17 @@ pt_status pt_maxnull_naive_noalloc(const float* X, int32_t n, int64_t v, int32_t
                                    float* maxnull, int32_t* argmax, uint32_t* counts,
                                    void* stream);
 
-/* Frees the context's device memory (returned to the library's cache). NULL ok. */
+/* Frees the context's device memory (returned to the library's cache). NULL ok.
+ * Does not wait for work the context has queued: its blocks are handed out
+ * again only after an event recorded on its stream at this call has completed,
+ * so a context created next on the same stream may be prepared at once. A
+ * context that took part in the cached pt_maxnull_naive_batched graph is waited
+ * for (the device is synchronised) before its memory is returned. Results the
+ * queued work writes into caller buffers still arrive in stream order. */
 void pt_destroy(pt_ctx* ctx);
 
-/* Returns every cached device block to the driver (cudaFree). Call only while no
- * context's work is in flight. */
+/* Returns every cached device block to the driver (cudaFree), after waiting for
+ * the work of destroyed contexts whose blocks are still held back. */
 void pt_release_cached_memory(void);
 
 #ifdef __cplusplus

@@ -22,6 +22,27 @@ namespace {
 std::mutex g_alloc_mu;
 std::map<std::pair<int, size_t>, std::vector<void*>> g_free;
 std::map<void*, std::pair<int, size_t>> g_live;
+// Blocks of destroyed contexts whose work may still be queued: reusable once
+// the event recorded behind that work has completed.
+struct Deferred {
+  cudaEvent_t ev;
+  std::vector<std::pair<void*, std::pair<int, size_t>>> blocks;
+};
+std::vector<Deferred> g_deferred;
+
+// Moves every block whose event has completed to the free lists (lock held).
+void reclaim_locked() {
+  for (size_t i = 0; i < g_deferred.size();) {
+    if (cudaEventQuery(g_deferred[i].ev) == cudaErrorNotReady) {
+      ++i;
+      continue;
+    }
+    for (auto& b : g_deferred[i].blocks) g_free[b.second].push_back(b.first);
+    cudaEventDestroy(g_deferred[i].ev);
+    g_deferred[i] = std::move(g_deferred.back());
+    g_deferred.pop_back();
+  }
+}
 
 size_t round_size(size_t b) {
   if (b == 0) b = 1;
@@ -47,6 +68,7 @@ void* dev_alloc(size_t bytes) {
   const size_t sz = round_size(bytes);
   {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (!g_deferred.empty()) reclaim_locked();
     auto it = g_free.find({dev, sz});
     if (it != g_free.end() && !it->second.empty()) {
       void* p = it->second.back();
@@ -86,6 +108,20 @@ void dev_free(void* p) {
   if (it == g_live.end()) return;
   g_free[it->second].push_back(p);
   g_live.erase(it);
+}
+
+// The blocks become reusable when ev (recorded behind the last work that
+// reads them; the cache owns it from here) has completed.
+void dev_free_after(const std::vector<void*>& ps, cudaEvent_t ev) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  Deferred d{ev, {}};
+  for (void* p : ps) {
+    auto it = g_live.find(p);
+    if (it == g_live.end()) continue;
+    d.blocks.push_back({p, it->second});
+    g_live.erase(it);
+  }
+  g_deferred.push_back(std::move(d));
 }
 
 bool Buf::ensure(size_t want) {
@@ -407,7 +443,9 @@ pt_status pt_profile_read(pt_ctx* ctx, double* total_ms, int64_t* launches) {
     return PT_ERR_INVALID;
   }
   cudaSetDevice(ctx->device);
-  PT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  // Waits for the last timed launch only (later work on the stream may run on).
+  if (!ctx->ev_pending.empty())
+    PT_CUDA_TRY(ctx, cudaEventSynchronize(ctx->ev_pending.back().second));
   double tot = 0.0;
   for (auto& ev : ctx->ev_pending) {
     float ms = 0.f;
@@ -433,13 +471,16 @@ pt_status pt_debug_device_reset(void) {
   return PT_OK;
 }
 
+// Does not wait for the context's queued work: its workspaces go back to the
+// cache behind an event recorded on its stream and are handed out again once
+// that work has finished. A context that took part in a captured batch (whose
+// graph runs on the lead context's stream) is waited for instead.
 void pt_destroy(pt_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  cudaStreamSynchronize(ctx->stream);
-  pt::batch_forget(ctx);
+  const bool member = pt::batch_forget(ctx);
   for (auto& ev : ctx->ev_pending) ctx->ev_pool.push_back(ev);
-  for (auto& ev : ctx->ev_pool) {
+  for (auto& ev : ctx->ev_pool) {  // released by the runtime once recorded work completes
     cudaEventDestroy(ev.first);
     cudaEventDestroy(ev.second);
   }
@@ -449,7 +490,22 @@ void pt_destroy(pt_ctx* ctx) {
                      &ctx->maxkey,  &ctx->cnt,      &ctx->scratch,   &ctx->tcdesc,
                      &ctx->moments, &ctx->glmQ,     &ctx->glm_coef,  &ctx->glm_inv,
                      &ctx->rowscale, &ctx->grid_inv};
-  for (pt::Buf* b : bufs) b->release();
+  cudaEvent_t done = nullptr;
+  if (!member && cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventRecord(done, ctx->stream) == cudaSuccess) {
+    std::vector<void*> ps;
+    for (pt::Buf* b : bufs) {
+      if (b->p) ps.push_back(b->p);
+      b->p = nullptr;
+      b->bytes = 0;
+    }
+    pt::dev_free_after(ps, done);
+  } else {
+    if (done) cudaEventDestroy(done);
+    if (member) cudaDeviceSynchronize();
+    else cudaStreamSynchronize(ctx->stream);
+    for (pt::Buf* b : bufs) b->release();
+  }
   delete ctx;
 }
 
@@ -457,6 +513,12 @@ void pt_release_cached_memory(void) {
   std::vector<void*> drop;
   {
     std::lock_guard<std::mutex> lk(pt::g_alloc_mu);
+    for (auto& d : pt::g_deferred) {  // blocks of destroyed contexts: after their work
+      cudaEventSynchronize(d.ev);
+      cudaEventDestroy(d.ev);
+      for (auto& b : d.blocks) drop.push_back(b.first);
+    }
+    pt::g_deferred.clear();
     for (auto& kv : pt::g_free) {
       drop.insert(drop.end(), kv.second.begin(), kv.second.end());
       kv.second.clear();

@@ -20,6 +20,9 @@ enum : uint32_t {
   kErrGlmSpan = 8u,   // a relabelled group column lies in the span of the covariates
 };
 
+// Relabelling rows finished per 256-thread CTA by finalize_max_kernel.
+constexpr int kFinRowsPerBlock = 16;
+
 // Covariate-adjusted statistic: at most this many columns in [1, Z].
 constexpr int kGlmMaxQ1 = 17;
 
@@ -27,6 +30,8 @@ constexpr int kGlmMaxQ1 = 17;
 // recycled, so steady-state calls never reach cudaMalloc.
 void* dev_alloc(size_t bytes);
 void dev_free(void* p);
+// Frees blocks once ev (owned by the cache from here) has completed.
+void dev_free_after(const std::vector<void*>& ps, cudaEvent_t ev);
 
 // A device buffer owned by a context; grows on demand, never shrinks.
 struct Buf {
@@ -169,8 +174,9 @@ pt_status cluster_observed_impl(pt_ctx* ctx, double tau, const int32_t* dims, in
                                 int32_t* label, int32_t* size);
 pt_status fwer_pvalues_impl(pt_ctx* ctx, const float* maxnull, int64_t P, int two_sided,
                             float* p_out);
-// Drops a cached batched graph that names this context (from pt_destroy).
-void batch_forget(const pt_ctx* ctx);
+// Drops a cached batched graph that names this context (from pt_destroy);
+// true if it did.
+bool batch_forget(const pt_ctx* ctx);
 // Drops the cached batched graph (the tuned configurations changed).
 void batch_drop_graph();
 

@@ -245,64 +245,69 @@ __global__ void __launch_bounds__(256, 2)
 // ---------------------------------------------------------------------------
 // Finalise: packed keys -> t (FP64 from u), masked argmax; counts -> masked order.
 // ---------------------------------------------------------------------------
-// One warp per relabelling row. The contraction only selects the winning voxel
-// (u orders voxels exactly as t does); its statistic is then recomputed here in
-// FP64 from the input values, two-pass, as Eq. (5) defines it, so the reported
-// maximum carries no FP32/BF16 error even where t = f(u) is ill-conditioned
-// (few degrees of freedom, very unequal groups).
-__global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxkey, int64_t P,
-                                    const int32_t* __restrict__ valid_map,
-                                    const float* __restrict__ Xraw, int n, int n1, int n_pad,
-                                    const int32_t* __restrict__ perms, int two_sided,
-                                    float* __restrict__ maxnull, int32_t* __restrict__ argmax) {
-  __shared__ uint32_t g1_all[8][32];
+// Sixteen lanes per relabelling row (two rows per warp, kFinRowsPerBlock rows
+// per 256-thread CTA, so a 10,000-row call fits in one wave of the GPU). The
+// contraction only selects the winning voxel (u orders voxels exactly as t
+// does); its statistic is then recomputed here in FP64 from the input values,
+// two-pass, as Eq. (5) defines it, so the reported maximum carries no
+// FP32/BF16 error even where t = f(u) is ill-conditioned (few degrees of
+// freedom, very unequal groups).
+__global__ void __launch_bounds__(256)
+    finalize_max_kernel(const unsigned long long* __restrict__ maxkey, int64_t P,
+                        const int32_t* __restrict__ valid_map, const float* __restrict__ Xraw,
+                        int n, int n1, int n_pad, const int32_t* __restrict__ perms,
+                        int two_sided, float* __restrict__ maxnull, int32_t* __restrict__ argmax) {
+  constexpr int L = 256 / kFinRowsPerBlock;  // lanes per row
+  __shared__ uint32_t g1_all[kFinRowsPerBlock][32];
   __shared__ double rc[3];  // 1/n1, 1/n2, (1/n1 + 1/n2)/(n - 2)
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t* g1 = g1_all[wib];
+  const int grp = threadIdx.x / L, gl = threadIdx.x % L;
+  const unsigned gmask = ((1u << L) - 1u) << (threadIdx.x & 31 & ~(L - 1));
+  uint32_t* g1 = g1_all[grp];
   if (threadIdx.x == 0) {
     rc[0] = __drcp_rn(double(n1));
     rc[1] = __drcp_rn(double(n - n1));
     rc[2] = (rc[0] + rc[1]) * __drcp_rn(double(n - 2));
   }
   __syncthreads();
-  for (int64_t i = int64_t(blockIdx.x) * 8 + wib; i < P; i += int64_t(gridDim.x) * 8) {
+  for (int64_t i = int64_t(blockIdx.x) * kFinRowsPerBlock + grp; i < P;
+       i += int64_t(gridDim.x) * kFinRowsPerBlock) {
     const unsigned long long key = maxkey[i];
     if (key == 0ull) {
-      if (lane == 0) {
+      if (gl == 0) {
         maxnull[i] = -INFINITY;
         argmax[i] = -1;
       }
       continue;
     }
     const uint32_t c = unpack_key_index(key);
-    g1[lane] = 0u;
-    __syncwarp();
+    for (int q = gl; q < 32; q += L) g1[q] = 0u;
+    __syncwarp(gmask);
     const int32_t* row = perms + i * n;
-    for (int q = lane; q < n1; q += 32) {
+    for (int q = gl; q < n1; q += L) {
       const int32_t e = row[q];
       if (e >= 0 && e < n) atomicOr(&g1[e >> 5], 1u << (e & 31));  // others: reported by labels
     }
-    __syncwarp();
+    __syncwarp(gmask);
     const float* x = Xraw + int64_t(valid_map[c]) * n_pad;  // Xraw is in masked order
     // Two-pass group sums in float-float (FP32 pipes; ~44 significant bits) of
     // the values scaled by the power of two that puts max |x| in [1, 2) (exact;
     // squares cannot overflow; t does not depend on the scale), the means and
     // the statistic in FP64.
     float amax = 0.0f;
-    for (int s = lane; s < n; s += 32) amax = fmaxf(amax, fabsf(x[s]));
-    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    for (int s = gl; s < n; s += L) amax = fmaxf(amax, fabsf(x[s]));
+    for (int o = L / 2; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(gmask, amax, o));
     int ex = int((__float_as_uint(amax) >> 23) & 0xffu) - 127;
     ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
     const float scale = __uint_as_float(uint32_t(127 - ex) << 23);
     float s1h = 0.0f, s1l = 0.0f, s2h = 0.0f, s2l = 0.0f;
-    for (int s = lane; s < n; s += 32) {
+    for (int s = gl; s < n; s += L) {
       const float xs = x[s] * scale;
       if ((g1[s >> 5] >> (s & 31)) & 1u) ff_acc(s1h, s1l, xs, 0.0f);
       else ff_acc(s2h, s2l, xs, 0.0f);
     }
-    for (int o = 16; o > 0; o >>= 1) {  // two-sum is exact, so every lane ends with the same sums
-      const float a = __shfl_xor_sync(0xffffffffu, s1h, o), b = __shfl_xor_sync(0xffffffffu, s1l, o);
-      const float c2 = __shfl_xor_sync(0xffffffffu, s2h, o), d = __shfl_xor_sync(0xffffffffu, s2l, o);
+    for (int o = L / 2; o > 0; o >>= 1) {  // two-sum is exact, so every lane ends with the same sums
+      const float a = __shfl_xor_sync(gmask, s1h, o), b = __shfl_xor_sync(gmask, s1l, o);
+      const float c2 = __shfl_xor_sync(gmask, s2h, o), d = __shfl_xor_sync(gmask, s2l, o);
       ff_acc(s1h, s1l, a, b);
       ff_acc(s2h, s2l, c2, d);
     }
@@ -310,7 +315,7 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
     const float m1h = float(m1), m1l = float(m1 - double(m1h));
     const float m2h = float(m2), m2l = float(m2 - double(m2h));
     float ssh = 0.0f, ssl = 0.0f;
-    for (int s = lane; s < n; s += 32) {
+    for (int s = gl; s < n; s += L) {
       const bool in1 = (g1[s >> 5] >> (s & 31)) & 1u;
       float dh, dl;
       two_sum(x[s] * scale, in1 ? -m1h : -m2h, dh, dl);
@@ -321,17 +326,17 @@ __global__ void finalize_max_kernel(const unsigned long long* __restrict__ maxke
       const float p = dh * dh;
       ff_acc(ssh, ssl, p, fmaf(2.0f * dh, dl, fmaf(dh, dh, -p)));
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const float a = __shfl_xor_sync(0xffffffffu, ssh, o), b = __shfl_xor_sync(0xffffffffu, ssl, o);
+    for (int o = L / 2; o > 0; o >>= 1) {
+      const float a = __shfl_xor_sync(gmask, ssh, o), b = __shfl_xor_sync(gmask, ssl, o);
       ff_acc(ssh, ssl, a, b);
     }
     const double ss = ff_d(ssh, ssl);
-    if (lane == 0) {
+    if (gl == 0) {
       const double t = (m1 - m2) * rsqrt(ss * rc[2]);
       maxnull[i] = float(two_sided ? fabs(t) : t);
       argmax[i] = valid_map[c];
     }
-    __syncwarp();
+    __syncwarp(gmask);
   }
 }
 
@@ -478,7 +483,8 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
     s = glm_finalize(ctx, perms, P, o.two_sided, maxnull, argmax);
     if (s != PT_OK) return s;
   } else {
-    finalize_max_kernel<<<grid_1d((P + 7) / 8, 1), 256, 0, st>>>(
+    const int fin_blocks = grid_1d((P + kFinRowsPerBlock - 1) / kFinRowsPerBlock, 1);
+    finalize_max_kernel<<<fin_blocks, 256, 0, st>>>(
         ctx->maxkey.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(),
         ctx->Xraw.as<float>(), ctx->n, ctx->n1, ctx->n_pad, perms, o.two_sided, maxnull, argmax);
     PT_LAUNCH_CHECK(ctx);
@@ -538,13 +544,14 @@ void batch_drop_graph() {
 }
 
 // Called by pt_destroy: a cached graph must not outlive the buffers it names.
-void batch_forget(const pt_ctx* ctx) {
+bool batch_forget(const pt_ctx* ctx) {
   std::lock_guard<std::mutex> lk(g_batch_mu);
   for (const pt_ctx* m : g_batch.members)
     if (m == ctx) {
       drop_graph_locked();
-      return;
+      return true;
     }
+  return false;
 }
 
 static pt_status batched_enqueue(pt_ctx* lead, pt_ctx* const* ctxs, int n,
@@ -566,7 +573,8 @@ static pt_status batched_enqueue(pt_ctx* lead, pt_ctx* const* ctxs, int n,
   if (s != PT_OK) return s;
   for (int i = 0; i < n; ++i) {
     pt_ctx* c = ctxs[i];
-    finalize_max_kernel<<<grid_1d((P[i] + 7) / 8, 1), 256, 0, st>>>(
+    const int fin_blocks = grid_1d((P[i] + kFinRowsPerBlock - 1) / kFinRowsPerBlock, 1);
+    finalize_max_kernel<<<fin_blocks, 256, 0, st>>>(
         c->maxkey.as<unsigned long long>(), P[i], c->valid_map.as<int32_t>(), c->Xraw.as<float>(),
         c->n, c->n1, c->n_pad, perms[i], o.two_sided, maxnull[i], argmax[i]);
     PT_LAUNCH_CHECK(lead);

@@ -311,7 +311,8 @@ extern "C" pt_status pt_maxnull_naive_noalloc(const float* X, int32_t n, int64_t
     simt_contract_kernel<<<grid, 256, 0, st>>>(L, Xn32, n_pad, P, v_valid, per, 0, two_sided,
                                                u_obs, rowflag, maxkey, cnt, nullptr);
   }
-  finalize_max_kernel<<<blocks_for((P + 7) / 8, 1), 256, 0, st>>>(
+  const int fin_blocks = blocks_for((P + kFinRowsPerBlock - 1) / kFinRowsPerBlock, 1);
+  finalize_max_kernel<<<fin_blocks, 256, 0, st>>>(
       maxkey, P, valid_map, Xraw, n, n1, n_pad, perms, two_sided, maxnull, argmax);
   if (counts && v_valid > 0)
     scatter_counts_kernel<<<blocks_for(v_valid, 256), 256, 0, st>>>(cnt, v_valid, valid_map,

@@ -118,121 +118,205 @@ __global__ void iota64_kernel(int64_t* __restrict__ out, int64_t N) {
 }
 
 // ---------------------------------------------------------------------------
-// Moments. A CTA takes 32 consecutive mask voxels (lane = voxel); warp w loads
-// subjects w, w + 8, ... of them into shared memory (reads of X along a grid
-// row are coalesced) and the tile is written out as voxel-major rows of Xraw.
-// Per voxel the values are scaled by the power of two that brings max |x| into
-// [1, 2) (exact; no overflow of squares for any finite input), then reduced in
-// float-float arithmetic (an unevaluated pair h + l, about 44 significant
-// bits; FP64 throughput on this part is a small fraction of FP32):
-//   pass 1: S = sum_s y_s, mean = S / n                 (y = scaled x)
-//   pass 2: d = y - mean, D_g = sum_{G_g} d, Q_g = sum_{G_g} d^2  (g = 1, 2)
-// and finished in FP64 per voxel (the textbook corrected two-pass formulas):
-//   delta = (D_1 + D_2)/n,  SS = Q_1 + Q_2 - (D_1 + D_2) delta,
-//   A_g = D_g - n_g delta = sum_{G_g} (y - mean(y)),
-//   SS_w = sum_g (Q_g - D_g^2 / n_g),
-//   t_obs = (A_1/n_1 - A_2/n_2) / sqrt(SS_w/(n-2) (1/n_1 + 1/n_2))   (Eq. (5)),
-//   u_obs = A_1 / sqrt(SS).
-// t and u do not depend on the scale; mean and 1/sqrt(SS) are unscaled.
-// A voxel is degenerate (no t) exactly when all its values are equal.
+// Moments. A CTA takes 32 consecutive mask voxels (lane = voxel); warp w holds
+// subjects w, w + 8, ... of them in a shared-memory tile (reads of X along a
+// grid row are coalesced), and the tile is written out as voxel-major rows of
+// Xraw. Per voxel:
+//   pass 1: FP32 sum of x (a seed mean m), max |x|, the flags;
+//   pass 2: with y = x s and s the power of two that brings max |x| into
+//           [1, 2) (exact; squares cannot overflow for any finite input),
+//           d = y - m s exactly as a pair (two-sum), and per group the sums
+//           D_g = sum_{G_g} d and Q_g = sum_{G_g} d^2 as float-float pairs
+//           (an unevaluated h + l, about 44 significant bits);
+// then finished in float-float (FP64 issues at a small fraction of the FP32
+// rate on this part; only the three outputs are widened to FP64):
+//   delta = (D_1 + D_2)/n,  SS = Q_1 + Q_2 - (D_1 + D_2) delta  (the corrected
+//   two-pass formula: the seed mean's rounding cancels),
+//   A_1 = sum_{G_1} (y - mean(y)) = (n_2 D_1 - n_1 D_2)/n,
+//   SS_w = SS - k A_1^2     (between-group SS = A_1^2/n_1 + A_2^2/n_2, A_2 = -A_1),
+//   t_obs = sqrt(k (n-2)) A_1 / sqrt(SS_w)                        (Eq. (5)),
+//   u_obs = A_1 / sqrt(SS),
+// with 1/sqrt from the FP32 estimate and one Newton step carried in
+// float-float (relative error about 2^-43). t and u do not depend on s; the
+// mean and 1/sqrt(SS) are unscaled exactly. A voxel is degenerate (no t)
+// exactly when all its values are equal.
 constexpr int kMV = 32;  // voxels per CTA (one per lane)
-constexpr int kMW = 8;   // warps per CTA; warp w sums subjects s = w, w + 8, ...
+constexpr int kMW = 8;   // warps per CTA; warp w holds subjects s = w, w + 8, ...
+constexpr int kMU = 4;   // subject loads in flight per warp (host-memory X)
+constexpr float kFltMax = 3.402823466e38f;
 
+// Float-float values: h + l with |l| <= ulp(h)/2.
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_norm(float s, float e) {  // needs |s| >= |e|
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return ff_norm(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, FF{-b.h, -b.l}); }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = a.h * b.h;
+  const float e = fmaf(a.h, b.h, -p);  // the product's rounding error, exact
+  return ff_norm(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+__device__ __forceinline__ FF ff_mulf(FF a, float b) {
+  const float p = a.h * b;
+  return ff_norm(p, fmaf(a.l, b, fmaf(a.h, b, -p)));
+}
+__device__ __forceinline__ double ff_d(FF a) { return double(a.h) + double(a.l); }
+// 1/sqrt(x), x > 0 (normal): r = rsqrtf(x.h) is within a few ulp, so y = x r^2
+// lies within 2^-20 of 1 and 1 - y.h is exact; one Newton step
+// r (1 + (1 - y)/2) squares the relative error (about 2^-43 after it).
+__device__ __forceinline__ FF ff_rsqrt(FF x) {
+  const float r = rsqrtf(x.h);
+  const float r2 = r * r;
+  const FF y = ff_mul(x, FF{r2, fmaf(r, r, -r2)});
+  const float e = (1.0f - y.h) - y.l;
+  return ff_norm(r, 0.5f * r * e);
+}
 
-// 1/n, 1/n_1, 1/n_2 and (1/n_1 + 1/n_2)/(n - 2), rounded once on the host.
+// 1/n, k = 1/n_1 + 1/n_2 and sqrt(k (n - 2)) as float-float pairs (host), n_1, n_2.
 struct MomentRecips {
-  double rn, rn1, rn2, kw;
+  FF rn, k, ct;
+  float n1f, n2f;
 };
 
-__global__ void __launch_bounds__(32 * kMW)
-    moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1, int n_pad,
-                   const MomentRecips rc,
-                   const int64_t* __restrict__ vox_grid, int64_t v, double* __restrict__ mean_out,
-                   double* __restrict__ inv_norm_out, double* __restrict__ t_obs,
-                   float* __restrict__ u_obs_m, uint8_t* __restrict__ valid,
-                   float* __restrict__ Xraw, uint32_t* __restrict__ status) {
-  extern __shared__ float tile[];  // [n][kMV + 1]
-  __shared__ float part[kMW][6][kMV];
-  __shared__ uint32_t flags[kMW][kMV];
+struct MomentOut {
+  double* mean;
+  double* inv_norm;
+  double* t_obs;
+  float* u_obs_m;
+  uint8_t* valid;
+  float* Xraw;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// One tile of kMV mask voxels starting at j0 (all threads of the CTA enter;
+// only warp 0 finishes the per-voxel part).
+template <bool kAsync>
+__device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_t n_grid, int n,
+                                             int n1, int n_pad, const MomentRecips& rc,
+                                             const int64_t* __restrict__ vox_grid, int64_t v,
+                                             int64_t j0, const MomentOut& o, float* tile,
+                                             float (*part)[8][kMV], uint32_t (*flags)[kMV]) {
   constexpr int LD = kMV + 1;
-  const int64_t j0 = int64_t(blockIdx.x) * kMV;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t j = j0 + lane;
   const int64_t g = j < v ? vox_grid[j] : -1;
 
-  // Load: lane = voxel; max |x| and the flags on the way.
-  const float x0f = g >= 0 ? X[g] : 0.0f;
-  float amax = 0.0f;
-  uint32_t fl = 0u;  // bit 0: non-finite seen, bit 1: a value differs from x_0
-  {
-    const float* xp = X + (g >= 0 ? g : 0) + int64_t(warp) * n_grid;
-    const int64_t step = int64_t(kMW) * n_grid;
-    for (int s = warp; s < n; s += kMW, xp += step) {
-      const float xf = g >= 0 ? *xp : 0.0f;
-      tile[s * LD + lane] = xf;
-      if (!isfinite(xf)) fl |= 1u;
-      if (xf != x0f) fl |= 2u;
-      amax = fmaxf(amax, fabsf(xf));
+  // Load: lane = voxel. From device memory every value of the tile is copied
+  // with cp.async at once (n x 32 x 4 bytes in flight per CTA, no registers
+  // held); from host memory (read over the host link) kMU subjects per warp
+  // go through registers. Each thread reads back only the values it copied.
+  const float x0f = g >= 0 ? __ldcs(X + g) : 0.0f;
+  const float* xp = X + (g >= 0 ? g : 0);
+  if constexpr (kAsync) {
+    for (int s = warp; s < n; s += kMW) {
+      float* dst = &tile[s * LD + lane];
+      if (g >= 0) cp_async_f32(dst, xp + int64_t(s) * n_grid);
+      else *dst = 0.0f;
+    }
+    cp_async_wait_all();
+  } else {
+    for (int s0 = warp; s0 < n; s0 += kMU * kMW) {
+      float xv[kMU];
+#pragma unroll
+      for (int q = 0; q < kMU; ++q) {
+        const int s = s0 + q * kMW;
+        xv[q] = (g >= 0 && s < n) ? __ldcs(xp + int64_t(s) * n_grid) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < kMU; ++q) {
+        const int s = s0 + q * kMW;
+        if (s < n) tile[s * LD + lane] = xv[q];
+      }
     }
   }
+
+  // Pass 1: FP32 sum (only the seed of the centring: the two-pass correction
+  // removes its rounding), max |x| and the flags (bit 0: NaN or Inf seen,
+  // bit 1: a value differs from x_0). A sum that overflows while every value
+  // is finite (|x| near the FP32 limit) is retaken on the scaled values.
+  float S = 0.0f, amax = 0.0f;
+  uint32_t fl = 0u;
+  for (int s = warp; s < n; s += kMW) {
+    const float x = tile[s * LD + lane];
+    S += x;
+    amax = fmaxf(amax, fabsf(x));
+    if (!(fabsf(x) <= kFltMax)) fl |= 1u;
+    if (x != x0f) fl |= 2u;
+  }
   part[warp][0][lane] = amax;
+  part[warp][1][lane] = S;
   flags[warp][lane] = fl;
   __syncthreads();
   // Voxel-major copy: warp w writes rows l = w, w + 8, ... (lane = subject;
   // tile reads at stride LD = 33 words fall in distinct banks).
   for (int l = warp; l < kMV && j0 + l < v; l += kMW) {
-    float* dst = Xraw + (j0 + l) * n_pad;
+    float* dst = o.Xraw + (j0 + l) * n_pad;
     for (int s = lane; s < n_pad; s += 32) dst[s] = s < n ? tile[s * LD + l] : 0.0f;
   }
   fl = 0u;
   amax = 0.0f;
+  S = 0.0f;
 #pragma unroll
   for (int w = 0; w < kMW; ++w) {
     amax = fmaxf(amax, part[w][0][lane]);
+    S += part[w][1][lane];
     fl |= flags[w][lane];
   }
   if (fl & 1u) amax = 1.0f;  // reported below; keep the arithmetic finite
   int ex = int((__float_as_uint(amax) >> 23) & 0xffu) - 127;
   ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
   const float scale = __uint_as_float(uint32_t(127 - ex) << 23);  // 2^-ex, exact
-
-  // Pass 1: sum of the scaled values, then the float-float mean.
-  float Sh = 0.0f, Sl = 0.0f;
-  for (int s = warp; s < n; s += kMW) ff_acc(Sh, Sl, tile[s * LD + lane] * scale, 0.0f);
-  __syncthreads();  // everyone has read part[.][0]
-  part[warp][0][lane] = Sh;
-  part[warp][1][lane] = Sl;
-  __syncthreads();
-  Sh = 0.0f;
-  Sl = 0.0f;
+  const float inv_n = 1.0f / float(n);
+  float ms = (S * inv_n) * scale;  // seed mean of the scaled values
+  if (__syncthreads_or(!(fabsf(S) <= kFltMax) && !(fl & 1u))) {
+    float Ss = 0.0f;  // overflowed sums only: the scaled sum (cannot overflow)
+    for (int s = warp; s < n; s += kMW) Ss += tile[s * LD + lane] * scale;
+    part[warp][2][lane] = Ss;
+    __syncthreads();
+    Ss = 0.0f;
 #pragma unroll
-  for (int w = 0; w < kMW; ++w) ff_acc(Sh, Sl, part[w][0][lane], part[w][1][lane]);
-  const float nf = float(n);
-  const float q1 = Sh / nf;
-  const float q2 = (fmaf(-q1, nf, Sh) + Sl) / nf;  // the residual Sh - q1 n is exact
-  float mh, ml;
-  two_sum(q1, q2, mh, ml);
+    for (int w = 0; w < kMW; ++w) Ss += part[w][2][lane];
+    if (!(fabsf(S) <= kFltMax)) ms = Ss * inv_n;
+  }
+  if (fl & 1u) ms = 0.0f;
 
-  // Pass 2: centred sums per observed group.
+  // Pass 2: d = y - m exactly as a pair, its square as a pair, and per group
+  // D_g and Q_g as (high, accumulated low) pairs: each addition's rounding
+  // error is exact (two-sum) and goes into the low word with the value's own
+  // low part.
   float D1h = 0.f, D1l = 0.f, D2h = 0.f, D2l = 0.f, Q1h = 0.f, Q1l = 0.f, Q2h = 0.f, Q2l = 0.f;
-  for (int s = warp; s < n; s += kMW) {
-    float dh, dl;
-    two_sum(tile[s * LD + lane] * scale, -mh, dh, dl);
-    dl -= ml;
-    const float t = dh + dl;  // renormalise d
-    dl = dl - (t - dh);
-    dh = t;
+  auto add_value = [&](float x, float& Dh, float& Dl, float& Qh, float& Ql) {
+    float dh, dl, sh, se;
+    two_sum(x * scale, -ms, dh, dl);
     const float p = dh * dh;
     const float pe = fmaf(2.0f * dh, dl, fmaf(dh, dh, -p));
-    if (s < n1) {
-      ff_acc(D1h, D1l, dh, dl);
-      ff_acc(Q1h, Q1l, p, pe);
-    } else {
-      ff_acc(D2h, D2l, dh, dl);
-      ff_acc(Q2h, Q2l, p, pe);
-    }
-  }
-  __syncthreads();  // everyone has read the pass-1 partials
+    two_sum(Dh, dh, sh, se);
+    Dh = sh;
+    Dl += se + dl;
+    two_sum(Qh, p, sh, se);
+    Qh = sh;
+    Ql += se + pe;
+  };
+  int s = warp;
+  for (; s < n1; s += kMW) add_value(tile[s * LD + lane], D1h, D1l, Q1h, Q1l);
+  for (; s < n; s += kMW) add_value(tile[s * LD + lane], D2h, D2l, Q2h, Q2l);
+  __syncthreads();  // everyone has read the pass-1 partials (and the tile)
   float* pp = &part[warp][0][0];
   pp[0 * kMV + lane] = D1h;
   pp[1 * kMV + lane] = D1l;
@@ -240,56 +324,69 @@ __global__ void __launch_bounds__(32 * kMW)
   pp[3 * kMV + lane] = D2l;
   pp[4 * kMV + lane] = Q1h;
   pp[5 * kMV + lane] = Q1l;
-  __syncthreads();
-  // Q2 stays in registers: a second round of partials after the first is read.
-  if (warp == 0) {
-    D1h = D1l = D2h = D2l = Q1h = Q1l = 0.0f;
-#pragma unroll
-    for (int w = 0; w < kMW; ++w) {
-      ff_acc(D1h, D1l, part[w][0][lane], part[w][1][lane]);
-      ff_acc(D2h, D2l, part[w][2][lane], part[w][3][lane]);
-      ff_acc(Q1h, Q1l, part[w][4][lane], part[w][5][lane]);
-    }
-  }
-  __syncthreads();
-  part[warp][0][lane] = Q2h;
-  part[warp][1][lane] = Q2l;
+  pp[6 * kMV + lane] = Q2h;
+  pp[7 * kMV + lane] = Q2l;
   __syncthreads();
   if (warp != 0) return;
-  Q2h = Q2l = 0.0f;
+  D1h = D1l = D2h = D2l = Q1h = Q1l = Q2h = Q2l = 0.0f;
 #pragma unroll
-  for (int w = 0; w < kMW; ++w) ff_acc(Q2h, Q2l, part[w][0][lane], part[w][1][lane]);
+  for (int w = 0; w < kMW; ++w) {
+    ff_acc(D1h, D1l, part[w][0][lane], part[w][1][lane]);
+    ff_acc(D2h, D2l, part[w][2][lane], part[w][3][lane]);
+    ff_acc(Q1h, Q1l, part[w][4][lane], part[w][5][lane]);
+    ff_acc(Q2h, Q2l, part[w][6][lane], part[w][7][lane]);
+  }
   if (j >= v) return;
   if (fl & 1u) {
-    atomicOr(status, kErrBadData);
-    valid[j] = 0;
-    t_obs[j] = nan("");
+    atomicOr(o.status, kErrBadData);
+    o.valid[j] = 0;
+    o.t_obs[j] = nan("");
     return;
   }
-  // FP64 from here on, with the reciprocals of n, n_1, n_2 and k/(n-2) passed
-  // in and reciprocal square roots (FP64 divides are many FP64 operations).
-  const int n2 = n - n1;
-  const double D1 = ff_d(D1h, D1l), D2 = ff_d(D2h, D2l);
-  const double Q1 = ff_d(Q1h, Q1l), Q2 = ff_d(Q2h, Q2l);
-  const double delta = (D1 + D2) * rc.rn;
-  const double SS = (Q1 + Q2) - (D1 + D2) * delta;
-  const double A1 = D1 - n1 * delta, A2 = D2 - n2 * delta;
-  double SSw = (Q1 - D1 * D1 * rc.rn1) + (Q2 - D2 * D2 * rc.rn2);
-  const double inv_scale = 1.0 / double(scale);  // exact power of two
-  const bool ok = (fl & 2u) && SS > 0.0;
-  valid[j] = ok ? 1 : 0;
-  mean_out[j] = (ff_d(mh, ml) + delta) * inv_scale;
+  // Finish in float-float; only the outputs are widened to FP64.
+  const FF D1{D1h, D1l}, D2{D2h, D2l};
+  const FF Dt = ff_add(D1, D2);
+  const FF delta = ff_mul(Dt, rc.rn);
+  const FF SS = ff_sub(ff_add(FF{Q1h, Q1l}, FF{Q2h, Q2l}), ff_mul(Dt, delta));
+  const FF A1 = ff_mul(ff_sub(ff_mulf(D1, rc.n2f), ff_mulf(D2, rc.n1f)), rc.rn);
+  // 1/s = 2^ex exactly (ex in [-126, 126])
+  const double unscale = __longlong_as_double(int64_t(1023 + ex) << 52);
+  const bool ok = (fl & 2u) && SS.h > 0.0f;
+  o.valid[j] = ok ? 1 : 0;
+  o.mean[j] = ff_d(ff_add(FF{ms, 0.0f}, delta)) * unscale;
   if (!ok) {
-    inv_norm_out[j] = 0.0;
-    t_obs[j] = nan("");
-    u_obs_m[j] = 0.0f;
+    o.inv_norm[j] = 0.0;
+    o.t_obs[j] = nan("");
+    o.u_obs_m[j] = 0.0f;
     return;
   }
-  if (SSw < 0.0) SSw = 0.0;
-  const double rs = rsqrt(SS);
-  inv_norm_out[j] = rs * double(scale);
-  t_obs[j] = (A1 * rc.rn1 - A2 * rc.rn2) * rsqrt(SSw * rc.kw);
-  u_obs_m[j] = float(A1 * rs);
+  const FF rs = ff_rsqrt(SS);
+  o.inv_norm[j] = ff_d(rs) * double(scale);
+  const FF SSw = ff_sub(SS, ff_mul(rc.k, ff_mul(A1, A1)));
+  // perfectly separated groups (SS_w = 0): t = +-infinity
+  o.t_obs[j] = SSw.h > 0.0f ? ff_d(ff_mul(ff_mul(rc.ct, A1), ff_rsqrt(SSw)))
+                            : copysign(double(INFINITY), double(A1.h));
+  o.u_obs_m[j] = ff_mul(A1, rs).h;
+}
+
+// Persistent over the tiles of the v mask voxels. v comes from the device
+// (v_dev, the mask compaction's count) when it is not known on the host; the
+// grid is then sized for the largest possible v.
+template <bool kAsync>
+__global__ void __launch_bounds__(32 * kMW, kAsync ? 8 : 6)
+    moments_kernel(const float* __restrict__ X, int64_t n_grid, int n, int n1, int n_pad,
+                   const MomentRecips rc, const int64_t* __restrict__ vox_grid, int64_t v_host,
+                   const uint32_t* __restrict__ v_dev, const MomentOut o) {
+  extern __shared__ float tile[];  // [n][kMV + 1]
+  __shared__ float part[kMW][8][kMV];
+  __shared__ uint32_t flags[kMW][kMV];
+  const int64_t v = v_dev ? int64_t(*v_dev) : v_host;
+  const int64_t tiles = (v + kMV - 1) / kMV;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    moments_tile<kAsync>(X, n_grid, n, n1, n_pad, rc, vox_grid, v, t * kMV, o, tile, part,
+                         flags);
+    __syncthreads();  // the tile and the partials are reused
+  }
 }
 
 // Per compact voxel: the FP64 mean and 1/sqrt(SS) as float pairs (hi + lo),
@@ -441,6 +538,17 @@ int grid_for(int64_t work, int threads) {
   return int(b);
 }
 
+FF to_ff(double d) {
+  const float h = float(d);
+  return FF{h, float(d - double(h))};
+}
+
+int sm_count(int dev) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
 pt_status nomem(pt_ctx* ctx, const char* what) {
   set_error(ctx, std::string("out of device memory (") + what + ")");
   return PT_ERR_NOMEM;
@@ -476,30 +584,40 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
     ~Guard() { b->release(); }
   } guard{&tmp2};
   Buf& mom = ctx->moments;
-  if (!ctx->status.ensure(2 * sizeof(uint32_t))) return nomem(ctx, "status");
-  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.p, 0, 2 * sizeof(uint32_t), st));
+  if (!ctx->status.ensure(4 * sizeof(uint32_t))) return nomem(ctx, "status");
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.p, 0, 4 * sizeof(uint32_t), st));
 
-  // 1. masked voxel list (raster order); one host sync to size the buffers
+  // 1. masked voxel list (raster order). Its length v stays on the device: the
+  //    buffers up to the validity compaction are sized for the whole grid and
+  //    the moments kernel reads v itself, so the stream is waited on once, at
+  //    the end (the covariate fit sizes its launch by v and waits here).
+  const uint32_t* v_dev = nullptr;
+  int64_t v_hi = ctx->n_grid;  // v, or an upper bound of it while v_dev is set
+  if (!ctx->vox_grid.ensure(sizeof(int64_t) * ctx->n_grid)) return nomem(ctx, "mask");
   if (mask) {
     uint32_t* tot = nullptr;
-    if (!ctx->vox_grid.ensure(sizeof(int64_t) * ctx->n_grid)) return nomem(ctx, "mask");
     pt_status s = compact<int64_t>(ctx, mask, ctx->n_grid, ctx->vox_grid.as<int64_t>(), &tot, tmp);
     if (s != PT_OK) return s;
-    uint32_t v = 0;
-    PT_CUDA_TRY(ctx, cudaMemcpyAsync(&v, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    ctx->v = v;
+    if (ctx->glm_q1) {
+      uint32_t vh = 0;
+      PT_CUDA_TRY(ctx, cudaMemcpyAsync(&vh, tot, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+      PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+      v_hi = vh;
+    } else {
+      v_dev = tot;
+      PT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->status.as<uint32_t>() + 2, tot, sizeof(uint32_t),
+                                       cudaMemcpyDeviceToDevice, st));
+    }
   } else {
-    ctx->v = ctx->n_grid;
-    if (!ctx->vox_grid.ensure(sizeof(int64_t) * ctx->v)) return nomem(ctx, "mask");
-    iota64_kernel<<<grid_for(ctx->v, 256), 256, 0, st>>>(ctx->vox_grid.as<int64_t>(), ctx->v);
+    iota64_kernel<<<grid_for(ctx->n_grid, 256), 256, 0, st>>>(ctx->vox_grid.as<int64_t>(),
+                                                              ctx->n_grid);
     PT_LAUNCH_CHECK(ctx);
   }
-  const int64_t v = ctx->v;
-  const int64_t vv = v > 0 ? v : 1;
+  ctx->v = v_hi;  // the covariate fit reads it; replaced by the count below
+  const int64_t vv = v_hi > 0 ? v_hi : 1;
   const int n_pad = ctx->n_pad;
 
-  // 2. FP64 moments, observed t and u, validity, raw voxel-major copy
+  // 2. moments, observed t and u, validity, raw voxel-major copy
   if (!mom.ensure(vv * (2 * sizeof(double) + sizeof(float) + 1) + 64) ||
       !ctx->t_obs64.ensure(sizeof(double) * vv) || !ctx->Xraw.ensure(sizeof(float) * vv * n_pad))
     return nomem(ctx, "moments");
@@ -507,18 +625,31 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
   double* inv_norm = mean + vv;
   float* u_obs_m = reinterpret_cast<float*>(inv_norm + vv);
   uint8_t* valid = reinterpret_cast<uint8_t*>(u_obs_m + vv);
-  if (v > 0) {
-    // dynamic tile plus ~7 KB of static partials: the opt-in is needed from
+  if (v_hi > 0) {
+    // flags past v stay 0 for the compaction over the upper bound
+    if (v_dev) PT_CUDA_TRY(ctx, cudaMemsetAsync(valid, 0, size_t(v_hi), st));
+    // device-resident X: cp.async tile loads; host memory: register loads
+    cudaPointerAttributes pa{};
+    const bool on_device = cudaPointerGetAttributes(&pa, X) == cudaSuccess &&
+                           (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    auto kern = on_device ? moments_kernel<true> : moments_kernel<false>;
+    // dynamic tile plus ~9 KB of static partials: the opt-in is needed from
     // well below 48 KB of dynamic memory, so it is always set
     const int smem = ctx->n * (kMV + 1) * int(sizeof(float));
-    PT_CUDA_TRY(ctx, cudaFuncSetAttribute(moments_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    moments_kernel<<<unsigned((v + kMV - 1) / kMV), 32 * kMW, smem, st>>>(
+    PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    PT_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kMW, smem));
+    const int64_t tiles = (v_hi + kMV - 1) / kMV;
+    const int64_t grid =
+        std::min<int64_t>(tiles, int64_t(std::max(per_sm, 1)) * sm_count(ctx->device));
+    kern<<<unsigned(grid), 32 * kMW, smem, st>>>(
         X, ctx->n_grid, ctx->n, ctx->n1, n_pad,
-        MomentRecips{1.0 / ctx->n, 1.0 / ctx->n1, 1.0 / ctx->n2, ctx->k / (ctx->n - 2)},
-        ctx->vox_grid.as<int64_t>(), v, mean, inv_norm,
-        ctx->t_obs64.as<double>(), u_obs_m, valid, ctx->Xraw.as<float>(),
-        ctx->status.as<uint32_t>());
+        MomentRecips{to_ff(1.0 / ctx->n), to_ff(ctx->k), to_ff(ctx->c_t), float(ctx->n1),
+                     float(ctx->n2)},
+        ctx->vox_grid.as<int64_t>(), v_hi, v_dev,
+        MomentOut{mean, inv_norm, ctx->t_obs64.as<double>(), u_obs_m, valid,
+                  ctx->Xraw.as<float>(), ctx->status.as<uint32_t>()});
     PT_LAUNCH_CHECK(ctx);
     if (ctx->glm_q1) {  // covariate-adjusted statistic: residual fit, validity, u/t_obs
       pt_status s = glm_moments(ctx, valid, u_obs_m);
@@ -526,19 +657,20 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
     }
   }
 
-  // 3. compact list of voxels with a defined t (sized by v; the count is read
-  //    together with the error bits at the single sync below)
+  // 3. compact list of voxels with a defined t (the count, v and the error
+  //    bits are read at the single wait below)
   if (!ctx->valid_map.ensure(sizeof(int32_t) * vv)) return nomem(ctx, "valid map");
   uint32_t* vtot = nullptr;
-  if (v > 0) {
-    pt_status s = compact<int32_t>(ctx, valid, v, ctx->valid_map.as<int32_t>(), &vtot, tmp2);
+  if (v_hi > 0) {
+    pt_status s = compact<int32_t>(ctx, valid, v_hi, ctx->valid_map.as<int32_t>(), &vtot, tmp2);
     if (s != PT_OK) return s;
     PT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->status.as<uint32_t>() + 1, vtot, sizeof(uint32_t),
                                      cudaMemcpyDeviceToDevice, st));
   }
-  uint32_t hb[2] = {0, 0};
+  uint32_t hb[4] = {0, 0, 0, 0};
   PT_CUDA_TRY(ctx, cudaMemcpyAsync(hb, ctx->status.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
   PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (v_dev) ctx->v = hb[2];
   if (hb[0] & kErrBadData) {
     set_error(ctx, "pt_prepare: X holds NaN or Inf in a mask voxel");
     return PT_ERR_INVALID;
@@ -546,7 +678,7 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
   ctx->v_valid = hb[1];
   ctx->v_pad = (ctx->v_valid + 255) / 256 * 256;
   if (ctx->v_pad == 0) ctx->v_pad = 256;
-  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.as<uint32_t>() + 1, 0, sizeof(uint32_t), st));
+  PT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->status.as<uint32_t>() + 1, 0, 3 * sizeof(uint32_t), st));
 
   // 4. per compact voxel constants for the operand builders
   if (!ctx->vstat.ensure(sizeof(float4) * ctx->v_pad) ||

@@ -1513,7 +1513,8 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
       }
     }
     if (s != PT_OK) return s;
-    finalize_max_kernel<<<grid_n((ell + 7) / 8, 1), 256, 0, st>>>(
+    const int fin_blocks = grid_n((ell + kFinRowsPerBlock - 1) / kFinRowsPerBlock, 1);
+    finalize_max_kernel<<<fin_blocks, 256, 0, st>>>(
         ctx->maxkey.as<unsigned long long>(), ell, ctx->valid_map.as<int32_t>(),
         ctx->Xraw.as<float>(), ctx->n, ctx->n1, ctx->n_pad, perms, 0, tmax.as<float>(),
         reinterpret_cast<int32_t*>(keys.p));

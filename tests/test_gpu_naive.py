@@ -141,6 +141,37 @@ def test_t_obs_matches_oracle(cuda_lib):
     ctx.close()
 
 
+@pytest.mark.parametrize("offset,unit", [(1.0e4, 1.0e-2), (-3.0e5, 1.0), (0.0, 1.0e-30),
+                                         (0.0, 1.0e30), (2.0e37, 1.0e36)])
+def test_moments_offsets_and_extreme_scales(cuda_lib, offset, unit):
+    """Data far from unit scale: a mean 10^6 standard deviations from zero (the
+    centring must not lose the spread; the FP32 values are quantised, so many
+    relabellings tie), values whose squares underflow or overflow FP32, and
+    values whose FP32 sum overflows (2e37 x 40 subjects). t_obs to FP32 output
+    rounding, and the max-null and counts of the FP32 and FP16x2 paths, against
+    the FP64 oracle on the same FP32 inputs."""
+    B = cuda_lib
+    n, n1, v, P = 40, 17, 3001, 300
+    X = (synth.gaussian_mean_shift(n, v, seed=31).astype(np.float64) * unit
+         + offset).astype(np.float32)
+    assert np.all(np.isfinite(X))
+    perms = synth.perms_pcg32(n, P, seed=32)
+    t_ref = oracle.naive(X, n1, synth.identity_perm(n)).t_obs
+    ok = ~np.isnan(t_ref)
+    assert ok.mean() > 0.99
+    ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1)
+    t = torch.empty(v, dtype=torch.float32, device="cuda")
+    B.pt_t_obs(ctx, t)
+    B.pt_sync(ctx)
+    t = t.cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.isnan(t), ~ok)
+    np.testing.assert_allclose(t[ok], t_ref[ok], rtol=2e-7, atol=1e-7)
+    ctx.close()
+    for precision in (0, 3):
+        ref = oracle.naive(X, n1, perms, tie_rel=tie_rel(precision, n))
+        check(ref, run_gpu(B, X, n1, perms, precision), precision, (offset, unit, precision))
+
+
 def test_invalid_relabelling_reported_and_context_survives(cuda_lib):
     B = cuda_lib
     n, n1, v, P = 16, 8, 300, 50
