@@ -352,10 +352,12 @@ pt_status pt_fwer_pvalues(pt_ctx* ctx, const float* maxnull, int64_t P, int32_t 
 /* subjects in the same order whatever the ring shape or the block split).    */
 /* ------------------------------------------------------------------------- */
 typedef struct {
-  int32_t voxel_tile;   /* voxels per work tile: 256, 128 or 64, fixed by n (the largest whose
-                           BF16 data pieces fit in shared memory; they stay there while the
-                           relabellings stream). It also fixes how the pieces' partial sums
-                           are combined, so a configuration must keep it. */
+  int32_t voxel_tile;   /* voxels per work tile: 256, 128, 96 or 64, fixed by n (the largest
+                           whose data pieces fit in shared memory beside a label ring deep
+                           enough to hide the label loads, else beside 4 stages; they stay
+                           there while the relabellings stream). It also fixes how the
+                           pieces' partial sums are combined, so a configuration must keep
+                           it. */
   int32_t stages;       /* depth of the shared-memory ring of label stages, 2..32 (limited by
                            what fits beside the data tile) */
   int32_t ksteps_per_stage; /* k-steps (128 relabellings x 16 subjects, 4 KB) per stage and per

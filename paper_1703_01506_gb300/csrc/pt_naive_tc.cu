@@ -149,6 +149,16 @@ __device__ __forceinline__ void flush_counts16(uint32_t (&r)[R], int lane, int64
 }
 
 // 8-bit counters (register g = local columns 4g..4g+3) -> 16-bit pairs -> flush.
+// flush_counts16 over R registers, R not a power of two: the largest power of
+// two first, then the rest (2 columns per register).
+template <int R>
+__device__ __forceinline__ void flush_counts16_any(uint32_t* r, int lane, int64_t col0, int64_t v,
+                                                   uint32_t* cnt) {
+  constexpr int Pw = (R & (R - 1)) == 0 ? R : (R >= 16 ? 16 : (R >= 8 ? 8 : (R >= 4 ? 4 : 2)));
+  flush_counts16<Pw>(*reinterpret_cast<uint32_t(*)[Pw]>(r), lane, col0, v, cnt);
+  if constexpr (Pw < R) flush_counts16_any<R - Pw>(r + Pw, lane, col0 + 2 * Pw, v, cnt);
+}
+
 template <int CW>
 __device__ __forceinline__ void flush_counts8(const uint32_t (&c8)[CW / 4], int lane, int64_t col0,
                                               int64_t v, uint32_t* cnt) {
@@ -158,12 +168,14 @@ __device__ __forceinline__ void flush_counts8(const uint32_t (&c8)[CW / 4], int 
     c16[2 * g] = (c8[g] & 0xffu) | ((c8[g] & 0xff00u) << 8);
     c16[2 * g + 1] = ((c8[g] >> 16) & 0xffu) | ((c8[g] >> 8) & 0xff0000u);
   }
-  flush_counts16<CW / 2>(c16, lane, col0, v, cnt);
+  flush_counts16_any<CW / 2>(c16, lane, col0, v, cnt);
 }
 
 template <int CW>
 __device__ __forceinline__ void tc_ld_cols(uint32_t taddr, uint32_t (&r)[CW]) {
-  if constexpr (CW == 16) {
+  if constexpr (CW == 8) {
+    tc_ld_32x32b_x8(taddr, r);
+  } else if constexpr (CW == 16) {
     tc_ld_32x32b_x16(taddr, r);
   } else {
 #pragma unroll
@@ -214,13 +226,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   // Accumulators per block (NACC), summed in the epilogue. The data pieces'
   // tiles are adjacent in shared memory, so one MMA of width q NT covers q of
   // them: NT = 256 accumulates every piece in one accumulator (one MMA per
-  // piece); NT = 128 keeps hi and mid(+lo) apart (one MMA of width 256 for
-  // hi and mid, one for lo); NT = 64 keeps every piece apart (one MMA of
+  // piece); NT = 128 and 96 keep hi and mid(+lo) apart (one MMA of width 2 NT
+  // for hi and mid, one for lo); NT = 64 keeps every piece apart (one MMA of
   // width PIECES x 64 per k-step, so the label operand is read once).
-  constexpr int NACC = NT == 256 ? 1 : (NT == 128 ? 2 : PIECES);
+  constexpr int NACC = NT == 256 ? 1 : (NT >= 96 ? 2 : PIECES);
   constexpr int ACC = NACC * NT;             // accumulator columns per buffer
   constexpr int CW = NT / 4;                 // voxel columns per epilogue thread
-  constexpr int CHK = NACC > 1 ? (CW < 16 ? CW : 16) : (CW < 32 ? CW : 32);  // per load
+  constexpr int CHK = NACC > 1 ? (CW % 16 == 0 ? 16 : 8) : (CW < 32 ? CW : 32);  // per load
   constexpr int NCH = CW / CHK;              // loads per block
   const bool do_reduce = !WRITE || a.do_reduce;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -592,10 +604,20 @@ int max_stages_fit(int NT, int n_pad, int pieces, int kps) {
   return s >= 2 ? s : 0;
 }
 
-// Largest voxel tile NT whose resident data tile fits beside at least 4
-// one-k-step label stages.
+// Largest voxel tile NT whose resident data tile leaves room for a label ring
+// that covers at least 2,048 MMA columns x k-steps (stages x pieces x NT; 8
+// one-k-step stages at two pieces of 128 voxels, about 1,000 cycles of MMA
+// work in flight, which the label loads' L2 latency needs), else the largest
+// that leaves at least 4 stages.
 bool choose_tile(int n_pad, int pieces, int* NT) {
-  for (int cand : {256, 128, 64}) {
+  for (int cand : {256, 128, 96, 64}) {
+    const int s = max_stages_fit(cand, n_pad, pieces, 1);
+    if (s >= 4 && s * pieces * cand >= 2048) {
+      *NT = cand;
+      return true;
+    }
+  }
+  for (int cand : {256, 128, 96, 64}) {
     if (max_stages_fit(cand, n_pad, pieces, 1) >= 4) {
       *NT = cand;
       return true;
@@ -679,10 +701,12 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   if (two_sided) {
     if (NT == 256) return launch_nt<256, true>(ctx, a, pieces, grid, smem);
     if (NT == 128) return launch_nt<128, true>(ctx, a, pieces, grid, smem);
+    if (NT == 96) return launch_nt<96, true>(ctx, a, pieces, grid, smem);
     return launch_nt<64, true>(ctx, a, pieces, grid, smem);
   }
   if (NT == 256) return launch_nt<256, false>(ctx, a, pieces, grid, smem);
   if (NT == 128) return launch_nt<128, false>(ctx, a, pieces, grid, smem);
+  if (NT == 96) return launch_nt<96, false>(ctx, a, pieces, grid, smem);
   return launch_nt<64, false>(ctx, a, pieces, grid, smem);
 }
 
@@ -781,7 +805,7 @@ pt_status tc_batch_plan(pt_ctx* lead, pt_ctx* const* ctxs, const int64_t* P, int
   // about items_per_sm work items per SM, each study by its share of voxels.
   const int sms = num_sms(lead->device);
   int filled = 0;
-  for (int NT : {256, 128, 64}) {
+  for (int NT : {256, 128, 96, 64}) {
     for (int kps : {8, 4, 2, 1}) {
       TcGroup g{NT, filled, 0, 16, 0, 0, kps};
       int ring = 1 << 30, items_per_sm = 1;

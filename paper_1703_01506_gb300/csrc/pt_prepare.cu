@@ -204,6 +204,21 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Adds d = y - m (exact pair) and d^2 (pair) to the running (high, low) sums.
+__device__ __forceinline__ void moment_add(float y, float m, float& Dh, float& Dl, float& Qh,
+                                           float& Ql) {
+  float dh, dl, sh, se;
+  two_sum(y, -m, dh, dl);
+  const float p = dh * dh;
+  const float pe = fmaf(2.0f * dh, dl, fmaf(dh, dh, -p));
+  two_sum(Dh, dh, sh, se);
+  Dh = sh;
+  Dl += se + dl;
+  two_sum(Qh, p, sh, se);
+  Qh = sh;
+  Ql += se + pe;
+}
+
 // One tile of kMV mask voxels starting at j0 (all threads of the CTA enter;
 // only warp 0 finishes the per-voxel part).
 template <bool kAsync>
@@ -211,7 +226,7 @@ __device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_
                                              int n1, int n_pad, const MomentRecips& rc,
                                              const int64_t* __restrict__ vox_grid, int64_t v,
                                              int64_t j0, const MomentOut& o, float* tile,
-                                             float (*part)[8][kMV], uint32_t (*flags)[kMV]) {
+                                             float (*part)[8][kMV]) {
   constexpr int LD = kMV + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t j = j0 + lane;
@@ -224,6 +239,7 @@ __device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_
   const float x0f = g >= 0 ? __ldcs(X + g) : 0.0f;
   const float* xp = X + (g >= 0 ? g : 0);
   if constexpr (kAsync) {
+#pragma unroll 4
     for (int s = warp; s < n; s += kMW) {
       float* dst = &tile[s * LD + lane];
       if (g >= 0) cp_async_f32(dst, xp + int64_t(s) * n_grid);
@@ -247,21 +263,27 @@ __device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_
   }
 
   // Pass 1: FP32 sum (only the seed of the centring: the two-pass correction
-  // removes its rounding), max |x| and the flags (bit 0: NaN or Inf seen,
-  // bit 1: a value differs from x_0). A sum that overflows while every value
-  // is finite (|x| near the FP32 limit) is retaken on the scaled values.
-  float S = 0.0f, amax = 0.0f;
-  uint32_t fl = 0u;
-  for (int s = warp; s < n; s += kMW) {
-    const float x = tile[s * LD + lane];
-    S += x;
-    amax = fmaxf(amax, fabsf(x));
-    if (!(fabsf(x) <= kFltMax)) fl |= 1u;
-    if (x != x0f) fl |= 2u;
+  // removes its rounding), minimum, maximum, and sum of x * 0, which is NaN
+  // exactly when some x is NaN or infinite. The flags follow at the end (bit
+  // 0: NaN or Inf seen, bit 1: not all values equal). A sum that overflows
+  // while every value is finite (|x| near the FP32 limit) is retaken on the
+  // scaled values.
+  float S = 0.0f, fin = 0.0f, xmin = x0f, xmax = x0f;
+  {
+    const float* col = tile + lane;
+#pragma unroll 4
+    for (int s = warp; s < n; s += kMW) {
+      const float x = col[s * LD];
+      S += x;
+      fin = fmaf(x, 0.0f, fin);
+      xmin = fminf(xmin, x);
+      xmax = fmaxf(xmax, x);
+    }
   }
-  part[warp][0][lane] = amax;
+  part[warp][0][lane] = xmin;
   part[warp][1][lane] = S;
-  flags[warp][lane] = fl;
+  part[warp][2][lane] = xmax;
+  part[warp][3][lane] = fin;
   __syncthreads();
   // Voxel-major copy: warp w writes rows l = w, w + 8, ... (lane = subject;
   // tile reads at stride LD = 33 words fall in distinct banks).
@@ -269,15 +291,18 @@ __device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_
     float* dst = o.Xraw + (j0 + l) * n_pad;
     for (int s = lane; s < n_pad; s += 32) dst[s] = s < n ? tile[s * LD + l] : 0.0f;
   }
-  fl = 0u;
-  amax = 0.0f;
   S = 0.0f;
+  fin = 0.0f;
 #pragma unroll
   for (int w = 0; w < kMW; ++w) {
-    amax = fmaxf(amax, part[w][0][lane]);
+    xmin = fminf(xmin, part[w][0][lane]);
     S += part[w][1][lane];
-    fl |= flags[w][lane];
+    xmax = fmaxf(xmax, part[w][2][lane]);
+    fin += part[w][3][lane];
   }
+  uint32_t fl = fin != fin ? 1u : 0u;
+  if (xmin != xmax) fl |= 2u;
+  float amax = fmaxf(fabsf(xmin), fabsf(xmax));
   if (fl & 1u) amax = 1.0f;  // reported below; keep the arithmetic finite
   int ex = int((__float_as_uint(amax) >> 23) & 0xffu) - 127;
   ex = ex < -126 ? -126 : (ex > 126 ? 126 : ex);
@@ -287,11 +312,11 @@ __device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_
   if (__syncthreads_or(!(fabsf(S) <= kFltMax) && !(fl & 1u))) {
     float Ss = 0.0f;  // overflowed sums only: the scaled sum (cannot overflow)
     for (int s = warp; s < n; s += kMW) Ss += tile[s * LD + lane] * scale;
-    part[warp][2][lane] = Ss;
+    part[warp][4][lane] = Ss;
     __syncthreads();
     Ss = 0.0f;
 #pragma unroll
-    for (int w = 0; w < kMW; ++w) Ss += part[w][2][lane];
+    for (int w = 0; w < kMW; ++w) Ss += part[w][4][lane];
     if (!(fabsf(S) <= kFltMax)) ms = Ss * inv_n;
   }
   if (fl & 1u) ms = 0.0f;
@@ -301,21 +326,12 @@ __device__ __forceinline__ void moments_tile(const float* __restrict__ X, int64_
   // error is exact (two-sum) and goes into the low word with the value's own
   // low part.
   float D1h = 0.f, D1l = 0.f, D2h = 0.f, D2l = 0.f, Q1h = 0.f, Q1l = 0.f, Q2h = 0.f, Q2l = 0.f;
-  auto add_value = [&](float x, float& Dh, float& Dl, float& Qh, float& Ql) {
-    float dh, dl, sh, se;
-    two_sum(x * scale, -ms, dh, dl);
-    const float p = dh * dh;
-    const float pe = fmaf(2.0f * dh, dl, fmaf(dh, dh, -p));
-    two_sum(Dh, dh, sh, se);
-    Dh = sh;
-    Dl += se + dl;
-    two_sum(Qh, p, sh, se);
-    Qh = sh;
-    Ql += se + pe;
-  };
+  const float* col = tile + lane;
   int s = warp;
-  for (; s < n1; s += kMW) add_value(tile[s * LD + lane], D1h, D1l, Q1h, Q1l);
-  for (; s < n; s += kMW) add_value(tile[s * LD + lane], D2h, D2l, Q2h, Q2l);
+#pragma unroll 4
+  for (; s < n1; s += kMW) moment_add(col[s * LD] * scale, ms, D1h, D1l, Q1h, Q1l);
+#pragma unroll 4
+  for (; s < n; s += kMW) moment_add(col[s * LD] * scale, ms, D2h, D2l, Q2h, Q2l);
   __syncthreads();  // everyone has read the pass-1 partials (and the tile)
   float* pp = &part[warp][0][0];
   pp[0 * kMV + lane] = D1h;
@@ -379,12 +395,10 @@ __global__ void __launch_bounds__(32 * kMW, kAsync ? 8 : 6)
                    const uint32_t* __restrict__ v_dev, const MomentOut o) {
   extern __shared__ float tile[];  // [n][kMV + 1]
   __shared__ float part[kMW][8][kMV];
-  __shared__ uint32_t flags[kMW][kMV];
   const int64_t v = v_dev ? int64_t(*v_dev) : v_host;
   const int64_t tiles = (v + kMV - 1) / kMV;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    moments_tile<kAsync>(X, n_grid, n, n1, n_pad, rc, vox_grid, v, t * kMV, o, tile, part,
-                         flags);
+    moments_tile<kAsync>(X, n_grid, n, n1, n_pad, rc, vox_grid, v, t * kMV, o, tile, part);
     __syncthreads();  // the tile and the partials are reused
   }
 }
@@ -634,7 +648,7 @@ pt_status prepare_impl(pt_ctx* ctx, const float* X, const uint8_t* mask) {
                            (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
     cudaGetLastError();
     auto kern = on_device ? moments_kernel<true> : moments_kernel<false>;
-    // dynamic tile plus ~9 KB of static partials: the opt-in is needed from
+    // dynamic tile plus 8 KB of static partials: the opt-in is needed from
     // well below 48 KB of dynamic memory, so it is always set
     const int smem = ctx->n * (kMV + 1) * int(sizeof(float));
     PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

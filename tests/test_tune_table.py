@@ -19,9 +19,10 @@ def B():
 
 
 def test_default_tile_follows_n(B):
-    # The largest voxel tile whose BF16 pieces fit in shared memory.
-    for n, tile in [(3, 256), (100, 256), (128, 256), (129, 128), (240, 128), (300, 64),
-                    (544, 64)]:
+    # The largest voxel tile whose BF16 pieces fit in shared memory beside a
+    # label ring of at least 2,048 columns x k-steps, else beside 4 stages (544).
+    for n, tile in [(3, 256), (100, 256), (128, 256), (129, 128), (240, 128), (300, 96),
+                    (336, 96), (352, 64), (544, 64)]:
         found, cfg = B.pt_tune_lookup(n, PREC_BF16X3, 0, 10000, 1000)
         assert found == 0 and cfg.voxel_tile == tile, (n, cfg.as_tuple())
         assert cfg.ksteps_per_stage in (1, 2, 4, 8) and cfg.stages >= 2
@@ -33,16 +34,16 @@ def test_default_tile_follows_n(B):
 
 
 def test_set_lookup_and_buckets(B):
-    B.pt_tune_set(300, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
-    found, cfg = B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 10000)
+    B.pt_tune_set(360, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
+    found, cfg = B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)
     assert found == 1 and cfg.as_tuple() == (64, 4, 4, 2)
-    # same half-octave buckets of v and P, same padded n (297..304 -> 304)
-    assert B.pt_tune_lookup(297, PREC_BF16X3, 0, 210000, 11000)[0] == 1
+    # same half-octave buckets of v and P, same padded n (353..368 -> 368)
+    assert B.pt_tune_lookup(357, PREC_BF16X3, 0, 210000, 11000)[0] == 1
     # other bucket, precision or sidedness: no entry
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 400000, 10000)[0] == 0
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 30000)[0] == 0
-    assert B.pt_tune_lookup(300, PREC_BF16X2, 0, 200000, 10000)[0] == 0
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 1, 200000, 10000)[0] == 0
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 400000, 10000)[0] == 0
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 30000)[0] == 0
+    assert B.pt_tune_lookup(360, PREC_BF16X2, 0, 200000, 10000)[0] == 0
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 1, 200000, 10000)[0] == 0
 
 
 @pytest.mark.parametrize("cfg", [
@@ -56,12 +57,12 @@ def test_set_lookup_and_buckets(B):
 ])
 def test_set_rejects_invalid(B, cfg):
     with pytest.raises(B.PtError):
-        B.pt_tune_set(300, PREC_BF16X3, 0, 200000, 10000, *cfg)
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 10000)[0] == 0
+        B.pt_tune_set(360, PREC_BF16X3, 0, 200000, 10000, *cfg)
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)[0] == 0
 
 
 def test_save_load_round_trip(B, tmp_path):
-    B.pt_tune_set(300, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
+    B.pt_tune_set(360, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
     B.pt_tune_set(100, PREC_BF16X3, 1, 231719, 10000, 256, 2, 4, 1)
     B.pt_tune_set(200, PREC_BF16X2, 0, 500000, 100000, 256, 2, 2, 4)
     path = str(tmp_path / "tune.txt")
@@ -70,22 +71,22 @@ def test_save_load_round_trip(B, tmp_path):
     assert lines[0].startswith("# pt tuned launch configurations")
     assert len([ln for ln in lines if not ln.startswith("#")]) == 3
     B.pt_tune_clear()
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 10000)[0] == 0
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)[0] == 0
     B.pt_tune_load(path)
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 4, 4, 2)
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 4, 4, 2)
     assert B.pt_tune_lookup(100, PREC_BF16X3, 1, 231719, 10000)[1].as_tuple() == (256, 2, 4, 1)
     assert B.pt_tune_lookup(200, PREC_BF16X2, 0, 500000, 100000)[1].as_tuple() == (256, 2, 2, 4)
 
 
 def test_load_rejects_bad_files_and_keeps_table(B, tmp_path):
-    B.pt_tune_set(300, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
+    B.pt_tune_set(360, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
     good = "# pt tuned launch configurations v2\n"
     cases = {
-        "missing_header": "304 2 0 35 26 64 4 4 2 1.0\n",
-        "short_line": good + "304 2 0 35 26 64 4 4\n",
-        "wrong_tile": good + "304 2 0 35 26 128 4 4 2 1.0\n",
+        "missing_header": "368 2 0 35 26 64 4 4 2 1.0\n",
+        "short_line": good + "368 2 0 35 26 64 4 4\n",
+        "wrong_tile": good + "368 2 0 35 26 128 4 4 2 1.0\n",
         "odd_n_pad": good + "300 2 0 35 26 64 4 4 2 1.0\n",
-        "bad_precision": good + "304 0 0 35 26 64 4 4 2 1.0\n",
+        "bad_precision": good + "368 0 0 35 26 64 4 4 2 1.0\n",
         "empty": "",
     }
     for name, text in cases.items():
@@ -95,10 +96,10 @@ def test_load_rejects_bad_files_and_keeps_table(B, tmp_path):
         with pytest.raises(B.PtError):
             B.pt_tune_load(path)
         # the earlier entry is untouched and no partial entry was merged
-        assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 4, 4, 2)
+        assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 4, 4, 2)
     with pytest.raises(B.PtError):
         B.pt_tune_load(str(tmp_path / "does_not_exist.txt"))
     with open(str(tmp_path / "ok.txt"), "w") as f:
-        f.write(good + "# comment\n\n304 2 0 35 26 64 2 8 1 2.5\n")
+        f.write(good + "# comment\n\n368 2 0 35 26 64 2 8 1 2.5\n")
     B.pt_tune_load(str(tmp_path / "ok.txt"))
-    assert B.pt_tune_lookup(300, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 2, 8, 1)
+    assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 2, 8, 1)
