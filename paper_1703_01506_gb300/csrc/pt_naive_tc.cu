@@ -605,19 +605,27 @@ int max_stages_fit(int NT, int n_pad, int pieces, int kps) {
 }
 
 // Largest voxel tile NT whose resident data tile leaves room for a label ring
-// that covers at least 2,048 MMA columns x k-steps (stages x pieces x NT; 8
-// one-k-step stages at two pieces of 128 voxels, about 1,000 cycles of MMA
-// work in flight, which the label loads' L2 latency needs), else the largest
-// that leaves at least 4 stages.
+// of at least 8 one-k-step stages that also covers at least 2,048 MMA columns
+// x k-steps (stages x pieces x NT: about 1,000 cycles of MMA work in flight,
+// which the label loads' L2 latency needs), else the largest that leaves at
+// least 4 stages. NT = 96 is taken with two data pieces only (one MMA of width
+// 192 per k-step; with three its lo piece would take a separate MMA of width
+// 96, slower than the 64-voxel tile's single MMA of width 192). Measured on
+// 10,000 relabellings: n = 392 FP16x2, 96 voxels 5.04 ms against 128 voxels
+// (6 stages) 6.85 ms; n = 200 FP16x2, 128 voxels 3.13 ms against 256 voxels
+// (4 stages) 3.30 ms; n = 300 BF16x3, 64 voxels 5.89 ms against 96 voxels
+// 6.38 ms.
 bool choose_tile(int n_pad, int pieces, int* NT) {
   for (int cand : {256, 128, 96, 64}) {
+    if (cand == 96 && pieces != 2) continue;
     const int s = max_stages_fit(cand, n_pad, pieces, 1);
-    if (s >= 4 && s * pieces * cand >= 2048) {
+    if (s >= 8 && s * pieces * cand >= 2048) {
       *NT = cand;
       return true;
     }
   }
   for (int cand : {256, 128, 96, 64}) {
+    if (cand == 96 && pieces != 2) continue;
     if (max_stages_fit(cand, n_pad, pieces, 1) >= 4) {
       *NT = cand;
       return true;

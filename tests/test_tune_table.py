@@ -19,16 +19,20 @@ def B():
 
 
 def test_default_tile_follows_n(B):
-    # The largest voxel tile whose BF16 pieces fit in shared memory beside a
-    # label ring of at least 2,048 columns x k-steps, else beside 4 stages (544).
-    for n, tile in [(3, 256), (100, 256), (128, 256), (129, 128), (240, 128), (300, 96),
-                    (336, 96), (352, 64), (544, 64)]:
+    # The largest voxel tile whose BF16x3 pieces fit in shared memory beside a
+    # label ring of at least 8 stages and 2,048 columns x k-steps, else beside
+    # 4 stages (544); the 96-voxel tile is for two pieces only.
+    for n, tile in [(3, 256), (100, 256), (128, 256), (129, 128), (240, 128), (256, 128),
+                    (300, 64), (352, 64), (544, 64)]:
         found, cfg = B.pt_tune_lookup(n, PREC_BF16X3, 0, 10000, 1000)
         assert found == 0 and cfg.voxel_tile == tile, (n, cfg.as_tuple())
         assert cfg.ksteps_per_stage in (1, 2, 4, 8) and cfg.stages >= 2
         assert cfg.items_per_sm == 8
     assert B.pt_tune_lookup(560, PREC_BF16X3, 0, 10000, 1000)[0] == -1  # no tile fits
     assert B.pt_tune_lookup(560, PREC_BF16X2, 0, 10000, 1000)[0] == 0
+    for n, tile in [(100, 256), (200, 128), (380, 128), (392, 96), (400, 96), (512, 64)]:
+        found, cfg = B.pt_tune_lookup(n, PREC_BF16X2, 0, 10000, 1000)  # two pieces
+        assert found == 0 and cfg.voxel_tile == tile, (n, cfg.as_tuple())
     assert B.pt_tune_lookup(2, PREC_BF16X3, 0, 10, 10)[0] == -1
     assert B.pt_tune_lookup(100, 0, 0, 10, 10)[0] == -1  # FP32 has no tensor-core config
 
@@ -64,7 +68,7 @@ def test_set_rejects_invalid(B, cfg):
 def test_save_load_round_trip(B, tmp_path):
     B.pt_tune_set(360, PREC_BF16X3, 0, 200000, 10000, 64, 4, 4, 2)
     B.pt_tune_set(100, PREC_BF16X3, 1, 231719, 10000, 256, 2, 4, 1)
-    B.pt_tune_set(200, PREC_BF16X2, 0, 500000, 100000, 256, 2, 2, 4)
+    B.pt_tune_set(200, PREC_BF16X2, 0, 500000, 100000, 128, 2, 2, 4)
     path = str(tmp_path / "tune.txt")
     B.pt_tune_save(path)
     lines = open(path).read().splitlines()
@@ -75,7 +79,7 @@ def test_save_load_round_trip(B, tmp_path):
     B.pt_tune_load(path)
     assert B.pt_tune_lookup(360, PREC_BF16X3, 0, 200000, 10000)[1].as_tuple() == (64, 4, 4, 2)
     assert B.pt_tune_lookup(100, PREC_BF16X3, 1, 231719, 10000)[1].as_tuple() == (256, 2, 4, 1)
-    assert B.pt_tune_lookup(200, PREC_BF16X2, 0, 500000, 100000)[1].as_tuple() == (256, 2, 2, 4)
+    assert B.pt_tune_lookup(200, PREC_BF16X2, 0, 500000, 100000)[1].as_tuple() == (128, 2, 2, 4)
 
 
 def test_load_rejects_bad_files_and_keeps_table(B, tmp_path):
