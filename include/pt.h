@@ -490,8 +490,8 @@ pt_status pt_selftest_bounded_wait(pt_ctx* ctx, int32_t limit_ms);
  *   two_sided: 0 statistic t, 1 statistic |t|.
  *   stream  : cudaStream_t to run on (NULL = legacy default stream).
  * Synchronous: it reads two status words back to the host and waits on the
- * stream during the work and at its end, so it cannot be recorded by stream
- * capture. Returns PT_ERR_INVALID for a bad argument, NaN/Inf in X, a row that
+ * stream during the work and at its end. Returns PT_ERR_INVALID for a bad
+ * argument, NaN/Inf in X, a row that
  * is not a permutation, or a problem whose buffers exceed the 64 MiB array
  * (the message gives the bytes needed). Each call looks up the array's device
  * address (cudaGetSymbolAddress) in the context current at the call, so it is

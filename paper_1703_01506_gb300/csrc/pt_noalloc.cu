@@ -17,11 +17,10 @@
 // module is loaded in that context.
 //
 // The call is synchronous: it copies two status words to host memory and
-// waits on the stream in the middle of the work and at its end, so it cannot
-// be recorded into a CUDA graph by stream capture. Every call shares the
-// array and it keeps the previous call's contents; calls that overlap on the
-// GPU (two streams, two host threads) race on it and must be serialised by
-// the caller.
+// waits on the stream in the middle of the work and at its end. Every call
+// shares the array and it keeps the previous call's contents; calls that
+// overlap on the GPU (two streams, two host threads) race on it and must be
+// serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <cmath>
