@@ -541,10 +541,21 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
     }
     __syncthreads();
     float* mine = f.slot + par * kSlot;
-    for (int c = tid; c < R; c += blockDim.x) {  // this CTA's share of w: G^-1 (A^T x)_local
-      float t = 0.0f;
-      for (int d = 0; d < R; ++d) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
-      mine[c] = t;
+    {
+      // this CTA's share of w: G^-1 (A^T x)_local; GS adjacent lanes share a
+      // column, each summing every GS-th term, then a shuffle tree (short
+      // dependent chains instead of R FMAs in a row)
+      constexpr int GS = kCluThreads / RP >= 8 ? 8 : (kCluThreads / RP >= 4 ? 4 : 2);
+      const int g = tid % GS;
+      for (int c0 = 0; c0 < R; c0 += kCluThreads / GS) {
+        const int c = c0 + tid / GS;
+        float t = 0.0f;
+        if (c < R)
+          for (int d = g; d < R; d += GS) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
+#pragma unroll
+        for (int o = GS / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (c < R && g == 0) mine[c] = t;
+      }
     }
     cl.sync();
     for (int c = tid; c < RP; c += blockDim.x)
