@@ -245,9 +245,11 @@ def test_full_size_sampled(cuda_lib, name, precision):
     ctx.close()
 
 
-def test_prepare_from_pinned_host_memory(cuda_lib):
-    """X and mask in page-locked host memory (read by the kernels over the
-    host link) give results identical to device copies."""
+@pytest.mark.parametrize("masked", [True, False])
+def test_prepare_from_pinned_host_memory(cuda_lib, masked):
+    """X and mask in page-locked host memory (the mask voxels' values gathered
+    over the host link, or all of X copied without a mask) give results
+    identical to device copies, and t_obs too."""
     B = cuda_lib
     n, n1, P = 24, 12, 300
     X, mask = synth.brain_field(n, n1, grid=(20, 24, 20), center=(10, 12, 10),
@@ -257,10 +259,14 @@ def test_prepare_from_pinned_host_memory(cuda_lib):
     outs = []
     for host in (False, True):
         Xa = X.contiguous().pin_memory() if host else X.cuda()
-        ma = mask.to(torch.uint8).contiguous()
-        ma = ma.pin_memory() if host else ma.cuda()
+        ma = None
+        if masked:
+            ma = mask.to(torch.uint8).contiguous()
+            ma = ma.pin_memory() if host else ma.cuda()
         ctx = B.pt_prepare(Xa, n1, ma)
-        outs.append([t.cpu() for t in B.maxnull_naive(ctx, perms, precision=2)])
+        t = torch.empty(B.pt_num_voxels(ctx), dtype=torch.float32, device="cuda")
+        B.pt_t_obs(ctx, t)
+        outs.append([x.cpu() for x in B.maxnull_naive(ctx, perms, precision=2)] + [t.cpu()])
         ctx.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
