@@ -12,6 +12,10 @@ method's arithmetic.
   counter-based generator (Philox4x32-10) both sides implement.
 * ``cluster`` -- clusters of thresholded maps (Sec. 6 cluster tables) and the
   largest cluster per relabelling, with scipy's connected-component labelling.
+* ``glm``, ``anova``, ``ancova`` -- other instances of the per-voxel "stat"
+  (Alg. 1/2 input): the two-group t with nuisance covariates, the one-way F of
+  g groups, and the F of a g-group factor with nuisance covariates, each from
+  its least-squares or sums-of-squares definition in FP64.
 """
 
 import ctypes
