@@ -116,7 +116,8 @@ pt_status pt_prepare(const float* X, int32_t n, int64_t n_grid, const uint8_t* m
  * (a voxel whose residual vanishes, e.g. constant, has no statistic), and the
  * observed statistic (pt_t_obs). Contexts from here run pt_maxnull_naive(_ex)
  * and pt_autotune_naive on the tensor-core precisions (PT_PREC_FP32, RapidPT
- * and the batched call return PT_ERR_UNSUPPORTED), pt_fwer_pvalues and pt_t_obs.
+ * and the batched call return PT_ERR_UNSUPPORTED), pt_fwer_pvalues, pt_t_obs and
+ * pt_maxnull_anova (the F of a factor with these covariates).
  * A relabelling whose group column lies in the span of [1, Z] makes the next
  * pt_sync return PT_ERR_INVALID.
  * Errors: as pt_prepare, and PT_ERR_INVALID for NaN/Inf in Z, [1, Z] without
@@ -292,8 +293,16 @@ pt_status pt_t_rows(pt_ctx* ctx, const int32_t* perms, int64_t P, int32_t precis
  *   maxnull, argmax : device float32[P] / int32[P]: max over voxels of F (the winner's F
  *                 recomputed in FP64 from the input values) and its masked voxel index.
  *   counts      : device uint32[v] or NULL: #{i : F_ij >= F_obs_j}.
+ * With a context from pt_prepare_glm (covariates Z, intercept added) the statistic is the
+ * factor's F in  y = E beta + [1, Z] gamma + e  (E: indicators of groups 1..g-1 of the
+ * relabelling; every subject keeps its covariate values):
+ *   F = ((RSS_reduced - RSS_full) / (g-1)) / (RSS_full / (n - g - q)),
+ * formed from the g - 1 group sums of each voxel's unit-norm residual on [1, Z] and, per
+ * relabelling, (E^T (I - H) E)^-1 in FP64 (H the projector on [1, Z]); BF16X2 / BF16X3
+ * only (PT_ERR_UNSUPPORTED otherwise), n - g - q >= 1. A relabelling whose group columns
+ * are not independent of [1, Z] makes the next pt_sync return PT_ERR_INVALID.
  * The context's n1 plays no part. Synchronous; a bad relabelling row makes the next
- * pt_sync return PT_ERR_INVALID. PT_ERR_UNSUPPORTED with covariates.
+ * pt_sync return PT_ERR_INVALID.
  */
 pt_status pt_maxnull_anova(pt_ctx* ctx, const int32_t* perms, int64_t P,
                            const int32_t* group_sizes, int32_t g, int32_t precision,

@@ -14,6 +14,18 @@
 // relabelling and group, written as u rows a batch at a time); a reduction
 // kernel forms B, the per-row maximum (packed keys) and the exceedance counts;
 // the winner's F is recomputed in FP64 from the input values.
+//
+// With nuisance covariates Z (a context from pt_prepare_glm: Q an orthonormal
+// basis of [1, Z], q1 columns, and the unit-norm residual r^ of every voxel on
+// it), the statistic is the factor's F in  y = E beta + [1, Z] gamma + e  (E the
+// indicators of groups 1..g-1 of the relabelling): with u = E^T r^ (the same
+// contraction, on the residual) and M = E^T (I - Q Q^T) E (per relabelling),
+//
+//   B = u^T M^-1 u = (RSS_reduced - RSS_full) / RSS_reduced,
+//   F = (B / (g - 1)) / ((1 - B) / (n - g - q1 + 1)).
+//
+// M^-1 is formed per relabelling in FP64 (Cholesky); a relabelling whose group
+// columns are not independent of [1, Z] has no statistic (error bit).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -117,10 +129,106 @@ __device__ __forceinline__ float b_of(const float* __restrict__ U, int64_t base,
   return fmaf(tot * tot, gr.inv_n[gr.g - 1], b);
 }
 
+__device__ __forceinline__ double warp_sum_d(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// M^-1 (FP64, (g-1) x (g-1), row-major) of relabellings [0, P) of `perms`, one
+// warp per relabelling: S[h][k] = sum over group h of Q[s][k], M = diag(n_h) -
+// S S^T, Cholesky M = L L^T on lane 0, M^-1 = L^-T L^-1. A non-positive pivot
+// (group columns dependent on [1, Z]) sets kErrGlmSpan and leaves zeros.
+__global__ void ancova_minv_kernel(const int32_t* __restrict__ perms, int64_t P, int n,
+                                   const double* __restrict__ Q, int q1, Groups gr,
+                                   double* __restrict__ Minv, uint32_t* __restrict__ status) {
+  __shared__ double sm[4][kMaxGroups * kMaxGroups];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = int64_t(blockIdx.x) * 4 + wib;
+  if (i >= P) return;
+  const int G1 = gr.g - 1;
+  const int32_t* row = perms + i * n;
+  bool bad = false;
+  for (int q = lane; q < n; q += 32) bad |= row[q] < 0 || row[q] >= n;
+  double* M = sm[wib];
+  double* out = Minv + i * G1 * G1;
+  if (__any_sync(0xffffffffu, bad)) {  // reported by the labels kernel
+    for (int e = lane; e < G1 * G1; e += 32) out[e] = 0.0;
+    return;
+  }
+  for (int e = lane; e < G1 * G1; e += 32) M[e] = 0.0;
+  __syncwarp();
+  for (int k = 0; k < q1; ++k) {
+    double S[kMaxGroups - 1];
+    for (int h = 0; h < G1; ++h) {
+      double acc = 0.0;
+      for (int q = gr.start[h] + lane; q < gr.start[h + 1]; q += 32)
+        acc += Q[int64_t(row[q]) * q1 + k];
+      S[h] = warp_sum_d(acc);
+    }
+    for (int e = lane; e < G1 * G1; e += 32) {
+      const int h = e / G1, c = e - h * G1;
+      M[e] -= S[h] * S[c];
+    }
+    __syncwarp();
+  }
+  if (lane != 0) return;
+  for (int h = 0; h < G1; ++h) M[h * G1 + h] += double(gr.start[h + 1] - gr.start[h]);
+  // Cholesky in place (lower triangle), then the inverse into out
+  double scale = 0.0;
+  for (int h = 0; h < G1; ++h) scale = fmax(scale, M[h * G1 + h]);
+  for (int c = 0; c < G1; ++c) {
+    double d = M[c * G1 + c];
+    for (int k = 0; k < c; ++k) d -= M[c * G1 + k] * M[c * G1 + k];
+    if (!(d > 1e-12 * scale)) {
+      atomicOr(status, kErrGlmSpan);
+      for (int e = 0; e < G1 * G1; ++e) out[e] = 0.0;
+      return;
+    }
+    const double l = sqrt(d);
+    M[c * G1 + c] = l;
+    for (int r = c + 1; r < G1; ++r) {
+      double t = M[r * G1 + c];
+      for (int k = 0; k < c; ++k) t -= M[r * G1 + k] * M[c * G1 + k];
+      M[r * G1 + c] = t / l;
+    }
+  }
+  // column c of M^-1: solve L y = e_c, then L^T x = y
+  for (int c = 0; c < G1; ++c) {
+    double y[kMaxGroups - 1];
+    for (int r = 0; r < G1; ++r) {
+      double t = r == c ? 1.0 : 0.0;
+      for (int k = 0; k < r; ++k) t -= M[r * G1 + k] * y[k];
+      y[r] = t / M[r * G1 + r];
+    }
+    for (int r = G1 - 1; r >= 0; --r) {
+      double t = y[r];
+      for (int k = r + 1; k < G1; ++k) t -= M[k * G1 + r] * y[k];
+      y[r] = t / M[r * G1 + r];
+    }
+    for (int r = 0; r < G1; ++r) out[r * G1 + c] = y[r];
+  }
+}
+
+// B = u^T M^-1 u over the g - 1 rows (M^-1 of the row's relabelling, FP64 in
+// memory, the same for every voxel of the row).
+__device__ __forceinline__ float b_of_cov(const float* __restrict__ U, int64_t base,
+                                          int64_t stride, int G1, const double* __restrict__ Mi) {
+  float u[kMaxGroups - 1];
+  for (int h = 0; h < G1; ++h) u[h] = U[base + h * stride];
+  float b = 0.0f;
+  for (int h = 0; h < G1; ++h) {
+    float t = 0.0f;
+    for (int k = 0; k < G1; ++k) t = fmaf(float(Mi[h * G1 + k]), u[k], t);
+    b = fmaf(u[h], t, b);
+  }
+  return b;
+}
+
 // B of relabellings [0, nb) of the batch over compact voxels: per-row maxima
 // (keys[i0 + i]: orderable B << 32 | ~voxel) and counts B >= B_obs (B_obs NULL:
 // write B of row 0 to bobs instead). Block = 256 voxels x 16 relabellings.
 __global__ void anova_reduce_kernel(const float* __restrict__ U, int64_t nb, int64_t V, Groups gr,
+                                    const double* __restrict__ Minv,
                                     const float* __restrict__ b_obs, float* __restrict__ bobs_out,
                                     int64_t i0, unsigned long long* __restrict__ keys,
                                     uint32_t* __restrict__ cnt) {
@@ -135,7 +243,8 @@ __global__ void anova_reduce_kernel(const float* __restrict__ U, int64_t nb, int
     if (i >= nb) break;
     unsigned long long key = 0ull;
     if (j < V) {
-      const float b = b_of(U, i * G1 * V + j, V, gr);
+      const float b = Minv ? b_of_cov(U, i * G1 * V + j, V, G1, Minv + (i0 + i) * G1 * G1)
+                           : b_of(U, i * G1 * V + j, V, gr);
       if (!b_obs) {
         if (i == 0) bobs_out[j] = b;
       } else {
@@ -211,6 +320,66 @@ __global__ void anova_finalize_kernel(const unsigned long long* __restrict__ key
   }
 }
 
+// With covariates: the winner's F in FP64 from the input values, one warp per
+// relabelling: the voxel's residual on [1, Z], its group sums b (groups
+// 1..g-1), B = b^T M^-1 b / ||r||^2, F = (B / (g-1)) / ((1 - B) / df).
+__global__ void ancova_finalize_kernel(const unsigned long long* __restrict__ keys, int64_t P,
+                                       const int32_t* __restrict__ valid_map,
+                                       const float* __restrict__ Xraw, int n, int n_pad,
+                                       const int32_t* __restrict__ perms, Groups gr,
+                                       const double* __restrict__ Q, int q1,
+                                       const double* __restrict__ coef,
+                                       const double* __restrict__ Minv, double df,
+                                       float* __restrict__ maxnull, int32_t* __restrict__ argmax) {
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G1 = gr.g - 1;
+  for (int64_t i = int64_t(blockIdx.x) * 8 + wib; i < P; i += int64_t(gridDim.x) * 8) {
+    const unsigned long long key = keys[i];
+    if (key == 0ull) {
+      if (lane == 0) {
+        maxnull[i] = -INFINITY;
+        argmax[i] = -1;
+      }
+      continue;
+    }
+    const int32_t j = valid_map[unpack_key_index(key)];
+    const float* x = Xraw + int64_t(j) * n_pad;
+    const double* cj = coef + int64_t(j) * q1;
+    const int32_t* row = perms + i * n;
+    auto resid = [&](int s) {
+      double r = double(x[s]);
+      for (int k = 0; k < q1; ++k) r -= Q[int64_t(s) * q1 + k] * cj[k];
+      return r;
+    };
+    double ss = 0.0;
+    for (int s = lane; s < n; s += 32) {
+      const double r = resid(s);
+      ss = fma(r, r, ss);
+    }
+    ss = warp_sum_d(ss);
+    double b[kMaxGroups - 1];
+    for (int h = 0; h < G1; ++h) {
+      double acc = 0.0;
+      for (int q = gr.start[h] + lane; q < gr.start[h + 1]; q += 32) {
+        const int32_t e = row[q];
+        acc += (e >= 0 && e < n) ? resid(e) : 0.0;
+      }
+      b[h] = warp_sum_d(acc);
+    }
+    if (lane != 0) continue;
+    const double* Mi = Minv + i * G1 * G1;
+    double B = 0.0;
+    for (int h = 0; h < G1; ++h) {
+      double t = 0.0;
+      for (int k = 0; k < G1; ++k) t += Mi[h * G1 + k] * b[k];
+      B += b[h] * t;
+    }
+    B /= ss;
+    maxnull[i] = B < 1.0 ? float((B / G1) / ((1.0 - B) / df)) : INFINITY;
+    argmax[i] = j;
+  }
+}
+
 __global__ void anova_scatter_counts_kernel(const uint32_t* __restrict__ cnt, int64_t V,
                                             const int32_t* __restrict__ valid_map,
                                             uint32_t* __restrict__ counts) {
@@ -223,8 +392,9 @@ __global__ void anova_scatter_counts_kernel(const uint32_t* __restrict__ cnt, in
 
 pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t* sizes, int g,
                      int precision, float* maxnull, int32_t* argmax, uint32_t* counts) {
-  if (ctx->glm_q1) {
-    set_error(ctx, "pt_maxnull_anova: the plain one-way layout only (context has covariates)");
+  const bool cov = ctx->glm_q1 > 0;
+  if (cov && precision != PT_PREC_BF16X2 && precision != PT_PREC_BF16X3) {
+    set_error(ctx, "pt_maxnull_anova with covariates runs on the BF16X2 / BF16X3 paths");
     return PT_ERR_UNSUPPORTED;
   }
   if (g < 2 || g > kMaxGroups) {
@@ -242,8 +412,10 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
     gr.start[h + 1] = gr.start[h] + sizes[h];
     gr.inv_n[h] = float(1.0 / sizes[h]);
   }
-  if (gr.start[g] != ctx->n || ctx->n <= g) {
-    set_error(ctx, "pt_maxnull_anova: group sizes must add up to n, and n > g");
+  // residual degrees of freedom of the full model (g group levels, q1 - 1 covariates)
+  const int df = ctx->n - g - (cov ? ctx->glm_q1 - 1 : 0);
+  if (gr.start[g] != ctx->n || df < 1) {
+    set_error(ctx, "pt_maxnull_anova: group sizes must add up to n, and n - g - q >= 1");
     return PT_ERR_INVALID;
   }
   cudaStream_t st = ctx->stream;
@@ -267,19 +439,21 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
   int64_t Bp = std::max<int64_t>(128, (int64_t(1) << 27) / (V * G1) / 128 * 128);
   Bp = std::min<int64_t>(Bp, (P + 127) / 128 * 128);
   const int64_t rows_pad_max = (Bp * G1 + 127) / 128 * 128;
-  Buf lab, ub, keys, cnt, bobs, ident;
+  Buf lab, ub, keys, cnt, bobs, ident, minv, minv_id;
   struct Gd {
     std::vector<Buf*> v;
     ~Gd() {
       for (Buf* b : v) b->release();
     }
-  } guard{{&lab, &ub, &keys, &cnt, &bobs, &ident}};
+  } guard{{&lab, &ub, &keys, &cnt, &bobs, &ident, &minv, &minv_id}};
   const size_t lab_elem = tc ? 2 : 4;
   if (!lab.ensure(lab_elem * size_t(rows_pad_max) * ctx->n_pad) ||
       !ub.ensure(sizeof(float) * size_t(rows_pad_max) * V) ||
       !keys.ensure(sizeof(unsigned long long) * size_t(P)) ||
       !cnt.ensure(sizeof(uint32_t) * size_t(V)) || !bobs.ensure(sizeof(float) * size_t(V)) ||
-      !ident.ensure(sizeof(int32_t) * ctx->n)) {
+      !ident.ensure(sizeof(int32_t) * ctx->n) ||
+      (cov && (!minv.ensure(sizeof(double) * size_t(P) * G1 * G1) ||
+               !minv_id.ensure(sizeof(double) * G1 * G1)))) {
     set_error(ctx, "out of device memory (one-way F)");
     return PT_ERR_NOMEM;
   }
@@ -290,6 +464,16 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
     for (int q = 0; q < ctx->n; ++q) id[q] = q;
     PT_CUDA_TRY(ctx, cudaMemcpyAsync(ident.p, id.data(), sizeof(int32_t) * ctx->n,
                                      cudaMemcpyHostToDevice, st));
+  }
+  if (cov) {  // M^-1 per relabelling and for the observed labelling
+    ancova_minv_kernel<<<unsigned((P + 3) / 4), 128, 0, st>>>(
+        perms, P, ctx->n, ctx->glmQ.as<double>(), ctx->glm_q1, gr, minv.as<double>(),
+        ctx->status.as<uint32_t>());
+    PT_LAUNCH_CHECK(ctx);
+    ancova_minv_kernel<<<1, 128, 0, st>>>(ident.as<int32_t>(), 1, ctx->n, ctx->glmQ.as<double>(),
+                                          ctx->glm_q1, gr, minv_id.as<double>(),
+                                          ctx->status.as<uint32_t>());
+    PT_LAUNCH_CHECK(ctx);
   }
   const int layout = prec_label_layout(precision);
   // rows of u for relabellings [i0, i0 + nb) of `rp`, then the reduction
@@ -311,20 +495,28 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
   s = rows_of(ident.as<int32_t>(), 0, 1);
   if (s != PT_OK) return s;
   anova_reduce_kernel<<<dim3(unsigned((V + 255) / 256), 1u, 1u), 256, 0, st>>>(
-      ub.as<float>(), 1, V, gr, nullptr, bobs.as<float>(), 0, nullptr, nullptr);
+      ub.as<float>(), 1, V, gr, cov ? minv_id.as<double>() : nullptr, nullptr, bobs.as<float>(),
+      0, nullptr, nullptr);
   PT_LAUNCH_CHECK(ctx);
   for (int64_t i0 = 0; i0 < P; i0 += Bp) {
     const int64_t nb = std::min(Bp, P - i0);
     s = rows_of(perms, i0, nb);
     if (s != PT_OK) return s;
     anova_reduce_kernel<<<dim3(unsigned((V + 255) / 256), unsigned((nb + 15) / 16), 1u), 256, 0,
-                          st>>>(ub.as<float>(), nb, V, gr, bobs.as<float>(), nullptr, i0,
-                                keys.as<unsigned long long>(), cnt.as<uint32_t>());
+                          st>>>(ub.as<float>(), nb, V, gr, cov ? minv.as<double>() : nullptr,
+                                bobs.as<float>(), nullptr, i0, keys.as<unsigned long long>(),
+                                cnt.as<uint32_t>());
     PT_LAUNCH_CHECK(ctx);
   }
-  anova_finalize_kernel<<<grid_for((P + 7) / 8, 1), 256, 0, st>>>(
-      keys.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(), ctx->Xraw.as<float>(),
-      ctx->n, ctx->n_pad, perms, gr, maxnull, argmax);
+  if (cov)
+    ancova_finalize_kernel<<<grid_for((P + 7) / 8, 1), 256, 0, st>>>(
+        keys.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(), ctx->Xraw.as<float>(),
+        ctx->n, ctx->n_pad, perms, gr, ctx->glmQ.as<double>(), ctx->glm_q1,
+        ctx->glm_coef.as<double>(), minv.as<double>(), double(df), maxnull, argmax);
+  else
+    anova_finalize_kernel<<<grid_for((P + 7) / 8, 1), 256, 0, st>>>(
+        keys.as<unsigned long long>(), P, ctx->valid_map.as<int32_t>(), ctx->Xraw.as<float>(),
+        ctx->n, ctx->n_pad, perms, gr, maxnull, argmax);
   PT_LAUNCH_CHECK(ctx);
   if (counts) {
     anova_scatter_counts_kernel<<<grid_for(V, 256), 256, 0, st>>>(

@@ -740,7 +740,8 @@ pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int 
   const int64_t items = ((st.v + NT - 1) / NT) * st.n_chunks;
   return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, cfg.stages,
                         cfg.ksteps_per_stage, pieces, ctx->n_pad, do_reduce, write_mode,
-                        two_sided, float(ctx->k), float(ctx->c_t), ctx->glm_q1 ? 1 : 0, f16);
+                        two_sided, float(ctx->k), float(ctx->c_t),
+                        ctx->glm_q1 && do_reduce && !write_mode ? 1 : 0, f16);
 }
 
 pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
