@@ -695,9 +695,28 @@ def anova_leg(dev, B, synth, torch, sizes=(33, 33, 34), reps=3):
     ms = e0.elapsed_time(e1) / reps
     ctx.close()
     m = mx.cpu().numpy().astype(np.float64)
+    # the same factor with two seeded N(0,1) covariates per subject (one-way
+    # ANCOVA: pt_prepare_glm context, BF16x3 pieces of the unit residual)
+    Z = np.random.default_rng(5).standard_normal((X.shape[0], 2))
+    ctx = B.pt_prepare_glm(X, sizes[0], Z, mask, stream=stream)
+    mc, _, _ = B.pt_maxnull_anova(ctx, perms, list(sizes), 2)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        mc, _, _ = B.pt_maxnull_anova(ctx, perms, list(sizes), 2)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_c = e0.elapsed_time(e1) / reps
+    B.pt_sync(ctx)
+    ctx.close()
+    mc = mc.cpu().numpy().astype(np.float64)
     return {"workload": "%s, groups %s (one-way F), %d voxels, P=%d" % (WORKLOAD, list(sizes), v, P),
             "ms_per_call": ms, "entries_per_s": P * v / (ms * 1e-3),
             "fwer_thr": {"%g" % a: fwer_thr(m, a) for a in (0.05, 0.01)},
+            "with_covariates": {"covariates": "2, seeded N(0,1) per subject; F of the factor "
+                                              "adjusted for them (BF16x3)",
+                                "ms_per_call": ms_c, "entries_per_s": P * v / (ms_c * 1e-3),
+                                "fwer_thr": {"%g" % a: fwer_thr(mc, a) for a in (0.05, 0.01)}},
             "timing": "device events over %d calls" % reps}
 
 
