@@ -63,19 +63,21 @@ int grid_for(int64_t work, int threads) {
   return int(b);
 }
 
-// Label rows of relabellings [i0, i0 + nb): row r = (i - i0) (g - 1) + h holds a 1
-// for every subject of group h (h < g - 1). layout 0: FP32 rows of n_pad;
-// 1 / 2: BF16 / FP16 core matrices in 128-row blocks (as the NaivePT labels).
-// One warp per relabelling; a row that is not a permutation sets kErrBadPerm.
+// Label rows of relabellings [i0, i0 + nb): row r = (i - i0) rs + h holds a 1
+// for every subject of group h (h < g - 1; rows g - 1 <= h < rs are zero).
+// layout 0: FP32 rows of n_pad; 1 / 2: BF16 / FP16 core matrices in 128-row
+// blocks (as the NaivePT labels). One warp per relabelling; a row that is not
+// a permutation sets kErrBadPerm.
 __global__ void anova_labels_kernel(const int32_t* __restrict__ perms, int64_t i0, int64_t nb,
-                                    int64_t rows_pad, int n, int n_pad, Groups gr, int layout,
-                                    void* __restrict__ Lout, uint32_t* __restrict__ status) {
+                                    int64_t rows_pad, int n, int n_pad, Groups gr, int rs,
+                                    int layout, void* __restrict__ Lout,
+                                    uint32_t* __restrict__ status) {
   __shared__ uint32_t seen_all[4][32];
   __shared__ uint16_t grp_all[4][1024];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = int64_t(blockIdx.x) * 4 + wib;
   const int G1 = gr.g - 1;
-  if (k * G1 >= rows_pad) return;
+  if (k * rs >= rows_pad) return;
   uint32_t* seen = seen_all[wib];
   uint16_t* grp = grp_all[wib];
   seen[lane] = 0u;
@@ -99,11 +101,11 @@ __global__ void anova_labels_kernel(const int32_t* __restrict__ perms, int64_t i
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, kErrBadPerm);
   __syncwarp();
-  for (int h = 0; h < G1; ++h) {
-    const int64_t r = k * G1 + h;
+  for (int h = 0; h < rs; ++h) {
+    const int64_t r = k * rs + h;
     if (r >= rows_pad) break;
     for (int s = lane; s < n_pad; s += 32) {
-      const bool in = k < nb && s < n && grp[s] == h;
+      const bool in = k < nb && s < n && h < G1 && grp[s] == h;
       if (layout == 0) {
         static_cast<float*>(Lout)[r * n_pad + s] = in ? 1.0f : 0.0f;
       } else {
@@ -140,7 +142,8 @@ __device__ __forceinline__ double warp_sum_d(double x) {
 // (group columns dependent on [1, Z]) sets kErrGlmSpan and leaves zeros.
 __global__ void ancova_minv_kernel(const int32_t* __restrict__ perms, int64_t P, int n,
                                    const double* __restrict__ Q, int q1, Groups gr,
-                                   double* __restrict__ Minv, uint32_t* __restrict__ status) {
+                                   double* __restrict__ Minv, float* __restrict__ wout, int FG,
+                                   uint32_t* __restrict__ status) {
   __shared__ double sm[4][kMaxGroups * kMaxGroups];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = int64_t(blockIdx.x) * 4 + wib;
@@ -151,6 +154,9 @@ __global__ void ancova_minv_kernel(const int32_t* __restrict__ perms, int64_t P,
   for (int q = lane; q < n; q += 32) bad |= row[q] < 0 || row[q] >= n;
   double* M = sm[wib];
   double* out = Minv + i * G1 * G1;
+  float* wo = wout ? wout + i * FG * FG : nullptr;
+  if (wo)
+    for (int e = lane; e < FG * FG; e += 32) wo[e] = 0.0f;
   if (__any_sync(0xffffffffu, bad)) {  // reported by the labels kernel
     for (int e = lane; e < G1 * G1; e += 32) out[e] = 0.0;
     return;
@@ -205,7 +211,24 @@ __global__ void ancova_minv_kernel(const int32_t* __restrict__ perms, int64_t P,
       for (int k = r + 1; k < G1; ++k) t -= M[k * G1 + r] * y[k];
       y[r] = t / M[r * G1 + r];
     }
-    for (int r = 0; r < G1; ++r) out[r * G1 + c] = y[r];
+    for (int r = 0; r < G1; ++r) {
+      out[r * G1 + c] = y[r];
+      if (wo) wo[r * FG + c] = float(y[r]);
+    }
+  }
+}
+
+// B_obs per compact voxel from the FG rows of u of the observed labelling, with
+// the fused kernel's arithmetic (f_quad), W for the observed labelling.
+template <int FG>
+__global__ void f_bobs_kernel(const float* __restrict__ U, int64_t V, const float* __restrict__ W,
+                              float* __restrict__ bobs) {
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < V;
+       j += int64_t(gridDim.x) * blockDim.x) {
+    float u[FG];
+#pragma unroll
+    for (int m = 0; m < FG; ++m) u[m] = U[m * V + j];
+    bobs[j] = f_quad<FG>(u, W);
   }
 }
 
@@ -435,25 +458,34 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
   pt_status s = tc ? tc_supported(ctx) : PT_OK;
   if (s == PT_OK) s = tc ? ensure_xnb(ctx, precision) : ensure_xn32(ctx);
   if (s != PT_OK) return s;
-  // batch: relabellings whose g - 1 u rows take about 512 MB
-  int64_t Bp = std::max<int64_t>(128, (int64_t(1) << 27) / (V * G1) / 128 * 128);
+  // g - 1 <= 4 on the tensor cores: B formed in the contraction's epilogue
+  // (FG label rows per relabelling, adjacent lanes), no rows of u in memory;
+  // otherwise rows of u a batch at a time and a reduction kernel.
+  const int FG = (tc && G1 <= 4) ? (G1 <= 2 ? 2 : 4) : 0;
+  const int rs = FG ? FG : G1;  // label rows per relabelling
+  // batch: relabellings whose g - 1 u rows take about 512 MB (all of them when fused)
+  int64_t Bp = FG ? (P + 127) / 128 * 128
+                  : std::max<int64_t>(128, (int64_t(1) << 27) / (V * G1) / 128 * 128);
   Bp = std::min<int64_t>(Bp, (P + 127) / 128 * 128);
-  const int64_t rows_pad_max = (Bp * G1 + 127) / 128 * 128;
-  Buf lab, ub, keys, cnt, bobs, ident, minv, minv_id;
+  const int64_t rows_pad_max = (Bp * rs + 127) / 128 * 128;
+  const int64_t urows = FG ? 128 : rows_pad_max;  // u rows held at once
+  Buf lab, ub, keys, cnt, bobs, ident, minv, minv_id, wall, wid;
   struct Gd {
     std::vector<Buf*> v;
     ~Gd() {
       for (Buf* b : v) b->release();
     }
-  } guard{{&lab, &ub, &keys, &cnt, &bobs, &ident, &minv, &minv_id}};
+  } guard{{&lab, &ub, &keys, &cnt, &bobs, &ident, &minv, &minv_id, &wall, &wid}};
   const size_t lab_elem = tc ? 2 : 4;
   if (!lab.ensure(lab_elem * size_t(rows_pad_max) * ctx->n_pad) ||
-      !ub.ensure(sizeof(float) * size_t(rows_pad_max) * V) ||
+      !ub.ensure(sizeof(float) * size_t(urows) * V) ||
       !keys.ensure(sizeof(unsigned long long) * size_t(P)) ||
       !cnt.ensure(sizeof(uint32_t) * size_t(V)) || !bobs.ensure(sizeof(float) * size_t(V)) ||
       !ident.ensure(sizeof(int32_t) * ctx->n) ||
       (cov && (!minv.ensure(sizeof(double) * size_t(P) * G1 * G1) ||
-               !minv_id.ensure(sizeof(double) * G1 * G1)))) {
+               !minv_id.ensure(sizeof(double) * G1 * G1))) ||
+      (FG && (!wall.ensure(sizeof(float) * (cov ? size_t(P) : 1) * FG * FG) ||
+              !wid.ensure(sizeof(float) * FG * FG)))) {
     set_error(ctx, "out of device memory (one-way F)");
     return PT_ERR_NOMEM;
   }
@@ -465,22 +497,37 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
     PT_CUDA_TRY(ctx, cudaMemcpyAsync(ident.p, id.data(), sizeof(int32_t) * ctx->n,
                                      cudaMemcpyHostToDevice, st));
   }
-  if (cov) {  // M^-1 per relabelling and for the observed labelling
+  if (cov) {  // M^-1 per relabelling and for the observed labelling (and W = M^-1 padded)
     ancova_minv_kernel<<<unsigned((P + 3) / 4), 128, 0, st>>>(
         perms, P, ctx->n, ctx->glmQ.as<double>(), ctx->glm_q1, gr, minv.as<double>(),
-        ctx->status.as<uint32_t>());
+        FG ? wall.as<float>() : nullptr, FG, ctx->status.as<uint32_t>());
     PT_LAUNCH_CHECK(ctx);
     ancova_minv_kernel<<<1, 128, 0, st>>>(ident.as<int32_t>(), 1, ctx->n, ctx->glmQ.as<double>(),
                                           ctx->glm_q1, gr, minv_id.as<double>(),
+                                          FG ? wid.as<float>() : nullptr, FG,
                                           ctx->status.as<uint32_t>());
     PT_LAUNCH_CHECK(ctx);
+  } else if (FG) {  // W = diag(1/n_h) + (1/n_g) 1 1^T over groups 1..g-1, zero-padded
+    std::vector<float> w(size_t(FG) * FG, 0.0f);
+    for (int h = 0; h < G1; ++h)
+      for (int k = 0; k < G1; ++k)
+        w[h * FG + k] = float((h == k ? 1.0 / sizes[h] : 0.0) + 1.0 / sizes[g - 1]);
+    PT_CUDA_TRY(ctx, cudaMemcpyAsync(wall.p, w.data(), sizeof(float) * w.size(),
+                                     cudaMemcpyHostToDevice, st));
+    PT_CUDA_TRY(ctx, cudaMemcpyAsync(wid.p, w.data(), sizeof(float) * w.size(),
+                                     cudaMemcpyHostToDevice, st));
   }
   const int layout = prec_label_layout(precision);
-  // rows of u for relabellings [i0, i0 + nb) of `rp`, then the reduction
+  auto labels_of = [&](const int32_t* rp, int64_t i0, int64_t nb) -> int64_t {
+    const int64_t rows = nb * rs, rows_pad = (rows + 127) / 128 * 128;
+    anova_labels_kernel<<<unsigned((rows_pad / rs + 4) / 4 + 1), 128, 0, st>>>(
+        rp, i0, nb, rows_pad, ctx->n, ctx->n_pad, gr, rs, layout, lab.p,
+        ctx->status.as<uint32_t>());
+    return rows;
+  };
+  // rows of u for relabellings [i0, i0 + nb) of `rp`
   auto rows_of = [&](const int32_t* rp, int64_t i0, int64_t nb) -> pt_status {
-    const int64_t rows = nb * G1, rows_pad = (rows + 127) / 128 * 128;
-    anova_labels_kernel<<<unsigned((rows_pad / G1 + 4) / 4 + 1), 128, 0, st>>>(
-        rp, i0, nb, rows_pad, ctx->n, ctx->n_pad, gr, layout, lab.p, ctx->status.as<uint32_t>());
+    const int64_t rows = labels_of(rp, i0, nb);
     PT_LAUNCH_CHECK(ctx);
     if (tc) return tc_rows(ctx, lab.p, rows, precision, 1, ub.as<float>(), 0, 0, nullptr, nullptr,
                            nullptr);
@@ -494,19 +541,36 @@ pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t
   // observed B: the identity labelling
   s = rows_of(ident.as<int32_t>(), 0, 1);
   if (s != PT_OK) return s;
-  anova_reduce_kernel<<<dim3(unsigned((V + 255) / 256), 1u, 1u), 256, 0, st>>>(
-      ub.as<float>(), 1, V, gr, cov ? minv_id.as<double>() : nullptr, nullptr, bobs.as<float>(),
-      0, nullptr, nullptr);
-  PT_LAUNCH_CHECK(ctx);
-  for (int64_t i0 = 0; i0 < P; i0 += Bp) {
-    const int64_t nb = std::min(Bp, P - i0);
-    s = rows_of(perms, i0, nb);
-    if (s != PT_OK) return s;
-    anova_reduce_kernel<<<dim3(unsigned((V + 255) / 256), unsigned((nb + 15) / 16), 1u), 256, 0,
-                          st>>>(ub.as<float>(), nb, V, gr, cov ? minv.as<double>() : nullptr,
-                                bobs.as<float>(), nullptr, i0, keys.as<unsigned long long>(),
-                                cnt.as<uint32_t>());
+  if (FG) {
+    if (FG == 2)
+      f_bobs_kernel<2><<<grid_for(V, 256), 256, 0, st>>>(ub.as<float>(), V, wid.as<float>(),
+                                                           bobs.as<float>());
+    else
+      f_bobs_kernel<4><<<grid_for(V, 256), 256, 0, st>>>(ub.as<float>(), V, wid.as<float>(),
+                                                           bobs.as<float>());
     PT_LAUNCH_CHECK(ctx);
+    const int64_t rows = labels_of(perms, 0, P);
+    PT_LAUNCH_CHECK(ctx);
+    s = tc_f_reduce(ctx, lab.p, rows, precision, FG, bobs.as<float>(), wall.as<float>(),
+                    cov ? int64_t(FG) * FG : 0, keys.as<unsigned long long>(),
+                    cnt.as<uint32_t>());
+    if (s != PT_OK) return s;
+  } else {
+    anova_reduce_kernel<<<dim3(unsigned((V + 255) / 256), 1u, 1u), 256, 0, st>>>(
+        ub.as<float>(), 1, V, gr, cov ? minv_id.as<double>() : nullptr, nullptr,
+        bobs.as<float>(), 0, nullptr, nullptr);
+    PT_LAUNCH_CHECK(ctx);
+    for (int64_t i0 = 0; i0 < P; i0 += Bp) {
+      const int64_t nb = std::min(Bp, P - i0);
+      s = rows_of(perms, i0, nb);
+      if (s != PT_OK) return s;
+      anova_reduce_kernel<<<dim3(unsigned((V + 255) / 256), unsigned((nb + 15) / 16), 1u), 256,
+                            0, st>>>(ub.as<float>(), nb, V, gr,
+                                     cov ? minv.as<double>() : nullptr, bobs.as<float>(),
+                                     nullptr, i0, keys.as<unsigned long long>(),
+                                     cnt.as<uint32_t>());
+      PT_LAUNCH_CHECK(ctx);
+    }
   }
   if (cov)
     ancova_finalize_kernel<<<grid_for((P + 7) / 8, 1), 256, 0, st>>>(

@@ -165,6 +165,11 @@ pt_status naive_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const pt_naiv
 pt_status naive_batched_impl(pt_ctx* const* ctxs, int n, const int32_t* const* perms,
                              const int64_t* P, const pt_naive_opts& o, float* const* maxnull,
                              int32_t* const* argmax, uint32_t* const* counts);
+// The F of a g-group factor in the fused kernel (FG = 2 or 4 label rows per
+// relabelling): per-relabelling maxima of B = u^T W u into keys, counts B >= B_obs.
+pt_status tc_f_reduce(pt_ctx* ctx, const void* Lb, int64_t rows, int precision, int fg,
+                      const float* b_obs, const float* fmat, int64_t fstride,
+                      unsigned long long* keys, uint32_t* cnt);
 pt_status anova_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, const int32_t* sizes, int g,
                      int precision, float* maxnull, int32_t* argmax, uint32_t* counts);
 pt_status cluster_maxnull_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, double tau,

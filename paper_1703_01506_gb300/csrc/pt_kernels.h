@@ -51,6 +51,22 @@ __device__ __forceinline__ void ff_acc(float& h, float& l, float bh, float bl) {
 
 __device__ __forceinline__ double ff_d(float h, float l) { return double(h) + double(l); }
 
+// B = u^T W u for the F of a g-group factor: u and W (FG x FG, row-major,
+// zero-padded past g - 1) in a fixed order of FMAs, so that the fused kernel
+// and the observed statistic's kernel round identically.
+template <int FG>
+__device__ __forceinline__ float f_quad(const float (&u)[FG], const float* W) {
+  float bq = 0.0f;
+#pragma unroll
+  for (int m = 0; m < FG; ++m) {
+    float t = 0.0f;
+#pragma unroll
+    for (int m2 = 0; m2 < FG; ++m2) t = fmaf(W[m * FG + m2], u[m2], t);
+    bq = fmaf(u[m], t, bq);
+  }
+  return bq;
+}
+
 // ---- bounded waits ----
 // Every spin-wait in this library gives up after kWaitLimitNs of wall time,
 // records kErrTimeout in the context's status word and returns false.

@@ -91,6 +91,12 @@ struct TcStudy {  // CUtensorMap members carry their own alignment
   float* uout;  // row writes (single-study launches only)
   const float* rowscale;  // covariate-adjusted statistic: per-row factor of the
                           // exceedance test (u * f >= u_obs); NULL for the plain t
+  // F of a g-group factor (kernel mode FG > 0): label row r = i FG + h is group h
+  // of relabelling i (rows h >= g - 1 are zero), u_obs holds B_obs per voxel,
+  // maxkey is indexed by relabelling, and fmat + i fstride is the FG x FG matrix
+  // W (zero-padded) with B = u^T W u (fstride 0: one matrix for every row).
+  const float* fmat;
+  int64_t fstride;
 };
 
 struct TcArgs {
@@ -218,8 +224,11 @@ __device__ __forceinline__ float cols_reduce(const uint32_t (&r)[CW], const floa
 // WRITE = false: reduce only (the NaivePT path); true: rows of u or t are
 // written (training rows of Alg. 2), optionally also reduced. SCALED: the
 // covariate-adjusted statistic (per-row factor in the exceedance test; the
-// launch's studies carry rowscale).
-template <int NT, bool TWO, int PIECES, bool WRITE, bool SCALED = false>
+// launch's studies carry rowscale). FG > 0: the F of a g-group factor, the
+// g - 1 group sums of a relabelling in FG adjacent lanes (g - 1 <= FG), which
+// exchange them by shuffles; B = u^T W u replaces u, and the group's first
+// lane takes the maximum and the counts.
+template <int NT, bool TWO, int PIECES, bool WRITE, bool SCALED = false, int FG = 0>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_contract_kernel(const TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -434,13 +443,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = etid; c < NT; c += 32 * kEpiWarps) {
         float x = INFINITY;
         if (do_reduce && v0 + c < V) {
-          x = u_obs[v0 + c] * a.uscale;  // power of two: exact
-          if (TWO) x = fabsf(x);
+          if constexpr (FG > 0) {
+            x = u_obs[v0 + c];  // B_obs
+          } else {
+            x = u_obs[v0 + c] * a.uscale;  // power of two: exact
+            if (TWO) x = fabsf(x);
+          }
         }
         su[c] = x;
       }
       for (int64_t c = etid; c < b1 - b0; c += 32 * kEpiWarps)
-        sbf[c] = (do_reduce && st.blockflag[b0 + c]) || (b0 + c + 1) * 128 > Pn ? 1 : 0;
+        sbf[c] = (do_reduce && st.blockflag && st.blockflag[b0 + c]) || (b0 + c + 1) * 128 > Pn
+                     ? 1
+                     : 0;
       epi_bar();
       uint32_t c8[CW / 4];
 #pragma unroll
@@ -450,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       unsigned long long gkey_next = 0ull;
       {
         const int64_t rowf = (b0 + rot % nb) * 128 + quad * 32 + lane;
-        if (do_reduce && rowf < Pn) gkey_next = __ldcg(&maxkey[rowf]);
+        if (do_reduce && rowf < Pn) gkey_next = __ldcg(&maxkey[FG > 0 ? rowf / FG : rowf]);
       }
       for (int64_t kb = 0; kb < nb; ++kb, ++j) {
         // Blocks run in a per-CTA rotated order so that the CTAs do not all
@@ -465,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           int64_t bn = bi + 1;
           if (bn >= nb) bn -= nb;
           const int64_t rown = (b0 + bn) * 128 + quad * 32 + lane;
-          if (do_reduce && rown < Pn) gkey_next = __ldcg(&maxkey[rown]);
+          if (do_reduce && rown < Pn) gkey_next = __ldcg(&maxkey[FG > 0 ? rown / FG : rown]);
         }
         const bool ragged = ragged_cols || sbf[bi];
         if (ok && !mbar_wait(BAR(2 + abuf), aph, a.status, abort_flag)) ok = false;
@@ -474,8 +489,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t taddr = tmem + (uint32_t(quad * 32) << 16) + abuf * ACC + colbase;
         const bool row_ok = row < Pn;
-        const bool cnt_ok = row_ok && !(ragged && do_reduce && rowflag[row]);
+        const bool lead = FG == 0 || (lane & (FG > 0 ? FG - 1 : 0)) == 0;
+        const bool cnt_ok =
+            row_ok && (FG > 0 ? lead : !(ragged && do_reduce && rowflag[row]));
         const float fr = SCALED && row_ok ? st.rowscale[row] : 1.0f;
+        // F mode: this lane's view of W (rows and columns taken in xor order
+        // of its position in the group, so every lane runs the same code)
+        float Wp[FG > 0 ? FG : 1][FG > 0 ? FG : 1];
+        if constexpr (FG > 0) {
+          const int hl = lane & (FG - 1);
+          const float* W = st.fmat + (row_ok ? (row / FG) * st.fstride : 0);
+#pragma unroll
+          for (int m = 0; m < FG; ++m)
+#pragma unroll
+            for (int m2 = 0; m2 < FG; ++m2)
+              Wp[m][m2] = row_ok ? W[(hl ^ m) * FG + (hl ^ m2)] : 0.0f;
+        }
         // Running row maximum over the chunks and, for a maximum that can beat
         // the row's current global key, its first column (found while the
         // chunk is still in registers).
@@ -523,11 +552,33 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (do_reduce) {
             uint32_t(&cc)[CHK / 4] = *reinterpret_cast<uint32_t(*)[CHK / 4]>(&c8[c * (CHK / 4)]);
-            const float cm =
-                ragged ? cols_reduce<CHK, TWO, true, SCALED>(r, su + colbase + c * CHK, g0, V,
-                                                             row_ok, cnt_ok, cc, fr)
-                       : cols_reduce<CHK, TWO, false, SCALED>(r, su + colbase + c * CHK, g0, V,
-                                                              true, true, cc, fr);
+            float cm;
+            if constexpr (FG > 0) {
+              // B = u^T W u of the group's relabelling, in place of u
+#pragma unroll
+              for (int jj = 0; jj < CHK; ++jj) {
+                float v[FG];
+                v[0] = __uint_as_float(r[jj]) * a.inv_uscale;
+#pragma unroll
+                for (int m = 1; m < FG; ++m) v[m] = __shfl_xor_sync(0xffffffffu, v[0], m);
+                float bq = 0.0f;
+#pragma unroll
+                for (int m = 0; m < FG; ++m) {
+                  float t = 0.0f;
+#pragma unroll
+                  for (int m2 = 0; m2 < FG; ++m2) t = fmaf(Wp[m][m2], v[m2], t);
+                  bq = fmaf(v[m], t, bq);
+                }
+                r[jj] = __float_as_uint(bq);
+              }
+              cm = cols_reduce<CHK, false, true>(r, su + colbase + c * CHK, g0, V, row_ok && lead,
+                                                 cnt_ok, cc);
+            } else {
+              cm = ragged ? cols_reduce<CHK, TWO, true, SCALED>(r, su + colbase + c * CHK, g0, V,
+                                                               row_ok, cnt_ok, cc, fr)
+                          : cols_reduce<CHK, TWO, false, SCALED>(r, su + colbase + c * CHK, g0,
+                                                                V, true, true, cc, fr);
+            }
             const bool cand = row_ok && cm > best && cm >= gval && cm > -INFINITY;
             if (cm > best) {
               best = cm;
@@ -547,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (do_reduce && bestcol >= 0) {
           const unsigned long long key = pack_key(best, uint32_t(bestcol));
-          if (key > gkey) atomicMax(&maxkey[row], key);
+          if (key > gkey) atomicMax(&maxkey[FG > 0 ? row / FG : row], key);
         }
         tc_fence_before();
         __syncwarp();
@@ -593,6 +644,25 @@ pt_status launch_nt(pt_ctx* ctx, const TcArgs& a, int pieces, int grid, int smem
   if (a.do_reduce) prof_end(ctx);
   PT_LAUNCH_CHECK(ctx);
   return PT_OK;
+}
+
+// F of a g-group factor (reduce only, one-sided).
+template <int NT, int FG>
+pt_status launch_f(pt_ctx* ctx, const TcArgs& a, int pieces, int grid, int smem) {
+  auto kern = pieces == 2 ? tc_contract_kernel<NT, false, 2, false, false, FG>
+                          : tc_contract_kernel<NT, false, 3, false, false, FG>;
+  PT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  kern<<<grid, kThreads, smem, ctx->stream>>>(a);
+  PT_LAUNCH_CHECK(ctx);
+  return PT_OK;
+}
+
+template <int FG>
+pt_status launch_f_nt(pt_ctx* ctx, const TcArgs& a, int NT, int pieces, int grid, int smem) {
+  if (NT == 256) return launch_f<256, FG>(ctx, a, pieces, grid, smem);
+  if (NT == 128) return launch_f<128, FG>(ctx, a, pieces, grid, smem);
+  if (NT == 96) return launch_f<96, FG>(ctx, a, pieces, grid, smem);
+  return launch_f<64, FG>(ctx, a, pieces, grid, smem);
 }
 
 // Label-ring stages of kps k-steps each that fit beside the resident data
@@ -677,7 +747,7 @@ bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int kps, int64_t t
 pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_items, int NT,
                          int stages, int kps, int pieces, int n_pad_max, int do_reduce,
                          int write_mode, int two_sided, float kf, float ctf, int scaled = 0,
-                         int f16 = 0) {
+                         int f16 = 0, int fg = 0) {
   if (scaled && (write_mode || !do_reduce)) {
     set_error(ctx, "covariate-adjusted statistic: reduce-only launches");
     return PT_ERR_UNSUPPORTED;
@@ -706,6 +776,14 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   const int sms = num_sms(ctx->device);
   const int grid = int(n_items < sms ? n_items : sms);
   const int smem = smem_bytes(NT, n_pad_max, pieces, stages, kps);
+  if (fg) {
+    if (two_sided || write_mode || !do_reduce || scaled) {
+      set_error(ctx, "F mode: one-sided reduce-only launches");
+      return PT_ERR_UNSUPPORTED;
+    }
+    return fg == 2 ? launch_f_nt<2>(ctx, a, NT, pieces, grid, smem)
+                   : launch_f_nt<4>(ctx, a, NT, pieces, grid, smem);
+  }
   if (two_sided) {
     if (NT == 256) return launch_nt<256, true>(ctx, a, pieces, grid, smem);
     if (NT == 128) return launch_nt<128, true>(ctx, a, pieces, grid, smem);
@@ -761,6 +839,48 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
 }
 
 }  // namespace
+
+// The F of a g-group factor fused into the contraction: `rows` label rows of
+// groups (FG per relabelling), B_obs per compact voxel, W per relabelling
+// (stride fstride), keys per relabelling, counts B >= B_obs per voxel.
+pt_status tc_f_reduce(pt_ctx* ctx, const void* Lb, int64_t rows, int precision, int fg,
+                      const float* b_obs, const float* fmat, int64_t fstride,
+                      unsigned long long* keys, uint32_t* cnt) {
+  if (fg != 2 && fg != 4) {
+    set_error(ctx, "F mode: 2 or 4 rows per relabelling");
+    return PT_ERR_INVALID;
+  }
+  const int pieces = prec_pieces(precision);
+  pt_tc_config cfg;
+  if (!tc_default_config(ctx->n_pad, pieces, &cfg)) {
+    set_error(ctx, "tensor-core path: n too large for the resident data tile");
+    return PT_ERR_UNSUPPORTED;
+  }
+  const int NT = cfg.voxel_tile;
+  TcStudy st;
+  if (!fill_study(ctx, Lb, rows, NT, cfg.ksteps_per_stage,
+                  int64_t(cfg.items_per_sm) * num_sms(ctx->device), 0, b_obs, keys, cnt, nullptr,
+                  &st)) {
+    set_error(ctx, "cuTensorMapEncodeTiled failed");
+    return PT_ERR_CUDA;
+  }
+  st.rowflag = nullptr;
+  st.blockflag = nullptr;
+  st.rowscale = nullptr;
+  st.fmat = fmat;
+  st.fstride = fstride;
+  if (!ctx->tcdesc.ensure(sizeof(TcStudy))) {
+    set_error(ctx, "out of device memory (descriptor)");
+    return PT_ERR_NOMEM;
+  }
+  PT_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->tcdesc.p, &st, sizeof(TcStudy), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  const int64_t items = ((st.v + NT - 1) / NT) * st.n_chunks;
+  return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, cfg.stages,
+                        cfg.ksteps_per_stage, pieces, ctx->n_pad, 1, 0, 0, float(ctx->k),
+                        float(ctx->c_t), 0, precision == PT_PREC_FP16X2 ? 1 : 0, fg);
+}
+
 
 pt_status tc_supported(pt_ctx* ctx) {
   int major = 0, minor = 0;
