@@ -60,7 +60,7 @@ METRIC = "T entries/s (perm x voxel t) & max-null wall time, RapidPT vs NaivePT,
 # fused kernel on brain_n100_v232k, per precision (BF16x3: 160.21 MB read +
 # 4.67 MB written; FP16x2: 108.21 MB read + 3.54 MB written); None where no
 # capture of the current kernel exists.
-TRAFFIC_BYTES = {2: 164.89e6, 3: 111.75e6}
+TRAFFIC_BYTES = {2: 164.89e6, 3: 111.97e6}
 WORKLOAD = "brain_n100_v232k"
 # NaivePT arithmetic of the RapidPT-vs-NaivePT and large legs: FP16x2 (two FP16
 # pieces of 2^15 Xn), the fastest path that meets the FP32-class tolerances.
@@ -765,6 +765,15 @@ def cluster_leg(dev, B, synth, torch, tau=3.2, conn=18, reps=3):
 
 
 def run_ours(args):
+    if args.anova_only:
+        import torch
+        from paper_1703_01506_gb300 import binding as B
+        from paper_1703_01506_gb300 import synth
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        B.load()
+        print(json.dumps({"anova": anova_leg(dev, B, synth, torch)}), flush=True)
+        return
     if args.rapid_only:
         import torch
         from paper_1703_01506_gb300 import binding as B
@@ -1044,6 +1053,8 @@ def main():
                     help="RapidPT training passes in the RapidPT leg (default 1, Alg. 2)")
     ap.add_argument("--rapid-rows", type=int, default=0,
                     help="relabellings of the RapidPT leg (default all 100,000)")
+    ap.add_argument("--anova-only", action="store_true",
+                    help="run only the F-statistic leg (one line with its object)")
     ap.add_argument("--rapid-only", action="store_true",
                     help="run the RapidPT leg alone (profiling); prints only its object")
     ap.add_argument("--no-batched", action="store_true",

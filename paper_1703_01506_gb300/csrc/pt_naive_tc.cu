@@ -552,15 +552,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (do_reduce) {
             uint32_t(&cc)[CHK / 4] = *reinterpret_cast<uint32_t(*)[CHK / 4]>(&c8[c * (CHK / 4)]);
-            float cm;
             if constexpr (FG > 0) {
-              // B = u^T W u of the group's relabelling, in place of u
+              // Lane hl of a group takes the chunk's columns FG j + hl: it gets
+              // their u from the group's other lanes (round m: partner hl ^ m
+              // sends its u of column FG j + hl), forms B = u^T W u once per
+              // column, and keeps that column's maximum and count.
+              const int hl = lane & (FG - 1);
+              const float* sc = su + colbase + c * CHK;
 #pragma unroll
-              for (int jj = 0; jj < CHK; ++jj) {
+              for (int j = 0; j < CHK / FG; ++j) {
+                float own[FG];
+#pragma unroll
+                for (int m = 0; m < FG; ++m) own[m] = __uint_as_float(r[FG * j + m]) * a.inv_uscale;
+                auto pick = [&](int idx) {  // own[idx] without indexing registers at run time
+                  float x = own[0];
+#pragma unroll
+                  for (int m = 1; m < FG; ++m) x = idx == m ? own[m] : x;
+                  return x;
+                };
                 float v[FG];
-                v[0] = __uint_as_float(r[jj]) * a.inv_uscale;
+                v[0] = pick(hl);
 #pragma unroll
-                for (int m = 1; m < FG; ++m) v[m] = __shfl_xor_sync(0xffffffffu, v[0], m);
+                for (int m = 1; m < FG; ++m) v[m] = __shfl_xor_sync(0xffffffffu, pick(hl ^ m), m);
                 float bq = 0.0f;
 #pragma unroll
                 for (int m = 0; m < FG; ++m) {
@@ -569,32 +582,55 @@ __global__ void __launch_bounds__(kThreads, 1)
                   for (int m2 = 0; m2 < FG; ++m2) t = fmaf(Wp[m][m2], v[m2], t);
                   bq = fmaf(v[m], t, bq);
                 }
-                r[jj] = __float_as_uint(bq);
+                const int col = FG * j + hl;
+                const bool valid = row_ok && g0 + col < V;
+                if (valid && bq > best) {
+                  best = bq;
+                  bestcol = g0 + col;
+                }
+                if (valid && bq >= sc[col]) {
+                  if constexpr (FG == 2)
+                    cc[j >> 1] += 1u << (8 * ((2 * j & 3) + hl));
+                  else
+                    cc[j] += 1u << (8 * hl);
+                }
               }
-              cm = cols_reduce<CHK, false, true>(r, su + colbase + c * CHK, g0, V, row_ok && lead,
-                                                 cnt_ok, cc);
             } else {
-              cm = ragged ? cols_reduce<CHK, TWO, true, SCALED>(r, su + colbase + c * CHK, g0, V,
+              const float cm =
+                  ragged ? cols_reduce<CHK, TWO, true, SCALED>(r, su + colbase + c * CHK, g0, V,
                                                                row_ok, cnt_ok, cc, fr)
-                          : cols_reduce<CHK, TWO, false, SCALED>(r, su + colbase + c * CHK, g0,
+                         : cols_reduce<CHK, TWO, false, SCALED>(r, su + colbase + c * CHK, g0,
                                                                 V, true, true, cc, fr);
-            }
-            const bool cand = row_ok && cm > best && cm >= gval && cm > -INFINITY;
-            if (cm > best) {
-              best = cm;
-              bestcol = -1;
-            }
-            if (__any_sync(0xffffffffu, cand) && cand) {
-              int jj_best = -1;
-#pragma unroll
-              for (int jj = CHK - 1; jj >= 0; --jj) {
-                float sv = __uint_as_float(r[jj]);
-                if (TWO) sv = fabsf(sv);
-                if (sv == cm && g0 + jj < V) jj_best = jj;
+              const bool cand = row_ok && cm > best && cm >= gval && cm > -INFINITY;
+              if (cm > best) {
+                best = cm;
+                bestcol = -1;
               }
-              bestcol = jj_best >= 0 ? g0 + jj_best : -1;
+              if (__any_sync(0xffffffffu, cand) && cand) {
+                int jj_best = -1;
+#pragma unroll
+                for (int jj = CHK - 1; jj >= 0; --jj) {
+                  float sv = __uint_as_float(r[jj]);
+                  if (TWO) sv = fabsf(sv);
+                  if (sv == cm && g0 + jj < V) jj_best = jj;
+                }
+                bestcol = jj_best >= 0 ? g0 + jj_best : -1;
+              }
             }
           }
+        }
+        if constexpr (FG > 0) {
+          // the group's best (largest B, smallest voxel on ties) to its first lane
+#pragma unroll
+          for (int o = FG / 2; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int64_t oc = __shfl_xor_sync(0xffffffffu, bestcol, o);
+            if (oc >= 0 && (bestcol < 0 || ob > best || (ob == best && oc < bestcol))) {
+              best = ob;
+              bestcol = oc;
+            }
+          }
+          if (!lead) bestcol = -1;
         }
         if (do_reduce && bestcol >= 0) {
           const unsigned long long key = pack_key(best, uint32_t(bestcol));
