@@ -88,7 +88,8 @@ def check(X, sizes, Z, perms, got, precision):
 
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("sizes,q,v,P", [([8, 9, 10], 2, 2000, 300), ([6, 7, 5, 9], 1, 3001, 257),
-                                         ([12, 13], 3, 1500, 200)])
+                                         ([12, 13], 3, 1500, 200),
+                                         ([100, 100, 100], 2, 1001, 120)])
 def test_ancova_matches_oracle(cuda_lib, precision, sizes, q, v, P):
     n = sum(sizes)
     X = synth.gaussian_mean_shift(n, v, seed=n + v + q)

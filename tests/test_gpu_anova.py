@@ -79,6 +79,20 @@ def test_anova_matches_oracle(cuda_lib, precision, sizes, v, P):
     assert got[2][4] == 0
 
 
+@pytest.mark.parametrize("sizes,precision", [([90, 80, 80], 3), ([140, 140, 140], 3),
+                                              ([100, 100, 100], 2), ([60, 70, 60, 60, 50], 3)])
+def test_anova_large_n_tiles(cuda_lib, sizes, precision):
+    """Large n: the fused F mode on the 128-, 96- and 64-voxel tiles (FP16x2 at
+    n = 250 and 420, BF16x3 at n = 300) and with four rows per relabelling."""
+    n = sum(sizes)
+    v, P = 1301, 140
+    X = synth.gaussian_mean_shift(n, v, seed=n)
+    perms = synth.perms_pcg32(n, P, seed=7)
+    perms[5] = np.arange(n, dtype=np.int32)
+    got = run(cuda_lib, X, sizes, perms, precision)
+    check(X, sizes, perms, got, precision)
+
+
 def test_anova_two_groups_is_t_squared(cuda_lib):
     """g = 2: the maximum of F is the square of the two-sided t maximum (both
     recomputed in FP64 at the same winning voxel)."""
