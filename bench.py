@@ -723,7 +723,7 @@ def anova_leg(dev, B, synth, torch, sizes=(33, 33, 34), reps=3):
 def cluster_leg(dev, B, synth, torch, tau=3.2, conn=18, reps=3):
     """Cluster-level inference on the benchmark workload (n=100, 231,719 voxels,
     10,000 relabellings): the largest cluster of {t >= tau} per relabelling
-    (pt_cluster_maxnull, FP16x2 rows of u, union-find on the 91x109x91 grid)
+    (pt_cluster_maxnull: the FP16x2 contraction writes one bit per entry, u >= u(tau); union-find over the active voxels of the 91x109x91 grid)
     and the observed map's clusters with their cluster-level FWER p-values."""
     w = synth.workload(WORKLOAD, device=dev)
     X, mask, n1 = w["X"], w["mask"], w["n1"]
@@ -760,11 +760,20 @@ def cluster_leg(dev, B, synth, torch, tau=3.2, conn=18, reps=3):
             "observed_clusters": int(reps_.size),
             "largest_observed": [{"k": int(k), "p_fwe_cluster": float(p)}
                                  for k, p in zip(ks[:5], pv)],
-            "timing": "device events over %d calls (rows of u in batches, union-find, max)"
+            "timing": "device events over %d calls (bit rows u >= u(tau) from the contraction, union-find over the active voxels, max)"
                       % reps}
 
 
 def run_ours(args):
+    if args.cluster_only:
+        import torch
+        from paper_1703_01506_gb300 import binding as B
+        from paper_1703_01506_gb300 import synth
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        B.load()
+        print(json.dumps({"cluster": cluster_leg(dev, B, synth, torch)}), flush=True)
+        return
     if args.anova_only:
         import torch
         from paper_1703_01506_gb300 import binding as B
@@ -1053,6 +1062,8 @@ def main():
                     help="RapidPT training passes in the RapidPT leg (default 1, Alg. 2)")
     ap.add_argument("--rapid-rows", type=int, default=0,
                     help="relabellings of the RapidPT leg (default all 100,000)")
+    ap.add_argument("--cluster-only", action="store_true",
+                    help="run only the cluster-level leg (one line with its object)")
     ap.add_argument("--anova-only", action="store_true",
                     help="run only the F-statistic leg (one line with its object)")
     ap.add_argument("--rapid-only", action="store_true",

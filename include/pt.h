@@ -321,8 +321,10 @@ pt_status pt_maxnull_anova(pt_ctx* ctx, const int32_t* perms, int64_t P,
  *
  * pt_cluster_maxnull -- maxsize[i] (device int32[P]) = size of the largest
  *   cluster of relabelling i (0 when no voxel is active). perms as
- *   pt_maxnull_naive; precision as pt_naive_opts. Rows of u are formed a batch
- *   of relabellings at a time (about 1 GB of device workspace). Synchronous.
+ *   pt_maxnull_naive; precision as pt_naive_opts. A batch of relabellings at a
+ *   time, the contraction writes one bit per relabelling and voxel (t >= tau)
+ *   and the components are found over the active voxels (about 2 GB of device
+ *   workspace, of which only the active voxels' entries are touched). Synchronous.
  * pt_cluster_observed -- the observed map's clusters, in masked order:
  *   label[j] (device int32[v]) = masked index of the smallest voxel of j's
  *   cluster, or -1; size[j] (device int32[v]) = that cluster's size, or 0.

@@ -5,16 +5,18 @@
 // A voxel is active when its statistic reaches the threshold tau; clusters are
 // the connected sets of active mask voxels on the 3D grid under 6-, 18- or
 // 26-connectivity. Through the monotone map of each relabelling the test
-// t >= tau is u >= u(tau), u = tau / sqrt(k (n-2) + k tau^2), so the rows come
-// from the NaivePT contraction writing u (a batch of relabellings at a time)
-// and never as t.
+// t >= tau is u >= u(tau), u = tau / sqrt(k (n-2) + k tau^2), so the NaivePT
+// contraction writes, per relabelling of a batch, one bit per voxel (u >=
+// u(tau)) and nothing else: T stays out of memory.
 //
-// Components by union-find over compact voxel indices, one label array per
-// relabelling of the batch: a link always points to a smaller index, so a
-// root is the smallest voxel of its component, every find walks strictly
-// decreasing indices and every unite retries on a strictly smaller index.
-// Nothing waits on another thread; links are made with atomicMin and read
-// through L2 (__ldcg), where the atomics land.
+// Components by union-find over the compact indices of the active voxels,
+// one label array per relabelling of the batch of which only active entries
+// are ever written or read (a neighbour's activity is a bit test): a link
+// always points to a smaller index, so a root is the smallest voxel of its
+// component, every find walks strictly decreasing indices and every unite
+// retries on a strictly smaller index. Nothing waits on another thread; links
+// are made with atomicMin and read through L2 (__ldcg), where the atomics land.
+// The kernels walk bit words, so their work follows the active voxels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -65,13 +67,15 @@ __global__ void grid_inv_set_kernel(const int64_t* __restrict__ vox_grid,
     inv[vox_grid[valid_map[c]]] = int32_t(c);
 }
 
-// L (in place over the u rows, B x V) = c where u >= u_tau, else -1.
-__global__ void cc_init_kernel(float* __restrict__ U, int64_t total, int64_t V, float u_tau) {
-  int32_t* L = reinterpret_cast<int32_t*>(U);
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+// Bit rows from rows of u (the FP32 path): bit c of row b = U[b][c] >= u_tau.
+__global__ void cc_bits_from_rows_kernel(const float* __restrict__ U, int64_t B, int64_t V,
+                                         int64_t W, float u_tau, uint32_t* __restrict__ BM) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < B * W;
        e += int64_t(gridDim.x) * blockDim.x) {
-    const float u = U[e];
-    L[e] = u >= u_tau ? int32_t(e % V) : -1;
+    const int64_t b = e / W, c0 = (e - b * W) * 32;
+    uint32_t w = 0u;
+    for (int k = 0; k < 32 && c0 + k < V; ++k) w |= uint32_t(U[b * V + c0 + k] >= u_tau) << k;
+    BM[e] = w;
   }
 }
 
@@ -100,47 +104,77 @@ __device__ __forceinline__ void cc_unite(int32_t* L, int32_t a, int32_t b) {
   }
 }
 
-__global__ void cc_union_kernel(int32_t* __restrict__ L, int64_t total, int64_t V,
-                                const int32_t* __restrict__ valid_map,
+__device__ __forceinline__ bool bit_at(const uint32_t* __restrict__ row, int32_t c) {
+  return (__ldg(row + (c >> 5)) >> (c & 31)) & 1u;
+}
+
+// Per bit word e of the batch (row b = e / W): the word's active voxels c.
+#define CC_FOR_ACTIVE(...)                                                         \
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < B * W;       \
+       e += int64_t(gridDim.x) * blockDim.x) {                                      \
+    uint32_t w = BM[e];                                                             \
+    if (!w) continue;                                                               \
+    const int64_t b = e / W;                                                        \
+    const int32_t c0 = int32_t((e - b * W) * 32);                                   \
+    while (w) {                                                                     \
+      const int32_t c = c0 + __ffs(int(w)) - 1;                                     \
+      w &= w - 1u;                                                                  \
+      __VA_ARGS__                                                                   \
+    }                                                                               \
+  }
+
+// L[b][c] = c and S[b][c] = 0 for every active voxel (the only entries used).
+__global__ void cc_init_kernel(const uint32_t* __restrict__ BM, int64_t B, int64_t W, int64_t V,
+                               int32_t* __restrict__ L, int32_t* __restrict__ S) {
+  CC_FOR_ACTIVE({
+    L[b * V + c] = c;
+    S[b * V + c] = 0;
+  })
+}
+
+__global__ void cc_union_kernel(const uint32_t* __restrict__ BM, int64_t B, int64_t W, int64_t V,
+                                int32_t* __restrict__ L, const int32_t* __restrict__ valid_map,
                                 const int64_t* __restrict__ vox_grid,
                                 const int32_t* __restrict__ inv, int64_t d0, int64_t d1,
                                 int64_t d2, int noff) {
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    if (__ldcg(L + e) < 0) continue;
-    const int64_t b = e / V;
-    const int32_t c = int32_t(e - b * V);
+  CC_FOR_ACTIVE({
     int32_t* Lb = L + b * V;
+    const uint32_t* row = BM + b * W;
     const int64_t g = vox_grid[valid_map[c]];
     const int64_t i2 = g % d2, i1 = (g / d2) % d1, i0 = g / (d1 * d2);
     for (int k = 0; k < noff; ++k) {
       const int64_t j0 = i0 + kOffsets[k][0], j1 = i1 + kOffsets[k][1], j2 = i2 + kOffsets[k][2];
       if (j0 < 0 || j0 >= d0 || j1 < 0 || j1 >= d1 || j2 < 0 || j2 >= d2) continue;
       const int32_t cn = inv[(j0 * d1 + j1) * d2 + j2];
-      if (cn < 0 || __ldcg(Lb + cn) < 0) continue;
+      if (cn < 0 || !bit_at(row, cn)) continue;
       cc_unite(Lb, c, cn);
     }
-  }
+  })
 }
 
-// S[b][root] += 1 for every active voxel (S zeroed).
-__global__ void cc_count_kernel(const int32_t* __restrict__ L, int64_t total, int64_t V,
-                                int32_t* __restrict__ S) {
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    if (__ldcg(L + e) < 0) continue;
-    const int64_t b = e / V;
-    const int32_t r = cc_find(L + b * V, int32_t(e - b * V));
+// S[b][root] += 1 for every active voxel.
+__global__ void cc_count_kernel(const uint32_t* __restrict__ BM, int64_t B, int64_t W, int64_t V,
+                                const int32_t* __restrict__ L, int32_t* __restrict__ S) {
+  CC_FOR_ACTIVE({
+    const int32_t r = cc_find(L + b * V, c);
     atomicAdd(S + b * V + r, 1);
-  }
+  })
 }
 
-// out[b] = max_c S[b][c] (0 with no active voxel); one block per row.
-__global__ void cc_max_kernel(const int32_t* __restrict__ S, int64_t V, int32_t* __restrict__ out) {
+// out[b] = max over the active voxels c of S[b][c] (0 with none); one block per row.
+__global__ void cc_max_kernel(const uint32_t* __restrict__ BM, int64_t W, int64_t V,
+                              const int32_t* __restrict__ S, int32_t* __restrict__ out) {
   __shared__ int32_t wm[32];
   const int64_t b = blockIdx.x;
   int32_t m = 0;
-  for (int64_t c = threadIdx.x; c < V; c += blockDim.x) m = max(m, S[b * V + c]);
+  for (int64_t q = threadIdx.x; q < W; q += blockDim.x) {
+    uint32_t w = BM[b * W + q];
+    while (w) {
+      const int32_t c = int32_t(q * 32) + __ffs(int(w)) - 1;
+      w &= w - 1u;
+      m = max(m, __ldcg(S + b * V + c));
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
   __syncthreads();
@@ -153,16 +187,17 @@ __global__ void cc_max_kernel(const int32_t* __restrict__ S, int64_t V, int32_t*
 
 // Observed map in mask order: label = mask index of the cluster's smallest
 // voxel (-1 inactive or without a statistic), size = its cluster's size.
-__global__ void cc_observed_out_kernel(const int32_t* __restrict__ L, const int32_t* __restrict__ S,
-                                       int64_t V, const int32_t* __restrict__ valid_map,
+__global__ void cc_observed_out_kernel(const uint32_t* __restrict__ BM, const int32_t* __restrict__ L,
+                                       const int32_t* __restrict__ S, int64_t V,
+                                       const int32_t* __restrict__ valid_map,
                                        int32_t* __restrict__ label, int32_t* __restrict__ size) {
   for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < V;
        c += int64_t(gridDim.x) * blockDim.x) {
+    if (!bit_at(BM, int32_t(c))) continue;  // label/size keep their -1 / 0 fill
     const int32_t j = valid_map[c];
-    if (__ldcg(L + c) < 0) continue;  // label/size keep their -1 / 0 fill
     const int32_t r = cc_find(L, int32_t(c));
     label[j] = valid_map[r];
-    size[j] = S[r];
+    size[j] = __ldcg(S + r);
   }
 }
 
@@ -220,17 +255,19 @@ float u_of_tau(const pt_ctx* ctx, double tau) {
   return float(tau / std::sqrt(ctx->k * (ctx->n - 2) + ctx->k * tau * tau));
 }
 
-// Labels rows (B x V int32, active = c) -> component sizes -> per-row maxima.
-pt_status components(pt_ctx* ctx, int32_t* L, int64_t B, int32_t* S, int connectivity) {
-  const int64_t V = ctx->v_valid, total = B * V;
+// Bit rows (B x W words) -> labels of the active voxels -> component sizes at the roots.
+pt_status components(pt_ctx* ctx, const uint32_t* BM, int64_t B, int32_t* L, int32_t* S,
+                     int connectivity) {
+  const int64_t V = ctx->v_valid, W = (V + 31) / 32;
   cudaStream_t st = ctx->stream;
-  cc_union_kernel<<<grid_for(total, 256), 256, 0, st>>>(
-      L, total, V, ctx->valid_map.as<int32_t>(), ctx->vox_grid.as<int64_t>(),
+  cc_init_kernel<<<grid_for(B * W, 256), 256, 0, st>>>(BM, B, W, V, L, S);
+  PT_LAUNCH_CHECK(ctx);
+  cc_union_kernel<<<grid_for(B * W, 256), 256, 0, st>>>(
+      BM, B, W, V, L, ctx->valid_map.as<int32_t>(), ctx->vox_grid.as<int64_t>(),
       ctx->grid_inv.as<int32_t>(), ctx->grid_dims[0], ctx->grid_dims[1], ctx->grid_dims[2],
       n_offsets(connectivity));
   PT_LAUNCH_CHECK(ctx);
-  PT_CUDA_TRY(ctx, cudaMemsetAsync(S, 0, sizeof(int32_t) * size_t(total), st));
-  cc_count_kernel<<<grid_for(total, 256), 256, 0, st>>>(L, total, V, S);
+  cc_count_kernel<<<grid_for(B * W, 256), 256, 0, st>>>(BM, B, W, V, L, S);
   PT_LAUNCH_CHECK(ctx);
   return PT_OK;
 }
@@ -248,22 +285,28 @@ pt_status cluster_maxnull_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, dou
     PT_CUDA_TRY(ctx, cudaMemsetAsync(maxsize, 0, sizeof(int32_t) * size_t(P), st));
     return PT_OK;
   }
-  // batch of relabellings: two int32/float arrays of B x V, about 1 GB in all
-  int64_t B = std::max<int64_t>(128, (int64_t(1) << 29) / (4 * V) / 128 * 128);
+  // batch of relabellings: label and size arrays of B x V int32 (about 1 GB each,
+  // of which only the active voxels' entries are touched) and B x W bit words
+  const bool tc = precision != PT_PREC_FP32;
+  const int64_t W = (V + 31) / 32;
+  int64_t B = std::max<int64_t>(128, (int64_t(1) << 28) / V / 128 * 128);
   B = std::min<int64_t>(B, (P + 127) / 128 * 128);
-  Buf ub, sb;
+  Buf lb, sb, bm, ub;
   struct G {
-    Buf *a, *b;
+    Buf *a, *b, *c, *d;
     ~G() {
       a->release();
       b->release();
+      c->release();
+      d->release();
     }
-  } guard{&ub, &sb};
-  if (!ub.ensure(sizeof(float) * size_t(B) * V) || !sb.ensure(sizeof(int32_t) * size_t(B) * V)) {
+  } guard{&lb, &sb, &bm, &ub};
+  if (!lb.ensure(sizeof(int32_t) * size_t(B) * V) || !sb.ensure(sizeof(int32_t) * size_t(B) * V) ||
+      !bm.ensure(sizeof(uint32_t) * size_t(B) * W) ||
+      (!tc && !ub.ensure(sizeof(float) * size_t(B) * V))) {
     set_error(ctx, "out of device memory (cluster rows)");
     return PT_ERR_NOMEM;
   }
-  const bool tc = precision != PT_PREC_FP32;
   if (tc) {
     s = tc_supported(ctx);
     if (s == PT_OK) s = ensure_xnb(ctx, precision);
@@ -282,8 +325,9 @@ pt_status cluster_maxnull_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, dou
     s = build_labels(ctx, perms + i0 * ctx->n, nb, prec_label_layout(precision), &P_pad);
     if (s != PT_OK) return s;
     if (tc) {
-      s = tc_rows(ctx, ctx->labels.p, nb, precision, 1, ub.as<float>(), 0, 0, nullptr, nullptr,
-                  nullptr);
+      PT_CUDA_TRY(ctx, cudaMemsetAsync(bm.p, 0, sizeof(uint32_t) * size_t(nb) * W, st));
+      s = tc_rows(ctx, ctx->labels.p, nb, precision, 3, bm.as<float>(), 0, 0, nullptr, nullptr,
+                  nullptr, ut);
       if (s != PT_OK) return s;
     } else {
       const dim3 grid{unsigned((V + 127) / 128), unsigned((nb + 127) / 128), 1u};
@@ -292,12 +336,14 @@ pt_status cluster_maxnull_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, dou
                                                  ctx->rowflag.as<uint8_t>(), nullptr, nullptr,
                                                  ub.as<float>());
       PT_LAUNCH_CHECK(ctx);
+      cc_bits_from_rows_kernel<<<grid_for(nb * W, 256), 256, 0, st>>>(ub.as<float>(), nb, V, W,
+                                                                      ut, bm.as<uint32_t>());
+      PT_LAUNCH_CHECK(ctx);
     }
-    cc_init_kernel<<<grid_for(nb * V, 256), 256, 0, st>>>(ub.as<float>(), nb * V, V, ut);
-    PT_LAUNCH_CHECK(ctx);
-    s = components(ctx, reinterpret_cast<int32_t*>(ub.p), nb, sb.as<int32_t>(), connectivity);
+    s = components(ctx, bm.as<uint32_t>(), nb, lb.as<int32_t>(), sb.as<int32_t>(), connectivity);
     if (s != PT_OK) return s;
-    cc_max_kernel<<<unsigned(nb), 256, 0, st>>>(sb.as<int32_t>(), V, maxsize + i0);
+    cc_max_kernel<<<unsigned(nb), 256, 0, st>>>(bm.as<uint32_t>(), W, V, sb.as<int32_t>(),
+                                                maxsize + i0);
     PT_LAUNCH_CHECK(ctx);
   }
   // the batch buffers are released on return: wait for the kernels that use them
@@ -317,27 +363,30 @@ pt_status cluster_observed_impl(pt_ctx* ctx, double tau, const int32_t* dims, in
     PT_CUDA_TRY(ctx, cudaMemsetAsync(size, 0, sizeof(int32_t) * size_t(v), st));
   }
   if (V == 0) return PT_OK;
-  Buf ub, sb;
+  const int64_t W = (V + 31) / 32;
+  Buf lb, sb, bm;
   struct G {
-    Buf *a, *b;
+    Buf *a, *b, *c;
     ~G() {
       a->release();
       b->release();
+      c->release();
     }
-  } guard{&ub, &sb};
-  if (!ub.ensure(sizeof(float) * size_t(V)) || !sb.ensure(sizeof(int32_t) * size_t(V))) {
+  } guard{&lb, &sb, &bm};
+  if (!lb.ensure(sizeof(int32_t) * size_t(V)) || !sb.ensure(sizeof(int32_t) * size_t(V)) ||
+      !bm.ensure(sizeof(uint32_t) * size_t(W))) {
     set_error(ctx, "out of device memory (cluster map)");
     return PT_ERR_NOMEM;
   }
-  PT_CUDA_TRY(ctx, cudaMemcpyAsync(ub.p, ctx->u_obs.p, sizeof(float) * size_t(V),
-                                   cudaMemcpyDeviceToDevice, st));
-  cc_init_kernel<<<grid_for(V, 256), 256, 0, st>>>(ub.as<float>(), V, V, u_of_tau(ctx, tau));
+  cc_bits_from_rows_kernel<<<grid_for(W, 256), 256, 0, st>>>(ctx->u_obs.as<float>(), 1, V, W,
+                                                             u_of_tau(ctx, tau),
+                                                             bm.as<uint32_t>());
   PT_LAUNCH_CHECK(ctx);
-  s = components(ctx, reinterpret_cast<int32_t*>(ub.p), 1, sb.as<int32_t>(), connectivity);
+  s = components(ctx, bm.as<uint32_t>(), 1, lb.as<int32_t>(), sb.as<int32_t>(), connectivity);
   if (s != PT_OK) return s;
   cc_observed_out_kernel<<<grid_for(V, 256), 256, 0, st>>>(
-      reinterpret_cast<int32_t*>(ub.p), sb.as<int32_t>(), V, ctx->valid_map.as<int32_t>(), label,
-      size);
+      bm.as<uint32_t>(), lb.as<int32_t>(), sb.as<int32_t>(), V, ctx->valid_map.as<int32_t>(),
+      label, size);
   PT_LAUNCH_CHECK(ctx);
   PT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   return PT_OK;

@@ -245,10 +245,12 @@ pt_status tc_supported(pt_ctx* ctx);
 // build_labels, layout 1); rowflag/blockflag from the labels kernel.
 pt_status tc_reduce(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int two_sided,
                     const float* u_obs, unsigned long long* maxkey, uint32_t* cnt);
-// Same contraction writing rows: write_mode 1 -> u, 2 -> t; optionally also reducing.
+// Same contraction writing rows: write_mode 1 -> u, 2 -> t (optionally also
+// reducing); 3 -> one bit per entry, u >= uthr, or-ed into rows of
+// (v + 31) / 32 uint32 words at out (zeroed by the caller; no reduction).
 pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int write_mode,
                   float* out, int do_reduce, int two_sided, const float* u_obs,
-                  unsigned long long* maxkey, uint32_t* cnt);
+                  unsigned long long* maxkey, uint32_t* cnt, float uthr = 0.0f);
 
 // Several studies in one persistent launch per tile class. tc_batch_plan
 // encodes every study's tensor maps and work split (labels and workspaces of

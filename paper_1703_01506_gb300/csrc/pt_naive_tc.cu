@@ -104,11 +104,12 @@ struct TcArgs {
   int n_studies, stages, kps;  // ring stages, k-steps per stage
   int n_pad_max;
   int64_t n_items;
-  int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t
+  int do_reduce, write_mode;  // write_mode: 0 none, 1 u, 2 t, 3 bits u >= uthr
   int scaled;                 // the studies carry per-row factors (covariate-adjusted t)
   int f16;                    // FP16 operands (labels and 2^15-scaled data pieces)
   float uscale, inv_uscale;   // accumulator = uscale * u (2^15 for FP16 pieces, else 1)
   float k_f, ct_f;
+  float uthr;                 // write_mode 3: threshold on the accumulator's scale
   uint32_t* status;
 };
 
@@ -535,7 +536,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_wait_ld();
           }
           const int64_t g0 = gcol0 + c * CHK;
-          if (WRITE && a.write_mode && row_ok) {
+          if (WRITE && a.write_mode == 3 && row_ok) {
+            // one bit per entry (u >= threshold) in rows of (V + 31) / 32 words,
+            // or-ed in: the chunk's columns span at most two words
+            uint32_t* bm = reinterpret_cast<uint32_t*>(st.uout) + row * ((V + 31) >> 5);
+            const int sh = int(g0 & 31);
+            uint32_t w0 = 0u, w1 = 0u;
+#pragma unroll
+            for (int jj = 0; jj < CHK; ++jj) {
+              if (g0 + jj < V && __uint_as_float(r[jj]) >= a.uthr) {
+                const int p = sh + jj;
+                if (p < 32) w0 |= 1u << p;
+                else w1 |= 1u << (p - 32);
+              }
+            }
+            if (w0) atomicOr(bm + (g0 >> 5), w0);
+            if (w1) atomicOr(bm + (g0 >> 5) + 1, w1);
+          } else if (WRITE && a.write_mode && row_ok) {
             float* dst = st.uout + row * V;
 #pragma unroll
             for (int jj = 0; jj < CHK; ++jj) {
@@ -783,7 +800,7 @@ bool fill_study(pt_ctx* c, const void* Lb, int64_t P, int NT, int kps, int64_t t
 pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_items, int NT,
                          int stages, int kps, int pieces, int n_pad_max, int do_reduce,
                          int write_mode, int two_sided, float kf, float ctf, int scaled = 0,
-                         int f16 = 0, int fg = 0) {
+                         int f16 = 0, int fg = 0, float uthr = 0.0f) {
   if (scaled && (write_mode || !do_reduce)) {
     set_error(ctx, "covariate-adjusted statistic: reduce-only launches");
     return PT_ERR_UNSUPPORTED;
@@ -808,6 +825,7 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
   a.f16 = f16;
   a.uscale = f16 ? kF16Scale : 1.0f;
   a.inv_uscale = f16 ? 1.0f / kF16Scale : 1.0f;
+  a.uthr = uthr * a.uscale;  // power of two: exact
   a.status = ctx->status.as<uint32_t>();
   const int sms = num_sms(ctx->device);
   const int grid = int(n_items < sms ? n_items : sms);
@@ -836,7 +854,7 @@ pt_status launch_studies(pt_ctx* ctx, const TcStudy* descs, int n, int64_t n_ite
 pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int do_reduce,
                         int write_mode, int two_sided, const float* u_obs,
                         unsigned long long* maxkey, uint32_t* cnt, float* uout,
-                        const pt_tc_config& cfg, int f16) {
+                        const pt_tc_config& cfg, int f16, float uthr = 0.0f) {
   const int NT = cfg.voxel_tile;
   TcStudy st;
   if (!fill_study(ctx, Lb, P, NT, cfg.ksteps_per_stage,
@@ -855,12 +873,12 @@ pt_status tc_launch_cfg(pt_ctx* ctx, const void* Lb, int64_t P, int pieces, int 
   return launch_studies(ctx, ctx->tcdesc.as<TcStudy>(), 1, items, NT, cfg.stages,
                         cfg.ksteps_per_stage, pieces, ctx->n_pad, do_reduce, write_mode,
                         two_sided, float(ctx->k), float(ctx->c_t),
-                        ctx->glm_q1 && do_reduce && !write_mode ? 1 : 0, f16);
+                        ctx->glm_q1 && do_reduce && !write_mode ? 1 : 0, f16, 0, uthr);
 }
 
 pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int do_reduce,
                     int write_mode, int two_sided, const float* u_obs,
-                    unsigned long long* maxkey, uint32_t* cnt, float* uout) {
+                    unsigned long long* maxkey, uint32_t* cnt, float* uout, float uthr = 0.0f) {
   const int pieces = prec_pieces(precision);
   pt_tc_config cfg;
   if (!tc_default_config(ctx->n_pad, pieces, &cfg)) {
@@ -871,7 +889,7 @@ pt_status tc_launch(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int d
   // recorded for this shape; row-writing launches keep the default.
   if (do_reduce && !write_mode) tune_find(ctx->n_pad, precision, two_sided, ctx->v_valid, P, &cfg);
   return tc_launch_cfg(ctx, Lb, P, pieces, do_reduce, write_mode, two_sided, u_obs, maxkey, cnt,
-                       uout, cfg, precision == PT_PREC_FP16X2 ? 1 : 0);
+                       uout, cfg, precision == PT_PREC_FP16X2 ? 1 : 0, uthr);
 }
 
 }  // namespace
@@ -941,9 +959,13 @@ pt_status tc_reduce(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int t
 
 pt_status tc_rows(pt_ctx* ctx, const void* Lb, int64_t P, int precision, int write_mode,
                   float* out, int do_reduce, int two_sided, const float* u_obs,
-                  unsigned long long* maxkey, uint32_t* cnt) {
+                  unsigned long long* maxkey, uint32_t* cnt, float uthr) {
+  if (write_mode == 3 && (do_reduce || two_sided)) {
+    set_error(ctx, "bit rows: one-sided, without the reduction");
+    return PT_ERR_INVALID;
+  }
   return tc_launch(ctx, Lb, P, precision, do_reduce, write_mode, two_sided, u_obs, maxkey, cnt,
-                   out);
+                   out, uthr);
 }
 
 // ---------------------------------------------------------------------------
