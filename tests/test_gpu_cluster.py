@@ -54,17 +54,18 @@ def test_cluster_maxnull_matches_oracle(cuda_lib, conn, precision):
 
 def test_cluster_extremes_and_batches(cuda_lib):
     """A threshold above every t gives 0; one below every t gives the largest
-    connected part of the mask; 3,500 relabellings of a ~40k-voxel mask take
-    two batches of rows (the batch holds about 2^29 / (4 v) relabellings), and
-    the rows on both sides of the batch boundary match the oracle."""
+    connected part of the mask; the relabellings of a ~40k-voxel mask take two
+    batches (a batch holds about 2^28 / v relabellings), and the rows on both
+    sides of the batch boundary match the oracle."""
     B = cuda_lib
     dims = (48, 56, 48)
     X, mask = synth.brain_field(20, 10, grid=dims, center=(24, 28, 24), semi_axes=(20, 24, 20),
                                 fwhm=5.0, seed=8)
     X, mask = X.numpy(), mask.numpy().astype(bool)
-    n, n1, P = 20, 10, 3500
+    n, n1 = 20, 10
     v = int(mask.sum())
-    batch = (2 ** 29 // (4 * v)) // 128 * 128
+    batch = (2 ** 28 // v) // 128 * 128
+    P = batch + 600
     assert batch < P
     perms = synth.perms_pcg32(n, P, seed=9)
     ctx = B.pt_prepare(torch.as_tensor(X).cuda(), n1, torch.as_tensor(mask.astype(np.uint8)).cuda())
