@@ -73,6 +73,26 @@ __device__ __forceinline__ float4 lds4(const float* p) {
   return v;
 }
 
+// Bulk copy of `bytes` from global src to this CTA's shared dst, completing
+// on the mbarrier bar (dst, src and bytes multiples of 16).
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (bulk copy) writes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int RP>
 __device__ __forceinline__ void geodesic_row(float4 (&x)[RP / 4], float lj, const float* w,
                                              const float* wh, const float* g2, float alpha,
@@ -119,15 +139,17 @@ struct CluSmem {
   float* y;
   float* x;
   int32_t* idx;  // mloc sampled voxel of each local row
-  float* G;      // R x R
-  float* Gi;     // R x R
-  float* Gp;     // R x RG (RG = R rounded up to 4), upper triangle: this CTA's Gram
-                 // partial, read by the whole cluster in float4 steps
-  float* slot;   // 2 x kSlot: this CTA's partial vectors (parity-alternated)
-  float* red;    // kCluWarps x RP cross-warp partials
+  float* G;      // R x RG (RG = R rounded up to 4): the Gram matrix, inverted in place
+  float* Gp;     // R x RG, upper triangle: this CTA's Gram partial, read by the cluster
+                 // in float4 steps
+  float* xch;    // 2 x CL x kSlot: the partial vectors every rank pushed here, one slot
+                 // per rank (parity-alternated)
+  float* stage;  // kSlot: this CTA's partial vector before it is pushed
+  float* red;    // kCluWarps x RP cross-warp partials; the Gauss-Jordan staging
   float* vec;    // kSlot: a cluster sum
   float* wv;     // RP: weights
   float* misc;   // 8 scalars, then one partial per warp
+  float* pinv;   // 16: inverse of the current Gauss-Jordan pivot block
   float* Lrow;   // n_pad labels of the relabelling (recovery)
 };
 constexpr int kSlot = kMaxRank + 8;
@@ -138,8 +160,9 @@ constexpr int kSlot = kMaxRank + 8;
 __host__ __device__ constexpr int clu_rs(int RP) { return (RP / 4) % 2 == 0 ? RP + 4 : RP; }
 
 __host__ __device__ inline size_t clu_carve(float* base, int mloc, int R, int RP, int n_pad,
-                                            CluSmem* f) {
+                                            int CL, CluSmem* f) {
   const int RS = clu_rs(RP);
+  const size_t RG = size_t(R + 3) / 4 * 4;
   size_t o = 0;
   auto take = [&](size_t nfl) {
     float* p = base ? base + o : nullptr;
@@ -153,52 +176,56 @@ __host__ __device__ inline size_t clu_carve(float* base, int mloc, int R, int RP
   t.y = take(mloc);
   t.x = take(mloc);
   t.idx = reinterpret_cast<int32_t*>(take(mloc));
-  t.G = take(size_t(R) * R);
-  t.Gi = take(size_t(R) * R);
+  t.G = take(size_t(R) * RG);
   // The Gram partial is dead once the cluster has summed it (a cluster barrier
   // follows the sum), before s, y and x are first written: it shares their
   // space when it fits there (contiguous: s, y, x are taken in a row).
-  const size_t gp = size_t(R) * ((R + 3) / 4 * 4);
+  const size_t gp = size_t(R) * RG;
   t.Gp = gp <= 3 * ((size_t(mloc) + 3) / 4 * 4) ? t.s : take(gp);
-  t.slot = take(2 * kSlot);
+  t.xch = take(2 * size_t(CL) * kSlot);
+  t.stage = take(kSlot);
   t.red = take(size_t(kCluWarps) * RP);
   t.vec = take(kSlot);
   t.wv = take(RP);
   t.misc = take(8 + kCluWarps);
+  t.pinv = take(16);
   t.Lrow = take(n_pad);
   if (f) *f = t;
   return o * sizeof(float);
 }
 
-// sum over the cluster's CTAs, in rank order, of p[e] (p in this CTA's shared
-// memory, mapped to each rank's copy); the loads are all issued before the
-// adds so their distributed-shared-memory latencies overlap.
-constexpr int kMaxCluster = 16;
-__device__ __forceinline__ float clu_gather_sum(cg::cluster_group& cl, const float* p, int e,
-                                                int CL) {
-  float t[kMaxCluster];
-#pragma unroll
-  for (int r = 0; r < kMaxCluster; ++r)
-    t[r] = r < CL ? cl.map_shared_rank(const_cast<float*>(p), r)[e] : 0.0f;
+// Pushes this CTA's partial vector p[0..len) into its slot (par, rank) in every
+// CTA of the cluster (remote shared-memory stores; the cluster barrier that
+// follows makes them visible).
+__device__ __forceinline__ void clu_push(cg::cluster_group& cl, const CluSmem& f, int par,
+                                         int rank, const float* p, int len, int CL) {
+  float* mine = f.xch + (size_t(par) * CL + rank) * kSlot;
+  for (int e = threadIdx.x; e < len * CL; e += blockDim.x) {
+    const int r = e / len, c = e - r * len;
+    cl.map_shared_rank(mine, r)[c] = p[c];
+  }
+}
+
+// Sum over the ranks, in rank order, of the pushed slots (par, .)[c].
+__device__ __forceinline__ float clu_slot_sum(const CluSmem& f, int par, int c, int CL) {
+  const float* s = f.xch + size_t(par) * CL * kSlot + c;
   float sum = 0.0f;
-#pragma unroll
-  for (int r = 0; r < kMaxCluster; ++r)
-    if (r < CL) sum += t[r];
+  for (int r = 0; r < CL; ++r) sum += s[size_t(r) * kSlot];
   return sum;
 }
 
-// Sum over the cluster's CTAs (rank order) of slot[par][0..len) into vec.
+// Sum over the cluster's CTAs (rank order) of stage[0..len) into vec.
 __device__ __forceinline__ void clu_sum(cg::cluster_group& cl, const CluSmem& f, int& par,
-                                        int len, int CL) {
+                                        int len, int CL, int rank) {
   __syncthreads();
+  clu_push(cl, f, par, rank, f.stage, len, CL);
   cl.sync();
-  float* mine = f.slot + par * kSlot;
-  for (int c = threadIdx.x; c < len; c += blockDim.x) f.vec[c] = clu_gather_sum(cl, mine, c, CL);
+  for (int c = threadIdx.x; c < len; c += blockDim.x) f.vec[c] = clu_slot_sum(f, par, c, CL);
   par ^= 1;
   __syncthreads();
 }
 
-// slot[par][c] = sum over local rows q of A[q][c] x[q], c < R.
+// out[c] = sum over local rows q of A[q][c] x[q], c < R.
 template <int RP>
 __device__ __forceinline__ void clu_AtX(const CluSmem& f, int mloc, int R, const float* x,
                                         float* out) {
@@ -230,7 +257,7 @@ __device__ __forceinline__ void clu_AtX(const CluSmem& f, int mloc, int R, const
   }
 }
 
-// Block sum of one value per thread into slot position `pos` (thread 0 writes).
+// Block sum of one value per thread into *dst (thread 0 writes).
 __device__ __forceinline__ void clu_block_sum_to(float v, const CluSmem& f, float* dst) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if ((threadIdx.x & 31) == 0) f.misc[8 + (threadIdx.x >> 5)] = v;
@@ -261,121 +288,150 @@ __device__ __forceinline__ float clu_row_dot(const float* row, const float* v) {
   return t0 + t1;
 }
 
-// Gram G = A^T A over the cluster, then G^-1 (Gauss-Jordan, no pivoting: G is
-// symmetric positive definite), then ADMM; leaves w in f.wv (zero-padded to RP).
-// An ADMM iteration: A^T x over the CTA's rows, one cluster barrier and a
-// rank-ordered gather of the R-vector, w = G^-1 v, then the s, y, x updates
-// with one thread per row.
+// Sum over local rows q = first, first + step, ... of the 4 x 4 outer products
+// of A's column blocks ti and tj (four rows per step in flight).
+template <int RP>
+__device__ __forceinline__ void gram_tile(const float* A, int mloc, int first, int step, int ti,
+                                          int tj, float (&acc)[4][4]) {
+  constexpr int RS = clu_rs(RP);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.0f;
+#pragma unroll 4
+  for (int q = first; q < mloc; q += step) {
+    const float4 u = *reinterpret_cast<const float4*>(A + q * RS + 4 * ti);
+    const float4 v = *reinterpret_cast<const float4*>(A + q * RS + 4 * tj);
+    const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(uu[a], vv[b2], acc[a][b2]);
+  }
+}
+
+__device__ __forceinline__ void tile_of(int tile, int RT, int& ti, int& tj) {
+  ti = 0;
+  int rem = tile;
+  while (rem >= RT - ti) {
+    rem -= RT - ti;
+    ++ti;
+  }
+  tj = ti + rem;
+}
+
+// Gram G = A^T A over the cluster, then G^-1 in place (block Gauss-Jordan
+// without pivoting: G is symmetric positive definite), then ADMM; leaves w in
+// f.wv (zero-padded to RP). An ADMM iteration: A^T x over the CTA's rows, the
+// CTA's share G^-1 (A^T x)_local pushed to every rank, one cluster barrier, the
+// rank-ordered sum of the pushed shares, then the s, y, x updates with one
+// thread per row.
 template <int RP>
 __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, int R, float rho,
-                           int iters, int CL, int& par) {
+                           int iters, int CL, int rank, int& par) {
   constexpr int RS = clu_rs(RP);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int RG = (R + 3) / 4 * 4;
-  // --- local Gram partial by 4x4 register tiles of the upper triangle; the
-  // rows are split over ngr thread groups whose sums are added in group order
+  // --- local Gram partial by 4x4 register tiles of the upper triangle. With
+  // fewer tiles than threads, ngr thread groups take every ngr-th row each,
+  // all at once, and add their sums into Gp in group order.
   constexpr int RT = RP / 4;
-  const int ntile = RT * (RT + 1) / 2;
-  const int ngr = ntile >= int(blockDim.x) ? 1 : int(blockDim.x) / ntile;
-  for (int g = 0; g < ngr; ++g) {
-    for (int t = tid; t < ntile * ngr; t += blockDim.x) {
-      const int tile = t % ntile, grp = t / ntile;
-      int ti = 0, rem = tile;
-      while (rem >= RT - ti) {
-        rem -= RT - ti;
-        ++ti;
-      }
-      const int tj = ti + rem;
-      float acc[4][4];
+  constexpr int ntile = RT * (RT + 1) / 2;
+  constexpr int ngr = ntile >= kCluThreads ? 1 : kCluThreads / ntile;
+  auto put_tile = [&](int ti, int tj, const float (&acc)[4][4], bool add) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = 0.0f;
-      if (grp == g || ngr == 1) {
-        for (int q = (ngr == 1 ? 0 : grp); q < mloc; q += ngr) {
-          const float4 u = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * ti);
-          const float4 v = *reinterpret_cast<const float4*>(f.A + q * RS + 4 * tj);
-          const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b2 = 0; b2 < 4; ++b2) acc[a][b2] = fmaf(uu[a], vv[b2], acc[a][b2]);
+      for (int b2 = 0; b2 < 4; ++b2) {
+        const int c = 4 * ti + a, d = 4 * tj + b2;
+        if (c < R && d < RG) {
+          const float val = (c <= d && d < R) ? acc[a][b2] : 0.0f;
+          f.Gp[c * RG + d] = add ? f.Gp[c * RG + d] + val : val;
         }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b2 = 0; b2 < 4; ++b2) {
-            const int c = 4 * ti + a, d = 4 * tj + b2;
-            if (c < R && d < RG) {
-              const float val = (c <= d && d < R) ? acc[a][b2] : 0.0f;
-              f.Gp[c * RG + d] = g == 0 ? val : f.Gp[c * RG + d] + val;
-            }
-          }
       }
+  };
+  if constexpr (ngr == 1) {
+    for (int t = tid; t < ntile; t += kCluThreads) {
+      int ti, tj;
+      tile_of(t, RT, ti, tj);
+      float acc[4][4];
+      gram_tile<RP>(f.A, mloc, 0, 1, ti, tj, acc);
+      put_tile(ti, tj, acc, false);
     }
-    if (ngr == 1) break;
-    __syncthreads();
+  } else {
+    const bool act = tid < ntile * ngr;
+    const int grp = tid / ntile;
+    int ti = 0, tj = 0;
+    tile_of(tid - grp * ntile, RT, ti, tj);
+    float acc[4][4];
+    gram_tile<RP>(f.A, act ? mloc : 0, grp, ngr, ti, tj, acc);
+    for (int g = 0; g < ngr; ++g) {
+      if (act && grp == g) put_tile(ti, tj, acc, g > 0);
+      __syncthreads();
+    }
   }
   __syncthreads();
-  cl.sync();
-  // cluster sum of the upper triangle in float4 steps (rank order), mirrored
+  cl.sync();  // every CTA's partial is complete
+  // --- cluster sum of the upper triangle: rank k sums the float4 units u with
+  // u % CL == k over all ranks (rank order) and writes the sum into every
+  // rank's G; then each CTA mirrors the upper triangle
   const int rg4 = RG / 4;
-  for (int e = tid; e < R * rg4; e += blockDim.x) {
+  for (int e = rank + CL * tid; e < R * rg4; e += CL * kCluThreads) {
     const int c = e / rg4, d4 = e - c * rg4;
     if (4 * d4 + 3 < c) continue;  // wholly below the diagonal
-    float4 t[kMaxCluster];
-#pragma unroll
-    for (int r = 0; r < kMaxCluster; ++r)
-      t[r] = r < CL ? *reinterpret_cast<const float4*>(cl.map_shared_rank(f.Gp, r) + c * RG + 4 * d4)
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r0 = 0; r0 < CL; r0 += 4) {  // four ranks' loads in flight, added in rank order
+      float4 t[4];
 #pragma unroll
-    for (int r = 0; r < kMaxCluster; ++r)
-      if (r < CL) {
-        sum.x += t[r].x;
-        sum.y += t[r].y;
-        sum.z += t[r].z;
-        sum.w += t[r].w;
-      }
-    const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+      for (int u = 0; u < 4; ++u)
+        if (r0 + u < CL)
+          t[u] = *reinterpret_cast<const float4*>(cl.map_shared_rank(f.Gp, r0 + u) + c * RG +
+                                                  4 * d4);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int d = 4 * d4 + u;
-      if (d >= c && d < R) {
-        f.G[c * R + d] = sv[u];
-        f.G[d * R + c] = sv[u];
-      }
+      for (int u = 0; u < 4; ++u)
+        if (r0 + u < CL) {
+          sum.x += t[u].x;
+          sum.y += t[u].y;
+          sum.z += t[u].z;
+          sum.w += t[u].w;
+        }
     }
+    for (int r = 0; r < CL; ++r)
+      *reinterpret_cast<float4*>(cl.map_shared_rank(f.G, r) + c * RG + 4 * d4) = sum;
   }
-  cl.sync();  // every CTA has read every Gram partial (their space is reused)
-  for (int e = tid; e < R * R; e += blockDim.x) f.Gi[e] = 0.0f;
-  __syncthreads();
-  for (int c = tid; c < R; c += blockDim.x) f.Gi[c * R + c] = 1.0f;
-  // --- G^-1 by block Gauss-Jordan on [G | I] with 4 x 4 pivot blocks (no
-  // pivoting: G is symmetric positive definite, so every pivot block is too).
-  // Round k: every thread inverts the pivot block P in registers; the scaled
-  // pivot rows P^-1 [G | G^-1]_k go to rowk and the pivot columns to fac
-  // (phase 1); then every row is updated from them (phase 2): two barriers per
-  // four pivots.
-  float* fac = f.red;           // R x 4: pivot columns of the other rows
-  float* rowk = f.red + 4 * R;  // 4 x R: scaled pivot rows (the round's R columns)
+  cl.sync();  // G's upper triangle is complete everywhere; the partials are dead
+  for (int e = tid; e < R * R; e += kCluThreads) {
+    const int c = e / R, d = e - c * R;
+    if (d < c) f.G[c * RG + d] = f.G[d * RG + c];
+  }
+  // --- G^-1 in place by block Gauss-Jordan with 4 x 4 pivot blocks K. Round:
+  // (A) warp 0 inverts P = G[K][K] while the other warps copy the pivot
+  // columns G[.][K] (fac) and rows G[K][.] (rowb); (B) z = P^-1 rowb, with
+  // P^-1 itself in the columns of K; (C) rows i in K become z, every other
+  // row i becomes (G[i] outside K) - G[i][K] z. Three block barriers a round.
+  float* fac = f.red;            // R x 4
+  float* rowb = f.red + 4 * R;   // 4 x R
+  float* zr = f.red + 8 * R;     // 4 x RG (16-byte aligned: 8 R floats are 32 R bytes)
   constexpr int kRowsPerWarp = (RP + kCluWarps - 1) / kCluWarps;
+  constexpr int CW = RP <= 64 ? 2 : 4;  // columns per lane
+  using VecT = typename std::conditional<CW == 2, float2, float4>::type;
+  static_assert(CW * 32 >= RP, "one pass over the columns");
   for (int k = 0; k < R; k += 4) {
     const int bk = R - k < 4 ? R - k : 4;
+    const int kb = k + bk;
     __syncthreads();
-    float pi[4][4];  // P^-1 (Gauss-Jordan on the b x b block, padded with I)
-    {
-      float pa[4][4];
+    if (warp == 0) {
+      float pa[4][4], pi[4][4];  // Gauss-Jordan on the bk x bk block, padded with I
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          pa[r][c] = (r < bk && c < bk) ? f.G[(k + r) * R + k + c] : (r == c ? 1.0f : 0.0f);
+          pa[r][c] = (r < bk && c < bk) ? f.G[(k + r) * RG + k + c] : (r == c ? 1.0f : 0.0f);
           pi[r][c] = r == c ? 1.0f : 0.0f;
         }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const float inv = 1.0f / pa[q][q];
+        const float inv = __frcp_rn(pa[q][q]);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           pa[q][c] *= inv;
@@ -392,74 +448,86 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
           }
         }
       }
-    }
-    // Only R of the 2R columns of [G | G^-1] can change in this round: the G
-    // columns right of the pivot block (those left of it are eliminated and
-    // never read again) and the G^-1 columns up to the pivot block's end (those
-    // right of it are still identity columns, which the round leaves alone).
-    // Column index jc < nG: G column kb + jc; else G^-1 column jc - nG.
-    const int kb = k + bk, nG = R - kb;
-    for (int e = tid; e < 4 * R; e += blockDim.x) {
-      const int r = e / R, jc = e - r * R;
-      const float* M = jc < nG ? f.G + kb + jc : f.Gi + (jc - nG);
-      float t = 0.0f;
-      if (r < bk)
+      if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c < bk) t = fmaf(pi[r][c], M[(k + c) * R], t);
-      rowk[e] = t;
-    }
-    for (int e = tid; e < 4 * R; e += blockDim.x) {
-      const int i = e >> 2, c = e & 3;
-      fac[e] = (c < bk && (i < k || i >= k + bk)) ? f.G[i * R + k + c] : 0.0f;
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) f.pinv[4 * r + c] = pi[r][c];
+    } else {
+      for (int e = tid - 32; e < 8 * R; e += kCluThreads - 32) {
+        if (e < 4 * R) {
+          const int i = e >> 2, c = e & 3;
+          fac[e] = c < bk ? f.G[i * RG + k + c] : 0.0f;
+        } else {
+          const int r = (e - 4 * R) / R, j = e - 4 * R - r * R;
+          rowb[r * R + j] = r < bk ? f.G[(k + r) * RG + j] : 0.0f;
+        }
+      }
     }
     __syncthreads();
-    // all loads of a thread's entries before its stores (the compiler cannot
-    // reorder loads past stores through these aliasing shared pointers)
-    for (int jc = lane; jc < R; jc += 32) {
-      float* M = jc < nG ? f.G + kb + jc : f.Gi + (jc - nG);
-      float rg[4];
+    for (int e = tid; e < 4 * RG; e += kCluThreads) {
+      const int r = e / RG, j = e - r * RG;
+      float t = 0.0f;
+      if (r < bk && j < R) {
+        if (j >= k && j < kb) {
+          t = f.pinv[4 * r + (j - k)];
+        } else {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) rg[c] = rowk[c * R + jc];
-      float gv[kRowsPerWarp];
-      float4 fv[kRowsPerWarp];
-#pragma unroll
-      for (int t = 0; t < kRowsPerWarp; ++t) {
-        const int i = warp + kCluWarps * t;
-        gv[t] = i < R ? M[i * R] : 0.0f;
-        fv[t] = i < R ? *reinterpret_cast<const float4*>(fac + 4 * i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int c = 0; c < 4; ++c)
+            if (c < bk) t = fmaf(f.pinv[4 * r + c], rowb[c * R + j], t);
+        }
       }
+      zr[e] = t;
+    }
+    __syncthreads();
+    // a thread's entries: rows warp + 16 t, the CW adjacent columns CW lane ..
+    // CW lane + CW - 1 (vector accesses; columns R .. RG - 1 are padding that
+    // is computed but never read)
+    if (CW * lane < RG) {
+      const int j0 = CW * lane;
+      VecT zc[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) zc[c] = *reinterpret_cast<const VecT*>(zr + c * RG + j0);
 #pragma unroll
       for (int t = 0; t < kRowsPerWarp; ++t) {
         const int i = warp + kCluWarps * t;
-        if (i < R) {
-          if (i >= k && i < kb) {
-            const int r = i - k;  // selected without indexing the register arrays
-            M[i * R] = r == 0 ? rg[0] : r == 1 ? rg[1] : r == 2 ? rg[2] : rg[3];
-          } else {
-            float g = gv[t];
-            g = fmaf(-fv[t].x, rg[0], g);
-            g = fmaf(-fv[t].y, rg[1], g);
-            g = fmaf(-fv[t].z, rg[2], g);
-            g = fmaf(-fv[t].w, rg[3], g);
-            M[i * R] = g;
+        if (i >= R) continue;
+        VecT* gp = reinterpret_cast<VecT*>(f.G + i * RG + j0);
+        if (i >= k && i < kb) {
+          const int r = i - k;  // selected without indexing a register array
+          *gp = r == 0 ? zc[0] : r == 1 ? zc[1] : r == 2 ? zc[2] : zc[3];
+        } else {
+          const float4 fi = *reinterpret_cast<const float4*>(fac + 4 * i);
+          VecT g = *gp;
+          float* gg = reinterpret_cast<float*>(&g);
+#pragma unroll
+          for (int u = 0; u < CW; ++u) {
+            const int j = j0 + u;
+            float v = (j >= k && j < kb) ? 0.0f : gg[u];
+            v = fmaf(-fi.x, reinterpret_cast<const float*>(&zc[0])[u], v);
+            v = fmaf(-fi.y, reinterpret_cast<const float*>(&zc[1])[u], v);
+            v = fmaf(-fi.z, reinterpret_cast<const float*>(&zc[2])[u], v);
+            v = fmaf(-fi.w, reinterpret_cast<const float*>(&zc[3])[u], v);
+            gg[u] = v;
           }
+          *gp = g;
         }
       }
     }
   }
-  __syncthreads();  // fac and rowk (in red) are read until here
+  __syncthreads();  // G holds G^-1; fac, rowb and zr (in red) are read until here
   // --- ADMM on min ||s||_1 s.t. A w + s = b (s = y = 0 at the start, so x = b).
   // Rows belong to warps in groups of 32: thread t handles rows t, t + 512, ...,
   // so a warp's rows form whole groups. Per group the warp first updates each
   // row with the current w (thread = row: A_q . w in float4 steps, then s, y, x)
-  // and then adds the group's rows into A^T x (lane = column, x_q passed by
-  // shuffle from its row's thread), so no block barrier separates the two.
+  // and then adds the group's rows into A^T x (lane = column, x_q read back
+  // from shared memory four rows at a time), so no block barrier separates
+  // the two.
   // Then: the warps' partial sums (one barrier), this CTA's sum (one barrier),
-  // its share of the next w, G^-1 (this CTA's A^T x), summed over the cluster
-  // in rank order (one cluster barrier), the sum (one barrier). G^-1 is the
-  // same in every CTA and the rank-ordered sum is too, so every CTA holds the
-  // same w. An iteration: three block barriers and one cluster barrier.
+  // its share of the next w, G^-1 (this CTA's A^T x), pushed to every rank (one
+  // cluster barrier), the rank-ordered sum of the shares (one barrier). G^-1 is
+  // the same in every CTA and the rank-ordered sum is too, so every CTA holds
+  // the same w.
   const float irho = 1.0f / rho;
   // A^T x pass: lane l takes the VW adjacent columns VW l .. VW l + VW - 1
   // (one 8- or 16-byte load per row), four rows per step.
@@ -485,7 +553,7 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
   auto rows_pass = [&](bool update) {
 #pragma unroll
     for (int k = 0; k < VW; ++k) acc[k] = 0.0f;
-    for (int base = warp * 32; base < mloc; base += int(blockDim.x)) {
+    for (int base = warp * 32; base < mloc; base += kCluThreads) {
       const int q = base + lane;
       float xq = 0.0f;
       if (q < mloc) {
@@ -507,59 +575,67 @@ __device__ void clu_l1_fit(cg::cluster_group& cl, const CluSmem& f, int mloc, in
         f.x[q] = xq;
       }
       const int rows_here = mloc - base < 32 ? mloc - base : 32;
+      __syncwarp();  // the group's x, written above by each row's thread
       int jq = 0;
       for (; jq + 4 <= rows_here; jq += 4) {
-        const float x0 = __shfl_sync(0xffffffffu, xq, jq);
-        const float x1 = __shfl_sync(0xffffffffu, xq, jq + 1);
-        const float x2 = __shfl_sync(0xffffffffu, xq, jq + 2);
-        const float x3 = __shfl_sync(0xffffffffu, xq, jq + 3);
+        const float4 x4 = *reinterpret_cast<const float4*>(f.x + base + jq);  // broadcast
         if (lane_on) {
-          add_row(base + jq, x0);
-          add_row(base + jq + 1, x1);
-          add_row(base + jq + 2, x2);
-          add_row(base + jq + 3, x3);
+          add_row(base + jq, x4.x);
+          add_row(base + jq + 1, x4.y);
+          add_row(base + jq + 2, x4.z);
+          add_row(base + jq + 3, x4.w);
         }
       }
-      for (; jq < rows_here; ++jq) {
-        const float xj = __shfl_sync(0xffffffffu, xq, jq);
-        if (lane_on) add_row(base + jq, xj);
-      }
+      for (; jq < rows_here; ++jq)
+        if (lane_on) add_row(base + jq, f.x[base + jq]);
     }
   };
   rows_pass(false);  // A^T b
+  // this CTA's share of w: GS adjacent lanes share a column c, each summing
+  // a CH-long run of the terms of G^-1 (A^T x)_local, then a shuffle tree
+  constexpr int GS = kCluThreads / RP >= 8 ? 8 : (kCluThreads / RP >= 4 ? 4 : 2);
+  constexpr int CH = ((RP + GS - 1) / GS + 3) / 4 * 4;
+  const int gsub = tid % GS;
+  for (int c = R + tid; c < RG; c += kCluThreads) f.vec[c] = 0.0f;  // padding of A^T x
   for (int it = 0; it < iters; ++it) {
     if (lane_on) {
 #pragma unroll
       for (int k = 0; k < VW; ++k) f.red[warp * RP + VW * lane + k] = acc[k];
     }
     __syncthreads();
-    for (int c = tid; c < R; c += blockDim.x) {
+    for (int c = tid; c < R; c += kCluThreads) {
       float t = 0.0f;
 #pragma unroll
       for (int ww = 0; ww < kCluWarps; ++ww) t += f.red[ww * RP + c];
       f.vec[c] = t;  // this CTA's A^T x
     }
     __syncthreads();
-    float* mine = f.slot + par * kSlot;
-    {
-      // this CTA's share of w: G^-1 (A^T x)_local; GS adjacent lanes share a
-      // column, each summing every GS-th term, then a shuffle tree (short
-      // dependent chains instead of R FMAs in a row)
-      constexpr int GS = kCluThreads / RP >= 8 ? 8 : (kCluThreads / RP >= 4 ? 4 : 2);
-      const int g = tid % GS;
-      for (int c0 = 0; c0 < R; c0 += kCluThreads / GS) {
-        const int c = c0 + tid / GS;
-        float t = 0.0f;
-        if (c < R)
-          for (int d = g; d < R; d += GS) t = fmaf(f.Gi[d * R + c], f.vec[d], t);
+    float* mine = f.xch + (size_t(par) * CL + rank) * kSlot;
+    for (int c0 = 0; c0 < R; c0 += kCluThreads / GS) {
+      const int c = c0 + tid / GS;
+      float t0 = 0.0f, t1 = 0.0f;
+      if (c < R) {
 #pragma unroll
-        for (int o = GS / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (c < R && g == 0) mine[c] = t;
+        for (int q4 = 0; q4 < CH / 4; ++q4) {
+          const int d = gsub * CH + 4 * q4;
+          if (d < RG) {  // row c of G^-1 (symmetric) against vec; both zero past R
+            const float4 g = *reinterpret_cast<const float4*>(f.G + c * RG + d);
+            const float4 v = *reinterpret_cast<const float4*>(f.vec + d);
+            t0 = fmaf(g.x, v.x, t0);
+            t1 = fmaf(g.y, v.y, t1);
+            t0 = fmaf(g.z, v.z, t0);
+            t1 = fmaf(g.w, v.w, t1);
+          }
+        }
       }
+      float t = t0 + t1;
+#pragma unroll
+      for (int o = GS / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (c < R)  // every lane of the column's group holds t: lane g pushes to ranks g, g + GS, ...
+        for (int r = gsub; r < CL; r += GS) cl.map_shared_rank(mine, r)[c] = t;
     }
     cl.sync();
-    for (int c = tid; c < RP; c += blockDim.x)
-      f.wv[c] = c < R ? clu_gather_sum(cl, mine, c, CL) : 0.0f;
+    for (int c = tid; c < RP; c += kCluThreads) f.wv[c] = c < R ? clu_slot_sum(f, par, c, CL) : 0.0f;
     par ^= 1;
     __syncthreads();
     rows_pass(true);
@@ -639,7 +715,7 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
   int q0, mloc;
   clu_rows(a.m, a.CL, rank, q0, mloc);
   CluSmem f;
-  clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, &f);
+  clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, a.CL, &f);
   const int tid = threadIdx.x;
   if (a.clear_pass >= 0)  // ordered before this step's lift adds by the fit's cluster barriers
     for (int q = tid; q < mloc; q += blockDim.x)
@@ -667,7 +743,7 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
   }
   __syncthreads();
   int par = 0;
-  clu_l1_fit<RP>(cl, f, mloc, a.R, a.rho, a.iters, a.CL, par);
+  clu_l1_fit<RP>(cl, f, mloc, a.R, a.rho, a.iters, a.CL, rank, par);
   // residual r (into x), lifted onto the sampled voxels; A^T r and ||r||^2
   float rr = 0.0f;
   for (int q = tid; q < mloc; q += blockDim.x) {
@@ -677,10 +753,9 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
     rr = fmaf(r, r, rr);
   }
   __syncthreads();
-  float* sl = f.slot + par * kSlot;
-  clu_AtX<RP>(f, mloc, a.R, f.x, sl);
-  clu_block_sum_to(rr, f, sl + a.R);
-  clu_sum(cl, f, par, a.R + 1, a.CL);  // the barrier also publishes the lift atomics
+  clu_AtX<RP>(f, mloc, a.R, f.x, f.stage);
+  clu_block_sum_to(rr, f, f.stage + a.R);
+  clu_sum(cl, f, par, a.R + 1, a.CL, rank);  // the barrier also publishes the lift atomics
   float* g2 = f.misc;                   // keep g2 and ||r||^2 before vec is reused
   if (tid == 0) f.misc[0] = f.vec[a.R];
   float* g2v = f.red;  // R values (red is free now)
@@ -689,8 +764,8 @@ __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluS
   float ll = 0.0f;
   for (int q = tid; q < mloc; q += blockDim.x) ll = fmaf(__ldcg(&a.lift[f.idx[q]]), f.x[q], ll);
   __syncthreads();
-  clu_block_sum_to(ll, f, f.slot + par * kSlot);
-  clu_sum(cl, f, par, 1, a.CL);
+  clu_block_sum_to(ll, f, f.stage);
+  clu_sum(cl, f, par, 1, a.CL, rank);
   cl.sync();  // no CTA leaves while another may still read its shared memory
   if (rank != 0) return;
   if (tid == 0) {
@@ -795,35 +870,62 @@ struct CluRecArgs {
   int iters;
   int64_t row_first, row_end;
   float* W;           // (row - row_first) x RP
+  uint32_t* status;   // device status word (a load that never completes: kErrTimeout)
 };
 
 template <int RP>
 __global__ void __launch_bounds__(kCluThreads, 1) recover_fit_cluster_kernel(CluRecArgs a) {
   extern __shared__ __align__(16) float smc[];
+  __shared__ __align__(8) unsigned long long load_bar;
+  __shared__ int abort_flag;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = int(cl.block_rank());
   const int64_t cid = blockIdx.x / a.CL, ncl = gridDim.x / a.CL;
   constexpr int RS = clu_rs(RP);
+  constexpr uint32_t kRowBytes = RP * sizeof(float);
   int q0, mloc;
   clu_rows(a.m, a.CL, rank, q0, mloc);
   CluSmem f;
-  clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, &f);
+  clu_carve(smc, (a.m + a.CL - 1) / a.CL, a.R, RP, 0, a.CL, &f);
   const int tid = threadIdx.x;
+  const uint32_t bar = smem_addr(&load_bar);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
   int par = 0;
+  uint32_t phase = 0;
+  bool have_idx = false;  // f.idx holds this relabelling's draws (from the previous prefetch)
   for (int64_t i = a.row_first + cid; i < a.row_end; i += ncl) {
-    const float* trow = a.Tt + (i - a.row_first) * a.m + q0;
-    for (int q = tid; q < mloc; q += blockDim.x) {
-      const uint32_t j = draw_index(a.k0, a.k1, TAG_REC, uint32_t(q0 + q), uint32_t(i), 0u, a.V);
-      f.b[q] = trow[q];
-      const float4* src = reinterpret_cast<const float4*>(a.U + int64_t(j) * RP);
-      float4* dst = reinterpret_cast<float4*>(f.A + q * RS);
-#pragma unroll
-      for (int c4 = 0; c4 < RP / 4; ++c4) dst[c4] = src[c4];
-    }
+    // this relabelling's rows of U, one bulk copy per row (each thread copies
+    // the rows whose draws it holds), completing on load_bar
+    if (!have_idx)
+      for (int q = tid; q < mloc; q += kCluThreads)
+        f.idx[q] = int32_t(draw_index(a.k0, a.k1, TAG_REC, uint32_t(q0 + q), uint32_t(i), 0u, a.V));
+    if (tid == 0) mbar_arrive_expect_tx(bar, uint32_t(mloc) * kRowBytes);
+    fence_proxy_async_smem();  // the last relabelling's reads of A precede the copies
     __syncthreads();
-    clu_l1_fit<RP>(cl, f, mloc, a.R, a.rho, a.iters, a.CL, par);
+    for (int q = tid; q < mloc; q += kCluThreads)
+      bulk_copy_g2s(smem_addr(f.A + q * RS), a.U + int64_t(f.idx[q]) * RP, kRowBytes, bar);
+    const float* trow = a.Tt + (i - a.row_first) * a.m + q0;
+    for (int q = tid; q < mloc; q += kCluThreads) f.b[q] = trow[q];
+    mbar_wait(bar, phase, a.status, &abort_flag);
+    phase ^= 1u;
+    __syncthreads();
+    // the next relabelling's rows of U go into L2 while this one is fitted
+    // (each thread keeps the draws of the rows it will copy)
+    have_idx = i + ncl < a.row_end;
+    if (have_idx)
+      for (int q = tid; q < mloc; q += kCluThreads) {
+        const uint32_t jn = draw_index(a.k0, a.k1, TAG_REC, uint32_t(q0 + q), uint32_t(i + ncl), 0u, a.V);
+        f.idx[q] = int32_t(jn);
+        prefetch_l2_bulk(a.U + int64_t(jn) * RP, kRowBytes);
+      }
+    clu_l1_fit<RP>(cl, f, mloc, a.R, a.rho, a.iters, a.CL, rank, par);
     if (rank == 0)
-      for (int c = tid; c < RP; c += blockDim.x)
+      for (int c = tid; c < RP; c += kCluThreads)
         a.W[(i - a.row_first) * RP + c] = c < a.R ? f.wv[c] : 0.0f;
     __syncthreads();
   }
@@ -1267,13 +1369,13 @@ int grid_n(int64_t work, int threads, int cap = 152 * 16) {
   return int(b);
 }
 
-constexpr size_t kCluSmemLimit = 227 * 1024;
+constexpr size_t kCluSmemLimit = 227 * 1024 - 64;  // the kernels add a few static bytes
 
 // Smallest cluster size (from `first`, doubling up to 16) whose per-CTA share
 // of the sampled rows fits in shared memory; 0 if none does.
 int choose_cluster(int m, int R, int RP, int n_pad, int first, size_t* smem) {
   for (int CL = first; CL <= 16; CL *= 2) {
-    const size_t b = clu_carve(nullptr, (m + CL - 1) / CL, R, RP, n_pad, nullptr);
+    const size_t b = clu_carve(nullptr, (m + CL - 1) / CL, R, RP, n_pad, CL, nullptr);
     if (b <= kCluSmemLimit) {
       *smem = b;
       return CL;
@@ -1907,6 +2009,7 @@ pt_status rapid_recover_impl(pt_ctx* ctx, const int32_t* perms, int64_t P, int64
   a.row_first = first_row;
   a.row_end = P;
   a.W = Wb.as<float>();
+  a.status = ctx->status.as<uint32_t>();
   cudaError_t lerr = cudaSuccess;
   with_rp(pl.RP, [&](auto rpc) {
     constexpr int RPc = decltype(rpc)::value;
