@@ -91,6 +91,38 @@ def test_recovery_large_rank_given_basis(cuda_lib, n, r, eta):
     ctx.close()
 
 
+@pytest.mark.parametrize("n,r,eta", [(30, 1, 0.05), (30, 3, 0.05), (40, 5, 0.1), (80, 50, 0.28)])
+def test_recovery_small_and_odd_ranks_given_basis(cuda_lib, n, r, eta):
+    """Ranks 1, 3 and 5 (a single or partial 4 x 4 pivot block, padded
+    columns in the fit's vector accesses) and rank 50 with ~2,500 samples per
+    relabelling (the fit's rows span a 4-CTA cluster), each with a random
+    orthonormal basis, against the oracle's weights and maxima."""
+    B = cuda_lib
+    n1, P, ell = n // 2, 200, 40
+    X = smooth_field(n, n1, seed=17)
+    X = X[:, : X.shape[1] - 11]
+    V = X.shape[1]
+    perms = synth.perms_pcg32(n, P, seed=8)
+    U = np.linalg.qr(np.random.default_rng(r).standard_normal((V, r)))[0]
+    sigma, mu = 0.7, -0.2
+    o = R.RapidOpts(seed=21)
+    m = int(np.ceil(eta * V))
+    rows = np.arange(ell, P)
+    want, w_want = R.rapid_recover(X, n1, perms, rows, U, sigma, mu, m, o, return_w=True)
+    ctx = gpu_ctx(B, X, n1)
+    got = torch.empty(P - ell, dtype=torch.float32, device="cuda")
+    W = torch.empty((P - ell, r), dtype=torch.float32, device="cuda")
+    B.pt_rapid_recover(ctx, torch.as_tensor(perms).cuda(), ell,
+                       torch.as_tensor(U.astype(np.float32)).cuda(), r, eta, sigma, mu,
+                       B.rapid_opts(seed=21), got, W)
+    B.pt_sync(ctx)
+    W = W.cpu().numpy().astype(np.float64)
+    wrel = np.linalg.norm(W - w_want, axis=1) / np.linalg.norm(w_want, axis=1)
+    assert np.max(wrel) < 1e-3, np.max(wrel)
+    np.testing.assert_allclose(got.cpu().numpy().astype(np.float64), want, rtol=2e-4, atol=2e-4)
+    ctx.close()
+
+
 def test_recovery_with_u_updates_matches_oracle(cuda_lib):
     """U updates during recovery (rec_step = 1): the GPU takes the training step
     after each recovery relabelling, in row order, from the oracle's trained U.
