@@ -679,34 +679,103 @@ struct CluStepArgs {
   float* gu_dst;              // ... updated into this buffer (all V rows)
   const float* gu_lift;       // that step's lift and coefficients
   const float* gu_coef;
+  int gu_chunk;               // rows of U per shared-memory buffer of the update
+  uint32_t* status;           // device status word (an update copy that never completes)
 };
 
-// U_next = U + coef w^T/||w|| over rows j = first.. of the grid (geodesic_row).
+// Bulk copy of `bytes` from this CTA's shared src to global dst (a bulk group
+// of the issuing thread; src, dst and bytes multiples of 16).
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until this thread's bulk groups have read their shared-memory source
+// (kReadOnly) or have completed.
+template <bool kReadOnly>
+__device__ __forceinline__ void bulk_wait_all() {
+  if constexpr (kReadOnly)
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  else
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// U_next = U + coef w^T/||w|| over all V rows (geodesic_row), by CTAs
+// first_cta.. of the grid. Chunks of gu_chunk rows of U come into shared
+// memory by bulk copies (one per row, two buffers: the CTA's next chunk is in
+// flight while it updates this one), thread q updates row q of the chunk in
+// place, and the row goes back out by a bulk copy. Lane-per-row global loads
+// of rows 4 RP bytes apart ran at ~12 GB/s per SM.
 template <int RP>
-__device__ __forceinline__ void geodesic_rows(const CluStepArgs& a, int first_cta, float* su) {
-  for (int e = threadIdx.x; e < 3 * RP + 2; e += blockDim.x) su[e] = a.gu_coef[e];
+__device__ __forceinline__ void geodesic_rows(const CluStepArgs& a, int first_cta, float* smc,
+                                              uint64_t* gbar, int* abort_flag) {
+  constexpr int RS = clu_rs(RP);
+  constexpr uint32_t kRowBytes = RP * sizeof(float);
+  const int tid = threadIdx.x;
+  const int CH = a.gu_chunk;
+  float* su = smc;  // w, w/||w||, g2, alpha, beta
+  float* const buf0 = smc + (3 * RP + 2 + 3) / 4 * 4;  // buffer b at buf0 + b CH RS
+  const uint32_t bar0 = smem_addr(&gbar[0]);           // barrier b at bar0 + 8 b
+  for (int e = tid; e < 3 * RP + 2; e += kCluThreads) su[e] = a.gu_coef[e];
+  if (tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8u, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
   __syncthreads();
   const float alpha = su[3 * RP], beta = su[3 * RP + 1];
-  const int64_t stride = int64_t(gridDim.x - first_cta) * blockDim.x;
-  for (int64_t j = int64_t(blockIdx.x - first_cta) * blockDim.x + threadIdx.x; j < a.V;
-       j += stride) {
-    const float4* u4 = reinterpret_cast<const float4*>(a.gu_src + j * RP);
-    float4 x[RP / 4];
+  const int64_t V = a.V, nchunks = (V + CH - 1) / CH;
+  const int64_t nctas = int64_t(gridDim.x) - first_cta, c0 = int64_t(blockIdx.x) - first_cta;
+  auto load = [&](int64_t c, int b) {  // thread 0 arms the barrier; row q's thread copies it
+    const int64_t r0 = c * CH;
+    const int rows = int(V - r0 < CH ? V - r0 : CH);
+    const uint32_t bar = bar0 + 8u * uint32_t(b);
+    if (tid == 0) mbar_arrive_expect_tx(bar, uint32_t(rows) * kRowBytes);
+    if (tid < rows)
+      bulk_copy_g2s(smem_addr(buf0 + (size_t(b) * CH + tid) * RS), a.gu_src + (r0 + tid) * RP,
+                    kRowBytes, bar);
+  };
+  if (c0 < nchunks) load(c0, 0);
+  if (c0 + nctas < nchunks) load(c0 + nctas, 1);
+  uint32_t phases = 0u;  // bit b: parity of buffer b's next phase
+  int k = 0;
+  for (int64_t c = c0; c < nchunks; c += nctas, ++k) {
+    const int b = k & 1;
+    const int64_t r0 = c * CH;
+    const int rows = int(V - r0 < CH ? V - r0 : CH);
+    mbar_wait(bar0 + 8u * uint32_t(b), (phases >> b) & 1u, a.status, abort_flag);
+    phases ^= 1u << b;
+    if (tid < rows) {
+      float4* row = reinterpret_cast<float4*>(buf0 + (size_t(b) * CH + tid) * RS);
+      float4 x[RP / 4];
 #pragma unroll
-    for (int c4 = 0; c4 < RP / 4; ++c4) x[c4] = __ldcs(u4 + c4);
-    geodesic_row<RP>(x, __ldcs(a.gu_lift + j), su, su + RP, su + 2 * RP, alpha, beta);
-    float4* o4 = reinterpret_cast<float4*>(a.gu_dst + j * RP);
+      for (int c4 = 0; c4 < RP / 4; ++c4) x[c4] = row[c4];
+      geodesic_row<RP>(x, __ldcs(a.gu_lift + r0 + tid), su, su + RP, su + 2 * RP, alpha, beta);
 #pragma unroll
-    for (int c4 = 0; c4 < RP / 4; ++c4) o4[c4] = x[c4];
+      for (int c4 = 0; c4 < RP / 4; ++c4) row[c4] = x[c4];
+      fence_proxy_async_smem();  // the row's writes precede its bulk copy out
+      bulk_copy_s2g(a.gu_dst + (r0 + tid) * RP, smem_addr(row), kRowBytes);
+    }
+    if (c + 2 * nctas < nchunks) {  // refill this buffer once every row copy has read it
+      bulk_wait_all<true>();
+      fence_proxy_async_smem();
+      __syncthreads();
+      load(c + 2 * nctas, b);
+    }
   }
+  bulk_wait_all<false>();
 }
 
 template <int RP>
 __global__ void __launch_bounds__(kCluThreads, 1) train_step_cluster_kernel(CluStepArgs a) {
   extern __shared__ __align__(16) float smc[];
+  __shared__ __align__(8) uint64_t gbar[2];
+  __shared__ int gabort;
   const int first = a.fit ? a.CL : 0;  // CTAs [0, CL) form cluster 0
   if (int(blockIdx.x) >= first) {
-    if (a.gu_src) geodesic_rows<RP>(a, first, smc);
+    if (a.gu_src) geodesic_rows<RP>(a, first, smc, gbar, &gabort);
     return;
   }
   cg::cluster_group cl = cg::this_cluster();
@@ -1371,6 +1440,12 @@ int grid_n(int64_t work, int threads, int cap = 152 * 16) {
 
 constexpr size_t kCluSmemLimit = 227 * 1024 - 64;  // the kernels add a few static bytes
 
+// Sequential fits (training steps, recovery with U updates) take 16-CTA
+// clusters: one fit at a time is latency-bound, and fewer rows per CTA win over
+// the dearer exchange (at r = 50, m = 1750 an ADMM iteration took ~5.6k cycles
+// on 16 CTAs, ~3.7k of them the exchange, and about twice that on 4 CTAs).
+constexpr int kTrainMinCluster = 16;
+
 // Smallest cluster size (from `first`, doubling up to 16) whose per-CTA share
 // of the sampled rows fits in shared memory; 0 if none does.
 int choose_cluster(int m, int R, int RP, int n_pad, int first, size_t* smem) {
@@ -1382,6 +1457,18 @@ int choose_cluster(int m, int R, int RP, int n_pad, int first, size_t* smem) {
     }
   }
   return 0;
+}
+
+// Shared memory of the training step's whole-U update (geodesic_rows): the
+// coefficients and two buffers of *chunk rows (256, fewer when that does not
+// fit).
+size_t update_smem(int RP, int* chunk) {
+  const size_t coef = size_t(3 * RP + 2 + 3) / 4 * 4 * sizeof(float);
+  const size_t row = size_t(clu_rs(RP)) * sizeof(float);
+  int ch = 256;
+  while (ch > 32 && coef + 2 * size_t(ch) * row > kCluSmemLimit - 4096) ch -= 32;
+  *chunk = ch;
+  return coef + 2 * size_t(ch) * row;
 }
 
 // Launch configuration of `kernel` as clusters of CL CTAs of kCluThreads threads.
@@ -1656,17 +1743,21 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
   //    into the other buffer. lift and the coefficients alternate by step
   //    parity; a step clears the lift entries of the step two before it.
   size_t csm = 0;
-  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 16, &csm);
+  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, kTrainMinCluster, &csm);
   if (CL == 0) {
     set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
     return PT_ERR_UNSUPPORTED;
   }
+  int gu_chunk = 0;
+  csm = std::max(csm, update_smem(pl.RP, &gu_chunk));
   float* ua = U;               // latest complete U (U_{t-1} while an update is pending)
   float* ub = Ub2.as<float>();
   float* liftb[2] = {lift.as<float>(), lift.as<float>() + V};
   float* updb[2] = {upd.as<float>(), upd.as<float>() + updw};
   PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * 2 * V, st));
   CluStepArgs sa;
+  sa.gu_chunk = gu_chunk;
+  sa.status = ctx->status.as<uint32_t>();
   sa.samp = nullptr;
   sa.tag = TAG_TRAIN;
   sa.V = uint32_t(V);
@@ -1849,11 +1940,13 @@ pt_status recover_with_updates(pt_ctx* ctx, const RapidPlan& pl, const pt_rapid_
       !upd.ensure(sizeof(float) * 2 * updw))
     return nomem_r(ctx, "RapidPT recovery updates");
   size_t csm = 0;
-  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, 16, &csm);
+  const int CL = choose_cluster(pl.m, pl.R, pl.RP, 0, kTrainMinCluster, &csm);
   if (CL == 0) {
     set_error(ctx, "RapidPT: the sampled rows do not fit a 16-CTA cluster");
     return PT_ERR_UNSUPPORTED;
   }
+  int gu_chunk = 0;
+  csm = std::max(csm, update_smem(pl.RP, &gu_chunk));
   PT_CUDA_TRY(ctx, cudaMemsetAsync(lift.p, 0, sizeof(float) * 2 * V, st));
   PT_CUDA_TRY(ctx, cudaMemsetAsync(Wrows, 0, sizeof(float) * size_t(rows) * pl.RP, st));
   PT_CUDA_TRY(ctx, cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * rows, st));
@@ -1862,6 +1955,8 @@ pt_status recover_with_updates(pt_ctx* ctx, const RapidPlan& pl, const pt_rapid_
   float* liftb[2] = {lift.as<float>(), lift.as<float>() + V};
   float* updb[2] = {upd.as<float>(), upd.as<float>() + updw};
   CluStepArgs sa;
+  sa.gu_chunk = gu_chunk;
+  sa.status = ctx->status.as<uint32_t>();
   sa.Trow = nullptr;
   sa.tag = TAG_REC;
   sa.V = uint32_t(V);
