@@ -1129,20 +1129,51 @@ __global__ void __launch_bounds__(1024) qr_factor_kernel(const double* __restric
 }
 
 // U[j] <- U[j] R^-1 (row times upper-triangular matrix).
-__global__ void qr_apply_kernel(float* __restrict__ U, int64_t V, int R, int RP,
-                                const float* __restrict__ Rinv) {
-  extern __shared__ float ri[];
-  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) ri[e] = Rinv[e];
-  __syncthreads();
-  float row[kMaxRank];
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < V;
-       j += int64_t(gridDim.x) * blockDim.x) {
-    float* u = U + j * RP;
-    for (int c = 0; c < R; ++c) row[c] = u[c];
-    for (int c = 0; c < R; ++c) {
-      float t = 0.0f;
-      for (int k = 0; k <= c; ++k) t = fmaf(row[k], ri[k * RP + c], t);
-      u[c] = t;
+// U <- U R^-1 (R^-1 upper triangular, zero below the diagonal, RP x RP). A CTA
+// takes kQrRows rows at a time: they come into shared memory along the rows
+// (coalesced) and are stored column-major, thread q forms row q's outputs four
+// columns at a time from the highest down, overwriting inputs no lower column
+// needs, and the rows go back out along the rows. The sums run over k = 0.. in
+// increasing order as in a plain row-times-matrix product (the terms past the
+// diagonal are exact zeros).
+constexpr int kQrRows = 128;
+__global__ void __launch_bounds__(kQrRows) qr_apply_kernel(float* __restrict__ U, int64_t V, int R,
+                                                           int RP, const float* __restrict__ Rinv) {
+  extern __shared__ __align__(16) float qsm[];
+  float* ri = qsm;                        // RP x RP
+  float* tile = qsm + size_t(RP) * RP;    // [RP][kQrRows]: column k of this step's rows
+  for (int e = threadIdx.x; e < RP * RP; e += kQrRows) ri[e] = Rinv[e];
+  const int q = threadIdx.x;
+  for (int64_t j0 = int64_t(blockIdx.x) * kQrRows; j0 < V; j0 += int64_t(gridDim.x) * kQrRows) {
+    const int rows = int(V - j0 < kQrRows ? V - j0 : kQrRows);
+    __syncthreads();  // R^-1 is in place; the last step's tile has been written out
+    for (int e = threadIdx.x; e < rows * RP; e += kQrRows) {
+      const int qq = e / RP, c = e - qq * RP;
+      tile[c * kQrRows + qq] = U[(j0 + qq) * RP + c];
+    }
+    __syncthreads();
+    if (q < rows) {
+      for (int c = (R - 1) / 4 * 4; c >= 0; c -= 4) {
+        const int kend = c + 3 < R ? c + 3 : R - 1;
+        float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+        for (int k = 0; k <= kend; ++k) {
+          const float x = tile[k * kQrRows + q];
+          const float4 rv = *reinterpret_cast<const float4*>(ri + k * RP + c);
+          t0 = fmaf(x, rv.x, t0);
+          t1 = fmaf(x, rv.y, t1);
+          t2 = fmaf(x, rv.z, t2);
+          t3 = fmaf(x, rv.w, t3);
+        }
+        tile[c * kQrRows + q] = t0;
+        if (c + 1 < R) tile[(c + 1) * kQrRows + q] = t1;
+        if (c + 2 < R) tile[(c + 2) * kQrRows + q] = t2;
+        if (c + 3 < R) tile[(c + 3) * kQrRows + q] = t3;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * RP; e += kQrRows) {
+      const int qq = e / RP, c = e - qq * RP;
+      if (c < R) U[(j0 + qq) * RP + c] = tile[c * kQrRows + qq];
     }
   }
 }
@@ -1150,46 +1181,58 @@ __global__ void qr_apply_kernel(float* __restrict__ U, int64_t V, int R, int RP,
 // ---------------------------------------------------------------------------
 // W_ex = U^T T_ex^T (split over voxels, FP64 reduction of the splits)
 // ---------------------------------------------------------------------------
+// part[split][i][c] = sum over the split's voxels j of T_ex[i][j] U[j][c] for one
+// 64 x 64 tile of (training column i, basis column c) per CTA: 32-voxel slabs of
+// T_ex (read along voxels, stored voxel-major) and of U in shared memory, a 4 x 4
+// register tile per thread (16 FMAs per two 16-byte shared loads).
+constexpr int kWexTile = 64;
 __global__ void __launch_bounds__(256) wex_partial_kernel(const float* __restrict__ U,
                                                           const float* __restrict__ Tex,
                                                           int64_t V, int ell, int RP,
                                                           int64_t per_split,
                                                           float* __restrict__ part) {
-  __shared__ float Ts[32][33];
-  __shared__ float Us[32][kMaxRank];
-  const int i0 = blockIdx.x * 32;
+  __shared__ __align__(16) float Ts[32][kWexTile + 4];  // [voxel][training column]
+  __shared__ __align__(16) float Us[32][kWexTile + 4];  // [voxel][basis column]
+  const int i0 = blockIdx.x * kWexTile, c0 = blockIdx.z * kWexTile;
   const int64_t j0 = blockIdx.y * per_split, j1 = min(V, j0 + per_split);
-  const int ti = threadIdx.x >> 3, cg = threadIdx.x & 7;  // row i0+ti, columns cg + 8k
-  float acc[kMaxRank / 8];
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  float acc[4][4];
 #pragma unroll
-  for (int k = 0; k < kMaxRank / 8; ++k) acc[k] = 0.0f;
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[q][p] = 0.0f;
   for (int64_t jb = j0; jb < j1; jb += 32) {
-    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    for (int e = tid; e < kWexTile * 32; e += 256) {
       const int r = e >> 5, jj = e & 31;
       const int64_t j = jb + jj;
-      Ts[r][jj] = (i0 + r < ell && j < j1) ? Tex[int64_t(i0 + r) * V + j] : 0.0f;
+      Ts[jj][r] = (i0 + r < ell && j < j1) ? __ldcs(&Tex[int64_t(i0 + r) * V + j]) : 0.0f;
     }
-    for (int e = threadIdx.x; e < 32 * RP; e += blockDim.x) {
-      const int jj = e / RP, c = e - jj * RP;
+    for (int e = tid; e < 32 * kWexTile; e += 256) {
+      const int jj = e >> 6, c = e & (kWexTile - 1);
       const int64_t j = jb + jj;
-      Us[jj][c] = j < j1 ? U[j * RP + c] : 0.0f;
+      Us[jj][c] = (c0 + c < RP && j < j1) ? U[j * RP + c0 + c] : 0.0f;
     }
     __syncthreads();
+#pragma unroll 8
     for (int jj = 0; jj < 32; ++jj) {
-      const float t = Ts[ti][jj];
+      const float4 t = *reinterpret_cast<const float4*>(&Ts[jj][4 * tr]);
+      const float4 u = *reinterpret_cast<const float4*>(&Us[jj][4 * tc]);
+      const float tv[4] = {t.x, t.y, t.z, t.w}, uv[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-      for (int k = 0; k < kMaxRank / 8; ++k) {
-        const int c = cg + 8 * k;
-        if (c < RP) acc[k] = fmaf(t, Us[jj][c], acc[k]);
-      }
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc[q][p] = fmaf(tv[q], uv[p], acc[q][p]);
     }
     __syncthreads();
   }
-  if (i0 + ti < ell) {
 #pragma unroll
-    for (int k = 0; k < kMaxRank / 8; ++k) {
-      const int c = cg + 8 * k;
-      if (c < RP) part[(int64_t(blockIdx.y) * ell + i0 + ti) * RP + c] = acc[k];
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + 4 * tr + q;
+    if (i >= ell) continue;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int c = c0 + 4 * tc + p;
+      if (c < RP) part[(int64_t(blockIdx.y) * ell + i) * RP + c] = acc[q][p];
     }
   }
 }
@@ -1596,9 +1639,15 @@ pt_status qr_inplace(pt_ctx* ctx, float* U, const RapidPlan& pl, Buf& part, Buf&
   qr_factor_kernel<<<1, 1024, fsm, ctx->stream>>>(part.as<double>(), nparts, pl.R, pl.RP,
                                                   rinv.as<float>());
   PT_LAUNCH_CHECK(ctx);
-  qr_apply_kernel<<<grid_n(pl.V, 256), 256, pl.RP * pl.RP * sizeof(float), ctx->stream>>>(
-      U, pl.V, pl.R, pl.RP, rinv.as<float>());
-  PT_LAUNCH_CHECK(ctx);
+  {
+    const size_t asm_bytes = sizeof(float) * size_t(pl.RP) * (pl.RP + kQrRows);
+    PT_CUDA_TRY(ctx, cudaFuncSetAttribute(qr_apply_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(asm_bytes)));
+    qr_apply_kernel<<<grid_n(pl.V, kQrRows, 152 * 2), kQrRows, asm_bytes, ctx->stream>>>(
+        U, pl.V, pl.R, pl.RP, rinv.as<float>());
+    PT_LAUNCH_CHECK(ctx);
+  }
   return PT_OK;
 }
 
@@ -1839,13 +1888,14 @@ pt_status rapid_train_impl(pt_ctx* ctx, const int32_t* perms, int32_t n_train, i
 
   // 4. W_ex = U^T T_ex (rows of Wex = weights of training columns)
   {
-    const int itiles = (ell + 31) / 32;
-    int nsplit = std::max(1, int(152 * 4 / itiles));
+    const int itiles = (ell + kWexTile - 1) / kWexTile;
+    const int ctiles = (pl.RP + kWexTile - 1) / kWexTile;
+    int nsplit = std::max(1, 152 * 3 / (itiles * ctiles));  // about three CTAs per SM
     nsplit = int(std::min<int64_t>(nsplit, (V + 1023) / 1024));
     const int64_t per = (V + nsplit - 1) / nsplit;
     if (!part.ensure(std::max(part.bytes, sizeof(float) * size_t(nsplit) * ell * pl.RP)))
       return nomem_r(ctx, "W_ex");
-    const dim3 grid{unsigned(itiles), unsigned(nsplit), 1u};
+    const dim3 grid{unsigned(itiles), unsigned(nsplit), unsigned(ctiles)};
     wex_partial_kernel<<<grid, 256, 0, st>>>(U, Tex.as<float>(), V, ell, pl.RP, per,
                                             part.as<float>());
     PT_LAUNCH_CHECK(ctx);
