@@ -740,13 +740,18 @@ __device__ __forceinline__ void geodesic_rows(const CluStepArgs& a, int first_ct
   if (c0 < nchunks) load(c0, 0);
   if (c0 + nctas < nchunks) load(c0 + nctas, 1);
   uint32_t phases = 0u;  // bit b: parity of buffer b's next phase
+  uint32_t inflight = (c0 < nchunks ? 1u : 0u) | (c0 + nctas < nchunks ? 2u : 0u);  // bit b: buffer b loading
+  bool stuck = false;  // a wait expired: no further loads, the rest is skipped
   int k = 0;
-  for (int64_t c = c0; c < nchunks; c += nctas, ++k) {
+  for (int64_t c = c0; c < nchunks && !stuck; c += nctas, ++k) {
     const int b = k & 1;
     const int64_t r0 = c * CH;
     const int rows = int(V - r0 < CH ? V - r0 : CH);
-    mbar_wait(bar0 + 8u * uint32_t(b), (phases >> b) & 1u, a.status, abort_flag);
+    stuck = __syncthreads_or(!mbar_wait(bar0 + 8u * uint32_t(b), (phases >> b) & 1u, a.status,
+                                        abort_flag)) != 0;
+    if (stuck) break;
     phases ^= 1u << b;
+    inflight &= ~(1u << b);
     if (tid < rows) {
       float4* row = reinterpret_cast<float4*>(buf0 + (size_t(b) * CH + tid) * RS);
       float4 x[RP / 4];
@@ -763,8 +768,15 @@ __device__ __forceinline__ void geodesic_rows(const CluStepArgs& a, int first_ct
       fence_proxy_async_smem();
       __syncthreads();
       load(c + 2 * nctas, b);
+      inflight |= 1u << b;
     }
   }
+  // loads still in flight after an expired wait: one more bounded wait each
+  // before the CTA (and its shared memory) goes away
+  for (int b = 0; b < 2; ++b)
+    if (stuck && (inflight >> b & 1u))
+      mbar_wait(bar0 + 8u * uint32_t(b), (phases >> b) & 1u, a.status, abort_flag, kWaitLimitNs,
+                false);
   bulk_wait_all<false>();
 }
 
@@ -967,22 +979,30 @@ __global__ void __launch_bounds__(kCluThreads, 1) recover_fit_cluster_kernel(Clu
   int par = 0;
   uint32_t phase = 0;
   bool have_idx = false;  // f.idx holds this relabelling's draws (from the previous prefetch)
+  bool stuck = false;     // a load whose wait expired may still be in flight (phase `phase`)
   for (int64_t i = a.row_first + cid; i < a.row_end; i += ncl) {
     // this relabelling's rows of U, one bulk copy per row (each thread copies
-    // the rows whose draws it holds), completing on load_bar
+    // the rows whose draws it holds), completing on load_bar; after an expired
+    // wait no further copies are issued (the fits then run on stale rows and
+    // the status word reports the timeout)
     if (!have_idx)
       for (int q = tid; q < mloc; q += kCluThreads)
         f.idx[q] = int32_t(draw_index(a.k0, a.k1, TAG_REC, uint32_t(q0 + q), uint32_t(i), 0u, a.V));
-    if (tid == 0) mbar_arrive_expect_tx(bar, uint32_t(mloc) * kRowBytes);
-    fence_proxy_async_smem();  // the last relabelling's reads of A precede the copies
-    __syncthreads();
-    for (int q = tid; q < mloc; q += kCluThreads)
-      bulk_copy_g2s(smem_addr(f.A + q * RS), a.U + int64_t(f.idx[q]) * RP, kRowBytes, bar);
+    if (!stuck) {
+      if (tid == 0) mbar_arrive_expect_tx(bar, uint32_t(mloc) * kRowBytes);
+      fence_proxy_async_smem();  // the last relabelling's reads of A precede the copies
+      __syncthreads();
+      for (int q = tid; q < mloc; q += kCluThreads)
+        bulk_copy_g2s(smem_addr(f.A + q * RS), a.U + int64_t(f.idx[q]) * RP, kRowBytes, bar);
+    }
     const float* trow = a.Tt + (i - a.row_first) * a.m + q0;
     for (int q = tid; q < mloc; q += kCluThreads) f.b[q] = trow[q];
-    mbar_wait(bar, phase, a.status, &abort_flag);
-    phase ^= 1u;
-    __syncthreads();
+    if (!stuck) {  // a wait that expired in any thread stops the loads for the whole CTA
+      stuck = __syncthreads_or(!mbar_wait(bar, phase, a.status, &abort_flag)) != 0;
+      if (!stuck) phase ^= 1u;
+    } else {
+      __syncthreads();
+    }
     // the next relabelling's rows of U go into L2 while this one is fitted
     // (each thread keeps the draws of the rows it will copy)
     have_idx = i + ncl < a.row_end;
@@ -998,6 +1018,9 @@ __global__ void __launch_bounds__(kCluThreads, 1) recover_fit_cluster_kernel(Clu
         a.W[(i - a.row_first) * RP + c] = c < a.R ? f.wv[c] : 0.0f;
     __syncthreads();
   }
+  // copies of a load whose wait expired: one more bounded wait before the CTA
+  // (and its shared memory) goes away
+  if (stuck) mbar_wait(bar, phase, a.status, &abort_flag, kWaitLimitNs, false);
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
