@@ -217,7 +217,11 @@ void pt_rapid_opts_default(pt_rapid_opts* o);
  *   perms, P   : device int32 P x n relabellings; rows 0..n_train-1 train.
  *   rank       : r, 1 <= r <= min(n, 128).
  *   sample_rate: eta in (0, 1]; m = ceil(eta * v_valid) >= r voxels are drawn
- *                (i.i.d. uniform, Alg. 2 "UNIF[1, v]") per relabelling.
+ *                (i.i.d. uniform, Alg. 2 "UNIF[1, v]") per relabelling. The m
+ *                sampled rows of U (4 m r bytes) and one r x r matrix per CTA must
+ *                fit the shared memory of a 16-CTA cluster: m <= 13,280 at r = 50,
+ *                4,480 at r = 100, 2,144 at r = 128; larger requests return
+ *                PT_ERR_UNSUPPORTED before any work.
  *   n_train    : l, 1 <= l < P.
  *   maxnull    : device float32[P]; rows < l: exact maxima of the training rows
  *                (statistic recomputed in FP64); rows >= l: max_j (U w + s)_j + mu.

@@ -1637,6 +1637,12 @@ pt_status check_rapid_args(pt_ctx* ctx, int32_t rank, double sample_rate, const 
     set_error(ctx, "RapidPT: ceil(sample_rate * v) must be at least the rank");
     return PT_ERR_INVALID;
   }
+  size_t fit_smem = 0;
+  if (choose_cluster(pl.m, pl.R, pl.RP, 0, 16, &fit_smem) == 0) {
+    set_error(ctx, "RapidPT: the m sampled rows of a relabelling do not fit the shared memory "
+                   "of a 16-CTA cluster (lower sample_rate or rank)");
+    return PT_ERR_UNSUPPORTED;
+  }
   pl.k0 = uint32_t(o.seed & 0xffffffffull);
   pl.k1 = uint32_t(o.seed >> 32);
   return PT_OK;

@@ -268,6 +268,23 @@ def test_rapid_rank100_training_runs_exact_rows(cuda_lib):
     ctx.close()
 
 
+def test_rapid_rejects_samples_beyond_a_cluster(cuda_lib):
+    """Rank 128 with more sampled rows than a 16-CTA cluster holds (m > 2,144):
+    PT_ERR_UNSUPPORTED before any work, and the context still computes."""
+    B = cuda_lib
+    n, n1 = 130, 65
+    X = synth.gaussian_mean_shift(n, 5000, seed=4)
+    perms = torch.as_tensor(synth.perms_pcg32(n, 40, seed=5)).cuda()
+    ctx = gpu_ctx(B, X, n1)
+    mx = torch.empty(40, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.PtError):
+        B.pt_maxnull_rapid(ctx, perms, 128, 0.5, 20, B.rapid_opts(), mx)
+    B.pt_maxnull_rapid(ctx, perms, 128, 0.4, 20, B.rapid_opts(), mx)  # m = 2,000 fits
+    B.pt_sync(ctx)
+    assert torch.isfinite(mx).all()
+    ctx.close()
+
+
 def test_rapid_rejects_bad_arguments(cuda_lib):
     B = cuda_lib
     n, n1 = 20, 10
