@@ -1152,51 +1152,20 @@ __global__ void __launch_bounds__(1024) qr_factor_kernel(const double* __restric
 }
 
 // U[j] <- U[j] R^-1 (row times upper-triangular matrix).
-// U <- U R^-1 (R^-1 upper triangular, zero below the diagonal, RP x RP). A CTA
-// takes kQrRows rows at a time: they come into shared memory along the rows
-// (coalesced) and are stored column-major, thread q forms row q's outputs four
-// columns at a time from the highest down, overwriting inputs no lower column
-// needs, and the rows go back out along the rows. The sums run over k = 0.. in
-// increasing order as in a plain row-times-matrix product (the terms past the
-// diagonal are exact zeros).
-constexpr int kQrRows = 128;
-__global__ void __launch_bounds__(kQrRows) qr_apply_kernel(float* __restrict__ U, int64_t V, int R,
-                                                           int RP, const float* __restrict__ Rinv) {
-  extern __shared__ __align__(16) float qsm[];
-  float* ri = qsm;                        // RP x RP
-  float* tile = qsm + size_t(RP) * RP;    // [RP][kQrRows]: column k of this step's rows
-  for (int e = threadIdx.x; e < RP * RP; e += kQrRows) ri[e] = Rinv[e];
-  const int q = threadIdx.x;
-  for (int64_t j0 = int64_t(blockIdx.x) * kQrRows; j0 < V; j0 += int64_t(gridDim.x) * kQrRows) {
-    const int rows = int(V - j0 < kQrRows ? V - j0 : kQrRows);
-    __syncthreads();  // R^-1 is in place; the last step's tile has been written out
-    for (int e = threadIdx.x; e < rows * RP; e += kQrRows) {
-      const int qq = e / RP, c = e - qq * RP;
-      tile[c * kQrRows + qq] = U[(j0 + qq) * RP + c];
-    }
-    __syncthreads();
-    if (q < rows) {
-      for (int c = (R - 1) / 4 * 4; c >= 0; c -= 4) {
-        const int kend = c + 3 < R ? c + 3 : R - 1;
-        float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
-        for (int k = 0; k <= kend; ++k) {
-          const float x = tile[k * kQrRows + q];
-          const float4 rv = *reinterpret_cast<const float4*>(ri + k * RP + c);
-          t0 = fmaf(x, rv.x, t0);
-          t1 = fmaf(x, rv.y, t1);
-          t2 = fmaf(x, rv.z, t2);
-          t3 = fmaf(x, rv.w, t3);
-        }
-        tile[c * kQrRows + q] = t0;
-        if (c + 1 < R) tile[(c + 1) * kQrRows + q] = t1;
-        if (c + 2 < R) tile[(c + 2) * kQrRows + q] = t2;
-        if (c + 3 < R) tile[(c + 3) * kQrRows + q] = t3;
-      }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < rows * RP; e += kQrRows) {
-      const int qq = e / RP, c = e - qq * RP;
-      if (c < R) U[(j0 + qq) * RP + c] = tile[c * kQrRows + qq];
+__global__ void qr_apply_kernel(float* __restrict__ U, int64_t V, int R, int RP,
+                                const float* __restrict__ Rinv) {
+  extern __shared__ float ri[];
+  for (int e = threadIdx.x; e < RP * RP; e += blockDim.x) ri[e] = Rinv[e];
+  __syncthreads();
+  float row[kMaxRank];
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < V;
+       j += int64_t(gridDim.x) * blockDim.x) {
+    float* u = U + j * RP;
+    for (int c = 0; c < R; ++c) row[c] = u[c];
+    for (int c = 0; c < R; ++c) {
+      float t = 0.0f;
+      for (int k = 0; k <= c; ++k) t = fmaf(row[k], ri[k * RP + c], t);
+      u[c] = t;
     }
   }
 }
@@ -1669,12 +1638,13 @@ pt_status qr_inplace(pt_ctx* ctx, float* U, const RapidPlan& pl, Buf& part, Buf&
                                                   rinv.as<float>());
   PT_LAUNCH_CHECK(ctx);
   {
-    const size_t asm_bytes = sizeof(float) * size_t(pl.RP) * (pl.RP + kQrRows);
+    // R^-1 in shared memory: 64 KB at RP = 128, above the 48 KB default
+    const size_t asm_bytes = sizeof(float) * size_t(pl.RP) * pl.RP;
     PT_CUDA_TRY(ctx, cudaFuncSetAttribute(qr_apply_kernel,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(asm_bytes)));
-    qr_apply_kernel<<<grid_n(pl.V, kQrRows, 152 * 2), kQrRows, asm_bytes, ctx->stream>>>(
-        U, pl.V, pl.R, pl.RP, rinv.as<float>());
+    qr_apply_kernel<<<grid_n(pl.V, 256), 256, asm_bytes, ctx->stream>>>(U, pl.V, pl.R, pl.RP,
+                                                                      rinv.as<float>());
     PT_LAUNCH_CHECK(ctx);
   }
   return PT_OK;

@@ -1,7 +1,7 @@
 """Host-side check of the cluster l1 fit's shared-memory carve-up and index
 arithmetic (no GPU), restated from the kernels' layout rules (csrc/pt_rapid.cu:
 clu_carve, choose_cluster, the Gauss-Jordan staging, the ADMM share split, the
-training update's chunks and the QR apply), for every rank 1..128 and sample
+training update's chunks and the QR apply's R^-1), for every rank 1..128 and sample
 counts from r to 20,000:
 
 * the smallest cluster (from 2 for recovery, 16 for the sequential fits) whose
@@ -16,7 +16,7 @@ counts from r to 20,000:
   vectors' space when it fits there;
 * every pushed vector fits a slot; the bulk copies' byte counts stay below the
   mbarrier transaction limit (2^20 - 1);
-* the training update's two buffers and the QR apply's tile fit shared memory.
+* the training update's two buffers and the QR apply's R^-1 fit shared memory.
 """
 import pytest
 
@@ -27,7 +27,6 @@ K_CLU_WARPS = K_CLU_THREADS // 32
 SMEM_LIMIT = 227 * 1024 - 64
 OPTIN_MAX = 232448
 TX_LIMIT = (1 << 20) - 1
-QR_ROWS = 128
 
 
 def padded_rank(r):
@@ -117,7 +116,7 @@ def test_fit_layout_for_every_rank(R):
     ch, ub = update_smem(RP)
     assert 32 <= ch <= 256 and ub <= SMEM_LIMIT - 4096
     assert ch * RP * 4 <= TX_LIMIT
-    assert 4 * RP * (RP + QR_ROWS) <= OPTIN_MAX - 1024
+    assert 4 * RP * RP <= OPTIN_MAX - 1024             # R^-1 of the QR apply
 
 
 @pytest.mark.parametrize("R", [1, 3, 5, 12, 20, 50, 52, 64, 70, 100, 104, 128])
